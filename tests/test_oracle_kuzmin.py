@@ -1,0 +1,80 @@
+"""End-to-end pins of the oracle against the Kuzmin disk (Section 3.1)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from tests import analytic as an
+
+G, A0 = 4.30e-3, 3.6
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def test_closed_form_mond_potential_derivative():
+    # F'(r) must equal nu(GM/(a0 r^2)) GM/r^2; check by central differences
+    M, a = 1e10, 2000.0
+    for R in (100.0, 2000.0, 50000.0):
+        d = 1e-3 * R
+        num = (an.kuzmin_phi_mond(R + d, 0.0, 0.0, M, 0.0, G, A0)
+               - an.kuzmin_phi_mond(R - d, 0.0, 0.0, M, 0.0, G, A0)) / (2 * d)
+        gN = G * M / R ** 2
+        assert num == pytest.approx(an.nu(gN / A0) * gN, rel=1e-6)
+
+
+def _kuzmin_run(ora, n, npart=1_000_000, M=1e10, a=2000.0):
+    p = synth.kuzmin_disk(npart, M, a, 1, stratified=True)
+    boxes = ora.pipeline(
+        p, n, 160000.0, 2, tol=1e-10, max_vcycles=40,
+        bc_newton=lambda x, y, z: an.kuzmin_phiN(x, y, z, M, a, G),
+        bc_mond=lambda x, y, z: an.kuzmin_phi_mond(x, y, z, M, a, G, A0))
+    r, vcN = ora.rotation_curve(n, 160000.0, (0.0, 0.0, 0.0), [b.phiN for b in boxes], 50, 20000.0)
+    _, vcM = ora.rotation_curve(n, 160000.0, (0.0, 0.0, 0.0), [b.phi for b in boxes], 50, 20000.0)
+    return boxes, r, vcN / an.kuzmin_vc_newton(r, M, a, G) - 1.0, vcM / an.kuzmin_vc_mond(r, M, a, G, A0) - 1.0
+
+
+def test_kuzmin_second_order_convergence(ora):
+    # the 40 kpc + 160 kpc geometry of the Kuzmin check, exact outer boundary
+    # values: in the finest box (3-8 kpc) the error falls at least ~4x per
+    # halving of h (faster while R/h is small)
+    runs = [_kuzmin_run(ora, n) for n in (32, 64, 128)]
+    r = runs[0][1]
+    sel = (r > 3000.0) & (r < 8000.0)
+    for kind in (2, 3):  # Newtonian, QUMOND
+        m = [np.max(np.abs(run[kind][sel])) for run in runs]
+        assert m[0] / m[1] > 3.5 and m[1] / m[2] > 3.5
+        assert m[2] < 0.01
+
+
+def test_algebraic_relation_holds_for_kuzmin(ora):
+    # Eq. 3 is exact for the Kuzmin disk (no curl field).  Off the plane
+    # (z = 2.5 kpc), where the grid field is smooth, the grid QUMOND force and
+    # nu(|g_N|/a0) g_N from the grid Newtonian force converge to each other.
+    L0 = 160000.0
+    R = np.linspace(3000.0, 7900.0, 30)
+    y, z = np.zeros_like(R), np.full_like(R, 2500.0)
+    errs = []
+    for n in (64, 128):
+        boxes, _, _, _ = _kuzmin_run(ora, n)
+        gN = ora.forces(n, L0, (0.0, 0.0, 0.0), [b.phiN for b in boxes], R, y, z)[:3]
+        gM = ora.forces(n, L0, (0.0, 0.0, 0.0), [b.phi for b in boxes], R, y, z)[:3]
+        nu = an.nu(np.sqrt(gN[0] ** 2 + gN[1] ** 2 + gN[2] ** 2) / A0)
+        errs.append(max(np.max(np.abs(gM[0] / (nu * gN[0]) - 1.0)), np.max(np.abs(gM[2] / (nu * gN[2]) - 1.0))))
+    assert errs[1] < 0.01 and errs[0] / errs[1] > 2.5
+
+
+@pytest.mark.slow
+def test_paper_kuzmin_accuracy_claim(ora):
+    """The paper's printed accuracy for its Kuzmin disk, in its own setup."""
+    gold = json.load(open(os.path.join(HERE, "golden", "kuzmin_paper_accuracy.json")))
+    s = gold["setup"]
+    n, nb = s["n_intervals"], s["n_boxes"]
+    L0 = s["finest_box_pc"] * 2 ** (nb - 1)
+    p = synth.kuzmin_disk(2_000_000, s["M_sun"], s["a_pc"], 1, stratified=True)
+    boxes = ora.pipeline(p, n, L0, nb, G=s["G"], a0=s["a0"], ncycle=s["ncycle"], npre=s["npre"], npost=s["npost"])
+    r, vc = ora.rotation_curve(n, L0, (0.0, 0.0, 0.0), [b.phi for b in boxes], 150, 15000.0,
+                               frac=s["box_rule_frac"])
+    err = np.abs(vc / an.kuzmin_vc_mond(r, s["M_sun"], s["a_pc"], s["G"], s["a0"]) - 1.0)
+    for c in gold["claims"]:
+        assert np.max(err[r > c["R_above_pc"]]) < c["max_rel_error"]
