@@ -1,0 +1,188 @@
+/*
+ * qumond.h -- C ABI of the GB300 QUMOND particle-mesh hot path.
+ *
+ * Angus et al., "A QUMOND galactic N-body code I: Poisson solver and rotation
+ * curve fitting" (arXiv:1201.3185).  One evaluation of the method (Section 2)
+ * is, for every nested box b = 0 (outermost) .. nboxes-1:
+ *   qumond_deposit       step 1, cloud-in-cell density
+ *   qumond_solve_newton  step 2, full multigrid for  lap Phi_N = 4 pi G rho  (Eq. 1)
+ *   qumond_source        step 3, the QUMOND source  div[nu(|grad Phi_N|/a0) grad Phi_N]  (Eq. 2)
+ *   qumond_solve_mond    step 4, full multigrid for  lap Phi = source  (Eq. 2)
+ * and then, over all boxes,
+ *   qumond_forces          gravity -grad Phi interpolated to points with CIC weights
+ *   qumond_rotation_curve  v_c^2 = R dPhi/dR at z = 0  (Eq. 4)
+ *
+ * Conventions (every entry point):
+ * - Grids are vertex grids of n intervals per side, (n+1)^3 nodes, x fastest:
+ *   node (i,j,k) is element i + (n+1)*(j + (n+1)*k).  Box b has side
+ *   L_b = L0 / box_ratio^b (box_ratio = 2 in the paper), is centred on
+ *   params.center, and has spacing h_b = L_b / n;
+ *   node i sits at center - L_b/2 + i*h_b.  Units: pc, Msun, km/s.
+ * - Every array argument is a DEVICE pointer to memory the caller owns and
+ *   keeps alive until the work queued on `stream` has finished.  Host
+ *   pointers are rejected with QUMOND_ERR_INVALID_ARG.  The context owns only
+ *   its scratch (multigrid levels, reduction buffers).
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream).  Work is queued asynchronously; argument errors are reported
+ *   synchronously before anything is queued.  The solves read residual norms
+ *   back to the host (they synchronise `stream`) when a tolerance is set or
+ *   when `stats` is non-NULL.
+ * - A context is not thread safe: one host thread per context.  Its calls
+ *   may be issued on any stream but must not overlap on the GPU (the
+ *   multigrid scratch is shared by all calls of a context).
+ * - On error the status is returned and qumond_last_error(ctx) describes it.
+ *   QUMOND_ERR_NOT_CONVERGED still leaves the best iterate in the output.
+ */
+#ifndef QUMOND_H
+#define QUMOND_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define QUMOND_API __attribute__((visibility("default")))
+#else
+#define QUMOND_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int qumond_status;
+enum {
+    QUMOND_OK = 0,
+    QUMOND_ERR_INVALID_ARG = 1,
+    QUMOND_ERR_CUDA = 2,
+    QUMOND_ERR_NOT_CONVERGED = 3,
+    QUMOND_ERR_TIMEOUT = 4,
+    QUMOND_ERR_OUT_OF_MEMORY = 5
+};
+
+/* Arithmetic of the multigrid solves. */
+enum {
+    /* FP64 everywhere: the plain full-multigrid baseline. */
+    QUMOND_PREC_FP64 = 0,
+    /* FP32 smoothing, residual restriction and prolongation; FP64 residual,
+       defect correction (iterative refinement) and master iterate; FP64 for
+       the coarsest grid of the FP64 steps and for all boundary values. */
+    QUMOND_PREC_MIXED = 1
+};
+
+/* Boundary values of box 0 (boxes b >= 1 always interpolate theirs from box
+   b-1, Section 2). */
+enum {
+    QUMOND_BC_ZERO = 0,  /* Phi = 0 on the outermost box, as in the paper */
+    QUMOND_BC_GIVEN = 1  /* the caller stores them in the boundary nodes of phi */
+};
+
+typedef struct {
+    int n;              /* intervals per side: a power of two, 2 <= n <= 1024 */
+    int nboxes;         /* nested boxes, 1 <= nboxes <= 16 */
+    double L0;          /* side of box 0, pc */
+    double center[3];   /* common centre of all boxes, pc */
+    double G;           /* gravitational constant, pc (km/s)^2 / Msun (4.30e-3) */
+    double a0;          /* MOND acceleration, (km/s)^2 / pc (3.6, Section 2) */
+    int npre, npost;    /* red-black Gauss-Seidel sweeps around the coarse-grid
+                           correction, each >= 1 (paper: 2 and 2, Section 2) */
+    int ncycle;         /* V-cycles per full-multigrid level, >= 1 (paper: 6) */
+    double rel_tol;     /* > 0: after FMG, V-cycles until ||f - L u||_2 <= rel_tol ||f||_2
+                           over interior nodes (absolute when f == 0); 0: paper mode */
+    int max_vcycles;    /* cap on those V-cycles; reaching it gives NOT_CONVERGED */
+    int precision;      /* QUMOND_PREC_* */
+    int bc_mode;        /* QUMOND_BC_* */
+    int warm_start;     /* 1: skip FMG and refine the interior values the caller
+                           left in phi (an initial guess); 0: FMG from scratch */
+    int deposit_shift;  /* fixed-point scale of the deposit: 2^shift units per Msun */
+    double rc_box_frac; /* rotation curve: radius R uses the finest box with
+                           R < rc_box_frac * L_b (0.2 gives Section 3.1's rule) */
+    int box_ratio;      /* side ratio of consecutive boxes: 2 (Section 2, each
+                           refinement halves the box), 4 or 8 */
+} qumond_params;
+
+/* Per-solve report (host struct). */
+typedef struct {
+    int vcycles;               /* V-cycles made after FMG */
+    int converged;             /* 1 if rel_tol was met (always 1 in paper mode) */
+    double rel_residual_fmg;   /* ||f - L u|| / ||f|| after FMG (or of the warm start) */
+    double rel_residual;       /* the same at return */
+} qumond_stats;
+
+typedef struct qumond_ctx qumond_ctx;
+
+/* Paper defaults: n = 256, one box of 120 kpc, G = 4.30e-3, a0 = 3.6,
+   npre = npost = 2, ncycle = 6, rel_tol = 0 (paper mode), max_vcycles = 50,
+   QUMOND_PREC_MIXED, QUMOND_BC_ZERO, warm_start = 0, deposit_shift = 24,
+   rc_box_frac = 0.2, box_ratio = 2. */
+QUMOND_API void qumond_default_params(qumond_params* p);
+
+/* Validates p and allocates the context's device scratch on the current
+   device (about 10 (n+1)^3 bytes in QUMOND_PREC_MIXED, 20 in FP64).
+   Returns INVALID_ARG, OUT_OF_MEMORY or CUDA_ERROR on failure (*out = NULL). */
+QUMOND_API qumond_status qumond_create(const qumond_params* p, qumond_ctx** out);
+
+/* Frees the scratch (synchronises the device first).  NULL is a no-op. */
+QUMOND_API void qumond_destroy(qumond_ctx* ctx);
+
+/* Message of the last error on ctx ("" if none).  Valid until the next call. */
+QUMOND_API const char* qumond_last_error(const qumond_ctx* ctx);
+
+/* Step 1 (Section 2): cloud-in-cell deposit of np particles into box `box`.
+   x, y, z, mass: np doubles each (positions in pc, mass in Msun; the stars
+   and the gas carry their own particle mass, Section 3.4).  A particle in
+   cell (i,j,k) (0 <= i,j,k < n, half open; others are skipped) adds
+   llrint(((mass*2^shift * w_x) * w_y) * w_z) to each of the 8 corner nodes,
+   w = 1-d or d, d the offset inside the cell: exact FP64 products, round half
+   to even, so the int64 grid does not depend on order.
+   rho_fixed: (n+1)^3 int64, overwritten (required).
+   rho: (n+1)^3 doubles = rho_fixed * 2^-shift / h^3 in Msun/pc^3, or NULL. */
+QUMOND_API qumond_status qumond_deposit(qumond_ctx* ctx, int box, const double* x, const double* y, const double* z,
+                             const double* mass, int64_t np, int64_t* rho_fixed, double* rho, void* stream);
+
+/* Step 2 (Section 2, Eq. 1): Phi_N of box `box` by full multigrid with
+   red-black Gauss-Seidel V-cycles (then refinement when rel_tol > 0).
+   rho: (n+1)^3 doubles (the deposit of this box), read at interior nodes.
+   phiN_parent: Phi_N of box-1 (required when box >= 1, ignored for box 0).
+   phiN: (n+1)^3 doubles, overwritten: its boundary nodes are set from the
+   parent (or by bc_mode for box 0), its interior by the solve.
+   stats: host struct or NULL. */
+QUMOND_API qumond_status qumond_solve_newton(qumond_ctx* ctx, int box, const double* rho, const double* phiN_parent,
+                                  double* phiN, qumond_stats* stats, void* stream);
+
+/* Step 3 (Section 2, Eq. 2): src = div[nu(|grad Phi_N|/a0) grad Phi_N] on
+   interior nodes by the face-flux difference
+     src(c) = h^-2 * sum over the 6 faces f of c: nu_f * (Phi_N(nbr) - Phi_N(c)),
+   nu(y) = 1/2 + 1/2 sqrt(1 + 4/y), y = |g_f|/a0, g_f the gradient at the face
+   (normal: the one-sided difference; transverse: mean of the central
+   differences at the face's two nodes); a face with g_f = 0 carries no flux.
+   Boundary nodes of src are set to 0.  phiN, src: (n+1)^3 doubles. */
+QUMOND_API qumond_status qumond_source(qumond_ctx* ctx, int box, const double* phiN, double* src, void* stream);
+
+/* Step 4 (Section 2, Eq. 2): Phi of box `box`; as qumond_solve_newton with
+   right-hand side src (no 4 pi G factor) and boundary values from phi_parent. */
+QUMOND_API qumond_status qumond_solve_mond(qumond_ctx* ctx, int box, const double* src, const double* phi_parent,
+                                double* phi, qumond_stats* stats, void* stream);
+
+/* Forces (Section 2): g = -grad Phi by central differences at the nodes,
+   interpolated to nq points with trilinear (CIC) weights.  A point uses the
+   finest box whose containing cell has all 8 corners at interior nodes;
+   a point in no such cell gets g = 0.
+   phi_boxes: HOST array of ctx->nboxes DEVICE pointers (box 0 first).
+   qx, qy, qz, gx, gy, gz: nq doubles each. */
+QUMOND_API qumond_status qumond_forces(qumond_ctx* ctx, const double* const* phi_boxes, const double* qx, const double* qy,
+                            const double* qz, int64_t nq, double* gx, double* gy, double* gz, void* stream);
+
+/* Rotation curve (Section 2, Eq. 4; box rule of Section 3.1): for nbins
+   radii R_k = (k + 1/2) rmax / nbins, the mean of dPhi/dR = -(g_x cos t +
+   g_y sin t) over nphi azimuths t_m = 2 pi m / nphi at z = center[2], taken
+   in index order; v_c = sign(s) sqrt(|s|), s = R_k * mean.  The forces come
+   from the finest box with R_k < rc_box_frac * L_b (box 0 if none),
+   falling back to coarser boxes where a cell is not interior.
+   r_out, vc_out: nbins doubles (device). */
+QUMOND_API qumond_status qumond_rotation_curve(qumond_ctx* ctx, const double* const* phi_boxes, int nbins, double rmax,
+                                    int nphi, double* r_out, double* vc_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QUMOND_H */

@@ -14,6 +14,7 @@ from .core import (  # noqa: F401
     rho_from_fixed,
     relax_rbgs,
     residual,
+    interior_sumsq,
     restrict_fw,
     prolong,
     coarsest,

@@ -57,8 +57,8 @@ def _load():
         "ora_solve": (_I, [_I, _D, _P, _P, _I, _I, _I, _I, _D, _I, _P, _I]),
         "ora_source": (None, [_I, _D, _D, _P, _P]),
         "ora_boundary_fill": (None, [_I, _D, _D, _D, _D, _P, _D, _D, _D, _D, _P]),
-        "ora_forces": (_L, [_I, _I, _D, _D, _D, _D, _P, _P, _P, _P, _L, _P, _P, _P]),
-        "ora_rotation_curve": (None, [_I, _I, _D, _D, _D, _D, _P, _I, _D, _I, _D, _P, _P]),
+        "ora_forces": (_L, [_I, _I, _D, _I, _D, _D, _D, _P, _P, _P, _P, _L, _P, _P, _P]),
+        "ora_rotation_curve": (None, [_I, _I, _D, _I, _D, _D, _D, _P, _I, _D, _I, _D, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -112,6 +112,10 @@ def residual(n, h, u, f):
     r = np.empty_like(u)
     _load().ora_residual(n, h, _ptr(u), _ptr(f), _ptr(r))
     return r
+
+
+def interior_sumsq(n, a):
+    return float(_load().ora_interior_sumsq(n, _ptr(_f64(a))))
 
 
 def restrict_fw(nf, fine):
@@ -169,20 +173,20 @@ def _ptr_array(arrs):
     return arr
 
 
-def forces(n, L0, center, phis, qx, qy, qz):
+def forces(n, L0, center, phis, qx, qy, qz, ratio=2):
     qx, qy, qz = _f64(qx), _f64(qy), _f64(qz)
     gx, gy, gz = np.empty_like(qx), np.empty_like(qx), np.empty_like(qx)
     pa = _ptr_array(phis)
-    missed = _load().ora_forces(len(phis), n, L0, center[0], center[1], center[2], ctypes.cast(pa, _P),
+    missed = _load().ora_forces(len(phis), n, L0, ratio, center[0], center[1], center[2], ctypes.cast(pa, _P),
                                 _ptr(qx), _ptr(qy), _ptr(qz), qx.size, _ptr(gx), _ptr(gy), _ptr(gz))
     return gx, gy, gz, int(missed)
 
 
-def rotation_curve(n, L0, center, phis, nbins, rmax, nphi=64, frac=0.2):
+def rotation_curve(n, L0, center, phis, nbins, rmax, nphi=64, frac=0.2, ratio=2):
     r = np.empty(nbins, dtype=np.float64)
     vc = np.empty(nbins, dtype=np.float64)
     pa = _ptr_array(phis)
-    _load().ora_rotation_curve(len(phis), n, L0, center[0], center[1], center[2], ctypes.cast(pa, _P),
+    _load().ora_rotation_curve(len(phis), n, L0, ratio, center[0], center[1], center[2], ctypes.cast(pa, _P),
                                nbins, rmax, nphi, frac, _ptr(r), _ptr(vc))
     return r, vc
 
@@ -210,10 +214,10 @@ class Box:
 
 
 def pipeline(particles, n, L0, nboxes, *, center=(0.0, 0.0, 0.0), G=4.30e-3, a0=3.6, shift=24,
-             ncycle=6, npre=2, npost=2, tol=0.0, max_vcycles=0, bc_newton=None, bc_mond=None):
+             ncycle=6, npre=2, npost=2, tol=0.0, max_vcycles=0, bc_newton=None, bc_mond=None, ratio=2):
     """Steps 1-4 of Section 2 for every nested box, outermost first.
 
-    Box b has side L0/2^b.  Box 0 takes its boundary values from bc_newton /
+    Box b has side L0/ratio^b (ratio 2 in the paper).  Box 0 takes its boundary values from bc_newton /
     bc_mond (callables (x, y, z) -> value; None means zero, as in the paper's
     outermost box); box b >= 1 interpolates them from box b-1 (Section 2)."""
     boxes = []
@@ -222,7 +226,7 @@ def pipeline(particles, n, L0, nboxes, *, center=(0.0, 0.0, 0.0), G=4.30e-3, a0=
     kk, jj, i3 = np.meshgrid(ii, ii, ii, indexing="ij")
     on_bnd = ((i3 == 0) | (i3 == n) | (jj == 0) | (jj == n) | (kk == 0) | (kk == n)).ravel()
     for b in range(nboxes):
-        L = L0 / 2 ** b
+        L = L0 / ratio ** b
         bx = Box(n=n, L=L, center=tuple(center))
         bx.rho_fixed, bx.kept = cic_deposit(n, L, center, shift, particles.x, particles.y, particles.z, particles.m)
         bx.rho = rho_from_fixed(n, L, shift, bx.rho_fixed)

@@ -400,7 +400,8 @@ void ora_boundary_fill(int n, double Lp, double cpx, double cpy, double cpz, con
 /* ------------------------------------------------------------------------ */
 /* Forces (Section 2): the gravity -grad Phi by central differences at the
  * nodes, interpolated to a point with the cloud-in-cell (trilinear) weights.
- * Boxes b = 0..nboxes-1 have side L0/2^b, all centred on c.  A point uses the
+ * Boxes b = 0..nboxes-1 have side L0/ratio^b (ratio 2 in the paper: each
+ * refinement halves the box), all centred on c.  A point uses the
  * finest box whose containing cell has all 8 corners at interior nodes
  * (where the central difference exists).  Points in no such cell get 0.
  * Returns the number of points that found no box. */
@@ -437,7 +438,7 @@ static void grad_at(int n, double L, const double* phi, const int* ijk, const do
             }
 }
 
-int64_t ora_forces(int nboxes, int n, double L0, double cx, double cy, double cz, const double* const* phi,
+int64_t ora_forces(int nboxes, int n, double L0, int ratio, double cx, double cy, double cz, const double* const* phi,
                    const double* qx, const double* qy, const double* qz, int64_t nq,
                    double* gx, double* gy, double* gz)
 {
@@ -446,7 +447,7 @@ int64_t ora_forces(int nboxes, int n, double L0, double cx, double cy, double cz
         double g[3] = {0.0, 0.0, 0.0};
         int found = 0;
         for (int b = nboxes - 1; b >= 0 && !found; --b) {
-            double L = ldexp(L0, -b);
+            double L = L0 / pow((double)ratio, (double)b);
             int ijk[3];
             double d[3];
             if (find_cell(n, L, cx, cy, cz, qx[p], qy[p], qz[p], ijk, d)) {
@@ -470,7 +471,7 @@ int64_t ora_forces(int nboxes, int n, double L0, double cx, double cy, double cz
  * 0.8 kpc for the 4 kpc box), falling back to coarser boxes whose cell is
  * interior.  The azimuthal mean is summed in index order.
  * vc_out = sign(v_c^2) sqrt(|v_c^2|). */
-void ora_rotation_curve(int nboxes, int n, double L0, double cx, double cy, double cz,
+void ora_rotation_curve(int nboxes, int n, double L0, int ratio, double cx, double cy, double cz,
                         const double* const* phi, int nbins, double rmax, int nphi, double frac,
                         double* r_out, double* vc_out)
 {
@@ -479,7 +480,7 @@ void ora_rotation_curve(int nboxes, int n, double L0, double cx, double cy, doub
         double R = ((double)kb + 0.5) * rmax / (double)nbins;
         int b0 = 0;
         for (int b = nboxes - 1; b >= 0; --b)
-            if (R < frac * ldexp(L0, -b)) { b0 = b; break; }
+            if (R < frac * (L0 / pow((double)ratio, (double)b))) { b0 = b; break; }
         double sum = 0.0;
         for (int m = 0; m < nphi; ++m) {
             double ph = twopi * (double)m / (double)nphi;
@@ -487,7 +488,7 @@ void ora_rotation_curve(int nboxes, int n, double L0, double cx, double cy, doub
             double x = cx + R * c, y = cy + R * s, z = cz;
             double g[3] = {0.0, 0.0, 0.0};
             for (int b = b0; b >= 0; --b) {
-                double L = ldexp(L0, -b);
+                double L = L0 / pow((double)ratio, (double)b);
                 int ijk[3];
                 double d[3];
                 if (find_cell(n, L, cx, cy, cz, x, y, z, ijk, d)) {

@@ -1,0 +1,457 @@
+// C ABI of the QUMOND path (include/qumond.h): argument checks, the
+// context's multigrid scratch, and the host-side schedule of the full
+// multigrid solves (Section 2).
+#include "qumond.h"
+#include "qumond_internal.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace qumond;
+
+namespace {
+
+struct Level {
+    LevelView v;
+    void* e = nullptr;  // iterate / correction, 2 colours
+    void* f = nullptr;  // right-hand side, 2 colours
+};
+
+}  // namespace
+
+struct qumond_ctx {
+    qumond_params p;
+    int L = 0;   // finest level index: n = 2 << L
+    int lc = 0;  // level handed to the coarse-grid kernel
+    size_t elt = 4;
+    std::vector<Level> lev;  // index l = 0..L; only l >= lc allocated
+    double* partials = nullptr;
+    int max_partials = 0;
+    double* d_norms = nullptr;
+    double* h_norms = nullptr;  // pinned
+    std::string err;
+};
+
+namespace {
+
+qumond_status fail(qumond_ctx* c, qumond_status st, const char* fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return st;
+}
+
+qumond_status cuda_fail(qumond_ctx* c, cudaError_t e, const char* where)
+{
+    (void)cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? QUMOND_ERR_OUT_OF_MEMORY : QUMOND_ERR_CUDA, "%s: %s", where,
+                cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(ctx, expr, where)                                                                                     \
+    do {                                                                                                               \
+        cudaError_t _e = (expr);                                                                                       \
+        if (_e != cudaSuccess) return cuda_fail(ctx, _e, where);                                                       \
+    } while (0)
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Device (or managed) memory check: a host pointer handed to a kernel would
+// fault, so it is refused before anything is launched.
+bool device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+qumond_status check_params(qumond_ctx* c, const qumond_params* p)
+{
+    if (!p) return fail(c, QUMOND_ERR_INVALID_ARG, "params is NULL");
+    if (!is_pow2(p->n) || p->n < 2 || p->n > 1024) return fail(c, QUMOND_ERR_INVALID_ARG, "n=%d: need a power of two in [2, 1024]", p->n);
+    if (p->nboxes < 1 || p->nboxes > kMaxBoxes) return fail(c, QUMOND_ERR_INVALID_ARG, "nboxes=%d: need 1..%d", p->nboxes, kMaxBoxes);
+    if (!(p->L0 > 0.0) || !std::isfinite(p->L0)) return fail(c, QUMOND_ERR_INVALID_ARG, "L0 must be positive and finite");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(p->center[a])) return fail(c, QUMOND_ERR_INVALID_ARG, "center must be finite");
+    if (!(p->G > 0.0) || !std::isfinite(p->G)) return fail(c, QUMOND_ERR_INVALID_ARG, "G must be positive");
+    if (!(p->a0 >= 0.0) || !std::isfinite(p->a0)) return fail(c, QUMOND_ERR_INVALID_ARG, "a0 must be >= 0");
+    if (p->npre < 1 || p->npost < 1 || p->npre > 16 || p->npost > 16)
+        return fail(c, QUMOND_ERR_INVALID_ARG, "npre, npost must be in [1, 16]");
+    if (p->ncycle < 1 || p->ncycle > 128) return fail(c, QUMOND_ERR_INVALID_ARG, "ncycle must be in [1, 128]");
+    if (!(p->rel_tol >= 0.0)) return fail(c, QUMOND_ERR_INVALID_ARG, "rel_tol must be >= 0");
+    if (p->max_vcycles < 0 || p->max_vcycles > 10000) return fail(c, QUMOND_ERR_INVALID_ARG, "max_vcycles must be in [0, 10000]");
+    if (p->precision != QUMOND_PREC_FP64 && p->precision != QUMOND_PREC_MIXED)
+        return fail(c, QUMOND_ERR_INVALID_ARG, "unknown precision %d", p->precision);
+    if (p->bc_mode != QUMOND_BC_ZERO && p->bc_mode != QUMOND_BC_GIVEN) return fail(c, QUMOND_ERR_INVALID_ARG, "unknown bc_mode %d", p->bc_mode);
+    if (p->warm_start != 0 && p->warm_start != 1) return fail(c, QUMOND_ERR_INVALID_ARG, "warm_start must be 0 or 1");
+    if (p->deposit_shift < 0 || p->deposit_shift > 40) return fail(c, QUMOND_ERR_INVALID_ARG, "deposit_shift must be in [0, 40]");
+    if (!(p->rc_box_frac > 0.0) || !(p->rc_box_frac <= 0.5)) return fail(c, QUMOND_ERR_INVALID_ARG, "rc_box_frac must be in (0, 0.5]");
+    if (p->box_ratio != 2 && p->box_ratio != 4 && p->box_ratio != 8)
+        return fail(c, QUMOND_ERR_INVALID_ARG, "box_ratio must be 2, 4 or 8");
+    if (p->nboxes > 1 && p->n < 2 * p->box_ratio)
+        return fail(c, QUMOND_ERR_INVALID_ARG, "n=%d too small for nested boxes of ratio %d", p->n, p->box_ratio);
+    return QUMOND_OK;
+}
+
+inline int log2i(int v) { int r = 0; while ((1 << r) < v) ++r; return r; }
+inline double box_side(const qumond_ctx* c, int box) { return std::ldexp(c->p.L0, -box * log2i(c->p.box_ratio)); }
+inline double box_h(const qumond_ctx* c, int box) { return box_side(c, box) / (double)c->p.n; }
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// --- the solver schedule ----------------------------------------------------
+template <typename T>
+T* E(qumond_ctx* c, int l) { return static_cast<T*>(c->lev[l].e); }
+template <typename T>
+T* F(qumond_ctx* c, int l) { return static_cast<T*>(c->lev[l].f); }
+
+inline double level_h(const qumond_ctx* c, int box, int l) { return box_h(c, box) * (double)(1 << (c->L - l)); }
+
+// One V-cycle at level l on the correction problem held in lev[l] (for l <
+// L the initial guess is zero; at l = L the caller says so).
+template <typename T>
+cudaError_t vcycle(qumond_ctx* c, int box, int l, bool zero_guess, cudaStream_t s)
+{
+    const qumond_params& p = c->p;
+    const double h = level_h(c, box, l);
+    if (l <= c->lc)
+        return launch_coarse<T>(0, E<T>(c, l), F<T>(c, l), c->lev[l].v, h, nullptr, 0, p.ncycle, p.npre, p.npost, s);
+    for (int q = 0; q < p.npre; ++q) {
+        launch_rb_half<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, 0, zero_guess && q == 0, h, s);
+        launch_rb_half<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, 1, false, h, s);
+    }
+    launch_restrict_resid_red<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, F<T>(c, l - 1), c->lev[l - 1].v, h, s);
+    cudaError_t err = vcycle<T>(c, box, l - 1, true, s);
+    if (err != cudaSuccess) return err;
+    launch_prolong_black<T>(E<T>(c, l - 1), c->lev[l - 1].v, E<T>(c, l), c->lev[l].v, true, s);
+    for (int q = 0; q < p.npost; ++q) {
+        launch_rb_half<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, 0, false, h, s);
+        launch_rb_half<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, 1, false, h, s);
+    }
+    return cudaSuccess;
+}
+
+// Full multigrid (Section 2) on lev[L].f with the boundary values of u64:
+// the right-hand side is restricted level by level, the coarse-grid kernel
+// solves up to level lc, and each finer level is interpolated and given
+// ncycle V-cycles.  Coarser levels take the finest boundary values at the
+// same positions; a level becomes a zero-boundary correction level once the
+// next finer level has been interpolated from it.
+template <typename T>
+cudaError_t fmg(qumond_ctx* c, int box, const double* u64, cudaStream_t s)
+{
+    const qumond_params& p = c->p;
+    for (int l = c->L - 1; l >= c->lc; --l)
+        launch_restrict_full<T>(F<T>(c, l + 1), c->lev[l + 1].v, F<T>(c, l), c->lev[l].v, s);
+    cudaError_t err = launch_coarse<T>(1, E<T>(c, c->lc), F<T>(c, c->lc), c->lev[c->lc].v, level_h(c, box, c->lc), u64,
+                                       p.n, p.ncycle, p.npre, p.npost, s);
+    if (err != cudaSuccess) return err;
+    for (int l = c->lc + 1; l <= c->L; ++l) {
+        launch_set_boundary<T>(E<T>(c, l), c->lev[l].v, u64, p.n, s);
+        launch_prolong_black<T>(E<T>(c, l - 1), c->lev[l - 1].v, E<T>(c, l), c->lev[l].v, false, s);
+        launch_set_boundary<T>(E<T>(c, l - 1), c->lev[l - 1].v, nullptr, p.n, s);
+        for (int q = 0; q < p.ncycle; ++q) {
+            err = vcycle<T>(c, box, l, false, s);
+            if (err != cudaSuccess) return err;
+        }
+    }
+    return cudaSuccess;
+}
+
+// Residual norms: returns ||coef*rhs - L u||^2 and ||coef*rhs||^2.
+template <typename T>
+qumond_status residual_norms(qumond_ctx* c, int box, const double* rhs, double coef, const double* u, cudaStream_t s,
+                             double* rr, double* ff)
+{
+    const int nb = launch_residual_outer<T>(u, rhs, coef, c->p.n, box_h(c, box), F<T>(c, c->L), c->lev[c->L].v,
+                                            c->partials, s);
+    launch_reduce_norms(c->partials, nb, c->d_norms, s);
+    CUDA_TRY(c, cudaGetLastError(), "residual launch");
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_norms, c->d_norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s), "norm copy");
+    CUDA_TRY(c, cudaStreamSynchronize(s), "residual");
+    *rr = c->h_norms[0];
+    *ff = c->h_norms[1];
+    return QUMOND_OK;
+}
+
+// Steps 2 and 4: boundary values, FMG, then defect correction to rel_tol.
+//   r = coef*rhs - L u   (FP64, caller's arrays)
+//   V-cycle on L e = r   (precision T, zero initial guess, zero boundary)
+//   u += e               (FP64)
+template <typename T>
+qumond_status solve_t(qumond_ctx* c, int box, const double* rhs, double coef, const double* parent, double* u,
+                      qumond_stats* st, cudaStream_t s)
+{
+    const qumond_params& p = c->p;
+    const int n = p.n;
+    if (box > 0) launch_boundary_from_parent(parent, u, n, p.box_ratio, s);
+    else if (p.bc_mode == QUMOND_BC_ZERO) launch_boundary_zero(u, n, s);
+    if (!p.warm_start) {
+        launch_convert_rhs<T>(rhs, coef, n, F<T>(c, c->L), c->lev[c->L].v, s);
+        cudaError_t err = fmg<T>(c, box, u, s);
+        if (err != cudaSuccess) return cuda_fail(c, err, "fmg");
+        launch_assign_outer<T>(u, n, E<T>(c, c->L), c->lev[c->L].v, false, s);
+        launch_set_boundary<T>(E<T>(c, c->L), c->lev[c->L].v, nullptr, n, s);
+    }
+    CUDA_TRY(c, cudaGetLastError(), "solve launch");
+    const bool refine = p.rel_tol > 0.0 && p.max_vcycles > 0;
+    if (!refine && !st) return QUMOND_OK;
+    double rr = 0.0, ff = 0.0;
+    qumond_status rs = residual_norms<T>(c, box, rhs, coef, u, s, &rr, &ff);
+    if (rs != QUMOND_OK) return rs;
+    const double denom = ff > 0.0 ? std::sqrt(ff) : 1.0;
+    double rel = std::sqrt(rr) / denom;
+    const double rel0 = rel;
+    int made = 0;
+    while (refine && rel > p.rel_tol && made < p.max_vcycles && std::isfinite(rel)) {
+        cudaError_t err = vcycle<T>(c, box, c->L, true, s);
+        if (err != cudaSuccess) return cuda_fail(c, err, "vcycle");
+        launch_assign_outer<T>(u, n, E<T>(c, c->L), c->lev[c->L].v, true, s);
+        ++made;
+        rs = residual_norms<T>(c, box, rhs, coef, u, s, &rr, &ff);
+        if (rs != QUMOND_OK) return rs;
+        rel = std::sqrt(rr) / denom;
+    }
+    const bool ok = std::isfinite(rel) && (!refine || rel <= p.rel_tol);
+    if (st) {
+        st->vcycles = made;
+        st->converged = ok ? 1 : 0;
+        st->rel_residual_fmg = rel0;
+        st->rel_residual = rel;
+    }
+    if (!ok)
+        return fail(c, QUMOND_ERR_NOT_CONVERGED, "box %d: relative residual %.3e after %d V-cycles (tol %.3e)", box, rel,
+                    made, p.rel_tol);
+    return QUMOND_OK;
+}
+
+qumond_status solve(qumond_ctx* c, int box, const double* rhs, double coef, const double* parent, double* u,
+                    qumond_stats* st, void* stream, const char* what)
+{
+    if (!c) return QUMOND_ERR_INVALID_ARG;
+    c->err.clear();
+    if (box < 0 || box >= c->p.nboxes) return fail(c, QUMOND_ERR_INVALID_ARG, "%s: box %d out of range", what, box);
+    if (!device_ptr(rhs) || !device_ptr(u)) return fail(c, QUMOND_ERR_INVALID_ARG, "%s: rhs and phi must be device pointers", what);
+    if (box > 0 && !device_ptr(parent)) return fail(c, QUMOND_ERR_INVALID_ARG, "%s: box %d needs the parent potential (device)", what, box);
+    if (rhs == u || (box > 0 && parent == u)) return fail(c, QUMOND_ERR_INVALID_ARG, "%s: phi must not alias its inputs", what);
+    if (c->p.precision == QUMOND_PREC_FP64) return solve_t<double>(c, box, rhs, coef, parent, u, st, S(stream));
+    return solve_t<float>(c, box, rhs, coef, parent, u, st, S(stream));
+}
+
+BoxSet box_set(const qumond_ctx* c, const double* const* phis)
+{
+    BoxSet bs;
+    memset(&bs, 0, sizeof(bs));
+    bs.nboxes = c->p.nboxes;
+    bs.n = c->p.n;
+    for (int b = 0; b < c->p.nboxes; ++b) {
+        const double L = box_side(c, b);
+        bs.b[b].phi = phis[b];
+        bs.b[b].L = L;
+        bs.b[b].h = L / (double)c->p.n;
+        bs.b[b].inv_h = (double)c->p.n / L;
+        bs.b[b].xlo = c->p.center[0] - 0.5 * L;
+        bs.b[b].ylo = c->p.center[1] - 0.5 * L;
+        bs.b[b].zlo = c->p.center[2] - 0.5 * L;
+    }
+    return bs;
+}
+
+qumond_status check_phis(qumond_ctx* c, const double* const* phis, const char* what)
+{
+    if (!phis) return fail(c, QUMOND_ERR_INVALID_ARG, "%s: phi_boxes is NULL", what);
+    for (int b = 0; b < c->p.nboxes; ++b)
+        if (!device_ptr(phis[b])) return fail(c, QUMOND_ERR_INVALID_ARG, "%s: phi_boxes[%d] is not a device pointer", what, b);
+    return QUMOND_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void qumond_default_params(qumond_params* p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->n = 256;
+    p->nboxes = 1;
+    p->L0 = 120000.0;
+    p->G = 4.30e-3;
+    p->a0 = 3.6;
+    p->npre = 2;
+    p->npost = 2;
+    p->ncycle = 6;
+    p->rel_tol = 0.0;
+    p->max_vcycles = 50;
+    p->precision = QUMOND_PREC_MIXED;
+    p->bc_mode = QUMOND_BC_ZERO;
+    p->warm_start = 0;
+    p->deposit_shift = 24;
+    p->rc_box_frac = 0.2;
+    p->box_ratio = 2;
+}
+
+qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
+{
+    if (!out) return QUMOND_ERR_INVALID_ARG;
+    *out = nullptr;
+    qumond_ctx* c = new qumond_ctx();
+    qumond_status st = check_params(c, p);
+    if (st != QUMOND_OK) {
+        delete c;
+        return st;
+    }
+    c->p = *p;
+    c->elt = p->precision == QUMOND_PREC_FP64 ? sizeof(double) : sizeof(float);
+    int L = 0;
+    while ((2 << L) < p->n) ++L;
+    c->L = L;
+    int lc = 0;
+    while ((2 << lc) < kCoarseN && lc < L) ++lc;
+    c->lc = lc;
+    c->lev.resize(L + 1);
+    bool ok = true;
+    for (int l = 0; l <= L; ++l) {
+        c->lev[l].v = make_view(2 << l);
+        if (l < lc) continue;
+        const size_t bytes = (size_t)(2 * c->lev[l].v.cs) * c->elt;
+        if (cudaMalloc(&c->lev[l].e, bytes) != cudaSuccess || cudaMalloc(&c->lev[l].f, bytes) != cudaSuccess) {
+            ok = false;
+            break;
+        }
+        if (cudaMemset(c->lev[l].e, 0, bytes) != cudaSuccess || cudaMemset(c->lev[l].f, 0, bytes) != cudaSuccess) {
+            ok = false;
+            break;
+        }
+    }
+    if (ok) {
+        c->max_partials = residual_outer_blocks(p->n > 2 ? p->n : 2);
+        ok = cudaMalloc(&c->partials, sizeof(double) * 2 * (size_t)(c->max_partials + 1)) == cudaSuccess &&
+             cudaMalloc(&c->d_norms, sizeof(double) * 2) == cudaSuccess &&
+             cudaMallocHost(&c->h_norms, sizeof(double) * 2) == cudaSuccess;
+    }
+    if (!ok) {
+        (void)cudaGetLastError();
+        qumond_destroy(c);
+        return QUMOND_ERR_OUT_OF_MEMORY;
+    }
+    *out = c;
+    return QUMOND_OK;
+}
+
+void qumond_destroy(qumond_ctx* c)
+{
+    if (!c) return;
+    cudaDeviceSynchronize();
+    for (auto& l : c->lev) {
+        if (l.e) cudaFree(l.e);
+        if (l.f) cudaFree(l.f);
+    }
+    if (c->partials) cudaFree(c->partials);
+    if (c->d_norms) cudaFree(c->d_norms);
+    if (c->h_norms) cudaFreeHost(c->h_norms);
+    (void)cudaGetLastError();
+    delete c;
+}
+
+const char* qumond_last_error(const qumond_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+
+qumond_status qumond_deposit(qumond_ctx* c, int box, const double* x, const double* y, const double* z,
+                             const double* mass, int64_t np, int64_t* rho_fixed, double* rho, void* stream)
+{
+    if (!c) return QUMOND_ERR_INVALID_ARG;
+    c->err.clear();
+    if (box < 0 || box >= c->p.nboxes) return fail(c, QUMOND_ERR_INVALID_ARG, "deposit: box %d out of range", box);
+    if (np < 0) return fail(c, QUMOND_ERR_INVALID_ARG, "deposit: np < 0");
+    if (np > 0 && (!device_ptr(x) || !device_ptr(y) || !device_ptr(z) || !device_ptr(mass)))
+        return fail(c, QUMOND_ERR_INVALID_ARG, "deposit: x, y, z, mass must be device pointers");
+    if (!device_ptr(rho_fixed)) return fail(c, QUMOND_ERR_INVALID_ARG, "deposit: rho_fixed must be a device pointer");
+    if (rho && !device_ptr(rho)) return fail(c, QUMOND_ERR_INVALID_ARG, "deposit: rho must be a device pointer or NULL");
+    const int n = c->p.n;
+    const long long count = (long long)(n + 1) * (n + 1) * (n + 1);
+    const double L = box_side(c, box);
+    const double inv_h = (double)n / L;
+    cudaStream_t s = S(stream);
+    CUDA_TRY(c, cudaMemsetAsync(rho_fixed, 0, sizeof(int64_t) * count, s), "deposit: clear");
+    launch_cic_deposit(x, y, z, mass, np, n, c->p.center[0] - 0.5 * L, c->p.center[1] - 0.5 * L,
+                       c->p.center[2] - 0.5 * L, inv_h, std::ldexp(1.0, c->p.deposit_shift), rho_fixed, s);
+    if (rho) {
+        const double scale = std::ldexp(1.0, -c->p.deposit_shift) * (inv_h * inv_h * inv_h);
+        launch_fixed_to_rho(rho_fixed, rho, count, scale, s);
+    }
+    CUDA_TRY(c, cudaGetLastError(), "deposit launch");
+    return QUMOND_OK;
+}
+
+qumond_status qumond_solve_newton(qumond_ctx* c, int box, const double* rho, const double* phiN_parent, double* phiN,
+                                  qumond_stats* stats, void* stream)
+{
+    if (!c) return QUMOND_ERR_INVALID_ARG;
+    return solve(c, box, rho, 4.0 * M_PI * c->p.G, phiN_parent, phiN, stats, stream, "solve_newton");
+}
+
+qumond_status qumond_solve_mond(qumond_ctx* c, int box, const double* src, const double* phi_parent, double* phi,
+                                qumond_stats* stats, void* stream)
+{
+    return solve(c, box, src, 1.0, phi_parent, phi, stats, stream, "solve_mond");
+}
+
+qumond_status qumond_source(qumond_ctx* c, int box, const double* phiN, double* src, void* stream)
+{
+    if (!c) return QUMOND_ERR_INVALID_ARG;
+    c->err.clear();
+    if (box < 0 || box >= c->p.nboxes) return fail(c, QUMOND_ERR_INVALID_ARG, "source: box %d out of range", box);
+    if (!device_ptr(phiN) || !device_ptr(src)) return fail(c, QUMOND_ERR_INVALID_ARG, "source: phiN and src must be device pointers");
+    if (phiN == src) return fail(c, QUMOND_ERR_INVALID_ARG, "source: src must not alias phiN");
+    launch_source(phiN, src, c->p.n, box_h(c, box), c->p.a0, S(stream));
+    CUDA_TRY(c, cudaGetLastError(), "source launch");
+    return QUMOND_OK;
+}
+
+qumond_status qumond_forces(qumond_ctx* c, const double* const* phi_boxes, const double* qx, const double* qy,
+                            const double* qz, int64_t nq, double* gx, double* gy, double* gz, void* stream)
+{
+    if (!c) return QUMOND_ERR_INVALID_ARG;
+    c->err.clear();
+    qumond_status st = check_phis(c, phi_boxes, "forces");
+    if (st != QUMOND_OK) return st;
+    if (nq < 0) return fail(c, QUMOND_ERR_INVALID_ARG, "forces: nq < 0");
+    if (nq == 0) return QUMOND_OK;
+    if (!device_ptr(qx) || !device_ptr(qy) || !device_ptr(qz) || !device_ptr(gx) || !device_ptr(gy) || !device_ptr(gz))
+        return fail(c, QUMOND_ERR_INVALID_ARG, "forces: point and force arrays must be device pointers");
+    launch_forces(box_set(c, phi_boxes), qx, qy, qz, nq, gx, gy, gz, S(stream));
+    CUDA_TRY(c, cudaGetLastError(), "forces launch");
+    return QUMOND_OK;
+}
+
+qumond_status qumond_rotation_curve(qumond_ctx* c, const double* const* phi_boxes, int nbins, double rmax, int nphi,
+                                    double* r_out, double* vc_out, void* stream)
+{
+    if (!c) return QUMOND_ERR_INVALID_ARG;
+    c->err.clear();
+    qumond_status st = check_phis(c, phi_boxes, "rotation_curve");
+    if (st != QUMOND_OK) return st;
+    if (nbins < 1 || nbins > 65535) return fail(c, QUMOND_ERR_INVALID_ARG, "rotation_curve: nbins must be in [1, 65535]");
+    if (nphi < 1 || nphi > 1024) return fail(c, QUMOND_ERR_INVALID_ARG, "rotation_curve: nphi must be in [1, 1024]");
+    if (!(rmax > 0.0) || !std::isfinite(rmax)) return fail(c, QUMOND_ERR_INVALID_ARG, "rotation_curve: rmax must be positive");
+    if (!device_ptr(r_out) || !device_ptr(vc_out)) return fail(c, QUMOND_ERR_INVALID_ARG, "rotation_curve: outputs must be device pointers");
+    launch_rotation_curve(box_set(c, phi_boxes), c->p.center[0], c->p.center[1], c->p.center[2], nbins, rmax, nphi,
+                          c->p.rc_box_frac, r_out, vc_out, S(stream));
+    CUDA_TRY(c, cudaGetLastError(), "rotation_curve launch");
+    return QUMOND_OK;
+}
+
+}  // extern "C"

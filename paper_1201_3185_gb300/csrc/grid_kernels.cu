@@ -1,0 +1,328 @@
+// Grid kernels of the QUMOND path on natural-layout FP64 arrays: the
+// fixed-point CIC deposit (Section 2 step 1), nested-box boundary values
+// (Section 2), the QUMOND source (Section 2 step 3, Eq. 2), forces and the
+// rotation curve (Section 2, Eq. 4; box rule of Section 3.1).
+#include "qumond_internal.h"
+
+namespace qumond {
+
+namespace {
+
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+__device__ __forceinline__ long long nat(int n, int i, int j, int k)
+{
+    const long long P = n + 1;
+    return (long long)i + P * ((long long)j + P * (long long)k);
+}
+
+// ---------------------------------------------------------------------------
+// Cloud-in-cell deposit in 64-bit fixed point.  Every product is an
+// individually rounded FP64 operation (no fused multiply-add), and the
+// conversion rounds half to even, so each corner's integer share is the same
+// on any machine and the grid does not depend on the order of the atomics.
+__global__ void cic_deposit_kernel(const double* __restrict__ x, const double* __restrict__ y,
+                                   const double* __restrict__ z, const double* __restrict__ m, long long np, int n,
+                                   double xlo, double ylo, double zlo, double inv_h, double two_shift,
+                                   unsigned long long* __restrict__ q)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const double tx = __dmul_rn(__dsub_rn(x[p], xlo), inv_h);
+    const double ty = __dmul_rn(__dsub_rn(y[p], ylo), inv_h);
+    const double tz = __dmul_rn(__dsub_rn(z[p], zlo), inv_h);
+    const double dn = (double)n;
+    if (!(tx >= 0.0 && tx < dn && ty >= 0.0 && ty < dn && tz >= 0.0 && tz < dn)) return;
+    const double fx = floor(tx), fy = floor(ty), fz = floor(tz);
+    const int i = (int)fx, j = (int)fy, k = (int)fz;
+    if (i >= n || j >= n || k >= n) return;
+    const double dx = __dsub_rn(tx, fx), dy = __dsub_rn(ty, fy), dz = __dsub_rn(tz, fz);
+    const double wx[2] = {__dsub_rn(1.0, dx), dx};
+    const double wy[2] = {__dsub_rn(1.0, dy), dy};
+    const double wz[2] = {__dsub_rn(1.0, dz), dz};
+    const double ms = __dmul_rn(m[p], two_shift);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const double mbc = ms;  // ((ms * wx) * wy) * wz, left to right
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const double w = __dmul_rn(__dmul_rn(__dmul_rn(mbc, wx[a]), wy[b]), wz[c]);
+                const long long qv = __double2ll_rn(w);
+                atomicAdd(q + nat(n, i + a, j + b, k + c), (unsigned long long)qv);
+            }
+        }
+}
+
+__global__ void fixed_to_rho_kernel(const long long* __restrict__ q, double* __restrict__ rho, long long count,
+                                    double scale)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < count) rho[t] = __ll2double_rn(q[t]) * scale;
+}
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void face_node(int face, int a, int b, int n, int& i, int& j, int& k)
+{
+    switch (face) {
+    case 0: i = 0; j = a; k = b; break;
+    case 1: i = n; j = a; k = b; break;
+    case 2: i = a; j = 0; k = b; break;
+    case 3: i = a; j = n; k = b; break;
+    case 4: i = a; j = b; k = 0; break;
+    default: i = a; j = b; k = n; break;
+    }
+}
+
+__global__ void boundary_zero_kernel(double* __restrict__ u, int n)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (a > n) return;
+    int i, j, k;
+    face_node(blockIdx.z, a, b, n, i, j, k);
+    u[nat(n, i, j, k)] = 0.0;
+}
+
+// Trilinear interpolation of a natural-layout grid at index coordinates t.
+__device__ __forceinline__ double trilinear_idx(const double* __restrict__ a, int n, double tx, double ty, double tz)
+{
+    const double t[3] = {tx, ty, tz};
+    int i0[3];
+    double d[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        int ii = (int)floor(t[q]);
+        ii = ii < 0 ? 0 : (ii > n - 1 ? n - 1 : ii);
+        i0[q] = ii;
+        d[q] = t[q] - (double)ii;
+    }
+    double v = 0.0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a3 = 0; a3 < 2; ++a3) {
+                const double w = (a3 ? d[0] : 1.0 - d[0]) * (b ? d[1] : 1.0 - d[1]) * (c ? d[2] : 1.0 - d[2]);
+                v += w * a[nat(n, i0[0] + a3, i0[1] + b, i0[2] + c)];
+            }
+    return v;
+}
+
+// Boundary of a box from its parent (box_ratio times the side, same centre,
+// same n): child node i sits at parent index n (r-1)/(2r) + i/r along each
+// axis (Section 2: the parent solution is interpolated onto the child's
+// boundary).
+__global__ void boundary_from_parent_kernel(const double* __restrict__ parent, double* __restrict__ u, int n, int ratio)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (a > n) return;
+    int i, j, k;
+    face_node(blockIdx.z, a, b, n, i, j, k);
+    const double inv_r = 1.0 / (double)ratio;
+    const double q = 0.5 * (double)n * (1.0 - inv_r);
+    u[nat(n, i, j, k)] = trilinear_idx(parent, n, q + inv_r * i, q + inv_r * j, q + inv_r * k);
+}
+
+// ---------------------------------------------------------------------------
+// QUMOND source by the face-flux difference.  Differences of the potential
+// are taken in FP64 (they carry the information); the gradient magnitude,
+// nu and the six fluxes are evaluated in FP32, which perturbs the solved
+// potential by ~1e-8 relative (FP64 arithmetic there is ~60x slower on this
+// GPU).  src = 0 on boundary nodes.
+constexpr int kSrcBX = 32, kSrcBY = 4;
+
+__global__ void __launch_bounds__(kSrcBX * kSrcBY)
+source_kernel(const double* __restrict__ phi, double* __restrict__ src, int n, float inv_h, float four_a0,
+              float inv_h2)
+{
+    const int i = blockIdx.x * kSrcBX + threadIdx.x;
+    const int j = blockIdx.y * kSrcBY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i > n || j > n) return;
+    const long long o = nat(n, i, j, k);
+    if (i == 0 || i == n || j == 0 || j == n || k == 0 || k == n) {
+        src[o] = 0.0;
+        return;
+    }
+    const long long P = n + 1;
+    const long long S[3] = {1, P, P * P};
+    const float q4 = 0.25f * inv_h;
+    float acc = 0.0f;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const long long oP = side == 0 ? o : o - S[ax];
+            const long long oQ = oP + S[ax];
+            const float dn = (float)(phi[oQ] - phi[oP]);
+            const float gn = dn * inv_h;
+            float g2 = gn * gn;
+#pragma unroll
+            for (int bx = 0; bx < 3; ++bx) {
+                if (bx == ax) continue;
+                const float cP = (float)(phi[oP + S[bx]] - phi[oP - S[bx]]);
+                const float cQ = (float)(phi[oQ + S[bx]] - phi[oQ - S[bx]]);
+                const float gt = (cP + cQ) * q4;
+                g2 += gt * gt;
+            }
+            if (g2 > 0.0f) {
+                const float nu = 0.5f * (1.0f + sqrtf(1.0f + four_a0 * rsqrtf(g2)));
+                acc += side == 0 ? nu * dn : -nu * dn;
+            }
+        }
+    }
+    src[o] = (double)(acc * inv_h2);
+}
+
+// ---------------------------------------------------------------------------
+// Forces at points: finest box whose containing cell has 8 interior corners.
+__device__ __forceinline__ bool find_cell(const BoxGeom& g, int n, double x, double y, double z, int* ijk, double* d)
+{
+    const double t[3] = {(x - g.xlo) * g.inv_h, (y - g.ylo) * g.inv_h, (z - g.zlo) * g.inv_h};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (!(t[a] >= 1.0 && t[a] < (double)(n - 1))) return false;
+        const double fl = floor(t[a]);
+        ijk[a] = (int)fl;
+        d[a] = t[a] - fl;
+        if (ijk[a] < 1 || ijk[a] > n - 2) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void grad_at(const BoxGeom& g, int n, const int* ijk, const double* d, double* out)
+{
+    const double* phi = g.phi;
+    const double s = -0.5 / g.h;
+    const long long P = n + 1, Q = P * P;
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const long long o = nat(n, ijk[0] + a, ijk[1] + b, ijk[2] + c);
+                const double w = (a ? d[0] : 1.0 - d[0]) * (b ? d[1] : 1.0 - d[1]) * (c ? d[2] : 1.0 - d[2]);
+                gx += w * ((phi[o + 1] - phi[o - 1]) * s);
+                gy += w * ((phi[o + P] - phi[o - P]) * s);
+                gz += w * ((phi[o + Q] - phi[o - Q]) * s);
+            }
+    out[0] = gx;
+    out[1] = gy;
+    out[2] = gz;
+}
+
+__global__ void forces_kernel(BoxSet boxes, const double* __restrict__ qx, const double* __restrict__ qy,
+                              const double* __restrict__ qz, long long nq, double* __restrict__ gx,
+                              double* __restrict__ gy, double* __restrict__ gz)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= nq) return;
+    const double x = qx[p], y = qy[p], z = qz[p];
+    double g[3] = {0.0, 0.0, 0.0};
+    for (int b = boxes.nboxes - 1; b >= 0; --b) {
+        int ijk[3];
+        double d[3];
+        if (find_cell(boxes.b[b], boxes.n, x, y, z, ijk, d)) {
+            grad_at(boxes.b[b], boxes.n, ijk, d, g);
+            break;
+        }
+    }
+    gx[p] = g[0];
+    gy[p] = g[1];
+    gz[p] = g[2];
+}
+
+// One CTA per radius bin, one thread per azimuth; the azimuthal mean is
+// summed in index order by thread 0, so the result is reproducible.
+constexpr int kMaxPhi = 1024;
+
+__global__ void rotation_curve_kernel(BoxSet boxes, double cx, double cy, double cz, int nbins, double rmax, int nphi,
+                                      double frac, double* __restrict__ r_out, double* __restrict__ vc_out)
+{
+    __shared__ double dphidr[kMaxPhi];
+    const int kb = blockIdx.x;
+    const double R = ((double)kb + 0.5) * rmax / (double)nbins;
+    int b0 = 0;
+    for (int b = boxes.nboxes - 1; b >= 0; --b)
+        if (R < frac * boxes.b[b].L) {
+            b0 = b;
+            break;
+        }
+    for (int m = threadIdx.x; m < nphi; m += blockDim.x) {
+        const double ph = 6.283185307179586476925286766559 * (double)m / (double)nphi;
+        double s, c;
+        sincos(ph, &s, &c);
+        const double x = cx + R * c, y = cy + R * s, z = cz;
+        double g[3] = {0.0, 0.0, 0.0};
+        for (int b = b0; b >= 0; --b) {
+            int ijk[3];
+            double d[3];
+            if (find_cell(boxes.b[b], boxes.n, x, y, z, ijk, d)) {
+                grad_at(boxes.b[b], boxes.n, ijk, d, g);
+                break;
+            }
+        }
+        dphidr[m] = -(g[0] * c + g[1] * s);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int m = 0; m < nphi; ++m) sum += dphidr[m];
+        const double v2 = R * (sum / (double)nphi);
+        r_out[kb] = R;
+        vc_out[kb] = v2 >= 0.0 ? sqrt(v2) : -sqrt(-v2);
+    }
+}
+
+}  // namespace
+
+// --- launchers ----------------------------------------------------------------
+void launch_cic_deposit(const double* x, const double* y, const double* z, const double* m, long long np, int n,
+                        double xlo, double ylo, double zlo, double inv_h, double two_shift, int64_t* q,
+                        cudaStream_t s)
+{
+    if (np <= 0) return;
+    cic_deposit_kernel<<<cdiv(np, 256), 256, 0, s>>>(x, y, z, m, np, n, xlo, ylo, zlo, inv_h, two_shift,
+                                                      reinterpret_cast<unsigned long long*>(q));
+}
+
+void launch_fixed_to_rho(const int64_t* q, double* rho, long long count, double scale, cudaStream_t s)
+{
+    fixed_to_rho_kernel<<<cdiv(count, 256), 256, 0, s>>>(reinterpret_cast<const long long*>(q), rho, count, scale);
+}
+
+void launch_boundary_zero(double* u, int n, cudaStream_t s)
+{
+    boundary_zero_kernel<<<dim3(cdiv(n + 1, 128), (unsigned)(n + 1), 6), 128, 0, s>>>(u, n);
+}
+
+void launch_boundary_from_parent(const double* parent, double* u, int n, int ratio, cudaStream_t s)
+{
+    boundary_from_parent_kernel<<<dim3(cdiv(n + 1, 128), (unsigned)(n + 1), 6), 128, 0, s>>>(parent, u, n, ratio);
+}
+
+void launch_source(const double* phi, double* src, int n, double h, double a0, cudaStream_t s)
+{
+    const dim3 grid(cdiv(n + 1, kSrcBX), cdiv(n + 1, kSrcBY), (unsigned)(n + 1));
+    source_kernel<<<grid, dim3(kSrcBX, kSrcBY), 0, s>>>(phi, src, n, (float)(1.0 / h), (float)(4.0 * a0),
+                                                        (float)(1.0 / (h * h)));
+}
+
+void launch_forces(const BoxSet& boxes, const double* qx, const double* qy, const double* qz, long long nq,
+                   double* gx, double* gy, double* gz, cudaStream_t s)
+{
+    if (nq <= 0) return;
+    forces_kernel<<<cdiv(nq, 128), 128, 0, s>>>(boxes, qx, qy, qz, nq, gx, gy, gz);
+}
+
+void launch_rotation_curve(const BoxSet& boxes, double cx, double cy, double cz, int nbins, double rmax, int nphi,
+                           double frac, double* r_out, double* vc_out, cudaStream_t s)
+{
+    rotation_curve_kernel<<<nbins, 128, 0, s>>>(boxes, cx, cy, cz, nbins, rmax, nphi, frac, r_out, vc_out);
+}
+
+}  // namespace qumond

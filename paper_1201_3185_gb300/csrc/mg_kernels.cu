@@ -1,0 +1,578 @@
+// Multigrid kernels of the QUMOND solves (Section 2, steps 2 and 4): red-black
+// Gauss-Seidel half-sweeps, residual restriction, prolongation, boundary
+// injection, the single-CTA coarse-grid solver, and the FP64 outer steps of
+// the defect correction.  T is the smoothing precision (float or double).
+//
+// Level arrays use the colour-split layout of qumond_internal.h.  Two facts
+// of red-black Gauss-Seidel are used to skip dead work (both exact in exact
+// arithmetic, so the iterates are those of the textbook V-cycle):
+//  * a node's update does not read its own old value, so after a coarse-grid
+//    correction only the black nodes need the prolonged correction before the
+//    next red half-sweep, and an FMG interpolation only has to fill black
+//    nodes;
+//  * right after a black half-sweep the black residuals are zero, so the
+//    residual to restrict is nonzero only at red nodes.
+#include "qumond_internal.h"
+
+#include <cstdio>
+
+namespace qumond {
+
+namespace {
+
+constexpr int kBX = 32;
+constexpr int kBY = 8;
+
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// One half-sweep: every interior node of `colour` is set to
+//   (sum of its 6 neighbours - h^2 f) / 6,
+// its neighbours all being of the other colour.  ZERO: the neighbours are
+// known to be zero (first sweep of a correction that starts from zero).
+template <typename T, bool ZERO>
+__global__ void __launch_bounds__(kBX * kBY)
+rb_half_kernel(T* __restrict__ own, const T* __restrict__ other, const T* __restrict__ f, LevelView v, int colour,
+               T h2, T sixth)
+{
+    const int half = v.n >> 1;
+    const int m = blockIdx.x * kBX + threadIdx.x;
+    const int j = blockIdx.y * kBY + threadIdx.y + 1;
+    const int k = blockIdx.z + 1;
+    if (m >= half || j >= v.n) return;
+    const int p = (colour + j + k) & 1;  // parity of i in this row
+    if (p == 0 && m == 0) return;        // i = 0 is a boundary node
+    const long long row = ((long long)k * (v.n + 1) + j) * v.M;
+    T s = T(0);
+    if (!ZERO) {
+        const T* o = other + row;
+        const long long P = v.M, Q = (long long)v.M * (v.n + 1);
+        s = (o[m - 1 + p] + o[m + p]) + (o[m - P] + o[m + P]) + (o[m - Q] + o[m + Q]);
+    }
+    own[row + m] = (s - h2 * f[row + m]) * sixth;
+}
+
+// Residual f - L u at the red node (i, j, k) of a level.
+template <typename T>
+__device__ __forceinline__ T red_residual(const T* __restrict__ e, const T* __restrict__ f, const LevelView& v, int i,
+                                          int j, int k, T ih2)
+{
+    const int p = (j + k) & 1;
+    const int m = i >> 1;
+    const long long row = ((long long)k * (v.n + 1) + j) * v.M;
+    const T* eb = e + v.cs + row;
+    const long long P = v.M, Q = (long long)v.M * (v.n + 1);
+    const T s = (eb[m - 1 + p] + eb[m + p]) + (eb[m - P] + eb[m + P]) + (eb[m - Q] + eb[m + Q]);
+    return f[row + m] - (s - T(6) * e[row + m]) * ih2;
+}
+
+// Full weighting of the residual onto the coarse interior node (I, J, K):
+// weight 1/8 at the coinciding fine node and 1/32 at its 12 edge neighbours
+// (the other 14 fine nodes of the stencil are black, residual zero).
+template <typename T>
+__global__ void __launch_bounds__(kBX * kBY)
+restrict_resid_red_kernel(const T* __restrict__ ef, const T* __restrict__ ff, LevelView vf, T* __restrict__ fc,
+                          LevelView vc, T ih2)
+{
+    const int I = blockIdx.x * kBX + threadIdx.x + 1;
+    const int J = blockIdx.y * kBY + threadIdx.y + 1;
+    const int K = blockIdx.z + 1;
+    if (I >= vc.n || J >= vc.n) return;
+    const int i = 2 * I, j = 2 * J, k = 2 * K;
+    T edge = (red_residual(ef, ff, vf, i + 1, j + 1, k, ih2) + red_residual(ef, ff, vf, i - 1, j + 1, k, ih2))
+           + (red_residual(ef, ff, vf, i + 1, j - 1, k, ih2) + red_residual(ef, ff, vf, i - 1, j - 1, k, ih2));
+    edge += (red_residual(ef, ff, vf, i + 1, j, k + 1, ih2) + red_residual(ef, ff, vf, i - 1, j, k + 1, ih2))
+          + (red_residual(ef, ff, vf, i + 1, j, k - 1, ih2) + red_residual(ef, ff, vf, i - 1, j, k - 1, ih2));
+    edge += (red_residual(ef, ff, vf, i, j + 1, k + 1, ih2) + red_residual(ef, ff, vf, i, j - 1, k + 1, ih2))
+          + (red_residual(ef, ff, vf, i, j + 1, k - 1, ih2) + red_residual(ef, ff, vf, i, j - 1, k - 1, ih2));
+    const T centre = red_residual(ef, ff, vf, i, j, k, ih2);
+    fc[node_off(vc, I, J, K)] = T(0.125) * centre + T(0.03125) * edge;
+}
+
+// Full weighting of a right-hand side (both colours) onto coarse interior nodes.
+template <typename T>
+__global__ void __launch_bounds__(kBX * kBY)
+restrict_full_kernel(const T* __restrict__ ff, LevelView vf, T* __restrict__ fc, LevelView vc)
+{
+    const int I = blockIdx.x * kBX + threadIdx.x + 1;
+    const int J = blockIdx.y * kBY + threadIdx.y + 1;
+    const int K = blockIdx.z + 1;
+    if (I >= vc.n || J >= vc.n) return;
+    const T w[3] = {T(0.25), T(0.5), T(0.25)};
+    T acc = T(0);
+    for (int c = -1; c <= 1; ++c)
+        for (int b = -1; b <= 1; ++b)
+            for (int a = -1; a <= 1; ++a)
+                acc += (w[a + 1] * w[b + 1] * w[c + 1]) * ff[node_off(vf, 2 * I + a, 2 * J + b, 2 * K + c)];
+    fc[node_off(vc, I, J, K)] = acc;
+}
+
+// Trilinear prolongation of a coarse array to the black interior nodes of the
+// next finer level: assign (FMG interpolation) or add (coarse-grid correction).
+template <typename T, bool ADD>
+__global__ void __launch_bounds__(kBX * kBY)
+prolong_black_kernel(const T* __restrict__ ec, LevelView vc, T* __restrict__ ef, LevelView vf)
+{
+    const int half = vf.n >> 1;
+    const int m = blockIdx.x * kBX + threadIdx.x;
+    const int j = blockIdx.y * kBY + threadIdx.y + 1;
+    const int k = blockIdx.z + 1;
+    if (m >= half || j >= vf.n) return;
+    const int p = (1 + j + k) & 1;
+    const int i = 2 * m + p;
+    if (i < 1) return;
+    const int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = j >> 1, J1 = (j + 1) >> 1, K0 = k >> 1, K1 = (k + 1) >> 1;
+    T s = (ec[node_off(vc, I0, J0, K0)] + ec[node_off(vc, I1, J0, K0)])
+        + (ec[node_off(vc, I0, J1, K0)] + ec[node_off(vc, I1, J1, K0)]);
+    s += (ec[node_off(vc, I0, J0, K1)] + ec[node_off(vc, I1, J0, K1)])
+       + (ec[node_off(vc, I0, J1, K1)] + ec[node_off(vc, I1, J1, K1)]);
+    s *= T(0.125);
+    const long long o = vf.cs + ((long long)k * (vf.n + 1) + j) * vf.M + m;
+    ef[o] = ADD ? ef[o] + s : s;
+}
+
+// Boundary nodes of a level <- the finest boundary values at the same
+// positions (u64: finest natural-layout array with nfine intervals), or 0.
+__device__ __forceinline__ void face_node(int face, int a, int b, int n, int& i, int& j, int& k)
+{
+    switch (face) {
+    case 0: i = 0; j = a; k = b; break;
+    case 1: i = n; j = a; k = b; break;
+    case 2: i = a; j = 0; k = b; break;
+    case 3: i = a; j = n; k = b; break;
+    case 4: i = a; j = b; k = 0; break;
+    default: i = a; j = b; k = n; break;
+    }
+}
+
+template <typename T>
+__global__ void set_boundary_kernel(T* __restrict__ e, LevelView v, const double* __restrict__ u64, int nfine)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (a > v.n) return;
+    int i, j, k;
+    face_node(blockIdx.z, a, b, v.n, i, j, k);
+    T val = T(0);
+    if (u64) {
+        const int s = nfine / v.n;
+        const long long P = nfine + 1;
+        val = (T)u64[(long long)i * s + P * ((long long)j * s + P * (long long)k * s)];
+    }
+    e[node_off(v, i, j, k)] = val;
+}
+
+// ---------------------------------------------------------------------------
+// Coarse-grid solver: one CTA runs every level with n <= kCoarseN in shared
+// memory (natural layout), so the small levels cost one launch instead of
+// dozens.  Level l has n_l = 2 << l intervals; `top` is the level it is
+// given (its right-hand side f comes from global memory).
+//  fmg = 1: full multigrid from 3^3 up to `top` (boundary values injected
+//           from u64, or zero), ncycle V-cycles per level;
+//  fmg = 0: one V-cycle from a zero initial guess with zero boundary values.
+// The result (all nodes, boundary included) is written to e.
+constexpr int kCoarseThreads = 512;
+constexpr int kMaxCoarseLevels = 4;  // n = 2, 4, 8, 16
+
+__host__ __device__ inline int cube(int n) { return (n + 1) * (n + 1) * (n + 1); }
+
+template <typename T>
+struct CoarseSmem {
+    T* u[kMaxCoarseLevels];
+    T* f[kMaxCoarseLevels];
+    T* r[kMaxCoarseLevels];
+};
+
+template <typename T>
+__device__ void sm_relax(T* u, const T* f, int n, T h2, int colour)
+{
+    const int m = n - 1, P = n + 1;
+    const int tot = m * m * m;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+        const int i = t % m + 1, j = (t / m) % m + 1, k = t / (m * m) + 1;
+        if (((i + j + k) & 1) != colour) continue;
+        const int o = i + P * (j + P * k);
+        const T s = (u[o + 1] + u[o - 1]) + (u[o + P] + u[o - P]) + (u[o + P * P] + u[o - P * P]);
+        u[o] = (s - h2 * f[o]) * (T(1) / T(6));
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void sm_residual(const T* u, const T* f, T* r, int n, T ih2)
+{
+    const int m = n - 1, P = n + 1;
+    const int tot = m * m * m;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+        const int i = t % m + 1, j = (t / m) % m + 1, k = t / (m * m) + 1;
+        const int o = i + P * (j + P * k);
+        const T s = (u[o + 1] + u[o - 1]) + (u[o + P] + u[o - P]) + (u[o + P * P] + u[o - P * P]);
+        r[o] = f[o] - (s - T(6) * u[o]) * ih2;
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void sm_restrict(const T* fine, int nf, T* coarse)
+{
+    const int nc = nf / 2, mc = nc - 1, Pf = nf + 1, Pc = nc + 1;
+    const int tot = mc * mc * mc;
+    const T w[3] = {T(0.25), T(0.5), T(0.25)};
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+        const int I = t % mc + 1, J = (t / mc) % mc + 1, K = t / (mc * mc) + 1;
+        T acc = T(0);
+        for (int c = -1; c <= 1; ++c)
+            for (int b = -1; b <= 1; ++b)
+                for (int a = -1; a <= 1; ++a)
+                    acc += (w[a + 1] * w[b + 1] * w[c + 1]) * fine[(2 * I + a) + Pf * ((2 * J + b) + Pf * (2 * K + c))];
+        coarse[I + Pc * (J + Pc * K)] = acc;
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void sm_prolong(const T* coarse, int nc, T* fine, bool add)
+{
+    const int nf = 2 * nc, m = nf - 1, Pf = nf + 1, Pc = nc + 1;
+    const int tot = m * m * m;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+        const int i = t % m + 1, j = (t / m) % m + 1, k = t / (m * m) + 1;
+        const int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = j >> 1, J1 = (j + 1) >> 1, K0 = k >> 1, K1 = (k + 1) >> 1;
+        T s = (coarse[I0 + Pc * (J0 + Pc * K0)] + coarse[I1 + Pc * (J0 + Pc * K0)])
+            + (coarse[I0 + Pc * (J1 + Pc * K0)] + coarse[I1 + Pc * (J1 + Pc * K0)]);
+        s += (coarse[I0 + Pc * (J0 + Pc * K1)] + coarse[I1 + Pc * (J0 + Pc * K1)])
+           + (coarse[I0 + Pc * (J1 + Pc * K1)] + coarse[I1 + Pc * (J1 + Pc * K1)]);
+        s *= T(0.125);
+        const int o = i + Pf * (j + Pf * k);
+        fine[o] = add ? fine[o] + s : s;
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void sm_fill(T* a, int n, T val)
+{
+    const int tot = cube(n);
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) a[t] = val;
+    __syncthreads();
+}
+
+// The single unknown of the 3^3 grid (Section 2): u = (sum of 6 nbrs - h^2 f)/6.
+template <typename T>
+__device__ void sm_coarsest(T* u, const T* f, T h)
+{
+    if (threadIdx.x == 0) {
+        const T s = (u[14] + u[12]) + (u[16] + u[10]) + (u[22] + u[4]);
+        u[13] = (s - h * h * f[13]) * (T(1) / T(6));
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void sm_vcycle(CoarseSmem<T>& S, int top, T htop, int npre, int npost)
+{
+    for (int l = top; l >= 1; --l) {
+        const int n = 2 << l;
+        const T h = htop * T(1 << (top - l));
+        if (l < top) sm_fill(S.u[l], n, T(0));
+        for (int s = 0; s < npre; ++s) {
+            sm_relax(S.u[l], S.f[l], n, h * h, 0);
+            sm_relax(S.u[l], S.f[l], n, h * h, 1);
+        }
+        sm_residual(S.u[l], S.f[l], S.r[l], n, T(1) / (h * h));
+        sm_restrict(S.r[l], n, S.f[l - 1]);
+    }
+    if (top >= 1) sm_fill(S.u[0], 2, T(0));
+    sm_coarsest(S.u[0], S.f[0], htop * T(1 << top));
+    for (int l = 1; l <= top; ++l) {
+        const int n = 2 << l;
+        const T h = htop * T(1 << (top - l));
+        sm_prolong(S.u[l - 1], n / 2, S.u[l], true);
+        for (int s = 0; s < npost; ++s) {
+            sm_relax(S.u[l], S.f[l], n, h * h, 0);
+            sm_relax(S.u[l], S.f[l], n, h * h, 1);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCoarseThreads)
+coarse_kernel(int fmg, T* __restrict__ e, const T* __restrict__ f, LevelView v, T htop, const double* __restrict__ u64,
+              int nfine, int ncycle, int npre, int npost)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* base = reinterpret_cast<T*>(smem_raw);
+    int top = 0;
+    while ((2 << top) < v.n) ++top;
+    CoarseSmem<T> S;
+    for (int l = 0; l <= top; ++l) {
+        const int c = cube(2 << l);
+        S.u[l] = base;
+        S.f[l] = base + c;
+        S.r[l] = base + 2 * c;
+        base += 3 * c;
+    }
+    const int n = v.n, P = n + 1;
+    // right-hand side of the top level (interior), zero elsewhere
+    for (int t = threadIdx.x; t < cube(n); t += blockDim.x) {
+        const int i = t % P, j = (t / P) % P, k = t / (P * P);
+        const bool inner = i > 0 && i < n && j > 0 && j < n && k > 0 && k < n;
+        S.f[top][t] = inner ? f[node_off(v, i, j, k)] : T(0);
+    }
+    __syncthreads();
+    if (fmg) {
+        for (int l = top - 1; l >= 0; --l) sm_restrict(S.f[l + 1], 2 << (l + 1), S.f[l]);
+        // boundary values of every level: injected from the finest grid
+        for (int l = 0; l <= top; ++l) {
+            const int nl = 2 << l, Pl = nl + 1;
+            const int s = u64 ? nfine / nl : 0;
+            const long long PF = nfine + 1;
+            for (int t = threadIdx.x; t < cube(nl); t += blockDim.x) {
+                const int i = t % Pl, j = (t / Pl) % Pl, k = t / (Pl * Pl);
+                const bool inner = i > 0 && i < nl && j > 0 && j < nl && k > 0 && k < nl;
+                T val = T(0);
+                if (!inner && u64) val = (T)u64[(long long)i * s + PF * ((long long)j * s + PF * (long long)k * s)];
+                S.u[l][t] = val;
+            }
+        }
+        __syncthreads();
+        sm_coarsest(S.u[0], S.f[0], htop * T(1 << top));
+        for (int l = 1; l <= top; ++l) {
+            sm_prolong(S.u[l - 1], 1 << l, S.u[l], false);
+            for (int c = 0; c < ncycle; ++c) sm_vcycle(S, l, htop * T(1 << (top - l)), npre, npost);
+        }
+    } else {
+        sm_fill(S.u[top], n, T(0));
+        sm_vcycle(S, top, htop, npre, npost);
+    }
+    for (int t = threadIdx.x; t < cube(n); t += blockDim.x) {
+        const int i = t % P, j = (t / P) % P, k = t / (P * P);
+        e[node_off(v, i, j, k)] = S.u[top][t];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 outer steps on the caller's natural-layout arrays (n intervals).
+__device__ __forceinline__ long long nat(int n, int i, int j, int k)
+{
+    const long long P = n + 1;
+    return (long long)i + P * ((long long)j + P * (long long)k);
+}
+
+template <typename T>
+__global__ void convert_rhs_kernel(const double* __restrict__ rhs, double coef, int n, T* __restrict__ f, LevelView v)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int j = blockIdx.y + 1, k = blockIdx.z + 1;
+    if (i >= n) return;
+    f[node_off(v, i, j, k)] = (T)(coef * rhs[nat(n, i, j, k)]);
+}
+
+template <typename T, bool ADD>
+__global__ void assign_outer_kernel(double* __restrict__ u, int n, const T* __restrict__ e, LevelView v)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int j = blockIdx.y + 1, k = blockIdx.z + 1;
+    if (i >= n) return;
+    const long long o = nat(n, i, j, k);
+    const double d = (double)e[node_off(v, i, j, k)];
+    u[o] = ADD ? u[o] + d : d;
+}
+
+constexpr int kOuterThreads = 128;
+
+// r = coef*rhs - L u in FP64 on interior nodes, stored in precision T; each
+// block writes its partial sums of r^2 and (coef*rhs)^2 (fixed-order
+// reductions, so the norms are reproducible run to run).
+template <typename T>
+__global__ void __launch_bounds__(kOuterThreads)
+residual_outer_kernel(const double* __restrict__ u, const double* __restrict__ rhs, double coef, int n, double ih2,
+                      T* __restrict__ r, LevelView v, double* __restrict__ partials)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int j = blockIdx.y + 1, k = blockIdx.z + 1;
+    double rr = 0.0, ff = 0.0;
+    if (i < n) {
+        const long long P = n + 1, Q = P * P;
+        const long long o = nat(n, i, j, k);
+        const double s = (u[o + 1] + u[o - 1]) + (u[o + P] + u[o - P]) + (u[o + Q] + u[o - Q]);
+        const double fv = coef * rhs[o];
+        const double res = fv - (s - 6.0 * u[o]) * ih2;
+        r[node_off(v, i, j, k)] = (T)res;
+        rr = res * res;
+        ff = fv * fv;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        rr += __shfl_down_sync(0xffffffffu, rr, off);
+        ff += __shfl_down_sync(0xffffffffu, ff, off);
+    }
+    __shared__ double sr[kOuterThreads / 32], sf[kOuterThreads / 32];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sr[w] = rr;
+        sf[w] = ff;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < kOuterThreads / 32; ++q) {
+            a += sr[q];
+            b += sf[q];
+        }
+        const long long bid = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+        partials[2 * bid] = a;
+        partials[2 * bid + 1] = b;
+    }
+}
+
+constexpr int kReduceThreads = 1024;
+
+__global__ void __launch_bounds__(kReduceThreads) reduce_norms_kernel(const double* __restrict__ partials, int nblocks,
+                                                                      double* __restrict__ out)
+{
+    double a = 0.0, b = 0.0;
+    for (int t = threadIdx.x; t < nblocks; t += kReduceThreads) {
+        a += partials[2 * t];
+        b += partials[2 * t + 1];
+    }
+    __shared__ double sa[kReduceThreads], sb[kReduceThreads];
+    sa[threadIdx.x] = a;
+    sb[threadIdx.x] = b;
+    __syncthreads();
+    for (int s = kReduceThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sa[threadIdx.x] += sa[threadIdx.x + s];
+            sb[threadIdx.x] += sb[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sa[0];
+        out[1] = sb[0];
+    }
+}
+
+inline dim3 half_grid(int n) { return dim3(cdiv(n / 2, kBX), cdiv(n - 1, kBY), (unsigned)(n - 1)); }
+inline dim3 inner_grid(int n) { return dim3(cdiv(n - 1, kBX), cdiv(n - 1, kBY), (unsigned)(n - 1)); }
+inline dim3 outer_grid(int n) { return dim3(cdiv(n - 1, kOuterThreads), (unsigned)(n - 1), (unsigned)(n - 1)); }
+
+template <typename T>
+size_t coarse_smem_bytes(int n)
+{
+    size_t tot = 0;
+    for (int m = 2; m <= n; m *= 2) tot += 3 * (size_t)cube(m);
+    return tot * sizeof(T);
+}
+
+}  // namespace
+
+// --- launchers ------------------------------------------------------------
+template <typename T>
+void launch_rb_half(T* e, const T* f, const LevelView& v, int colour, bool zero_guess, double h, cudaStream_t s)
+{
+    T* own = e + (long long)colour * v.cs;
+    const T* other = e + (long long)(colour ^ 1) * v.cs;
+    const T* fc = f + (long long)colour * v.cs;
+    const dim3 blk(kBX, kBY);
+    if (zero_guess)
+        rb_half_kernel<T, true><<<half_grid(v.n), blk, 0, s>>>(own, other, fc, v, colour, (T)(h * h), T(1) / T(6));
+    else
+        rb_half_kernel<T, false><<<half_grid(v.n), blk, 0, s>>>(own, other, fc, v, colour, (T)(h * h), T(1) / T(6));
+}
+
+template <typename T>
+void launch_restrict_resid_red(const T* ef, const T* ff, const LevelView& vf, T* fc, const LevelView& vc, double hf,
+                               cudaStream_t s)
+{
+    restrict_resid_red_kernel<T><<<inner_grid(vc.n), dim3(kBX, kBY), 0, s>>>(ef, ff, vf, fc, vc, (T)(1.0 / (hf * hf)));
+}
+
+template <typename T>
+void launch_restrict_full(const T* ff, const LevelView& vf, T* fc, const LevelView& vc, cudaStream_t s)
+{
+    restrict_full_kernel<T><<<inner_grid(vc.n), dim3(kBX, kBY), 0, s>>>(ff, vf, fc, vc);
+}
+
+template <typename T>
+void launch_prolong_black(const T* ec, const LevelView& vc, T* ef, const LevelView& vf, bool add, cudaStream_t s)
+{
+    if (add)
+        prolong_black_kernel<T, true><<<half_grid(vf.n), dim3(kBX, kBY), 0, s>>>(ec, vc, ef, vf);
+    else
+        prolong_black_kernel<T, false><<<half_grid(vf.n), dim3(kBX, kBY), 0, s>>>(ec, vc, ef, vf);
+}
+
+template <typename T>
+void launch_set_boundary(T* e, const LevelView& v, const double* u64, int nfine, cudaStream_t s)
+{
+    set_boundary_kernel<T><<<dim3(cdiv(v.n + 1, 128), (unsigned)(v.n + 1), 6), 128, 0, s>>>(e, v, u64, nfine);
+}
+
+template <typename T>
+cudaError_t launch_coarse(int fmg, T* e, const T* f, const LevelView& v, double h, const double* u64, int nfine,
+                          int ncycle, int npre, int npost, cudaStream_t s)
+{
+    const size_t bytes = coarse_smem_bytes<T>(v.n);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t err = cudaFuncSetAttribute(coarse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)coarse_smem_bytes<T>(kCoarseN));
+        if (err != cudaSuccess) return err;
+        attr_set = true;
+    }
+    coarse_kernel<T><<<1, kCoarseThreads, bytes, s>>>(fmg, e, f, v, (T)h, u64, nfine, ncycle, npre, npost);
+    return cudaSuccess;
+}
+
+template <typename T>
+void launch_convert_rhs(const double* rhs, double coef, int n, T* f, const LevelView& v, cudaStream_t s)
+{
+    convert_rhs_kernel<T><<<outer_grid(n), kOuterThreads, 0, s>>>(rhs, coef, n, f, v);
+}
+
+template <typename T>
+void launch_assign_outer(double* u, int n, const T* e, const LevelView& v, bool add, cudaStream_t s)
+{
+    if (add)
+        assign_outer_kernel<T, true><<<outer_grid(n), kOuterThreads, 0, s>>>(u, n, e, v);
+    else
+        assign_outer_kernel<T, false><<<outer_grid(n), kOuterThreads, 0, s>>>(u, n, e, v);
+}
+
+int residual_outer_blocks(int n)
+{
+    const dim3 g = outer_grid(n);
+    return (int)(g.x * g.y * g.z);
+}
+
+template <typename T>
+int launch_residual_outer(const double* u, const double* rhs, double coef, int n, double h, T* r, const LevelView& v,
+                          double* partials, cudaStream_t s)
+{
+    residual_outer_kernel<T><<<outer_grid(n), kOuterThreads, 0, s>>>(u, rhs, coef, n, 1.0 / (h * h), r, v, partials);
+    return residual_outer_blocks(n);
+}
+
+void launch_reduce_norms(const double* partials, int nblocks, double* out, cudaStream_t s)
+{
+    reduce_norms_kernel<<<1, kReduceThreads, 0, s>>>(partials, nblocks, out);
+}
+
+#define QUMOND_INSTANTIATE(T)                                                                                          \
+    template void launch_rb_half<T>(T*, const T*, const LevelView&, int, bool, double, cudaStream_t);                 \
+    template void launch_restrict_resid_red<T>(const T*, const T*, const LevelView&, T*, const LevelView&, double,    \
+                                               cudaStream_t);                                                          \
+    template void launch_restrict_full<T>(const T*, const LevelView&, T*, const LevelView&, cudaStream_t);            \
+    template void launch_prolong_black<T>(const T*, const LevelView&, T*, const LevelView&, bool, cudaStream_t);      \
+    template void launch_set_boundary<T>(T*, const LevelView&, const double*, int, cudaStream_t);                     \
+    template cudaError_t launch_coarse<T>(int, T*, const T*, const LevelView&, double, const double*, int, int, int,  \
+                                          int, cudaStream_t);                                                          \
+    template void launch_convert_rhs<T>(const double*, double, int, T*, const LevelView&, cudaStream_t);              \
+    template void launch_assign_outer<T>(double*, int, const T*, const LevelView&, bool, cudaStream_t);               \
+    template int launch_residual_outer<T>(const double*, const double*, double, int, double, T*, const LevelView&,    \
+                                          double*, cudaStream_t);
+
+QUMOND_INSTANTIATE(float)
+QUMOND_INSTANTIATE(double)
+
+}  // namespace qumond

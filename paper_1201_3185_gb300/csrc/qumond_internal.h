@@ -1,0 +1,101 @@
+// Internal declarations shared by the CUDA translation units of libqumond.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qumond {
+
+// Colour-split storage of one multigrid level (n intervals, (n+1)^3 nodes).
+// Node (i,j,k) has colour c = (i+j+k) & 1 (0 = red, updated first).  Each
+// colour is its own array of rows: row (j,k) of colour c holds that colour's
+// nodes of the row, node i at position i >> 1.  Rows are M entries long
+// (M >= n/2 + 1, a multiple of 4 so rows start on 16-byte boundaries) and the
+// two colour arrays sit cs elements apart.
+//
+// With this layout a red-black half-sweep streams only the colour it writes
+// and the colour it reads: the six neighbours of node (2m+p, j, k) of colour
+// c are, in colour 1-c, entries m-1+p and m+p of the same row (x), entry m of
+// rows j-1 and j+1 (y) and entry m of planes k-1 and k+1 (z), where
+// p = (c + j + k) & 1 is the parity of i in that row.
+struct LevelView {
+    int n;
+    int M;
+    long long cs;
+};
+
+__host__ __device__ inline long long row_off(const LevelView& v, int c, int j, int k)
+{
+    return (long long)c * v.cs + ((long long)k * (v.n + 1) + j) * (long long)v.M;
+}
+
+__host__ __device__ inline long long node_off(const LevelView& v, int i, int j, int k)
+{
+    return row_off(v, (i + j + k) & 1, j, k) + (i >> 1);
+}
+
+inline LevelView make_view(int n)
+{
+    LevelView v;
+    v.n = n;
+    v.M = ((n / 2 + 1) + 3) & ~3;
+    long long plane = (long long)v.M * (n + 1) * (n + 1);
+    v.cs = (plane + 63) & ~63LL;
+    return v;
+}
+
+// Largest level handled entirely by the single-CTA coarse-grid kernel.
+constexpr int kCoarseN = 16;
+
+// --- multigrid kernels (mg_kernels.cu), T = float or double ---------------
+template <typename T> void launch_rb_half(T* e, const T* f, const LevelView& v, int colour, bool zero_guess,
+                                          double h, cudaStream_t s);
+template <typename T> void launch_restrict_resid_red(const T* ef, const T* ff, const LevelView& vf, T* fc,
+                                                     const LevelView& vc, double hf, cudaStream_t s);
+template <typename T> void launch_restrict_full(const T* ff, const LevelView& vf, T* fc, const LevelView& vc,
+                                                cudaStream_t s);
+template <typename T> void launch_prolong_black(const T* ec, const LevelView& vc, T* ef, const LevelView& vf,
+                                                bool add, cudaStream_t s);
+template <typename T> void launch_set_boundary(T* e, const LevelView& v, const double* u64, int nfine,
+                                               cudaStream_t s);
+template <typename T> cudaError_t launch_coarse(int fmg, T* e, const T* f, const LevelView& v, double h,
+                                                const double* u64, int nfine, int ncycle, int npre, int npost,
+                                                cudaStream_t s);
+// FP64 outer steps on the caller's natural-layout arrays.
+template <typename T> void launch_convert_rhs(const double* rhs, double coef, int n, T* f, const LevelView& v,
+                                              cudaStream_t s);
+template <typename T> void launch_assign_outer(double* u, int n, const T* e, const LevelView& v, bool add,
+                                               cudaStream_t s);
+template <typename T> int launch_residual_outer(const double* u, const double* rhs, double coef, int n, double h,
+                                                T* r, const LevelView& v, double* partials, cudaStream_t s);
+void launch_reduce_norms(const double* partials, int nblocks, double* out, cudaStream_t s);
+int residual_outer_blocks(int n);
+
+// --- grid kernels (grid_kernels.cu) ------------------------------------------
+void launch_cic_deposit(const double* x, const double* y, const double* z, const double* m, long long np, int n,
+                        double xlo, double ylo, double zlo, double inv_h, double two_shift, int64_t* q,
+                        cudaStream_t s);
+void launch_fixed_to_rho(const int64_t* q, double* rho, long long count, double scale, cudaStream_t s);
+void launch_boundary_zero(double* u, int n, cudaStream_t s);
+void launch_boundary_from_parent(const double* parent, double* u, int n, int ratio, cudaStream_t s);
+void launch_source(const double* phi, double* src, int n, double h, double a0, cudaStream_t s);
+
+struct BoxGeom {
+    const double* phi;
+    double xlo, ylo, zlo;
+    double inv_h;
+    double h;
+    double L;
+};
+constexpr int kMaxBoxes = 16;
+struct BoxSet {
+    BoxGeom b[kMaxBoxes];
+    int nboxes;
+    int n;
+};
+void launch_forces(const BoxSet& boxes, const double* qx, const double* qy, const double* qz, long long nq,
+                   double* gx, double* gy, double* gz, cudaStream_t s);
+void launch_rotation_curve(const BoxSet& boxes, double cx, double cy, double cz, int nbins, double rmax, int nphi,
+                           double frac, double* r_out, double* vc_out, cudaStream_t s);
+
+}  // namespace qumond

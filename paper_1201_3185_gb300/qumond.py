@@ -1,0 +1,255 @@
+"""Python binding of libqumond's C ABI (include/qumond.h).
+
+Argument marshalling only: every function checks tensor placement, dtype,
+shape and contiguity, then calls the C entry point of the same name with raw
+device pointers and the current CUDA stream.  All arithmetic of the path runs
+in the library's CUDA kernels; there is no fallback.  If the shared library
+is missing or fails to load, importing this module raises.
+
+Grids are 1-D tensors of (n+1)^3 elements (x fastest) or (n+1, n+1, n+1)
+tensors indexed [k, j, i].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+_LIB_PATH = _build.LIB
+
+QUMOND_OK = 0
+QUMOND_ERR_INVALID_ARG = 1
+QUMOND_ERR_CUDA = 2
+QUMOND_ERR_NOT_CONVERGED = 3
+QUMOND_ERR_TIMEOUT = 4
+QUMOND_ERR_OUT_OF_MEMORY = 5
+
+QUMOND_PREC_FP64 = 0
+QUMOND_PREC_MIXED = 1
+QUMOND_BC_ZERO = 0
+QUMOND_BC_GIVEN = 1
+
+EXPORTED = (
+    "qumond_default_params", "qumond_create", "qumond_destroy", "qumond_last_error", "qumond_deposit",
+    "qumond_solve_newton", "qumond_source", "qumond_solve_mond", "qumond_forces", "qumond_rotation_curve",
+)
+
+
+class qumond_params(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int),
+        ("nboxes", ctypes.c_int),
+        ("L0", ctypes.c_double),
+        ("center", ctypes.c_double * 3),
+        ("G", ctypes.c_double),
+        ("a0", ctypes.c_double),
+        ("npre", ctypes.c_int),
+        ("npost", ctypes.c_int),
+        ("ncycle", ctypes.c_int),
+        ("rel_tol", ctypes.c_double),
+        ("max_vcycles", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("bc_mode", ctypes.c_int),
+        ("warm_start", ctypes.c_int),
+        ("deposit_shift", ctypes.c_int),
+        ("rc_box_frac", ctypes.c_double),
+        ("box_ratio", ctypes.c_int),
+    ]
+
+
+class qumond_stats(ctypes.Structure):
+    _fields_ = [
+        ("vcycles", ctypes.c_int),
+        ("converged", ctypes.c_int),
+        ("rel_residual_fmg", ctypes.c_double),
+        ("rel_residual", ctypes.c_double),
+    ]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_L = ctypes.c_int64
+_D = ctypes.c_double
+
+
+def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError("libqumond.so not built (%s): run paper_1201_3185_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    sigs = {
+        "qumond_default_params": (None, [ctypes.POINTER(qumond_params)]),
+        "qumond_create": (_I, [ctypes.POINTER(qumond_params), ctypes.POINTER(_P)]),
+        "qumond_destroy": (None, [_P]),
+        "qumond_last_error": (ctypes.c_char_p, [_P]),
+        "qumond_deposit": (_I, [_P, _I, _P, _P, _P, _P, _L, _P, _P, _P]),
+        "qumond_solve_newton": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(qumond_stats), _P]),
+        "qumond_source": (_I, [_P, _I, _P, _P, _P]),
+        "qumond_solve_mond": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(qumond_stats), _P]),
+        "qumond_forces": (_I, [_P, _P, _P, _P, _P, _L, _P, _P, _P, _P]),
+        "qumond_rotation_curve": (_I, [_P, _P, _I, _D, _I, _P, _P, _P]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+class QumondError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("qumond status %d: %s" % (status, message))
+        self.status = status
+
+
+class NotConverged(QumondError):
+    pass
+
+
+def default_params(**overrides) -> qumond_params:
+    p = qumond_params()
+    _lib.qumond_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "center":
+            p.center[0], p.center[1], p.center[2] = (float(c) for c in v)
+        elif not hasattr(p, k):
+            raise TypeError("unknown parameter %r" % k)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype, numel=None, name="tensor") -> ctypes.c_void_p:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch.Tensor" % name)
+    if t.device.type != "cuda":
+        raise ValueError("%s must live on a CUDA device" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s must have %d elements, got %d" % (name, numel, t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class SolveStats:
+    vcycles: int
+    converged: bool
+    rel_residual_fmg: float
+    rel_residual: float
+
+
+class Context:
+    """A qumond_ctx: parameters plus the multigrid scratch on the current device."""
+
+    def __init__(self, params: qumond_params | None = None, **overrides):
+        if params is None:
+            params = default_params(**overrides)
+        elif overrides:
+            raise TypeError("give either params or keyword overrides")
+        self.params = params
+        self._ptr = ctypes.c_void_p()
+        st = _lib.qumond_create(ctypes.byref(params), ctypes.byref(self._ptr))
+        if st != QUMOND_OK:
+            raise QumondError(st, "qumond_create failed (invalid parameters or out of memory)")
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self):
+        if self._ptr:
+            _lib.qumond_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def n(self) -> int:
+        return self.params.n
+
+    @property
+    def nodes(self) -> int:
+        return (self.params.n + 1) ** 3
+
+    def box_side(self, box: int) -> float:
+        return self.params.L0 / self.params.box_ratio ** box
+
+    def _check(self, st: int):
+        if st == QUMOND_OK:
+            return
+        msg = _lib.qumond_last_error(self._ptr).decode()
+        if st == QUMOND_ERR_NOT_CONVERGED:
+            raise NotConverged(st, msg)
+        raise QumondError(st, msg)
+
+    # -- entry points -------------------------------------------------------------
+    def qumond_deposit(self, box, x, y, z, mass, rho_fixed, rho=None, stream=None):
+        npart = x.numel()
+        args = [_dev(a, torch.float64, npart, nm) for a, nm in ((x, "x"), (y, "y"), (z, "z"), (mass, "mass"))]
+        q = _dev(rho_fixed, torch.int64, self.nodes, "rho_fixed")
+        r = _dev(rho, torch.float64, self.nodes, "rho") if rho is not None else None
+        self._check(_lib.qumond_deposit(self._ptr, box, *args, npart, q, r, _stream(stream)))
+
+    def _solve(self, fn, box, rhs, parent, out, want_stats, stream):
+        a = _dev(rhs, torch.float64, self.nodes, "rhs")
+        par = _dev(parent, torch.float64, self.nodes, "parent") if parent is not None else None
+        o = _dev(out, torch.float64, self.nodes, "phi")
+        st = qumond_stats()
+        status = fn(self._ptr, box, a, par, o, ctypes.byref(st) if want_stats else None, _stream(stream))
+        self._check(status)
+        if want_stats:
+            return SolveStats(st.vcycles, bool(st.converged), st.rel_residual_fmg, st.rel_residual)
+        return None
+
+    def qumond_solve_newton(self, box, rho, phiN_parent, phiN, stats=False, stream=None):
+        return self._solve(_lib.qumond_solve_newton, box, rho, phiN_parent, phiN, stats, stream)
+
+    def qumond_source(self, box, phiN, src, stream=None):
+        a = _dev(phiN, torch.float64, self.nodes, "phiN")
+        b = _dev(src, torch.float64, self.nodes, "src")
+        self._check(_lib.qumond_source(self._ptr, box, a, b, _stream(stream)))
+
+    def qumond_solve_mond(self, box, src, phi_parent, phi, stats=False, stream=None):
+        return self._solve(_lib.qumond_solve_mond, box, src, phi_parent, phi, stats, stream)
+
+    def _phis(self, phis):
+        if len(phis) != self.params.nboxes:
+            raise ValueError("need one potential per box (%d)" % self.params.nboxes)
+        ptrs = [_dev(p, torch.float64, self.nodes, "phi_boxes[%d]" % b).value for b, p in enumerate(phis)]
+        return (ctypes.c_void_p * len(ptrs))(*ptrs)
+
+    def qumond_forces(self, phis, qx, qy, qz, gx, gy, gz, stream=None):
+        nq = qx.numel()
+        arr = self._phis(phis)
+        pts = [_dev(a, torch.float64, nq, nm) for a, nm in ((qx, "qx"), (qy, "qy"), (qz, "qz"),
+                                                             (gx, "gx"), (gy, "gy"), (gz, "gz"))]
+        self._check(_lib.qumond_forces(self._ptr, ctypes.cast(arr, _P), *pts[:3], nq, *pts[3:], _stream(stream)))
+
+    def qumond_rotation_curve(self, phis, nbins, rmax, nphi, r_out, vc_out, stream=None):
+        arr = self._phis(phis)
+        r = _dev(r_out, torch.float64, nbins, "r_out")
+        v = _dev(vc_out, torch.float64, nbins, "vc_out")
+        self._check(_lib.qumond_rotation_curve(self._ptr, ctypes.cast(arr, _P), nbins, float(rmax), nphi, r, v,
+                                               _stream(stream)))

@@ -1,0 +1,301 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (derivations in the design doc):
+* deposit: bit-exact int64 grid, bit-exact FP64 density;
+* FP64 solves at a fixed number of V-cycles: 1e-11 of max|u| (same iterates,
+  only the rounding order differs);
+* FP32-smoothing + FP64-refinement solves to rel. residual 1e-10: 1e-6 of
+  max|Phi| (the stated bound of the path), v_c 1e-5;
+* source: 1e-6 of max|src| (FP32 nu and fluxes from FP64 differences);
+* forces, rotation curve, boundary fill from identical inputs: 1e-12.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from tests import analytic as an
+from tests.gpu_helpers import G, A0, gpu_pipeline, rel_max, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    import paper_1201_3185_gb300 as q
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return q
+
+
+def solve_given(q, n, L, f, bc, *, stats=True, **params):
+    """Solve L u = f on one box with the caller's boundary values (C ABI)."""
+    ctx = q.Context(n=n, nboxes=1, L0=L, bc_mode=q.QUMOND_BC_GIVEN, **params)
+    u = to_dev(np.where(an.boundary_mask(n), bc, 0.0))
+    st = None
+    err = None
+    try:
+        st = ctx.qumond_solve_mond(0, to_dev(f), None, u, stats=stats)
+    except q.NotConverged as e:
+        err = e
+    torch.cuda.synchronize()
+    out = u.cpu().numpy()
+    ctx.close()
+    return out, st, err
+
+
+# --- step 1: deposit ---------------------------------------------------------------
+@pytest.mark.parametrize("n,L", [(8, 800.0), (64, 40000.0), (256, 120000.0)])
+def test_deposit_bit_exact(q, ora, n, L):
+    rng = np.random.default_rng(n)
+    npart = 300_000
+    x, y, z = (rng.random((3, npart)) - 0.5) * 1.05 * L  # some outside
+    m = rng.random(npart) * 1e5
+    h = L / n
+    # edge cases: exactly on nodes, on the upper face, at the lower corner, NaN
+    x[:5] = [-0.5 * L, 0.5 * L, -0.5 * L + 3 * h, np.nan, 0.0]
+    y[:5] = [-0.5 * L, 0.0, -0.5 * L + 2 * h, 0.0, 0.5 * L - 1e-9 * h]
+    z[:5] = [-0.5 * L, 0.0, 0.0, 0.0, 0.0]
+    want, kept = ora.cic_deposit(n, L, (0.0, 0.0, 0.0), 24, x, y, z, m)
+    ctx = q.Context(n=n, nboxes=1, L0=L)
+    qf = torch.empty((n + 1) ** 3, dtype=torch.int64, device="cuda")
+    rho = torch.empty((n + 1) ** 3, dtype=torch.float64, device="cuda")
+    ctx.qumond_deposit(0, to_dev(x), to_dev(y), to_dev(z), to_dev(m), qf, rho)
+    torch.cuda.synchronize()
+    assert np.array_equal(qf.cpu().numpy(), want)
+    assert np.array_equal(rho.cpu().numpy(), ora.rho_from_fixed(n, L, 24, want))
+    ctx.close()
+
+
+def test_deposit_empty_and_outside(q):
+    n, L = 16, 1600.0
+    ctx = q.Context(n=n, nboxes=1, L0=L)
+    qf = torch.full(((n + 1) ** 3,), 7, dtype=torch.int64, device="cuda")
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    ctx.qumond_deposit(0, e, e, e, e, qf)
+    assert int(qf.abs().sum()) == 0
+    far = to_dev(np.full(10, 1e6))
+    ctx.qumond_deposit(0, far, far, far, far, qf)
+    assert int(qf.abs().sum()) == 0
+    ctx.close()
+
+
+# --- steps 2 and 4: the solver -------------------------------------------------------
+@pytest.mark.parametrize("n", [2, 4, 16, 32, 64, 128])
+def test_fp64_paper_mode_matches_oracle_fmg(q, ora, n):
+    # six V-cycles per FMG level, no tolerance (Section 3.2's default)
+    rng = np.random.default_rng(100 + n)
+    L = 1000.0
+    f = rng.standard_normal((n + 1) ** 3)
+    bc = rng.standard_normal((n + 1) ** 3) * 50.0
+    got, _, _ = solve_given(q, n, L, f, bc, precision=q.QUMOND_PREC_FP64, rel_tol=0.0)
+    want = np.where(an.boundary_mask(n), bc, 0.0)
+    ora.fmg(n, L / n, want, f, 6, 2, 2)
+    assert rel_max(got, want) < 1e-11
+
+
+@pytest.mark.parametrize("n,ncycle,npre,npost", [(64, 1, 1, 1), (64, 2, 2, 2), (128, 3, 1, 2)])
+def test_fp64_fmg_variants_match_oracle(q, ora, n, ncycle, npre, npost):
+    x, y, z = an.node_coords(n, 2.0)
+    f = np.exp(-(x * x + 2 * y * y + 3 * z * z) / 0.1) * 100.0
+    bc = 1.0 + x - 0.5 * y + z * z
+    got, _, _ = solve_given(q, n, 2.0, f, bc, precision=q.QUMOND_PREC_FP64, ncycle=ncycle, npre=npre, npost=npost)
+    want = np.where(an.boundary_mask(n), bc, 0.0)
+    ora.fmg(n, 2.0 / n, want, f, ncycle, npre, npost)
+    assert rel_max(got, want) < 1e-11
+
+
+@pytest.mark.parametrize("n", [8, 64])
+def test_fp64_extra_vcycles_match_oracle(q, ora, n):
+    # the same number of V-cycles after FMG on both sides (tolerance never met)
+    rng = np.random.default_rng(7)
+    f = rng.standard_normal((n + 1) ** 3)
+    bc = rng.standard_normal((n + 1) ** 3)
+    got, _, err = solve_given(q, n, 10.0, f, bc, precision=q.QUMOND_PREC_FP64, ncycle=1, rel_tol=1e-300,
+                              max_vcycles=3)
+    assert err is not None and err.status == 3  # NOT_CONVERGED, best iterate kept
+    want = np.where(an.boundary_mask(n), bc, 0.0)
+    made, _ = ora.solve(n, 10.0 / n, want, f, ncycle=1, tol=1e-300, max_vcycles=3)
+    assert made == -1
+    assert rel_max(got, want) < 1e-11
+
+
+@pytest.mark.parametrize("n", [16, 64, 128])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_tolerance_mode_matches_oracle(q, ora, n, prec):
+    x, y, z = an.node_coords(n, 4000.0)
+    f = np.exp(-(x * x + y * y + 4 * z * z) / 2e5) * 0.05
+    bc = -1000.0 / np.sqrt(x * x + y * y + z * z + 1e6)
+    got, st, _ = solve_given(q, n, 4000.0, f, bc, precision=prec, rel_tol=1e-10, max_vcycles=40)
+    assert st.converged and st.rel_residual <= 1e-10
+    want = np.where(an.boundary_mask(n), bc, 0.0)
+    ora.solve(n, 4000.0 / n, want, f, tol=1e-12, max_vcycles=60)
+    assert rel_max(got, want) < (1e-9 if prec == 0 else 1e-6)
+    # the reported residual is the true one
+    r = ora.residual(n, 4000.0 / n, got, f)
+    rel = np.sqrt(ora.interior_sumsq(n, r) / ora.interior_sumsq(n, f))
+    assert rel == pytest.approx(st.rel_residual, rel=1e-3, abs=1e-14)
+
+
+def test_coarsest_grid_special_case(q):
+    # Section 2: with zero boundary values the 3^3 centre potential is -h^2 f/6
+    f = np.zeros(27)
+    f[13] = 3.0
+    got, _, _ = solve_given(q, 2, 8.0, f, np.zeros(27), precision=q.QUMOND_PREC_FP64)
+    assert got[13] == pytest.approx(-16.0 * 3.0 / 6.0, rel=1e-15)
+
+
+def test_warm_start_from_solution_needs_no_vcycle(q, ora):
+    n = 32
+    x, y, z = an.node_coords(n, 2.0)
+    f = np.cos(3 * x) * np.sin(2 * y) * z
+    bc = x * y
+    want = np.where(an.boundary_mask(n), bc, 0.0)
+    ora.solve(n, 2.0 / n, want, f, tol=1e-13, max_vcycles=60)
+    # warm start: pass the converged solution's interior as the initial guess
+    ctx = q.Context(n=n, nboxes=1, L0=2.0, bc_mode=q.QUMOND_BC_GIVEN, warm_start=1, rel_tol=1e-10,
+                    max_vcycles=10)
+    u = to_dev(want.copy())
+    st = ctx.qumond_solve_mond(0, to_dev(f), None, u, stats=True)
+    assert st.vcycles == 0 and st.rel_residual_fmg < 1e-10
+    ctx.close()
+
+
+# --- step 3: source --------------------------------------------------------------
+def test_source_matches_oracle(q, ora):
+    p = synth.two_component_disk(200_000, seed=4, rmax=27000.0, zmax=27000.0)
+    n, L0 = 64, 60000.0
+    boxes = ora.pipeline(p, n, L0, 1, tol=1e-11, max_vcycles=50)
+    phiN = boxes[0].phiN
+    ctx = q.Context(n=n, nboxes=1, L0=L0)
+    src = torch.empty_like(to_dev(phiN))
+    ctx.qumond_source(0, to_dev(phiN), src)
+    got = src.cpu().numpy()
+    assert rel_max(got, boxes[0].src) < 1e-6
+    assert np.all(got[an.boundary_mask(n)] == 0.0)
+    ctx.close()
+
+
+def test_source_linear_and_plain_laplacian(q):
+    n, L = 32, 3200.0
+    x, y, z = an.node_coords(n, L)
+    phi = 3.0 * x - 1.5 * y + 0.7 * z
+    ctx = q.Context(n=n, nboxes=1, L0=L)
+    src = torch.empty((n + 1) ** 3, dtype=torch.float64, device="cuda")
+    ctx.qumond_source(0, to_dev(phi), src)
+    assert float(src.abs().max()) < 1e-5 * 3.0 / (L / n)
+    ctx.close()
+    rng = np.random.default_rng(1)
+    phi = rng.standard_normal((n + 1) ** 3)
+    ctx = q.Context(n=n, nboxes=1, L0=L, a0=0.0)
+    ctx.qumond_source(0, to_dev(phi), src)
+    lap = an.laplacian7(phi, n, L / n)
+    assert rel_max(src.cpu().numpy(), lap) < 1e-6
+    ctx.close()
+
+
+# --- nested boxes, forces and rotation curve -------------------------------------
+@pytest.mark.parametrize("ratio", [2, 4])
+def test_boundary_fill_matches_oracle(q, ora, ratio):
+    n, L0 = 32, 32000.0
+    rng = np.random.default_rng(ratio)
+    parent = rng.standard_normal((n + 1) ** 3)
+    ctx = q.Context(n=n, nboxes=2, L0=L0, box_ratio=ratio, precision=q.QUMOND_PREC_FP64)
+    u = torch.zeros((n + 1) ** 3, dtype=torch.float64, device="cuda")
+    ctx.qumond_solve_mond(1, to_dev(np.zeros((n + 1) ** 3)), to_dev(parent), u)
+    got = u.cpu().numpy()
+    want = np.zeros((n + 1) ** 3)
+    ora.boundary_fill(n, L0, (0.0, 0.0, 0.0), parent, L0 / ratio, (0.0, 0.0, 0.0), want)
+    bnd = an.boundary_mask(n)
+    assert np.max(np.abs(got[bnd] - want[bnd])) < 1e-12
+    ctx.close()
+
+
+def test_forces_and_rotation_curve_match_oracle(q, ora):
+    n, L0, nb = 64, 120000.0, 3
+    p = synth.two_component_disk(100_000, seed=8, rmax=54000.0, zmax=54000.0)
+    boxes = ora.pipeline(p, n, L0, nb, tol=1e-10, max_vcycles=40)
+    phis = [b.phi for b in boxes]
+    ctx = q.Context(n=n, nboxes=nb, L0=L0)
+    dphis = [to_dev(a) for a in phis]
+    qx, qy, qz = (to_dev(a) for a in (p.x, p.y, p.z))
+    g = [torch.empty_like(qx) for _ in range(3)]
+    ctx.qumond_forces(dphis, qx, qy, qz, *g)
+    want = ora.forces(n, L0, (0.0, 0.0, 0.0), phis, p.x, p.y, p.z)
+    scale = max(np.max(np.abs(w)) for w in want[:3])
+    for a, b in zip(g, want[:3]):
+        assert np.max(np.abs(a.cpu().numpy() - b)) < 1e-12 * scale
+    r = torch.empty(50, dtype=torch.float64, device="cuda")
+    vc = torch.empty(50, dtype=torch.float64, device="cuda")
+    ctx.qumond_rotation_curve(dphis, 50, 30000.0, 64, r, vc)
+    r_w, vc_w = ora.rotation_curve(n, L0, (0.0, 0.0, 0.0), phis, 50, 30000.0, 64)
+    assert np.allclose(r.cpu().numpy(), r_w, rtol=0, atol=1e-9)
+    assert np.max(np.abs(vc.cpu().numpy() / vc_w - 1.0)) < 1e-12
+    ctx.close()
+
+
+# --- the whole path --------------------------------------------------------------
+def _compare_pipelines(gpu, boxes, n, L0, nbins, rmax, phi_tol, vc_tol, ratio=2, phiN_tol=None):
+    phiN_tol = phi_tol if phiN_tol is None else phiN_tol
+    for b, bx in enumerate(boxes):
+        assert np.array_equal(gpu["rho_fixed"][b], bx.rho_fixed), "box %d deposit" % b
+        assert rel_max(gpu["phiN"][b], bx.phiN) < phiN_tol, "box %d Phi_N" % b
+        assert rel_max(gpu["phi"][b], bx.phi) < phi_tol, "box %d Phi" % b
+    _, vc_w = __import__("oracle").rotation_curve(n, L0, (0.0, 0.0, 0.0), [b.phi for b in boxes], nbins, rmax,
+                                                  ratio=ratio)
+    assert np.max(np.abs(gpu["vc"] / vc_w - 1.0)) < vc_tol
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_kuzmin_check_config(q, ora, prec):
+    # Kuzmin disk, M = 1e10, a = 2 kpc, 2e5 particles at z = 0; a 64^3 grid on
+    # 40 kpc inside a 64^3 boundary box of 160 kpc; tolerance 1e-10; 50 bins
+    M, a = 1e10, 2000.0
+    p = synth.kuzmin_disk(200_000, M, a, seed=1)
+    n, L0, nb, ratio = 64, 160000.0, 2, 4
+    bcn = lambda x, y, z: an.kuzmin_phiN(x, y, z, M, a, G)
+    bcm = lambda x, y, z: an.kuzmin_phi_mond(x, y, z, M, a, G, A0)
+    gpu = gpu_pipeline(p, n, L0, nb, nbins=50, rmax=20000.0, box_ratio=ratio, rel_tol=1e-10, max_vcycles=40,
+                       precision=prec, bc_newton=bcn, bc_mond=bcm)
+    boxes = ora.pipeline(p, n, L0, nb, tol=1e-12, max_vcycles=60, bc_newton=bcn, bc_mond=bcm, ratio=ratio)
+    _compare_pipelines(gpu, boxes, n, L0, 50, 20000.0, 1e-6, 1e-5, ratio=ratio)
+    for st in gpu["newton_stats"] + gpu["mond_stats"]:
+        assert st.converged and st.rel_residual <= 1e-10
+
+
+def test_paper_mode_pipeline_fp64(q, ora):
+    # the paper's defaults (6 V-cycles per level, zero outer boundary), 3 boxes
+    p = synth.two_component_disk(100_000, seed=2, rmax=54000.0, zmax=54000.0)
+    n, L0, nb = 64, 120000.0, 3
+    gpu = gpu_pipeline(p, n, L0, nb, nbins=40, rmax=20000.0, precision=q.QUMOND_PREC_FP64, rel_tol=0.0)
+    boxes = ora.pipeline(p, n, L0, nb)
+    # Phi_N: identical iterates (FP64 FMG); Phi also carries the FP32 nu of the source
+    _compare_pipelines(gpu, boxes, n, L0, 40, 20000.0, 1e-6, 1e-5, phiN_tol=1e-11)
+
+
+def test_deterministic(q):
+    p = synth.two_component_disk(50_000, seed=3, rmax=54000.0, zmax=54000.0)
+    a = gpu_pipeline(p, 64, 120000.0, 2, rel_tol=1e-10, max_vcycles=40)
+    b = gpu_pipeline(p, 64, 120000.0, 2, rel_tol=1e-10, max_vcycles=40)
+    for key in ("phiN", "phi"):
+        for x, y in zip(a[key], b[key]):
+            assert np.array_equal(x, y)
+    assert np.array_equal(a["vc"], b["vc"])
+
+
+def test_invalid_arguments_rejected(q):
+    with pytest.raises(q.QumondError):
+        q.Context(n=48, nboxes=1, L0=1.0)
+    with pytest.raises(q.QumondError):
+        q.Context(n=64, nboxes=1, L0=1.0, npre=0)
+    ctx = q.Context(n=8, nboxes=2, L0=100.0)
+    # a host pointer handed to the C ABI is refused before any launch
+    host = np.zeros(9 ** 3)
+    st = q.qumond._lib.qumond_source(ctx._ptr, 0, host.ctypes.data_as(q.qumond._P),
+                                     host.ctypes.data_as(q.qumond._P), None)
+    assert st == q.qumond.QUMOND_ERR_INVALID_ARG
+    dev = torch.zeros(9 ** 3, dtype=torch.float64, device="cuda")
+    with pytest.raises(q.QumondError):  # box 1 without its parent
+        ctx.qumond_solve_newton(1, dev, None, torch.zeros_like(dev))
+    with pytest.raises(q.QumondError):  # box out of range
+        ctx.qumond_source(2, dev, torch.zeros_like(dev))
+    ctx.close()
