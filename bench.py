@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Throughput of the QUMOND particle-mesh path on GB300.
+
+One step = one evaluation of the whole path for one galaxy: for each of the
+3 nested boxes (120, 60, 30 kpc; 257^3 nodes each) the CIC deposit of 2e6
+particles, the Newtonian FMG solve, the QUMOND source and the QUMOND FMG
+solve (FP32 smoothing with FP64 defect correction to a relative residual of
+1e-10), then the forces at every particle and a 50-bin rotation curve.
+The metric is QUMOND solves per second (one solve = one step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own replica of the workload (independent
+galaxies; no data-path collective), the timed region is bracketed by a
+barrier and a device synchronise, the maximum time over ranks is taken, and
+rank 0 prints one JSON line.  --impl reference times the FP64 CPU oracle on
+the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "QUMOND solves/sec and cell-updates/s at 256^3 (HBM % of peak) vs plain FMG"
+UNIT = "solves/s"
+
+WORKLOAD = dict(
+    n=256, nboxes=3, L0=120000.0, particles=2_000_000, seed=1, rel_tol=1e-10, max_vcycles=40, ncycle=1,
+    npre=2, npost=2, nbins=50, rmax=30000.0, nphi=64,
+)
+
+
+def workload_config(precision="FP32 smoothing + FP64 defect correction"):
+    w = WORKLOAD
+    return {
+        "workload": "two-disk galaxy (stellar exponential disk Sigma0=500 Msun/pc^2, R_d=3 kpc, sech^2 "
+                    "h_* drawn in [0.3,0.6] kpc; gas disk 1e9 Msun, R_g=8 kpc, h_g=0.1 kpc), %d particles, "
+                    "%d^3 nodes x %d nested boxes of 120/60/30 kpc" % (w["particles"], w["n"] + 1, w["nboxes"]),
+        "n_intervals": w["n"],
+        "boxes_kpc": [w["L0"] / 1000.0 / 2 ** b for b in range(w["nboxes"])],
+        "particles": w["particles"],
+        "precision": precision,
+        "rel_tol": w["rel_tol"],
+        "fmg_vcycles_per_level": w["ncycle"],
+        "npre_npost": [w["npre"], w["npost"]],
+        "rotation_curve": "%d bins to %g kpc, %d azimuths" % (w["nbins"], w["rmax"] / 1000.0, w["nphi"]),
+        "seed": w["seed"],
+        "l2": "inputs larger than L2: each 257^3 FP64 grid is 136 MB and one step streams tens of GB",
+        "data": "synthetic (seeded generator)",
+    }
+
+
+def make_particles():
+    import synth
+    w = WORKLOAD
+    lim = 0.45 * w["L0"]
+    return synth.two_component_disk(w["particles"], seed=w["seed"], rmax=lim, zmax=lim)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# --- clocks -------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((int(f[0]), float(f[1]), float(f[2]), float(f[3]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        idx = self.index if any(r[0] == self.index for r in rows) else rows[0][0]
+        rows = [r for r in rows if r[0] == idx]
+        loaded = [r for r in rows if r[3] > 0.3 * max(x[3] for x in rows)] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in loaded for q, v in enumerate(r[4]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in loaded), "sm_max_mhz": max(r[2] for r in rows),
+                "reasons": reasons, "samples": len(loaded)}
+
+
+# --- roofline helpers ------------------------------------------------------------
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1201_3185_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".h", ".cuh")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when the summary is missing or the kernels changed since."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    except (OSError, ValueError):
+        return None
+    if t.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    k = t.get("kernels", {}).get(kernel)
+    if not k:
+        return None
+    return k.get("dram_bytes_per_launch_full_size")
+
+
+# --- our arm -------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1201_3185_gb300 as q
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if ws == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = WORKLOAD
+    p = make_particles()
+    prec = q.QUMOND_PREC_FP64 if args.precision == "fp64" else q.QUMOND_PREC_MIXED
+
+    def new_pipeline(precision):
+        ctx = q.Context(n=w["n"], nboxes=w["nboxes"], L0=w["L0"], rel_tol=w["rel_tol"], max_vcycles=w["max_vcycles"],
+                        ncycle=w["ncycle"], npre=w["npre"], npost=w["npost"], precision=precision)
+        return ctx, q.Pipeline(ctx, dev)
+
+    ctx, pipe = new_pipeline(prec)
+    xd, yd, zd, md = (torch.from_numpy(a).to(dev) for a in (p.x, p.y, p.z, p.m))
+    g = tuple(torch.empty_like(xd) for _ in range(3))
+
+    def step(pp=None):
+        pp = pp or pipe
+        return pp.run(xd, yd, zd, md, nbins=w["nbins"], rmax=w["rmax"], nphi=w["nphi"], forces=g)
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        step()
+    st_check = pipe.potentials(xd, yd, zd, md, stats=True)
+    vcycles = [s.vcycles for s in st_check[0] + st_check[1]]
+    torch.cuda.synchronize()
+
+    # --- timed region: inputs resident in HBM ---------------------------------------------
+    ctx.qumond_trace_read(reset=True)
+    ctx.qumond_trace_timing(True)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for _ in range(args.steps):
+        res = step()
+    s1.record()
+    barrier()
+    clk = clocks.stop()
+    ms_total = max_over_ranks(s0.elapsed_time(s1))
+    kstats, launches, cell_updates = ctx.qumond_trace_read(reset=True)
+    ctx.qumond_trace_timing(False)
+    ms_step = ms_total / args.steps
+    value = ws * args.steps / (ms_total / 1000.0)
+
+    # dominant kernel and its roofline
+    dom = max(kstats.values(), key=lambda k: k.ms)
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = (dom.bytes / dom.launches) / (dom.ms / dom.timed) / 1e6 if dom.timed else None  # GB/s
+    roofline = {"bound": "hbm", "kernel": dom.name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None,
+                "traffic": ncu_traffic(dom.name),
+                "algorithmic_bytes_per_launch": dom.bytes / max(dom.launches, 1),
+                "avg_launch_ms": dom.ms / max(dom.timed, 1),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s"}
+    total_kernel_ms = sum(k.ms for k in kstats.values())
+    total_bytes = sum(k.bytes for k in kstats.values())
+    kernels = {k.name: {"launches_per_step": k.launches / args.steps, "ms_per_step": k.ms / args.steps,
+                        "share": k.ms / total_kernel_ms if total_kernel_ms else None,
+                        "GBps": (k.bytes / k.ms / 1e6) if k.ms else None}
+               for k in sorted(kstats.values(), key=lambda k: -k.ms) if k.launches}
+
+    # --- end to end through the public API, host buffers ---------------------------------
+    host = [torch.from_numpy(a).pin_memory() for a in (p.x, p.y, p.z, p.m)]
+    out_g = [torch.empty(w["particles"], dtype=torch.float64).pin_memory() for _ in range(3)]
+    out_vc = torch.empty(w["nbins"], dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host)
+    d2h = sum(t.numel() * t.element_size() for t in out_g) + out_vc.numel() * 8 * 2
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        xs, ys, zs, ms_ = (t.to(dev, non_blocking=True) for t in host)
+        gg = tuple(torch.empty_like(xs) for _ in range(3))
+        r = pipe.run(xs, ys, zs, ms_, nbins=w["nbins"], rmax=w["rmax"], nphi=w["nphi"], forces=gg)
+        for a, b in zip(out_g, gg):
+            a.copy_(b, non_blocking=True)
+        out_vc.copy_(r.vc, non_blocking=True)
+        r_host = r.r.to("cpu", non_blocking=True)
+    e1.record()
+    barrier()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1))
+    e2e_value = ws * args.steps / (e2e_ms / 1000.0)
+
+    # --- plain FP64 full multigrid at the same final residual ------------------------------
+    plain = None
+    if not args.no_plain and prec == q.QUMOND_PREC_MIXED:
+        ctx.close()
+        del pipe
+        torch.cuda.empty_cache()
+        ctx64, pipe64 = new_pipeline(q.QUMOND_PREC_FP64)
+        step(pipe64)
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        nplain = max(1, min(args.steps, 3))
+        f0.record()
+        for _ in range(nplain):
+            step(pipe64)
+        f1.record()
+        barrier()
+        pms = max_over_ranks(f0.elapsed_time(f1)) / nplain
+        plain = {"value": ws * 1000.0 / pms, "unit": UNIT, "ms_per_step": pms, "steps": nplain,
+                 "precision": "FP64 smoothing, residual and correction (same kernels, same tolerance)",
+                 "speedup_of_value": value / (ws * 1000.0 / pms)}
+        ctx64.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(p, sample_boxes=2)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if prec == q.QUMOND_PREC_MIXED else "f64",
+            "data": "synthetic", "config": workload_config() if prec == q.QUMOND_PREC_MIXED else
+            workload_config("FP64 throughout"),
+            "cell_updates_per_s": ws * cell_updates / (ms_total / 1000.0),
+            "hbm_algorithmic_GBps_all_kernels": total_bytes / (total_kernel_ms * 1e6) if total_kernel_ms else None,
+            "kernel_time_fraction_of_step": total_kernel_ms / ms_total,
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "gpu_launches_per_step": launches / args.steps,
+            "vcycles_after_fmg_per_solve": vcycles,
+            "plain_fmg": plain,
+            "kernels": kernels,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+# --- the oracle (CPU) ------------------------------------------------------------------
+def oracle_sample(p, sample_boxes):
+    """Steps 1-4 for the first `sample_boxes` boxes of the workload with the
+    FP64 oracle, plus the rotation curve (over the boxes solved)."""
+    import oracle
+    w = WORKLOAD
+    t0 = time.perf_counter()
+    boxes = oracle.pipeline(p, w["n"], w["L0"], sample_boxes, ncycle=w["ncycle"], npre=w["npre"], npost=w["npost"],
+                            tol=w["rel_tol"], max_vcycles=w["max_vcycles"])
+    oracle.rotation_curve(w["n"], w["L0"], (0.0, 0.0, 0.0), [b.phi for b in boxes], w["nbins"], w["rmax"], w["nphi"])
+    return time.perf_counter() - t0
+
+
+def cpu_cores():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+def cpu_baseline(p, sample_boxes=1):
+    import oracle
+    oracle.build()
+    t = oracle_sample(p, sample_boxes)
+    w = WORKLOAD
+    value = sample_boxes / (w["nboxes"] * t)
+    return {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": "boxes 0..%d of %d (deposit, both FMG solves to rel. residual %g, source, rotation curve) "
+                      "in %.1f s, scaled by %d/%d to a whole %d-box solve" % (sample_boxes - 1, w["nboxes"],
+                                                                             w["rel_tol"], t, sample_boxes,
+                                                                             w["nboxes"], w["nboxes"])}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    import oracle
+    oracle.build()
+    p = make_particles()
+    w = WORKLOAD
+    for _ in range(args.warmup):
+        oracle_sample(p, 1)
+    times = [oracle_sample(p, 1) for _ in range(args.steps)]
+    per_solve = w["nboxes"] * statistics.mean(times)
+    value = 1.0 / per_solve
+    sample = "each step: box 0 of %d at full size (deposit, both FMG solves, source, rotation curve), " \
+             "scaled by 1/%d" % (w["nboxes"], w["nboxes"])
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_solve * 1000.0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config("FP64 CPU oracle"),
+        "cpu_baseline": {"kind": "oracle", "cores": cpu_cores(), "sample": sample, "value": value, "unit": UNIT},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 FMG comparison")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip timing the oracle on the host")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -181,6 +181,38 @@ QUMOND_API qumond_status qumond_forces(qumond_ctx* ctx, const double* const* phi
 QUMOND_API qumond_status qumond_rotation_curve(qumond_ctx* ctx, const double* const* phi_boxes, int nbins, double rmax,
                                     int nphi, double* r_out, double* vc_out, void* stream);
 
+/* --- tracing (not part of the method: instrumentation of the kernels) ------ */
+
+/* Per-kernel-class counters of a context since it was created or last reset. */
+typedef struct {
+    const char* name;     /* kernel class, e.g. "rb_half_finest" (static storage) */
+    int64_t launches;     /* kernels of this class launched */
+    double bytes;         /* algorithmic HBM bytes of those launches (the minimum
+                             each kernel must read and write) */
+    double ms;            /* summed CUDA-event time of the launches that were
+                             bracketed while timing was on (0 otherwise) */
+    int64_t timed;        /* how many launches were bracketed */
+} qumond_kernel_stat;
+
+typedef struct {
+    int64_t launches;      /* all kernels launched by this context */
+    int64_t cell_updates;  /* red-black node updates, all levels */
+} qumond_counters;
+
+/* Number of kernel classes (size of the array qumond_trace_read fills). */
+QUMOND_API int qumond_trace_classes(void);
+
+/* Start (on != 0) or stop bracketing every launch with CUDA events on its
+   stream (at most 32768 launches per start; later ones are counted but not
+   timed).  Starting discards earlier timings.  Counters are always kept. */
+QUMOND_API qumond_status qumond_trace_timing(qumond_ctx* ctx, int on);
+
+/* Copies the per-class statistics into out[0 .. min(cap, classes)-1] and the
+   totals into *totals (either may be NULL).  Synchronises the device when
+   timed launches are pending.  reset != 0 then zeroes every counter. */
+QUMOND_API qumond_status qumond_trace_read(qumond_ctx* ctx, qumond_kernel_stat* out, int cap,
+                                           qumond_counters* totals, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,6 +21,30 @@ struct Level {
     void* f = nullptr;  // right-hand side, 2 colours
 };
 
+// Kernel classes of the tracer.
+enum Kind {
+    K_DEPOSIT, K_FIXED_TO_RHO, K_BOUNDARY, K_CONVERT_RHS, K_RESTRICT_FULL, K_COARSE, K_RB_FINEST, K_RB_COARSER,
+    K_RESTRICT_RESID, K_PROLONG, K_SET_BOUNDARY, K_ASSIGN_OUTER, K_RESIDUAL_OUTER, K_REDUCE, K_SOURCE, K_FORCES,
+    K_ROTATION_CURVE, K_COUNT
+};
+const char* const kKindNames[K_COUNT] = {
+    "cic_deposit", "fixed_to_rho", "boundary_fill", "convert_rhs", "restrict_full", "coarse_solver",
+    "rb_half_finest", "rb_half_coarser", "restrict_resid_red", "prolong_black", "set_boundary", "update_outer",
+    "residual_outer", "reduce_norms", "qumond_source", "forces", "rotation_curve",
+};
+constexpr int kMaxTimed = 32768;
+
+struct Tracer {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;  // 2 per timed launch
+    std::vector<int> kind_of;     // per timed launch
+    long long launches[K_COUNT] = {};
+    double bytes[K_COUNT] = {};
+    double ms[K_COUNT] = {};
+    long long timed[K_COUNT] = {};
+    long long cell_updates = 0;
+};
+
 }  // namespace
 
 struct qumond_ctx {
@@ -33,6 +57,7 @@ struct qumond_ctx {
     int max_partials = 0;
     double* d_norms = nullptr;
     double* h_norms = nullptr;  // pinned
+    Tracer tr;
     std::string err;
 };
 
@@ -120,6 +145,70 @@ T* F(qumond_ctx* c, int l) { return static_cast<T*>(c->lev[l].f); }
 
 inline double level_h(const qumond_ctx* c, int box, int l) { return box_h(c, box) * (double)(1 << (c->L - l)); }
 
+inline double cube(int n) { return (double)(n + 1) * (double)(n + 1) * (double)(n + 1); }
+
+// Every launch goes through here: counted, and bracketed by events while
+// timing is on.
+template <class Launch>
+void run(qumond_ctx* c, int kind, double bytes, cudaStream_t s, Launch&& launch)
+{
+    Tracer& t = c->tr;
+    const size_t slot = t.kind_of.size();
+    const bool rec = t.on && slot < (size_t)kMaxTimed;
+    if (rec) cudaEventRecord(t.ev[2 * slot], s);
+    launch();
+    if (rec) {
+        cudaEventRecord(t.ev[2 * slot + 1], s);
+        t.kind_of.push_back(kind);
+    }
+    t.launches[kind] += 1;
+    t.bytes[kind] += bytes;
+}
+
+// One V-cycle at level l on the correction problem held in lev[l] (for l <
+// L the initial guess is zero; at l = L the caller says so).
+template <typename T>
+void rb(qumond_ctx* c, int l, int colour, bool zero, double h, cudaStream_t s)
+{
+    const int n = c->lev[l].v.n;
+    const double nodes = cube(n);
+    c->tr.cell_updates += ((long long)(n - 1) * (n - 1) * (n - 1) + (colour == 0 ? 1 : 0)) / 2;
+    run(c, l == c->L ? K_RB_FINEST : K_RB_COARSER, (zero ? 1.0 : 1.5) * nodes * sizeof(T), s,
+        [&] { launch_rb_half<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, colour, zero, h, s); });
+}
+
+template <typename T>
+void prolong(qumond_ctx* c, int l, bool add, cudaStream_t s)
+{
+    const double nodes = cube(c->lev[l].v.n);
+    run(c, K_PROLONG, ((add ? 1.0 : 0.5) + 0.125) * nodes * sizeof(T), s,
+        [&] { launch_prolong_black<T>(E<T>(c, l - 1), c->lev[l - 1].v, E<T>(c, l), c->lev[l].v, add, s); });
+}
+
+template <typename T>
+void set_bnd(qumond_ctx* c, int l, const double* u64, cudaStream_t s)
+{
+    const double nb = 6.0 * (c->lev[l].v.n + 1) * (double)(c->lev[l].v.n + 1);
+    run(c, K_SET_BOUNDARY, nb * (sizeof(T) + (u64 ? 8.0 : 0.0)), s,
+        [&] { launch_set_boundary<T>(E<T>(c, l), c->lev[l].v, u64, c->p.n, s); });
+}
+
+template <typename T>
+cudaError_t coarse(qumond_ctx* c, int box, int fmg_mode, const double* u64, cudaStream_t s)
+{
+    const int l = c->lc;
+    const int n = c->lev[l].v.n;
+    long long upd = 0;  // red-black updates inside the kernel (approximate count of its sweeps)
+    for (int m = 4; m <= n; m *= 2) upd += (long long)(c->p.npre + c->p.npost) * (m - 1) * (m - 1) * (m - 1);
+    c->tr.cell_updates += fmg_mode ? upd * c->p.ncycle : upd;
+    cudaError_t err = cudaSuccess;
+    run(c, K_COARSE, 2.0 * cube(n) * sizeof(T), s, [&] {
+        err = launch_coarse<T>(fmg_mode, E<T>(c, l), F<T>(c, l), c->lev[l].v, level_h(c, box, l), u64, c->p.n,
+                               c->p.ncycle, c->p.npre, c->p.npost, s);
+    });
+    return err;
+}
+
 // One V-cycle at level l on the correction problem held in lev[l] (for l <
 // L the initial guess is zero; at l = L the caller says so).
 template <typename T>
@@ -127,19 +216,21 @@ cudaError_t vcycle(qumond_ctx* c, int box, int l, bool zero_guess, cudaStream_t 
 {
     const qumond_params& p = c->p;
     const double h = level_h(c, box, l);
-    if (l <= c->lc)
-        return launch_coarse<T>(0, E<T>(c, l), F<T>(c, l), c->lev[l].v, h, nullptr, 0, p.ncycle, p.npre, p.npost, s);
+    if (l <= c->lc) return coarse<T>(c, box, 0, nullptr, s);
     for (int q = 0; q < p.npre; ++q) {
-        launch_rb_half<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, 0, zero_guess && q == 0, h, s);
-        launch_rb_half<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, 1, false, h, s);
+        rb<T>(c, l, 0, zero_guess && q == 0, h, s);
+        rb<T>(c, l, 1, false, h, s);
     }
-    launch_restrict_resid_red<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, F<T>(c, l - 1), c->lev[l - 1].v, h, s);
+    const double nodes = cube(c->lev[l].v.n);
+    run(c, K_RESTRICT_RESID, (1.5 + 0.125) * nodes * sizeof(T), s, [&] {
+        launch_restrict_resid_red<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, F<T>(c, l - 1), c->lev[l - 1].v, h, s);
+    });
     cudaError_t err = vcycle<T>(c, box, l - 1, true, s);
     if (err != cudaSuccess) return err;
-    launch_prolong_black<T>(E<T>(c, l - 1), c->lev[l - 1].v, E<T>(c, l), c->lev[l].v, true, s);
+    prolong<T>(c, l, true, s);
     for (int q = 0; q < p.npost; ++q) {
-        launch_rb_half<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, 0, false, h, s);
-        launch_rb_half<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, 1, false, h, s);
+        rb<T>(c, l, 0, false, h, s);
+        rb<T>(c, l, 1, false, h, s);
     }
     return cudaSuccess;
 }
@@ -154,15 +245,18 @@ template <typename T>
 cudaError_t fmg(qumond_ctx* c, int box, const double* u64, cudaStream_t s)
 {
     const qumond_params& p = c->p;
-    for (int l = c->L - 1; l >= c->lc; --l)
-        launch_restrict_full<T>(F<T>(c, l + 1), c->lev[l + 1].v, F<T>(c, l), c->lev[l].v, s);
-    cudaError_t err = launch_coarse<T>(1, E<T>(c, c->lc), F<T>(c, c->lc), c->lev[c->lc].v, level_h(c, box, c->lc), u64,
-                                       p.n, p.ncycle, p.npre, p.npost, s);
+    for (int l = c->L - 1; l >= c->lc; --l) {
+        const double nodes = cube(c->lev[l + 1].v.n);
+        run(c, K_RESTRICT_FULL, 1.125 * nodes * sizeof(T), s, [&] {
+            launch_restrict_full<T>(F<T>(c, l + 1), c->lev[l + 1].v, F<T>(c, l), c->lev[l].v, s);
+        });
+    }
+    cudaError_t err = coarse<T>(c, box, 1, u64, s);
     if (err != cudaSuccess) return err;
     for (int l = c->lc + 1; l <= c->L; ++l) {
-        launch_set_boundary<T>(E<T>(c, l), c->lev[l].v, u64, p.n, s);
-        launch_prolong_black<T>(E<T>(c, l - 1), c->lev[l - 1].v, E<T>(c, l), c->lev[l].v, false, s);
-        launch_set_boundary<T>(E<T>(c, l - 1), c->lev[l - 1].v, nullptr, p.n, s);
+        set_bnd<T>(c, l, u64, s);
+        prolong<T>(c, l, false, s);
+        set_bnd<T>(c, l - 1, nullptr, s);
         for (int q = 0; q < p.ncycle; ++q) {
             err = vcycle<T>(c, box, l, false, s);
             if (err != cudaSuccess) return err;
@@ -176,9 +270,12 @@ template <typename T>
 qumond_status residual_norms(qumond_ctx* c, int box, const double* rhs, double coef, const double* u, cudaStream_t s,
                              double* rr, double* ff)
 {
-    const int nb = launch_residual_outer<T>(u, rhs, coef, c->p.n, box_h(c, box), F<T>(c, c->L), c->lev[c->L].v,
-                                            c->partials, s);
-    launch_reduce_norms(c->partials, nb, c->d_norms, s);
+    int nb = 0;
+    run(c, K_RESIDUAL_OUTER, cube(c->p.n) * (16.0 + sizeof(T)), s, [&] {
+        nb = launch_residual_outer<T>(u, rhs, coef, c->p.n, box_h(c, box), F<T>(c, c->L), c->lev[c->L].v,
+                                      c->partials, s);
+    });
+    run(c, K_REDUCE, 16.0 * nb, s, [&] { launch_reduce_norms(c->partials, nb, c->d_norms, s); });
     CUDA_TRY(c, cudaGetLastError(), "residual launch");
     CUDA_TRY(c, cudaMemcpyAsync(c->h_norms, c->d_norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s), "norm copy");
     CUDA_TRY(c, cudaStreamSynchronize(s), "residual");
@@ -197,14 +294,20 @@ qumond_status solve_t(qumond_ctx* c, int box, const double* rhs, double coef, co
 {
     const qumond_params& p = c->p;
     const int n = p.n;
-    if (box > 0) launch_boundary_from_parent(parent, u, n, p.box_ratio, s);
-    else if (p.bc_mode == QUMOND_BC_ZERO) launch_boundary_zero(u, n, s);
+    const double nodes = cube(n);
+    const double nbnd = 6.0 * (n + 1) * (double)(n + 1);
+    if (box > 0)
+        run(c, K_BOUNDARY, nbnd * 16.0, s, [&] { launch_boundary_from_parent(parent, u, n, p.box_ratio, s); });
+    else if (p.bc_mode == QUMOND_BC_ZERO)
+        run(c, K_BOUNDARY, nbnd * 8.0, s, [&] { launch_boundary_zero(u, n, s); });
     if (!p.warm_start) {
-        launch_convert_rhs<T>(rhs, coef, n, F<T>(c, c->L), c->lev[c->L].v, s);
+        run(c, K_CONVERT_RHS, nodes * (8.0 + sizeof(T)), s,
+            [&] { launch_convert_rhs<T>(rhs, coef, n, F<T>(c, c->L), c->lev[c->L].v, s); });
         cudaError_t err = fmg<T>(c, box, u, s);
         if (err != cudaSuccess) return cuda_fail(c, err, "fmg");
-        launch_assign_outer<T>(u, n, E<T>(c, c->L), c->lev[c->L].v, false, s);
-        launch_set_boundary<T>(E<T>(c, c->L), c->lev[c->L].v, nullptr, n, s);
+        run(c, K_ASSIGN_OUTER, nodes * (8.0 + sizeof(T)), s,
+            [&] { launch_assign_outer<T>(u, n, E<T>(c, c->L), c->lev[c->L].v, false, s); });
+        set_bnd<T>(c, c->L, nullptr, s);
     }
     CUDA_TRY(c, cudaGetLastError(), "solve launch");
     const bool refine = p.rel_tol > 0.0 && p.max_vcycles > 0;
@@ -219,7 +322,8 @@ qumond_status solve_t(qumond_ctx* c, int box, const double* rhs, double coef, co
     while (refine && rel > p.rel_tol && made < p.max_vcycles && std::isfinite(rel)) {
         cudaError_t err = vcycle<T>(c, box, c->L, true, s);
         if (err != cudaSuccess) return cuda_fail(c, err, "vcycle");
-        launch_assign_outer<T>(u, n, E<T>(c, c->L), c->lev[c->L].v, true, s);
+        run(c, K_ASSIGN_OUTER, nodes * (16.0 + sizeof(T)), s,
+            [&] { launch_assign_outer<T>(u, n, E<T>(c, c->L), c->lev[c->L].v, true, s); });
         ++made;
         rs = residual_norms<T>(c, box, rhs, coef, u, s, &rr, &ff);
         if (rs != QUMOND_OK) return rs;
@@ -363,6 +467,7 @@ void qumond_destroy(qumond_ctx* c)
     if (c->partials) cudaFree(c->partials);
     if (c->d_norms) cudaFree(c->d_norms);
     if (c->h_norms) cudaFreeHost(c->h_norms);
+    for (cudaEvent_t e : c->tr.ev) cudaEventDestroy(e);
     (void)cudaGetLastError();
     delete c;
 }
@@ -386,11 +491,14 @@ qumond_status qumond_deposit(qumond_ctx* c, int box, const double* x, const doub
     const double inv_h = (double)n / L;
     cudaStream_t s = S(stream);
     CUDA_TRY(c, cudaMemsetAsync(rho_fixed, 0, sizeof(int64_t) * count, s), "deposit: clear");
-    launch_cic_deposit(x, y, z, mass, np, n, c->p.center[0] - 0.5 * L, c->p.center[1] - 0.5 * L,
-                       c->p.center[2] - 0.5 * L, inv_h, std::ldexp(1.0, c->p.deposit_shift), rho_fixed, s);
+    run(c, K_DEPOSIT, 32.0 * (double)np, s, [&] {
+        launch_cic_deposit(x, y, z, mass, np, n, c->p.center[0] - 0.5 * L, c->p.center[1] - 0.5 * L,
+                           c->p.center[2] - 0.5 * L, inv_h, std::ldexp(1.0, c->p.deposit_shift), rho_fixed, s);
+    });
     if (rho) {
         const double scale = std::ldexp(1.0, -c->p.deposit_shift) * (inv_h * inv_h * inv_h);
-        launch_fixed_to_rho(rho_fixed, rho, count, scale, s);
+        run(c, K_FIXED_TO_RHO, 16.0 * (double)count, s,
+            [&] { launch_fixed_to_rho(rho_fixed, rho, count, scale, s); });
     }
     CUDA_TRY(c, cudaGetLastError(), "deposit launch");
     return QUMOND_OK;
@@ -416,7 +524,8 @@ qumond_status qumond_source(qumond_ctx* c, int box, const double* phiN, double* 
     if (box < 0 || box >= c->p.nboxes) return fail(c, QUMOND_ERR_INVALID_ARG, "source: box %d out of range", box);
     if (!device_ptr(phiN) || !device_ptr(src)) return fail(c, QUMOND_ERR_INVALID_ARG, "source: phiN and src must be device pointers");
     if (phiN == src) return fail(c, QUMOND_ERR_INVALID_ARG, "source: src must not alias phiN");
-    launch_source(phiN, src, c->p.n, box_h(c, box), c->p.a0, S(stream));
+    run(c, K_SOURCE, 16.0 * cube(c->p.n), S(stream),
+        [&] { launch_source(phiN, src, c->p.n, box_h(c, box), c->p.a0, S(stream)); });
     CUDA_TRY(c, cudaGetLastError(), "source launch");
     return QUMOND_OK;
 }
@@ -432,7 +541,8 @@ qumond_status qumond_forces(qumond_ctx* c, const double* const* phi_boxes, const
     if (nq == 0) return QUMOND_OK;
     if (!device_ptr(qx) || !device_ptr(qy) || !device_ptr(qz) || !device_ptr(gx) || !device_ptr(gy) || !device_ptr(gz))
         return fail(c, QUMOND_ERR_INVALID_ARG, "forces: point and force arrays must be device pointers");
-    launch_forces(box_set(c, phi_boxes), qx, qy, qz, nq, gx, gy, gz, S(stream));
+    run(c, K_FORCES, 48.0 * (double)nq, S(stream),
+        [&] { launch_forces(box_set(c, phi_boxes), qx, qy, qz, nq, gx, gy, gz, S(stream)); });
     CUDA_TRY(c, cudaGetLastError(), "forces launch");
     return QUMOND_OK;
 }
@@ -448,9 +558,76 @@ qumond_status qumond_rotation_curve(qumond_ctx* c, const double* const* phi_boxe
     if (nphi < 1 || nphi > 1024) return fail(c, QUMOND_ERR_INVALID_ARG, "rotation_curve: nphi must be in [1, 1024]");
     if (!(rmax > 0.0) || !std::isfinite(rmax)) return fail(c, QUMOND_ERR_INVALID_ARG, "rotation_curve: rmax must be positive");
     if (!device_ptr(r_out) || !device_ptr(vc_out)) return fail(c, QUMOND_ERR_INVALID_ARG, "rotation_curve: outputs must be device pointers");
-    launch_rotation_curve(box_set(c, phi_boxes), c->p.center[0], c->p.center[1], c->p.center[2], nbins, rmax, nphi,
-                          c->p.rc_box_frac, r_out, vc_out, S(stream));
+    run(c, K_ROTATION_CURVE, 16.0 * nbins, S(stream), [&] {
+        launch_rotation_curve(box_set(c, phi_boxes), c->p.center[0], c->p.center[1], c->p.center[2], nbins, rmax,
+                              nphi, c->p.rc_box_frac, r_out, vc_out, S(stream));
+    });
     CUDA_TRY(c, cudaGetLastError(), "rotation_curve launch");
+    return QUMOND_OK;
+}
+
+int qumond_trace_classes(void) { return K_COUNT; }
+
+qumond_status qumond_trace_timing(qumond_ctx* c, int on)
+{
+    if (!c) return QUMOND_ERR_INVALID_ARG;
+    c->err.clear();
+    Tracer& t = c->tr;
+    if (on) {
+        if (t.ev.empty()) {
+            t.ev.resize(2 * (size_t)kMaxTimed);
+            for (auto& e : t.ev) CUDA_TRY(c, cudaEventCreate(&e), "trace: event create");
+            t.kind_of.reserve(kMaxTimed);
+        }
+        CUDA_TRY(c, cudaDeviceSynchronize(), "trace: start");
+        t.kind_of.clear();
+        for (int k = 0; k < K_COUNT; ++k) {
+            t.ms[k] = 0.0;
+            t.timed[k] = 0;
+        }
+    }
+    t.on = on != 0;
+    return QUMOND_OK;
+}
+
+qumond_status qumond_trace_read(qumond_ctx* c, qumond_kernel_stat* out, int cap, qumond_counters* totals, int reset)
+{
+    if (!c) return QUMOND_ERR_INVALID_ARG;
+    c->err.clear();
+    Tracer& t = c->tr;
+    if (!t.kind_of.empty()) {
+        CUDA_TRY(c, cudaEventSynchronize(t.ev[2 * (t.kind_of.size() - 1) + 1]), "trace: sync");
+        for (size_t q = 0; q < t.kind_of.size(); ++q) {
+            float ms = 0.0f;
+            CUDA_TRY(c, cudaEventElapsedTime(&ms, t.ev[2 * q], t.ev[2 * q + 1]), "trace: elapsed");
+            t.ms[t.kind_of[q]] += ms;
+            t.timed[t.kind_of[q]] += 1;
+        }
+        t.kind_of.clear();
+    }
+    long long total = 0;
+    for (int k = 0; k < K_COUNT; ++k) total += t.launches[k];
+    if (out)
+        for (int k = 0; k < K_COUNT && k < cap; ++k) {
+            out[k].name = kKindNames[k];
+            out[k].launches = t.launches[k];
+            out[k].bytes = t.bytes[k];
+            out[k].ms = t.ms[k];
+            out[k].timed = t.timed[k];
+        }
+    if (totals) {
+        totals->launches = total;
+        totals->cell_updates = t.cell_updates;
+    }
+    if (reset) {
+        for (int k = 0; k < K_COUNT; ++k) {
+            t.launches[k] = 0;
+            t.bytes[k] = 0.0;
+            t.ms[k] = 0.0;
+            t.timed[k] = 0;
+        }
+        t.cell_updates = 0;
+    }
     return QUMOND_OK;
 }
 

@@ -36,6 +36,7 @@ QUMOND_BC_GIVEN = 1
 EXPORTED = (
     "qumond_default_params", "qumond_create", "qumond_destroy", "qumond_last_error", "qumond_deposit",
     "qumond_solve_newton", "qumond_source", "qumond_solve_mond", "qumond_forces", "qumond_rotation_curve",
+    "qumond_trace_classes", "qumond_trace_timing", "qumond_trace_read",
 )
 
 
@@ -70,6 +71,20 @@ class qumond_stats(ctypes.Structure):
     ]
 
 
+class qumond_kernel_stat(ctypes.Structure):
+    _fields_ = [
+        ("name", ctypes.c_char_p),
+        ("launches", ctypes.c_int64),
+        ("bytes", ctypes.c_double),
+        ("ms", ctypes.c_double),
+        ("timed", ctypes.c_int64),
+    ]
+
+
+class qumond_counters(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("cell_updates", ctypes.c_int64)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _L = ctypes.c_int64
@@ -91,6 +106,9 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
         "qumond_solve_mond": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(qumond_stats), _P]),
         "qumond_forces": (_I, [_P, _P, _P, _P, _P, _L, _P, _P, _P, _P]),
         "qumond_rotation_curve": (_I, [_P, _P, _I, _D, _I, _P, _P, _P]),
+        "qumond_trace_classes": (_I, []),
+        "qumond_trace_timing": (_I, [_P, _I]),
+        "qumond_trace_read": (_I, [_P, ctypes.POINTER(qumond_kernel_stat), _I, ctypes.POINTER(qumond_counters), _I]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -143,6 +161,15 @@ def _dev(t: torch.Tensor, dtype, numel=None, name="tensor") -> ctypes.c_void_p:
     if numel is not None and t.numel() != numel:
         raise ValueError("%s must have %d elements, got %d" % (name, numel, t.numel()))
     return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class KernelStat:
+    name: str
+    launches: int
+    bytes: float
+    ms: float
+    timed: int
 
 
 @dataclass
@@ -253,3 +280,16 @@ class Context:
         v = _dev(vc_out, torch.float64, nbins, "vc_out")
         self._check(_lib.qumond_rotation_curve(self._ptr, ctypes.cast(arr, _P), nbins, float(rmax), nphi, r, v,
                                                _stream(stream)))
+
+    # -- tracing ------------------------------------------------------------------
+    def qumond_trace_timing(self, on: bool):
+        self._check(_lib.qumond_trace_timing(self._ptr, 1 if on else 0))
+
+    def qumond_trace_read(self, reset: bool = False):
+        """Returns ({class name: KernelStat}, total launches, cell updates)."""
+        k = _lib.qumond_trace_classes()
+        arr = (qumond_kernel_stat * k)()
+        tot = qumond_counters()
+        self._check(_lib.qumond_trace_read(self._ptr, arr, k, ctypes.byref(tot), 1 if reset else 0))
+        stats = {a.name.decode(): KernelStat(a.name.decode(), a.launches, a.bytes, a.ms, a.timed) for a in arr}
+        return stats, tot.launches, tot.cell_updates
