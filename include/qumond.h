@@ -36,6 +36,7 @@
 #ifndef QUMOND_H
 #define QUMOND_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -212,6 +213,34 @@ QUMOND_API qumond_status qumond_trace_timing(qumond_ctx* ctx, int on);
    timed launches are pending.  reset != 0 then zeroes every counter. */
 QUMOND_API qumond_status qumond_trace_read(qumond_ctx* ctx, qumond_kernel_stat* out, int cap,
                                            qumond_counters* totals, int reset);
+
+/* --- a solve that allocates nothing ------------------------------------------
+   The paper has no counterpart: this is a service to callers that cannot
+   allocate device memory when they need a solve (a caller whose memory pool
+   or arena already owns the whole device budget, or a thread that must not
+   enter the allocator).  qumond_create allocates the multigrid scratch; this
+   entry point instead keeps it in one fixed device array inside the library,
+   QUMOND_NOALLOC_SCRATCH_BYTES long, which exists on every device that loads
+   the library until the process exits.  That bounds the grid: n must be a
+   power of two <= QUMOND_NOALLOC_MAX_N; larger n is rejected with
+   QUMOND_ERR_INVALID_ARG and a message.  Only QUMOND_PREC_MIXED is offered.
+
+   Arguments and result: as qumond_solve_mond (the parameters are passed
+   directly since there is no context; they are checked as qumond_create
+   checks them).  err (may be NULL): receives a message of at most err_len
+   bytes on failure.
+
+   The call makes no cudaMalloc, cudaFree or other allocating call.  The first
+   call on each device looks up the array's device address (with that device
+   current) and caches it; make that first call before any stream capture.
+   All calls on a device share the array, which keeps the previous call's
+   contents (each call clears it before use): calls whose GPU work overlaps,
+   on different streams or host threads, race and give wrong results. */
+#define QUMOND_NOALLOC_MAX_N 64
+#define QUMOND_NOALLOC_SCRATCH_BYTES 2903552
+QUMOND_API qumond_status qumond_solve_mond_noalloc(const qumond_params* p, int box, const double* src,
+                                                   const double* phi_parent, double* phi, qumond_stats* stats,
+                                                   void* stream, char* err, size_t err_len);
 
 #ifdef __cplusplus
 }

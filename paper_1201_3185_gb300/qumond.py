@@ -36,8 +36,9 @@ QUMOND_BC_GIVEN = 1
 EXPORTED = (
     "qumond_default_params", "qumond_create", "qumond_destroy", "qumond_last_error", "qumond_deposit",
     "qumond_solve_newton", "qumond_source", "qumond_solve_mond", "qumond_forces", "qumond_rotation_curve",
-    "qumond_trace_classes", "qumond_trace_timing", "qumond_trace_read",
+    "qumond_trace_classes", "qumond_trace_timing", "qumond_trace_read", "qumond_solve_mond_noalloc",
 )
+NOALLOC_MAX_N = 64
 
 
 class qumond_params(ctypes.Structure):
@@ -109,6 +110,8 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
         "qumond_trace_classes": (_I, []),
         "qumond_trace_timing": (_I, [_P, _I]),
         "qumond_trace_read": (_I, [_P, ctypes.POINTER(qumond_kernel_stat), _I, ctypes.POINTER(qumond_counters), _I]),
+        "qumond_solve_mond_noalloc": (_I, [ctypes.POINTER(qumond_params), _I, _P, _P, _P, ctypes.POINTER(qumond_stats),
+                                           _P, ctypes.c_char_p, ctypes.c_size_t]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -161,6 +164,25 @@ def _dev(t: torch.Tensor, dtype, numel=None, name="tensor") -> ctypes.c_void_p:
     if numel is not None and t.numel() != numel:
         raise ValueError("%s must have %d elements, got %d" % (name, numel, t.numel()))
     return ctypes.c_void_p(t.data_ptr())
+
+
+def qumond_solve_mond_noalloc(params: qumond_params, box, src, phi_parent, phi, stats=False, stream=None):
+    """The solve of qumond_solve_mond for callers that cannot allocate device
+    memory: no context, scratch in the library's fixed device array (n <= 64)."""
+    nodes = (params.n + 1) ** 3
+    a = _dev(src, torch.float64, nodes, "src")
+    par = _dev(phi_parent, torch.float64, nodes, "phi_parent") if phi_parent is not None else None
+    o = _dev(phi, torch.float64, nodes, "phi")
+    st = qumond_stats()
+    buf = ctypes.create_string_buffer(512)
+    status = _lib.qumond_solve_mond_noalloc(ctypes.byref(params), box, a, par, o,
+                                            ctypes.byref(st) if stats else None, _stream(stream), buf, 512)
+    if status != QUMOND_OK:
+        cls = NotConverged if status == QUMOND_ERR_NOT_CONVERGED else QumondError
+        raise cls(status, buf.value.decode())
+    if stats:
+        return SolveStats(st.vcycles, bool(st.converged), st.rel_residual_fmg, st.rel_residual)
+    return None
 
 
 @dataclass
