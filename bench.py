@@ -32,6 +32,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "QUMOND solves/sec and cell-updates/s at 256^3 (HBM % of peak) vs plain FMG"
+PRECISION_NAMES = {
+    "mixed": "FP32 smoothing + FP64 defect correction",
+    "fixed": "FP32 smoothing + defect correction on a 64-bit fixed-point iterate (exact integer residual)",
+    "fp64": "FP64 throughout",
+}
 UNIT = "solves/s"
 
 WORKLOAD = dict(
@@ -188,7 +193,7 @@ def run_ours(args):
 
     w = WORKLOAD
     p = make_particles()
-    prec = q.QUMOND_PREC_FP64 if args.precision == "fp64" else q.QUMOND_PREC_MIXED
+    prec = {"fp64": q.QUMOND_PREC_FP64, "mixed": q.QUMOND_PREC_MIXED, "fixed": q.QUMOND_PREC_MIXED_FIXED}[args.precision]
 
     def new_pipeline(precision):
         ctx = q.Context(n=w["n"], nboxes=w["nboxes"], L0=w["L0"], rel_tol=w["rel_tol"], max_vcycles=w["max_vcycles"],
@@ -210,9 +215,8 @@ def run_ours(args):
     vcycles = [s.vcycles for s in st_check[0] + st_check[1]]
     torch.cuda.synchronize()
 
-    # --- timed region: inputs resident in HBM ---------------------------------------------
+    # --- timed region: inputs resident in HBM; each solve is one CUDA graph ---------------
     ctx.qumond_trace_read(reset=True)
-    ctx.qumond_trace_timing(True)
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
@@ -225,10 +229,24 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     ms_total = max_over_ranks(s0.elapsed_time(s1))
-    kstats, launches, cell_updates = ctx.qumond_trace_read(reset=True)
-    ctx.qumond_trace_timing(False)
+    _, launches, cell_updates = ctx.qumond_trace_read(reset=True)
     ms_step = ms_total / args.steps
     value = ws * args.steps / (ms_total / 1000.0)
+
+    # --- per-kernel CUDA-event timing: the same steps replayed with every kernel
+    # launched one by one and bracketed by events on its stream -------------------------
+    ctx.qumond_trace_timing(True)
+    barrier()
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    r0.record()
+    for _ in range(args.steps):
+        step()
+    r1.record()
+    barrier()
+    replay_ms = r0.elapsed_time(r1) / args.steps
+    kstats, _, _ = ctx.qumond_trace_read(reset=True)
+    ctx.qumond_trace_timing(False)
 
     # dominant kernel and its roofline
     dom = max(kstats.values(), key=lambda k: k.ms)
@@ -240,7 +258,9 @@ def run_ours(args):
                 "traffic": ncu_traffic(dom.name),
                 "algorithmic_bytes_per_launch": dom.bytes / max(dom.launches, 1),
                 "avg_launch_ms": dom.ms / max(dom.timed, 1),
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s"}
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s",
+                "timing": "CUDA events around each launch on its stream, over a replay of the timed steps with "
+                          "kernels launched one by one (the timed region runs each solve as one CUDA graph)"}
     total_kernel_ms = sum(k.ms for k in kstats.values())
     total_bytes = sum(k.bytes for k in kstats.values())
     kernels = {k.name: {"launches_per_step": k.launches / args.steps, "ms_per_step": k.ms / args.steps,
@@ -273,7 +293,7 @@ def run_ours(args):
 
     # --- plain FP64 full multigrid at the same final residual ------------------------------
     plain = None
-    if not args.no_plain and prec == q.QUMOND_PREC_MIXED:
+    if not args.no_plain and prec != q.QUMOND_PREC_FP64:
         ctx.close()
         del pipe
         torch.cuda.empty_cache()
@@ -302,12 +322,13 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64" if prec == q.QUMOND_PREC_MIXED else "f64",
-            "data": "synthetic", "config": workload_config() if prec == q.QUMOND_PREC_MIXED else
-            workload_config("FP64 throughout"),
+            "vs_baseline": None, "dtype": {q.QUMOND_PREC_MIXED: "f32+f64", q.QUMOND_PREC_MIXED_FIXED: "f32+int64",
+                                            q.QUMOND_PREC_FP64: "f64"}[prec],
+            "data": "synthetic", "config": workload_config(PRECISION_NAMES[args.precision]),
             "cell_updates_per_s": ws * cell_updates / (ms_total / 1000.0),
             "hbm_algorithmic_GBps_all_kernels": total_bytes / (total_kernel_ms * 1e6) if total_kernel_ms else None,
-            "kernel_time_fraction_of_step": total_kernel_ms / ms_total,
+            "kernel_ms_per_step": total_kernel_ms / args.steps,
+            "replay_ms_per_step_one_by_one": replay_ms,
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
@@ -386,7 +407,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["fixed", "mixed", "fp64"], default="mixed")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 FMG comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip timing the oracle on the host")
     args = ap.parse_args()

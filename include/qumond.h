@@ -29,7 +29,10 @@
  *   when `stats` is non-NULL.
  * - A context is not thread safe: one host thread per context.  Its calls
  *   may be issued on any stream but must not overlap on the GPU (the
- *   multigrid scratch is shared by all calls of a context).
+ *   multigrid scratch is shared by all calls of a context).  With use_graphs,
+ *   each solve is captured once per (box, arrays) into a CUDA graph on the
+ *   context's own stream and relaunched on `stream`; the caller's stream must
+ *   not itself be capturing.
  * - On error the status is returned and qumond_last_error(ctx) describes it.
  *   QUMOND_ERR_NOT_CONVERGED still leaves the best iterate in the output.
  */
@@ -66,7 +69,14 @@ enum {
     /* FP32 smoothing, residual restriction and prolongation; FP64 residual,
        defect correction (iterative refinement) and master iterate; FP64 for
        the coarsest grid of the FP64 steps and for all boundary values. */
-    QUMOND_PREC_MIXED = 1
+    QUMOND_PREC_MIXED = 1,
+    /* As QUMOND_PREC_MIXED, but the defect correction carries its master
+       iterate u and right-hand side in 64-bit fixed point (u * 2^S, S chosen
+       per solve so that max|u| * 2^S ~ 2^56): the 7-point residual is then an
+       exact integer sum, rounded once to FP32 for the V-cycle.  Resolution
+       ~2^-56 max|u| (FP64: 2^-53 |u|); the FP64 pipe, slow on this GPU, is
+       used only to convert the FP64 inputs and output once per solve. */
+    QUMOND_PREC_MIXED_FIXED = 2
 };
 
 /* Boundary values of box 0 (boxes b >= 1 always interpolate theirs from box
@@ -98,6 +108,9 @@ typedef struct {
                            R < rc_box_frac * L_b (0.2 gives Section 3.1's rule) */
     int box_ratio;      /* side ratio of consecutive boxes: 2 (Section 2, each
                            refinement halves the box), 4 or 8 */
+    int use_graphs;     /* 1: each solve runs as one cached CUDA graph (FMG and
+                           the whole tolerance loop, decided on the device);
+                           0: kernels are launched one by one */
 } qumond_params;
 
 /* Per-solve report (host struct). */
@@ -113,7 +126,7 @@ typedef struct qumond_ctx qumond_ctx;
 /* Paper defaults: n = 256, one box of 120 kpc, G = 4.30e-3, a0 = 3.6,
    npre = npost = 2, ncycle = 6, rel_tol = 0 (paper mode), max_vcycles = 50,
    QUMOND_PREC_MIXED, QUMOND_BC_ZERO, warm_start = 0, deposit_shift = 24,
-   rc_box_frac = 0.2, box_ratio = 2. */
+   rc_box_frac = 0.2, box_ratio = 2, use_graphs = 1. */
 QUMOND_API void qumond_default_params(qumond_params* p);
 
 /* Validates p and allocates the context's device scratch on the current

@@ -11,6 +11,7 @@ from .qumond import (  # noqa: F401
     default_params,
     QUMOND_PREC_FP64,
     QUMOND_PREC_MIXED,
+    QUMOND_PREC_MIXED_FIXED,
     QUMOND_BC_ZERO,
     QUMOND_BC_GIVEN,
     EXPORTED,

@@ -25,14 +25,21 @@ struct Level {
 enum Kind {
     K_DEPOSIT, K_FIXED_TO_RHO, K_BOUNDARY, K_CONVERT_RHS, K_RESTRICT_FULL, K_COARSE, K_RB_FINEST, K_RB_COARSER,
     K_RESTRICT_RESID, K_PROLONG, K_SET_BOUNDARY, K_ASSIGN_OUTER, K_RESIDUAL_OUTER, K_REDUCE, K_SOURCE, K_FORCES,
-    K_ROTATION_CURVE, K_COUNT
+    K_ROTATION_CURVE, K_FIXED_SETUP, K_FIXED_OUTPUT, K_COUNT
 };
 const char* const kKindNames[K_COUNT] = {
     "cic_deposit", "fixed_to_rho", "boundary_fill", "convert_rhs", "restrict_full", "coarse_solver",
     "rb_half_finest", "rb_half_coarser", "restrict_resid_red", "prolong_black", "set_boundary", "update_outer",
-    "residual_outer", "reduce_norms", "qumond_source", "forces", "rotation_curve",
+    "residual_outer", "reduce_norms", "qumond_source", "forces", "rotation_curve", "fixed_setup", "fixed_output",
 };
 constexpr int kMaxTimed = 32768;
+
+// Launch counts of a sequence of kernels (a captured graph phase).
+struct Phase {
+    long long launches[K_COUNT] = {};
+    double bytes[K_COUNT] = {};
+    long long cell_updates = 0;
+};
 
 struct Tracer {
     bool on = false;
@@ -43,7 +50,34 @@ struct Tracer {
     double ms[K_COUNT] = {};
     long long timed[K_COUNT] = {};
     long long cell_updates = 0;
+    Phase* sink = nullptr;  // while capturing: counts go here, nothing is timed
+
+    void add(const Phase& ph, long long times)
+    {
+        for (int k = 0; k < K_COUNT; ++k) {
+            launches[k] += ph.launches[k] * times;
+            bytes[k] += ph.bytes[k] * (double)times;
+        }
+        cell_updates += ph.cell_updates * times;
+    }
 };
+
+// One captured solve: the preamble (boundary values, FMG, first residual
+// check) and, in tolerance mode, a WHILE node whose body is one V-cycle of
+// the defect correction plus its residual check.
+struct SolveGraph {
+    int kind = -1;  // 0 Newton, 1 QUMOND
+    int box = -1;
+    const double* rhs = nullptr;
+    const double* parent = nullptr;
+    double* u = nullptr;
+    bool norms = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    Phase pre, body;
+    unsigned long long last_use = 0;
+};
+constexpr size_t kMaxGraphs = 32;
 
 }  // namespace
 
@@ -57,6 +91,14 @@ struct qumond_ctx {
     int max_partials = 0;
     double* d_norms = nullptr;
     double* h_norms = nullptr;  // pinned
+    SolveState* d_state = nullptr;
+    SolveState* h_state = nullptr;  // pinned
+    int64_t* Ufix = nullptr;        // fixed-point master iterate (QUMOND_PREC_MIXED_FIXED)
+    int64_t* Ffix = nullptr;        // fixed-point right-hand side
+    unsigned* maxbits = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<SolveGraph> graphs;
+    unsigned long long use_clock = 0;
     Tracer tr;
     std::string err;
 };
@@ -119,7 +161,7 @@ qumond_status check_params(qumond_ctx* c, const qumond_params* p)
     if (p->ncycle < 1 || p->ncycle > 128) return fail(c, QUMOND_ERR_INVALID_ARG, "ncycle must be in [1, 128]");
     if (!(p->rel_tol >= 0.0)) return fail(c, QUMOND_ERR_INVALID_ARG, "rel_tol must be >= 0");
     if (p->max_vcycles < 0 || p->max_vcycles > 10000) return fail(c, QUMOND_ERR_INVALID_ARG, "max_vcycles must be in [0, 10000]");
-    if (p->precision != QUMOND_PREC_FP64 && p->precision != QUMOND_PREC_MIXED)
+    if (p->precision != QUMOND_PREC_FP64 && p->precision != QUMOND_PREC_MIXED && p->precision != QUMOND_PREC_MIXED_FIXED)
         return fail(c, QUMOND_ERR_INVALID_ARG, "unknown precision %d", p->precision);
     if (p->bc_mode != QUMOND_BC_ZERO && p->bc_mode != QUMOND_BC_GIVEN) return fail(c, QUMOND_ERR_INVALID_ARG, "unknown bc_mode %d", p->bc_mode);
     if (p->warm_start != 0 && p->warm_start != 1) return fail(c, QUMOND_ERR_INVALID_ARG, "warm_start must be 0 or 1");
@@ -127,6 +169,7 @@ qumond_status check_params(qumond_ctx* c, const qumond_params* p)
     if (!(p->rc_box_frac > 0.0) || !(p->rc_box_frac <= 0.5)) return fail(c, QUMOND_ERR_INVALID_ARG, "rc_box_frac must be in (0, 0.5]");
     if (p->box_ratio != 2 && p->box_ratio != 4 && p->box_ratio != 8)
         return fail(c, QUMOND_ERR_INVALID_ARG, "box_ratio must be 2, 4 or 8");
+    if (p->use_graphs != 0 && p->use_graphs != 1) return fail(c, QUMOND_ERR_INVALID_ARG, "use_graphs must be 0 or 1");
     if (p->nboxes > 1 && p->n < 2 * p->box_ratio)
         return fail(c, QUMOND_ERR_INVALID_ARG, "n=%d too small for nested boxes of ratio %d", p->n, p->box_ratio);
     return QUMOND_OK;
@@ -153,6 +196,12 @@ template <class Launch>
 void run(qumond_ctx* c, int kind, double bytes, cudaStream_t s, Launch&& launch)
 {
     Tracer& t = c->tr;
+    if (t.sink) {
+        launch();
+        t.sink->launches[kind] += 1;
+        t.sink->bytes[kind] += bytes;
+        return;
+    }
     const size_t slot = t.kind_of.size();
     const bool rec = t.on && slot < (size_t)kMaxTimed;
     if (rec) cudaEventRecord(t.ev[2 * slot], s);
@@ -165,14 +214,18 @@ void run(qumond_ctx* c, int kind, double bytes, cudaStream_t s, Launch&& launch)
     t.bytes[kind] += bytes;
 }
 
-// One V-cycle at level l on the correction problem held in lev[l] (for l <
-// L the initial guess is zero; at l = L the caller says so).
+inline void count_cells(qumond_ctx* c, long long n)
+{
+    if (c->tr.sink) c->tr.sink->cell_updates += n;
+    else c->tr.cell_updates += n;
+}
+
 template <typename T>
 void rb(qumond_ctx* c, int l, int colour, bool zero, double h, cudaStream_t s)
 {
     const int n = c->lev[l].v.n;
     const double nodes = cube(n);
-    c->tr.cell_updates += ((long long)(n - 1) * (n - 1) * (n - 1) + (colour == 0 ? 1 : 0)) / 2;
+    count_cells(c, ((long long)(n - 1) * (n - 1) * (n - 1) + (colour == 0 ? 1 : 0)) / 2);
     run(c, l == c->L ? K_RB_FINEST : K_RB_COARSER, (zero ? 1.0 : 1.5) * nodes * sizeof(T), s,
         [&] { launch_rb_half<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, colour, zero, h, s); });
 }
@@ -200,7 +253,7 @@ cudaError_t coarse(qumond_ctx* c, int box, int fmg_mode, const double* u64, cuda
     const int n = c->lev[l].v.n;
     long long upd = 0;  // red-black updates inside the kernel (approximate count of its sweeps)
     for (int m = 4; m <= n; m *= 2) upd += (long long)(c->p.npre + c->p.npost) * (m - 1) * (m - 1) * (m - 1);
-    c->tr.cell_updates += fmg_mode ? upd * c->p.ncycle : upd;
+    count_cells(c, fmg_mode ? upd * c->p.ncycle : upd);
     cudaError_t err = cudaSuccess;
     run(c, K_COARSE, 2.0 * cube(n) * sizeof(T), s, [&] {
         err = launch_coarse<T>(fmg_mode, E<T>(c, l), F<T>(c, l), c->lev[l].v, level_h(c, box, l), u64, c->p.n,
@@ -265,32 +318,39 @@ cudaError_t fmg(qumond_ctx* c, int box, const double* u64, cudaStream_t s)
     return cudaSuccess;
 }
 
-// Residual norms: returns ||coef*rhs - L u||^2 and ||coef*rhs||^2.
+// Residual r = coef*rhs - L u into the finest level and the decision whether
+// to continue (device-side; drives the graph's WHILE node when capturing).
+inline bool fixed_mode(const qumond_ctx* c) { return c->p.precision == QUMOND_PREC_MIXED_FIXED; }
+
 template <typename T>
-qumond_status residual_norms(qumond_ctx* c, int box, const double* rhs, double coef, const double* u, cudaStream_t s,
-                             double* rr, double* ff)
+void check(qumond_ctx* c, int box, const double* rhs, double coef, const double* u, bool first,
+           const cudaGraphConditionalHandle* handle, cudaStream_t s)
 {
-    int nb = 0;
-    run(c, K_RESIDUAL_OUTER, cube(c->p.n) * (16.0 + sizeof(T)), s, [&] {
-        nb = launch_residual_outer<T>(u, rhs, coef, c->p.n, box_h(c, box), F<T>(c, c->L), c->lev[c->L].v,
-                                      c->partials, s);
+    const qumond_params& p = c->p;
+    int nb = residual_rows_blocks(p.n);
+    if (fixed_mode(c)) {
+        nb = fixed_residual_blocks(p.n);
+        run(c, K_RESIDUAL_OUTER, cube(p.n) * 20.0, s, [&] {
+            launch_fixed_residual(c->Ufix, c->Ffix, p.n, box_h(c, box), c->d_state, first,
+                                  reinterpret_cast<float*>(F<T>(c, c->L)), c->lev[c->L].v, c->partials, s);
+        });
+    } else {
+        run(c, K_RESIDUAL_OUTER, cube(p.n) * (16.0 + sizeof(T)), s, [&] {
+            launch_residual_rows<T>(u, rhs, coef, p.n, box_h(c, box), F<T>(c, c->L), c->lev[c->L].v, c->partials, s);
+        });
+    }
+    run(c, K_REDUCE, 16.0 * nb, s, [&] {
+        launch_decide(c->partials, nb, c->d_state, p.rel_tol, p.max_vcycles, first, p.rel_tol > 0.0 && p.max_vcycles > 0,
+                      handle, s);
     });
-    run(c, K_REDUCE, 16.0 * nb, s, [&] { launch_reduce_norms(c->partials, nb, c->d_norms, s); });
-    CUDA_TRY(c, cudaGetLastError(), "residual launch");
-    CUDA_TRY(c, cudaMemcpyAsync(c->h_norms, c->d_norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s), "norm copy");
-    CUDA_TRY(c, cudaStreamSynchronize(s), "residual");
-    *rr = c->h_norms[0];
-    *ff = c->h_norms[1];
-    return QUMOND_OK;
 }
 
-// Steps 2 and 4: boundary values, FMG, then defect correction to rel_tol.
-//   r = coef*rhs - L u   (FP64, caller's arrays)
-//   V-cycle on L e = r   (precision T, zero initial guess, zero boundary)
-//   u += e               (FP64)
+// --- the solve, as a sequence of launches ------------------------------------
+// Preamble: boundary values (from the parent box, or zero for box 0 in the
+// paper's setup), FMG, and (when norms are wanted) the first residual check.
 template <typename T>
-qumond_status solve_t(qumond_ctx* c, int box, const double* rhs, double coef, const double* parent, double* u,
-                      qumond_stats* st, cudaStream_t s)
+cudaError_t enqueue_preamble(qumond_ctx* c, int box, const double* rhs, double coef, const double* parent, double* u,
+                             bool norms, const cudaGraphConditionalHandle* handle, cudaStream_t s)
 {
     const qumond_params& p = c->p;
     const int n = p.n;
@@ -300,45 +360,217 @@ qumond_status solve_t(qumond_ctx* c, int box, const double* rhs, double coef, co
         run(c, K_BOUNDARY, nbnd * 16.0, s, [&] { launch_boundary_from_parent(parent, u, n, p.box_ratio, s); });
     else if (p.bc_mode == QUMOND_BC_ZERO)
         run(c, K_BOUNDARY, nbnd * 8.0, s, [&] { launch_boundary_zero(u, n, s); });
+    const bool fixed = fixed_mode(c) && norms;
     if (!p.warm_start) {
         run(c, K_CONVERT_RHS, nodes * (8.0 + sizeof(T)), s,
             [&] { launch_convert_rhs<T>(rhs, coef, n, F<T>(c, c->L), c->lev[c->L].v, s); });
         cudaError_t err = fmg<T>(c, box, u, s);
-        if (err != cudaSuccess) return cuda_fail(c, err, "fmg");
-        run(c, K_ASSIGN_OUTER, nodes * (8.0 + sizeof(T)), s,
-            [&] { launch_assign_outer<T>(u, n, E<T>(c, c->L), c->lev[c->L].v, false, s); });
-        set_bnd<T>(c, c->L, nullptr, s);
+        if (err != cudaSuccess) return err;
+        if (!fixed)
+            run(c, K_ASSIGN_OUTER, nodes * (8.0 + sizeof(T)), s,
+                [&] { launch_assign_outer<T>(u, n, E<T>(c, c->L), c->lev[c->L].v, false, s); });
     }
-    CUDA_TRY(c, cudaGetLastError(), "solve launch");
-    const bool refine = p.rel_tol > 0.0 && p.max_vcycles > 0;
-    if (!refine && !st) return QUMOND_OK;
-    double rr = 0.0, ff = 0.0;
-    qumond_status rs = residual_norms<T>(c, box, rhs, coef, u, s, &rr, &ff);
-    if (rs != QUMOND_OK) return rs;
-    const double denom = ff > 0.0 ? std::sqrt(ff) : 1.0;
-    double rel = std::sqrt(rr) / denom;
-    const double rel0 = rel;
-    int made = 0;
-    while (refine && rel > p.rel_tol && made < p.max_vcycles && std::isfinite(rel)) {
-        cudaError_t err = vcycle<T>(c, box, c->L, true, s);
-        if (err != cudaSuccess) return cuda_fail(c, err, "vcycle");
-        run(c, K_ASSIGN_OUTER, nodes * (16.0 + sizeof(T)), s,
+    if (fixed) {
+        const float* eL = reinterpret_cast<const float*>(E<T>(c, c->L));
+        run(c, K_FIXED_SETUP, nodes * 32.0, s, [&] {
+            launch_fixed_scale(eL, c->lev[c->L].v, u, n, p.warm_start != 0, c->maxbits, c->d_state, s);
+            launch_fixed_init(eL, c->lev[c->L].v, u, rhs, coef, box_h(c, box), n, p.warm_start != 0, c->d_state,
+                              c->Ufix, c->Ffix, s);
+        });
+    }
+    if (!p.warm_start) set_bnd<T>(c, c->L, nullptr, s);
+    if (norms) check<T>(c, box, rhs, coef, u, true, handle, s);
+    return cudaGetLastError();
+}
+
+// After the defect correction (fixed-point mode): u = U 2^-S.
+template <typename T>
+cudaError_t enqueue_post(qumond_ctx* c, double* u, cudaStream_t s)
+{
+    if (!fixed_mode(c)) return cudaSuccess;
+    run(c, K_FIXED_OUTPUT, cube(c->p.n) * 16.0, s, [&] { launch_fixed_output(c->Ufix, u, c->p.n, c->d_state, s); });
+    return cudaGetLastError();
+}
+
+// Body of the defect correction: one V-cycle on L e = r from e = 0, u += e,
+// and the residual check that decides whether to go on.
+template <typename T>
+cudaError_t enqueue_body(qumond_ctx* c, int box, const double* rhs, double coef, double* u,
+                         const cudaGraphConditionalHandle* handle, cudaStream_t s)
+{
+    const int n = c->p.n;
+    cudaError_t err = vcycle<T>(c, box, c->L, true, s);
+    if (err != cudaSuccess) return err;
+    if (fixed_mode(c))
+        run(c, K_ASSIGN_OUTER, cube(n) * 20.0, s, [&] {
+            launch_fixed_update(c->Ufix, reinterpret_cast<const float*>(E<T>(c, c->L)), c->lev[c->L].v, n, c->d_state, s);
+        });
+    else
+        run(c, K_ASSIGN_OUTER, cube(n) * (16.0 + sizeof(T)), s,
             [&] { launch_assign_outer<T>(u, n, E<T>(c, c->L), c->lev[c->L].v, true, s); });
-        ++made;
-        rs = residual_norms<T>(c, box, rhs, coef, u, s, &rr, &ff);
-        if (rs != QUMOND_OK) return rs;
-        rel = std::sqrt(rr) / denom;
+    check<T>(c, box, rhs, coef, u, false, handle, s);
+    return cudaGetLastError();
+}
+
+SolveGraph* find_graph(qumond_ctx* c, int kind, int box, const double* rhs, const double* parent, double* u,
+                       bool norms)
+{
+    for (auto& g : c->graphs)
+        if (g.kind == kind && g.box == box && g.rhs == rhs && g.parent == parent && g.u == u && g.norms == norms)
+            return &g;
+    return nullptr;
+}
+
+void destroy_graph(SolveGraph& g)
+{
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g.exec = nullptr;
+    g.graph = nullptr;
+}
+
+// Captures the solve into a graph on the context's private stream.  The
+// WHILE node's condition is set on the device by the residual check, so a
+// launch runs FMG and every V-cycle the tolerance needs without the host.
+template <typename T>
+qumond_status capture(qumond_ctx* c, int kind, int box, const double* rhs, double coef, const double* parent,
+                      double* u, bool norms, bool refine, SolveGraph* out)
+{
+    cudaStream_t cs = c->cap_stream;
+    SolveGraph g;
+    g.kind = kind;
+    g.box = box;
+    g.rhs = rhs;
+    g.parent = parent;
+    g.u = u;
+    g.norms = norms;
+    CUDA_TRY(c, cudaGraphCreate(&g.graph, 0), "graph create");
+    cudaGraphConditionalHandle handle = 0;
+    cudaError_t err = cudaSuccess;
+    if (refine) err = cudaGraphConditionalHandleCreate(&handle, g.graph, 0, cudaGraphCondAssignDefault);
+    std::vector<cudaGraphNode_t> tail;
+    if (err == cudaSuccess) err = cudaStreamBeginCaptureToGraph(cs, g.graph, nullptr, nullptr, 0,
+                                                                cudaStreamCaptureModeThreadLocal);
+    if (err == cudaSuccess) {
+        c->tr.sink = &g.pre;
+        cudaError_t e1 = enqueue_preamble<T>(c, box, rhs, coef, parent, u, norms, refine ? &handle : nullptr, cs);
+        if (e1 == cudaSuccess && !refine && norms) e1 = enqueue_post<T>(c, u, cs);
+        c->tr.sink = nullptr;
+        if (refine && e1 == cudaSuccess) {
+            cudaStreamCaptureStatus cst;
+            const cudaGraphNode_t* deps = nullptr;
+            size_t nd = 0;
+            e1 = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &nd);
+            if (e1 == cudaSuccess) tail.assign(deps, deps + nd);
+        }
+        cudaGraph_t captured = g.graph;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+        err = e1 != cudaSuccess ? e1 : e2;
     }
-    const bool ok = std::isfinite(rel) && (!refine || rel <= p.rel_tol);
+    cudaGraphNode_t wnode = nullptr;
+    if (err == cudaSuccess && refine) {
+        // cudaGraphNodeParams has no usable default constructor: zeroed storage
+        alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+        memset(raw, 0, sizeof(raw));
+        cudaGraphNodeParams* cp = reinterpret_cast<cudaGraphNodeParams*>(raw);
+        cp->type = cudaGraphNodeTypeConditional;
+        cp->conditional.handle = handle;
+        cp->conditional.type = cudaGraphCondTypeWhile;
+        cp->conditional.size = 1;
+        err = cudaGraphAddNode(&wnode, g.graph, tail.data(), nullptr, tail.size(), cp);
+        if (err == cudaSuccess) {
+            cudaGraph_t body = cp->conditional.phGraph_out[0];
+            err = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (err == cudaSuccess) {
+                c->tr.sink = &g.body;
+                cudaError_t e1 = enqueue_body<T>(c, box, rhs, coef, u, &handle, cs);
+                c->tr.sink = nullptr;
+                cudaGraph_t captured = body;
+                cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+                err = e1 != cudaSuccess ? e1 : e2;
+            }
+        }
+        if (err == cudaSuccess) {  // after the loop
+            err = cudaStreamBeginCaptureToGraph(cs, g.graph, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+            if (err == cudaSuccess) {
+                c->tr.sink = &g.pre;
+                cudaError_t e1 = enqueue_post<T>(c, u, cs);
+                c->tr.sink = nullptr;
+                cudaGraph_t captured = g.graph;
+                cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+                err = e1 != cudaSuccess ? e1 : e2;
+            }
+        }
+    }
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&g.exec, g.graph, 0);
+    if (err != cudaSuccess) {
+        destroy_graph(g);
+        return cuda_fail(c, err, "graph capture");
+    }
+    *out = g;
+    return QUMOND_OK;
+}
+
+// Steps 2 and 4: boundary values, FMG, then defect correction to rel_tol.
+//   r = coef*rhs - L u   (FP64, caller's arrays)
+//   V-cycle on L e = r   (precision T, zero initial guess, zero boundary)
+//   u += e               (FP64)
+// Launched as one cached CUDA graph per (solve, box, arrays); with kernel
+// timing on, the same launches are issued one by one and the host reads the
+// residual after each V-cycle instead.
+template <typename T>
+qumond_status solve_t(qumond_ctx* c, int kind, int box, const double* rhs, double coef, const double* parent,
+                      double* u, qumond_stats* st, cudaStream_t s)
+{
+    const qumond_params& p = c->p;
+    const bool refine = p.rel_tol > 0.0 && p.max_vcycles > 0;
+    const bool norms = refine || st != nullptr;
+    if (p.use_graphs && !c->tr.on) {
+        SolveGraph* g = find_graph(c, kind, box, rhs, parent, u, norms);
+        if (!g) {
+            if (c->graphs.size() >= kMaxGraphs) {
+                size_t oldest = 0;
+                for (size_t q = 1; q < c->graphs.size(); ++q)
+                    if (c->graphs[q].last_use < c->graphs[oldest].last_use) oldest = q;
+                CUDA_TRY(c, cudaDeviceSynchronize(), "graph eviction");
+                destroy_graph(c->graphs[oldest]);
+                c->graphs.erase(c->graphs.begin() + oldest);
+            }
+            SolveGraph ng;
+            qumond_status cs = capture<T>(c, kind, box, rhs, coef, parent, u, norms, refine, &ng);
+            if (cs != QUMOND_OK) return cs;
+            c->graphs.push_back(ng);
+            g = &c->graphs.back();
+        }
+        g->last_use = ++c->use_clock;
+        CUDA_TRY(c, cudaGraphLaunch(g->exec, s), "graph launch");
+        c->tr.add(g->pre, 1);
+        if (!norms) return QUMOND_OK;
+        CUDA_TRY(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, s), "state copy");
+        CUDA_TRY(c, cudaStreamSynchronize(s), "solve");
+        c->tr.add(g->body, c->h_state->it);
+    } else {
+        CUDA_TRY(c, enqueue_preamble<T>(c, box, rhs, coef, parent, u, norms, nullptr, s), "solve launch");
+        if (!norms) return QUMOND_OK;
+        for (;;) {
+            CUDA_TRY(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, s),
+                     "state copy");
+            CUDA_TRY(c, cudaStreamSynchronize(s), "solve");
+            if (!c->h_state->cont) break;
+            CUDA_TRY(c, enqueue_body<T>(c, box, rhs, coef, u, nullptr, s), "vcycle launch");
+        }
+        CUDA_TRY(c, enqueue_post<T>(c, u, s), "output launch");
+    }
+    const SolveState& r = *c->h_state;
     if (st) {
-        st->vcycles = made;
-        st->converged = ok ? 1 : 0;
-        st->rel_residual_fmg = rel0;
-        st->rel_residual = rel;
+        st->vcycles = r.it;
+        st->converged = r.converged;
+        st->rel_residual_fmg = r.rel0;
+        st->rel_residual = r.rel;
     }
-    if (!ok)
-        return fail(c, QUMOND_ERR_NOT_CONVERGED, "box %d: relative residual %.3e after %d V-cycles (tol %.3e)", box, rel,
-                    made, p.rel_tol);
+    if (!r.converged)
+        return fail(c, QUMOND_ERR_NOT_CONVERGED, "box %d: relative residual %.3e after %d V-cycles (tol %.3e)", box,
+                    r.rel, r.it, p.rel_tol);
     return QUMOND_OK;
 }
 
@@ -351,8 +583,9 @@ qumond_status solve(qumond_ctx* c, int box, const double* rhs, double coef, cons
     if (!device_ptr(rhs) || !device_ptr(u)) return fail(c, QUMOND_ERR_INVALID_ARG, "%s: rhs and phi must be device pointers", what);
     if (box > 0 && !device_ptr(parent)) return fail(c, QUMOND_ERR_INVALID_ARG, "%s: box %d needs the parent potential (device)", what, box);
     if (rhs == u || (box > 0 && parent == u)) return fail(c, QUMOND_ERR_INVALID_ARG, "%s: phi must not alias its inputs", what);
-    if (c->p.precision == QUMOND_PREC_FP64) return solve_t<double>(c, box, rhs, coef, parent, u, st, S(stream));
-    return solve_t<float>(c, box, rhs, coef, parent, u, st, S(stream));
+    const int kind = coef == 1.0 ? 1 : 0;
+    if (c->p.precision == QUMOND_PREC_FP64) return solve_t<double>(c, kind, box, rhs, coef, parent, u, st, S(stream));
+    return solve_t<float>(c, kind, box, rhs, coef, parent, u, st, S(stream));
 }
 
 BoxSet box_set(const qumond_ctx* c, const double* const* phis)
@@ -406,6 +639,7 @@ void qumond_default_params(qumond_params* p)
     p->deposit_shift = 24;
     p->rc_box_frac = 0.2;
     p->box_ratio = 2;
+    p->use_graphs = 1;
 }
 
 qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
@@ -419,7 +653,7 @@ qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
         return st;
     }
     c->p = *p;
-    c->elt = p->precision == QUMOND_PREC_FP64 ? sizeof(double) : sizeof(float);
+    c->elt = p->precision == QUMOND_PREC_FP64 ? sizeof(double) : sizeof(float);  // FIXED smooths in FP32
     int L = 0;
     while ((2 << L) < p->n) ++L;
     c->L = L;
@@ -442,10 +676,26 @@ qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
         }
     }
     if (ok) {
-        c->max_partials = residual_outer_blocks(p->n > 2 ? p->n : 2);
+        const int nrows = residual_rows_blocks(p->n > 2 ? p->n : 2);
+        const int nouter = residual_outer_blocks(p->n > 2 ? p->n : 2);
+        c->max_partials = nrows > nouter ? nrows : nouter;
         ok = cudaMalloc(&c->partials, sizeof(double) * 2 * (size_t)(c->max_partials + 1)) == cudaSuccess &&
              cudaMalloc(&c->d_norms, sizeof(double) * 2) == cudaSuccess &&
-             cudaMallocHost(&c->h_norms, sizeof(double) * 2) == cudaSuccess;
+             cudaMallocHost(&c->h_norms, sizeof(double) * 2) == cudaSuccess &&
+             cudaMalloc(&c->d_state, sizeof(SolveState)) == cudaSuccess &&
+             cudaMallocHost(&c->h_state, sizeof(SolveState)) == cudaSuccess &&
+             cudaMemset(c->d_state, 0, sizeof(SolveState)) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
+             prepare_kernels() == cudaSuccess;
+        if (ok && p->precision == QUMOND_PREC_MIXED_FIXED) {
+            const size_t nn = (size_t)(p->n + 1) * (p->n + 1) * (p->n + 1);
+            const int nfix = fixed_residual_blocks(p->n > 2 ? p->n : 2);
+            if (nfix > c->max_partials) ok = false;  // partial buffer sized above covers it
+            ok = ok && cudaMalloc(&c->Ufix, nn * sizeof(int64_t)) == cudaSuccess &&
+                 cudaMalloc(&c->Ffix, nn * sizeof(int64_t)) == cudaSuccess &&
+                 cudaMalloc(&c->maxbits, sizeof(unsigned)) == cudaSuccess &&
+                 cudaMemset(c->maxbits, 0, sizeof(unsigned)) == cudaSuccess;
+        }
     }
     if (!ok) {
         (void)cudaGetLastError();
@@ -467,6 +717,13 @@ void qumond_destroy(qumond_ctx* c)
     if (c->partials) cudaFree(c->partials);
     if (c->d_norms) cudaFree(c->d_norms);
     if (c->h_norms) cudaFreeHost(c->h_norms);
+    if (c->d_state) cudaFree(c->d_state);
+    if (c->Ufix) cudaFree(c->Ufix);
+    if (c->Ffix) cudaFree(c->Ffix);
+    if (c->maxbits) cudaFree(c->maxbits);
+    if (c->h_state) cudaFreeHost(c->h_state);
+    for (auto& g : c->graphs) destroy_graph(g);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (cudaEvent_t e : c->tr.ev) cudaEventDestroy(e);
     (void)cudaGetLastError();
     delete c;

@@ -1,0 +1,254 @@
+// Defect correction with a 64-bit fixed-point master iterate
+// (QUMOND_PREC_MIXED_FIXED).
+//
+// The outer loop of the mixed-precision solve needs a residual r = f - L u
+// accurate well beyond FP32.  On this GPU FP64 arithmetic and every 64-bit
+// float conversion run at ~2 operations per clock per SM (FP32: ~110), so a
+// 7-point FP64 residual is bound by the FP64 pipe at ~4x its memory time.
+// Here the iterate is held as integers U = u * 2^S and the right-hand side as
+// F = coef * rhs * h^2 * 2^S, both int64.  Then
+//   R = F - (sum of the 6 neighbours of U - 6 U)
+// is exact integer arithmetic, and r = R * 2^-S / h^2 is rounded once, to
+// FP32, for the V-cycle.  S is chosen per solve so that max|u| * 2^S is about
+// 2^56 (the FMG result bounds max|u| to ~1%); the resolution 2^-S is then
+// ~2^-56 max|u|, finer than FP64's 2^-53 relative spacing near max|u|, and
+// |F| <= 12 max|U| < 2^60 cannot overflow for a solution of the problem.
+//
+// Only the once-per-solve conversions (FP64 right-hand side and boundary
+// values in, FP64 potential out) use the FP64 pipe; the per-V-cycle kernels
+// use integer and FP32 instructions only.
+#include "qumond_internal.h"
+
+namespace qumond {
+
+namespace {
+
+__device__ __forceinline__ long long nat(int n, int i, int j, int k)
+{
+    const long long P = n + 1;
+    return (long long)i + P * ((long long)j + P * (long long)k);
+}
+
+// int64 -> FP32 through its two 32-bit halves (within one FP32 rounding of
+// the exact value); integer and FP32 pipes only.
+__device__ __forceinline__ float i64_to_f32(long long x)
+{
+    const float hi = (float)(int)(x >> 32);
+    const float lo = (float)(unsigned)(x & 0xffffffffLL);
+    return fmaf(hi, 4294967296.0f, lo);
+}
+
+// FP32 -> int64, round to nearest: exact when |v| >= 2^23 (v is then an
+// integer), __float2int_rn below that.
+__device__ __forceinline__ long long f32_to_i64(float v)
+{
+    if (fabsf(v) < 8388608.0f) return (long long)__float2int_rn(v);
+    const unsigned bits = __float_as_uint(v);
+    const int ex = (int)((bits >> 23) & 0xffu) - 150;
+    if (ex > 38) return (bits >> 31) ? -(1LL << 62) : (1LL << 62);  // saturate (only a diverging solve gets here)
+    const long long m = (long long)((bits & 0x7fffffu) | 0x800000u) << ex;
+    return (bits >> 31) ? -m : m;
+}
+
+// 2^e as FP32 / FP64 from an integer exponent.
+__device__ __forceinline__ float pow2f(int e) { return ldexpf(1.0f, e); }
+__device__ __forceinline__ double pow2d(int e) { return ldexp(1.0, e); }
+
+constexpr int kThreads = 128;
+constexpr int kMaxBlocks = 152 * 16;
+
+// --- choice of the scale S ---------------------------------------------------
+// Largest |u| over the FMG result (FP32, both colours, interior) or, for a
+// warm start, over the caller's interior values, and over the boundary values.
+__global__ void __launch_bounds__(kThreads)
+scan_max_kernel(const float* __restrict__ e, LevelView v, const double* __restrict__ u64, int n, int from_u64,
+                unsigned* __restrict__ out)
+{
+    unsigned local = 0u;
+    const int rows = (n + 1) * (n + 1);
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int j = row % (n + 1), k = row / (n + 1);
+        const bool brow = j == 0 || j == n || k == 0 || k == n;
+        for (int i = threadIdx.x; i <= n; i += kThreads) {
+            const bool bnd = brow || i == 0 || i == n;
+            float val;
+            if (bnd || from_u64) val = (float)u64[nat(n, i, j, k)];
+            else val = e[node_off(v, i, j, k)];
+            const unsigned b = __float_as_uint(fabsf(val));
+            local = b > local ? b : local;
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned o = __shfl_down_sync(0xffffffffu, local, off);
+        local = o > local ? o : local;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, local);
+}
+
+// S = 56 - ceil(log2(max|u|)), kept in [-60, 100] so that 2^S and 2^-S stay
+// normal FP32 numbers; also clears the max for the next solve.
+__global__ void choose_scale_kernel(unsigned* __restrict__ maxbits, SolveState* __restrict__ st)
+{
+    const float m = __uint_as_float(*maxbits);
+    int S = 0;
+    if (m > 0.0f && isfinite(m)) {
+        int ex;
+        frexpf(m, &ex);  // m = f * 2^ex, 0.5 <= f < 1, so m < 2^ex
+        S = 56 - ex;
+        S = S < -60 ? -60 : (S > 100 ? 100 : S);
+    }
+    st->scale_exp = S;
+    *maxbits = 0u;
+}
+
+// U = round(u * 2^S) on every node (interior from the FP32 FMG result or the
+// caller's warm start, boundary from the caller's FP64 values) and
+// F = round(coef * rhs * h^2 * 2^S) on interior nodes.
+__global__ void __launch_bounds__(kThreads)
+fixed_init_kernel(const float* __restrict__ e, LevelView v, const double* __restrict__ u64,
+                  const double* __restrict__ rhs, double coef_h2, int n, int from_u64,
+                  const SolveState* __restrict__ st, long long* __restrict__ U, long long* __restrict__ F)
+{
+    const int S = st->scale_exp;
+    const double sc = pow2d(S);
+    const float scf = pow2f(S);
+    const double kf = coef_h2 * sc;
+    const int rows = (n + 1) * (n + 1);
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int j = row % (n + 1), k = row / (n + 1);
+        const bool brow = j == 0 || j == n || k == 0 || k == n;
+        for (int i = threadIdx.x; i <= n; i += kThreads) {
+            const long long o = nat(n, i, j, k);
+            const bool bnd = brow || i == 0 || i == n;
+            if (bnd || from_u64) U[o] = __double2ll_rn(u64[o] * sc);
+            else U[o] = f32_to_i64(e[node_off(v, i, j, k)] * scf);
+            F[o] = bnd ? 0LL : __double2ll_rn(rhs[o] * kf);
+        }
+    }
+}
+
+// R = F - (sum of 6 neighbours - 6 U), exact; r = R 2^-S / h^2 in FP32 into
+// the finest level; per-block partial sums of r^2 (and, on the first check,
+// of f^2 with f = F 2^-S / h^2).  The squares are summed as (R 2^-30)^2 in
+// FP32 (|R| <= 2^60, so they lie in [2^-60, 2^60]: no overflow or
+// underflow) and scaled back per block in FP64.
+__global__ void __launch_bounds__(kThreads)
+fixed_residual_kernel(const long long* __restrict__ U, const long long* __restrict__ F, int n, float ih2,
+                      const SolveState* __restrict__ st, int want_f, float* __restrict__ r, LevelView v,
+                      double* __restrict__ partials)
+{
+    const long long P = n + 1, Q = P * P;
+    const float k = pow2f(-st->scale_exp) * ih2;
+    const int rows = (n - 1) * (n - 1);
+    float rr = 0.0f, ff = 0.0f;
+    constexpr float kDown = 9.313225746154785e-10f;  // 2^-30
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int j = row % (n - 1) + 1, kk = row / (n - 1) + 1;
+        for (int i = threadIdx.x + 1; i < n; i += kThreads) {
+            const long long o = nat(n, i, j, kk);
+            const long long s = (U[o + 1] + U[o - 1]) + (U[o + P] + U[o - P]) + (U[o + Q] + U[o - Q]) - 6 * U[o];
+            const long long fv = F[o];
+            const float R = i64_to_f32(fv - s);
+            r[node_off(v, i, j, kk)] = R * k;
+            const float Rs = R * kDown;
+            rr = fmaf(Rs, Rs, rr);
+            if (want_f) {
+                const float Fs = i64_to_f32(fv) * kDown;
+                ff = fmaf(Fs, Fs, ff);
+            }
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        rr += __shfl_down_sync(0xffffffffu, rr, off);
+        ff += __shfl_down_sync(0xffffffffu, ff, off);
+    }
+    __shared__ double sr[kThreads / 32], sf[kThreads / 32];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sr[w] = rr;
+        sf[w] = ff;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < kThreads / 32; ++q) {
+            a += sr[q];
+            b += sf[q];
+        }
+        const double up = ldexp((double)k, 30);  // back to r = R k
+        partials[2 * blockIdx.x] = a * up * up;
+        partials[2 * blockIdx.x + 1] = b * up * up;
+    }
+}
+
+// U += round(e 2^S) on interior nodes.
+__global__ void __launch_bounds__(kThreads)
+fixed_update_kernel(long long* __restrict__ U, const float* __restrict__ e, LevelView v, int n,
+                    const SolveState* __restrict__ st)
+{
+    const float scf = pow2f(st->scale_exp);
+    const int rows = (n - 1) * (n - 1);
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int j = row % (n - 1) + 1, k = row / (n - 1) + 1;
+        for (int i = threadIdx.x + 1; i < n; i += kThreads) U[nat(n, i, j, k)] += f32_to_i64(e[node_off(v, i, j, k)] * scf);
+    }
+}
+
+// u = U 2^-S on interior nodes (the boundary values are left as given).
+__global__ void __launch_bounds__(kThreads)
+fixed_output_kernel(const long long* __restrict__ U, double* __restrict__ u, int n, const SolveState* __restrict__ st)
+{
+    const double isc = pow2d(-st->scale_exp);
+    const int rows = (n - 1) * (n - 1);
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int j = row % (n - 1) + 1, k = row / (n - 1) + 1;
+        for (int i = threadIdx.x + 1; i < n; i += kThreads) {
+            const long long o = nat(n, i, j, k);
+            u[o] = __ll2double_rn(U[o]) * isc;
+        }
+    }
+}
+
+inline int blocks_for_rows(long long rows) { return (int)(rows < kMaxBlocks ? rows : kMaxBlocks); }
+
+}  // namespace
+
+void launch_fixed_scale(const float* e, const LevelView& v, const double* u64, int n, bool from_u64, unsigned* maxbits,
+                        SolveState* st, cudaStream_t s)
+{
+    scan_max_kernel<<<blocks_for_rows((long long)(n + 1) * (n + 1)), kThreads, 0, s>>>(e, v, u64, n, from_u64 ? 1 : 0,
+                                                                                     maxbits);
+    choose_scale_kernel<<<1, 1, 0, s>>>(maxbits, st);
+}
+
+void launch_fixed_init(const float* e, const LevelView& v, const double* u64, const double* rhs, double coef, double h,
+                       int n, bool from_u64, const SolveState* st, int64_t* U, int64_t* F, cudaStream_t s)
+{
+    fixed_init_kernel<<<blocks_for_rows((long long)(n + 1) * (n + 1)), kThreads, 0, s>>>(
+        e, v, u64, rhs, coef * h * h, n, from_u64 ? 1 : 0, st, reinterpret_cast<long long*>(U),
+        reinterpret_cast<long long*>(F));
+}
+
+int fixed_residual_blocks(int n) { return blocks_for_rows((long long)(n - 1) * (n - 1)); }
+
+int launch_fixed_residual(const int64_t* U, const int64_t* F, int n, double h, const SolveState* st, bool want_f,
+                          float* r, const LevelView& v, double* partials, cudaStream_t s)
+{
+    const int nb = fixed_residual_blocks(n);
+    fixed_residual_kernel<<<nb, kThreads, 0, s>>>(reinterpret_cast<const long long*>(U),
+                                                  reinterpret_cast<const long long*>(F), n, (float)(1.0 / (h * h)), st,
+                                                  want_f ? 1 : 0, r, v, partials);
+    return nb;
+}
+
+void launch_fixed_update(int64_t* U, const float* e, const LevelView& v, int n, const SolveState* st, cudaStream_t s)
+{
+    fixed_update_kernel<<<fixed_residual_blocks(n), kThreads, 0, s>>>(reinterpret_cast<long long*>(U), e, v, n, st);
+}
+
+void launch_fixed_output(const int64_t* U, double* u, int n, const SolveState* st, cudaStream_t s)
+{
+    fixed_output_kernel<<<fixed_residual_blocks(n), kThreads, 0, s>>>(reinterpret_cast<const long long*>(U), u, n, st);
+}
+
+}  // namespace qumond

@@ -425,6 +425,53 @@ residual_outer_kernel(const double* __restrict__ u, const double* __restrict__ r
     }
 }
 
+// The same residual, with rows of the grid dealt to a fixed number of blocks
+// (so only a few thousand partial sums need reducing).
+constexpr int kResidBlocksPerSM = 16;
+constexpr int kResidMaxBlocks = 152 * kResidBlocksPerSM;
+
+template <typename T>
+__global__ void __launch_bounds__(kOuterThreads)
+residual_rows_kernel(const double* __restrict__ u, const double* __restrict__ rhs, double coef, int n, double ih2,
+                     T* __restrict__ r, LevelView v, double* __restrict__ partials)
+{
+    const long long P = n + 1, Q = P * P;
+    const int rows = (n - 1) * (n - 1);
+    double rr = 0.0, ff = 0.0;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int j = row % (n - 1) + 1, k = row / (n - 1) + 1;
+        for (int i = threadIdx.x + 1; i < n; i += kOuterThreads) {
+            const long long o = nat(n, i, j, k);
+            const double s = (u[o + 1] + u[o - 1]) + (u[o + P] + u[o - P]) + (u[o + Q] + u[o - Q]);
+            const double fv = coef * rhs[o];
+            const double res = fv - (s - 6.0 * u[o]) * ih2;
+            r[node_off(v, i, j, k)] = (T)res;
+            rr = fma(res, res, rr);
+            ff = fma(fv, fv, ff);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        rr += __shfl_down_sync(0xffffffffu, rr, off);
+        ff += __shfl_down_sync(0xffffffffu, ff, off);
+    }
+    __shared__ double sr[kOuterThreads / 32], sf[kOuterThreads / 32];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sr[w] = rr;
+        sf[w] = ff;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < kOuterThreads / 32; ++q) {
+            a += sr[q];
+            b += sf[q];
+        }
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = b;
+    }
+}
+
 constexpr int kReduceThreads = 1024;
 
 __global__ void __launch_bounds__(kReduceThreads) reduce_norms_kernel(const double* __restrict__ partials, int nblocks,
@@ -449,6 +496,50 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_norms_kernel(const doub
     if (threadIdx.x == 0) {
         out[0] = sa[0];
         out[1] = sb[0];
+    }
+}
+
+// Sums the partial norms in a fixed order and decides whether the defect
+// correction goes on: continue = refine && rel > tol && it < max_it && rel
+// finite.  first: this is the residual after FMG (sets the denominator
+// ||coef*rhs||, or 1 when it is 0, and it = 0).  Inside a graph the decision
+// drives the WHILE node through `handle`.
+template <bool GRAPH>
+__global__ void __launch_bounds__(kReduceThreads)
+decide_kernel(const double* __restrict__ partials, int nblocks, SolveState* __restrict__ st, double tol, int max_it,
+              int first, int refine, cudaGraphConditionalHandle handle)
+{
+    double a = 0.0, b = 0.0;
+    for (int t = threadIdx.x; t < nblocks; t += kReduceThreads) {
+        a += partials[2 * t];
+        b += partials[2 * t + 1];
+    }
+    __shared__ double sa[kReduceThreads], sb[kReduceThreads];
+    sa[threadIdx.x] = a;
+    sb[threadIdx.x] = b;
+    __syncthreads();
+    for (int s = kReduceThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sa[threadIdx.x] += sa[threadIdx.x + s];
+            sb[threadIdx.x] += sb[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (first) {
+            st->denom = sb[0] > 0.0 ? sqrt(sb[0]) : 1.0;
+            st->it = 0;
+        } else {
+            st->it += 1;
+        }
+        const double rel = sqrt(sa[0]) / st->denom;
+        if (first) st->rel0 = rel;
+        st->rel = rel;
+        const bool finite = isfinite(rel);
+        st->converged = (finite && (!refine || rel <= tol)) ? 1 : 0;
+        const int cont = (refine && finite && rel > tol && st->it < max_it) ? 1 : 0;
+        st->cont = cont;
+        if (GRAPH) cudaGraphSetConditional(handle, (unsigned)cont);
     }
 }
 
@@ -553,6 +644,39 @@ int launch_residual_outer(const double* u, const double* rhs, double coef, int n
     return residual_outer_blocks(n);
 }
 
+int residual_rows_blocks(int n)
+{
+    const int rows = (n - 1) * (n - 1);
+    return rows < kResidMaxBlocks ? rows : kResidMaxBlocks;
+}
+
+template <typename T>
+int launch_residual_rows(const double* u, const double* rhs, double coef, int n, double h, T* r, const LevelView& v,
+                         double* partials, cudaStream_t s)
+{
+    const int nb = residual_rows_blocks(n);
+    residual_rows_kernel<T><<<nb, kOuterThreads, 0, s>>>(u, rhs, coef, n, 1.0 / (h * h), r, v, partials);
+    return nb;
+}
+
+void launch_decide(const double* partials, int nblocks, SolveState* st, double tol, int max_it, bool first,
+                   bool refine, const cudaGraphConditionalHandle* handle, cudaStream_t s)
+{
+    if (handle)
+        decide_kernel<true><<<1, kReduceThreads, 0, s>>>(partials, nblocks, st, tol, max_it, first, refine, *handle);
+    else
+        decide_kernel<false><<<1, kReduceThreads, 0, s>>>(partials, nblocks, st, tol, max_it, first, refine, 0);
+}
+
+cudaError_t prepare_kernels()
+{
+    cudaError_t e = cudaFuncSetAttribute(coarse_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)coarse_smem_bytes<float>(kCoarseN));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(coarse_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)coarse_smem_bytes<double>(kCoarseN));
+}
+
 void launch_reduce_norms(const double* partials, int nblocks, double* out, cudaStream_t s)
 {
     reduce_norms_kernel<<<1, kReduceThreads, 0, s>>>(partials, nblocks, out);
@@ -570,7 +694,9 @@ void launch_reduce_norms(const double* partials, int nblocks, double* out, cudaS
     template void launch_convert_rhs<T>(const double*, double, int, T*, const LevelView&, cudaStream_t);              \
     template void launch_assign_outer<T>(double*, int, const T*, const LevelView&, bool, cudaStream_t);               \
     template int launch_residual_outer<T>(const double*, const double*, double, int, double, T*, const LevelView&,    \
-                                          double*, cudaStream_t);
+                                          double*, cudaStream_t);                                                      \
+    template int launch_residual_rows<T>(const double*, const double*, double, int, double, T*, const LevelView&,     \
+                                         double*, cudaStream_t);
 
 QUMOND_INSTANTIATE(float)
 QUMOND_INSTANTIATE(double)

@@ -71,6 +71,40 @@ template <typename T> int launch_residual_outer(const double* u, const double* r
 void launch_reduce_norms(const double* partials, int nblocks, double* out, cudaStream_t s);
 int residual_outer_blocks(int n);
 
+// Residual with a fixed number of blocks (residual_rows_blocks(n) partial sums).
+template <typename T> int launch_residual_rows(const double* u, const double* rhs, double coef, int n, double h, T* r,
+                                               const LevelView& v, double* partials, cudaStream_t s);
+int residual_rows_blocks(int n);
+
+// Device-side state of a defect-correction loop.
+struct SolveState {
+    double denom;  // ||coef*rhs||_2 (1 when zero)
+    double rel0;   // relative residual after FMG / of the warm start
+    double rel;    // latest relative residual
+    int it;        // V-cycles made after FMG
+    int cont;      // 1: another V-cycle is needed
+    int converged; // 1: rel <= tol (or no tolerance) and finite
+    int scale_exp; // fixed-point outer loop: U = u * 2^scale_exp
+};
+// Reduces the partial norms and decides whether to continue; with a
+// non-null handle it also sets the graph's WHILE condition.
+void launch_decide(const double* partials, int nblocks, SolveState* st, double tol, int max_it, bool first,
+                   bool refine, const cudaGraphConditionalHandle* handle, cudaStream_t s);
+// Sets kernel attributes (shared memory of the coarse-grid kernel); call
+// before any stream capture.
+cudaError_t prepare_kernels();
+
+// --- fixed-point defect correction (fixed_outer.cu) ---------------------------
+void launch_fixed_scale(const float* e, const LevelView& v, const double* u64, int n, bool from_u64, unsigned* maxbits,
+                        SolveState* st, cudaStream_t s);
+void launch_fixed_init(const float* e, const LevelView& v, const double* u64, const double* rhs, double coef, double h,
+                       int n, bool from_u64, const SolveState* st, int64_t* U, int64_t* F, cudaStream_t s);
+int fixed_residual_blocks(int n);
+int launch_fixed_residual(const int64_t* U, const int64_t* F, int n, double h, const SolveState* st, bool want_f,
+                          float* r, const LevelView& v, double* partials, cudaStream_t s);
+void launch_fixed_update(int64_t* U, const float* e, const LevelView& v, int n, const SolveState* st, cudaStream_t s);
+void launch_fixed_output(const int64_t* U, double* u, int n, const SolveState* st, cudaStream_t s);
+
 // --- grid kernels (grid_kernels.cu) ------------------------------------------
 void launch_cic_deposit(const double* x, const double* y, const double* z, const double* m, long long np, int n,
                         double xlo, double ylo, double zlo, double inv_h, double two_shift, int64_t* q,

@@ -30,6 +30,7 @@ QUMOND_ERR_OUT_OF_MEMORY = 5
 
 QUMOND_PREC_FP64 = 0
 QUMOND_PREC_MIXED = 1
+QUMOND_PREC_MIXED_FIXED = 2
 QUMOND_BC_ZERO = 0
 QUMOND_BC_GIVEN = 1
 
@@ -60,6 +61,7 @@ class qumond_params(ctypes.Structure):
         ("deposit_shift", ctypes.c_int),
         ("rc_box_frac", ctypes.c_double),
         ("box_ratio", ctypes.c_int),
+        ("use_graphs", ctypes.c_int),
     ]
 
 

@@ -120,7 +120,7 @@ def test_fp64_extra_vcycles_match_oracle(q, ora, n):
 
 
 @pytest.mark.parametrize("n", [16, 64, 128])
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_tolerance_mode_matches_oracle(q, ora, n, prec):
     x, y, z = an.node_coords(n, 4000.0)
     f = np.exp(-(x * x + y * y + 4 * z * z) / 2e5) * 0.05
@@ -133,7 +133,9 @@ def test_tolerance_mode_matches_oracle(q, ora, n, prec):
     # the reported residual is the true one
     r = ora.residual(n, 4000.0 / n, got, f)
     rel = np.sqrt(ora.interior_sumsq(n, r) / ora.interior_sumsq(n, f))
-    assert rel == pytest.approx(st.rel_residual, rel=1e-3, abs=1e-14)
+    # within 1%: the fixed-point mode reports the residual of its exact integer
+    # iterate, the oracle recomputes it from the FP64-rounded output
+    assert rel == pytest.approx(st.rel_residual, rel=1e-2, abs=1e-14)
 
 
 def test_coarsest_grid_special_case(q):
@@ -144,7 +146,8 @@ def test_coarsest_grid_special_case(q):
     assert got[13] == pytest.approx(-16.0 * 3.0 / 6.0, rel=1e-15)
 
 
-def test_warm_start_from_solution_needs_no_vcycle(q, ora):
+@pytest.mark.parametrize("prec", [1, 2])
+def test_warm_start_from_solution_needs_no_vcycle(q, ora, prec):
     n = 32
     x, y, z = an.node_coords(n, 2.0)
     f = np.cos(3 * x) * np.sin(2 * y) * z
@@ -153,7 +156,7 @@ def test_warm_start_from_solution_needs_no_vcycle(q, ora):
     ora.solve(n, 2.0 / n, want, f, tol=1e-13, max_vcycles=60)
     # warm start: pass the converged solution's interior as the initial guess
     ctx = q.Context(n=n, nboxes=1, L0=2.0, bc_mode=q.QUMOND_BC_GIVEN, warm_start=1, rel_tol=1e-10,
-                    max_vcycles=10)
+                    max_vcycles=10, precision=prec)
     u = to_dev(want.copy())
     st = ctx.qumond_solve_mond(0, to_dev(f), None, u, stats=True)
     assert st.vcycles == 0 and st.rel_residual_fmg < 1e-10
@@ -245,7 +248,7 @@ def _compare_pipelines(gpu, boxes, n, L0, nbins, rmax, phi_tol, vc_tol, ratio=2,
     assert np.max(np.abs(gpu["vc"] / vc_w - 1.0)) < vc_tol
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_kuzmin_check_config(q, ora, prec):
     # Kuzmin disk, M = 1e10, a = 2 kpc, 2e5 particles at z = 0; a 64^3 grid on
     # 40 kpc inside a 64^3 boundary box of 160 kpc; tolerance 1e-10; 50 bins
@@ -280,6 +283,36 @@ def test_deterministic(q):
         for x, y in zip(a[key], b[key]):
             assert np.array_equal(x, y)
     assert np.array_equal(a["vc"], b["vc"])
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_graph_and_one_by_one_launches_agree(q, prec):
+    # each solve as one CUDA graph (device-side tolerance loop) or as kernels
+    # launched one by one with host-side residual checks: the same kernels in
+    # the same order, so the same bits
+    p = synth.two_component_disk(50_000, seed=5, rmax=54000.0, zmax=54000.0)
+    a = gpu_pipeline(p, 64, 120000.0, 3, rel_tol=1e-10, max_vcycles=40, use_graphs=1, precision=prec)
+    b = gpu_pipeline(p, 64, 120000.0, 3, rel_tol=1e-10, max_vcycles=40, use_graphs=0, precision=prec)
+    for key in ("phiN", "phi"):
+        for x, y in zip(a[key], b[key]):
+            assert np.array_equal(x, y)
+    assert [s.vcycles for s in a["newton_stats"]] == [s.vcycles for s in b["newton_stats"]]
+    assert np.array_equal(a["vc"], b["vc"])
+
+
+def test_graph_paper_mode_and_relaunch(q, ora):
+    # paper mode (no residual checks) as a graph, launched twice on the same arrays
+    p = synth.two_component_disk(50_000, seed=6, rmax=54000.0, zmax=54000.0)
+    n, L0 = 32, 120000.0
+    ctx = q.Context(n=n, nboxes=1, L0=L0, precision=q.QUMOND_PREC_FP64, rel_tol=0.0)
+    pipe = q.Pipeline(ctx)
+    x, y, z, m = (to_dev(a) for a in (p.x, p.y, p.z, p.m))
+    for _ in range(2):
+        pipe.potentials(x, y, z, m)
+    torch.cuda.synchronize()
+    boxes = ora.pipeline(p, n, L0, 1)
+    assert rel_max(pipe.phiN[0].cpu().numpy(), boxes[0].phiN) < 1e-11
+    ctx.close()
 
 
 def test_invalid_arguments_rejected(q):
