@@ -126,55 +126,167 @@ __global__ void boundary_from_parent_kernel(const double* __restrict__ parent, d
 }
 
 // ---------------------------------------------------------------------------
-// QUMOND source by the face-flux difference.  Differences of the potential
-// are taken in FP64 (they carry the information); the gradient magnitude,
-// nu and the six fluxes are evaluated in FP32, which perturbs the solved
-// potential by ~1e-8 relative (FP64 arithmetic there is ~60x slower on this
-// GPU).  src = 0 on boundary nodes.
-constexpr int kSrcBX = 32, kSrcBY = 4;
+// QUMOND source by the face-flux difference (Section 2 step 3, Eq. 2).
+//
+// Precision: the differences of the potential carry the information and are
+// taken to ~48 bits; the gradient magnitude, nu and the fluxes are FP32
+// (which perturbs the solved potential by ~1e-8 relative).  FP64 arithmetic
+// and 64-bit conversions are ~60x slower than FP32 on this GPU, so each FP64
+// value is split once, with integer instructions, into an exact pair of FP32
+// numbers hi + lo (hi: the top 24 significant bits, lo: the next 24), and a
+// difference is (hi_a - hi_b) + (lo_a - lo_b).
+//
+// Layout: a CTA owns a 32 x 8 tile of (i, j) and walks k through a chunk of
+// planes.  Three consecutive planes of the tile plus a one-node halo sit in
+// shared memory as hi/lo pairs; every node computes the fluxes through its
+// +x, +y and +z faces once, and its source is the difference of its own
+// fluxes and those of its -x, -y, -z neighbours (the -z one carried over from
+// the previous plane).
+constexpr int kSrcTX = 32, kSrcTY = 8, kSrcKC = 16;
+constexpr int kSrcPX = kSrcTX + 2, kSrcPY = kSrcTY + 2;
 
-__global__ void __launch_bounds__(kSrcBX * kSrcBY)
+// x = hi + lo exactly up to the 48th significant bit, both FP32, integer ops
+// only.  |x| < 2^-126 gives (0, 0); lo is dropped below |x| < 2^-74.
+__device__ __forceinline__ void split_hi_lo(double x, float& hi, float& lo)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    const int E = (int)((b >> 52) & 0x7ffu);
+    if (E < 897) {
+        hi = 0.0f;
+        lo = 0.0f;
+        return;
+    }
+    if (E > 1150) {  // beyond FP32 range (or inf/nan): no split
+        hi = __double2float_rn(x);
+        lo = 0.0f;
+        return;
+    }
+    const unsigned long long M = b & 0xFFFFFFFFFFFFFull;
+    hi = __uint_as_float(sign | ((unsigned)(E - 896) << 23) | (unsigned)(M >> 29));
+    if (E < 949) {
+        lo = 0.0f;
+        return;
+    }
+    const float r = __uint2float_rn((unsigned)(M & 0x1FFFFFFFull));  // < 2^29
+    lo = __uint_as_float(sign | __float_as_uint(r * __uint_as_float((unsigned)(E - 948) << 23)));
+}
+
+// Exact FP32 -> FP64 with integer ops (subnormals flushed to zero).
+__device__ __forceinline__ double f32_to_f64(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0) return __longlong_as_double((long long)sign);
+    const unsigned long long ed = e == 255 ? 2047ull : (unsigned long long)(e + 896);
+    return __longlong_as_double((long long)(sign | (ed << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
+struct SrcPlanes {
+    float hi[3][kSrcPY][kSrcPX];
+    float lo[3][kSrcPY][kSrcPX];
+};
+
+// Phi(a) - Phi(b) for smem positions (plane, y, x).
+#define SRC_D(pa, ya, xa, pb, yb, xb)                                                                                  \
+    ((S.hi[pa][ya][xa] - S.hi[pb][yb][xb]) + (S.lo[pa][ya][xa] - S.lo[pb][yb][xb]))
+
+// Flux (times h) through the face from node P to node P + e_axis:
+// nu(|g|/a0) * (Phi(Q) - Phi(P)); |g| from the normal difference and the
+// means of the two nodes' transverse central differences.
+__device__ __forceinline__ float face_flux(float dn, float ta, float tb, float inv_h, float four_a0)
+{
+    const float gn = dn * inv_h;
+    const float q = 0.25f * inv_h;
+    const float g2 = gn * gn + (ta * q) * (ta * q) + (tb * q) * (tb * q);
+    if (!(g2 > 0.0f)) return 0.0f;
+    const float nu = 0.5f * (1.0f + sqrtf(1.0f + four_a0 * rsqrtf(g2)));
+    return nu * dn;
+}
+
+// Face fluxes with P at smem position (plane p, y, x).  pm/pp: planes below/above p.
+__device__ __forceinline__ float flux_x(const SrcPlanes& S, int pm, int p, int pp, int y, int x, float ih, float fa)
+{
+    const float dn = SRC_D(p, y, x + 1, p, y, x);
+    const float ty = SRC_D(p, y + 1, x, p, y - 1, x) + SRC_D(p, y + 1, x + 1, p, y - 1, x + 1);
+    const float tz = SRC_D(pp, y, x, pm, y, x) + SRC_D(pp, y, x + 1, pm, y, x + 1);
+    return face_flux(dn, ty, tz, ih, fa);
+}
+__device__ __forceinline__ float flux_y(const SrcPlanes& S, int pm, int p, int pp, int y, int x, float ih, float fa)
+{
+    const float dn = SRC_D(p, y + 1, x, p, y, x);
+    const float tx = SRC_D(p, y, x + 1, p, y, x - 1) + SRC_D(p, y + 1, x + 1, p, y + 1, x - 1);
+    const float tz = SRC_D(pp, y, x, pm, y, x) + SRC_D(pp, y + 1, x, pm, y + 1, x);
+    return face_flux(dn, tx, tz, ih, fa);
+}
+// face between plane p (P) and plane pp (Q = P + e_z)
+__device__ __forceinline__ float flux_z(const SrcPlanes& S, int p, int pp, int y, int x, float ih, float fa)
+{
+    const float dn = SRC_D(pp, y, x, p, y, x);
+    const float tx = SRC_D(p, y, x + 1, p, y, x - 1) + SRC_D(pp, y, x + 1, pp, y, x - 1);
+    const float ty = SRC_D(p, y + 1, x, p, y - 1, x) + SRC_D(pp, y + 1, x, pp, y - 1, x);
+    return face_flux(dn, tx, ty, ih, fa);
+}
+
+__global__ void __launch_bounds__(kSrcTX * kSrcTY)
 source_kernel(const double* __restrict__ phi, double* __restrict__ src, int n, float inv_h, float four_a0,
               float inv_h2)
 {
-    const int i = blockIdx.x * kSrcBX + threadIdx.x;
-    const int j = blockIdx.y * kSrcBY + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i > n || j > n) return;
-    const long long o = nat(n, i, j, k);
-    if (i == 0 || i == n || j == 0 || j == n || k == 0 || k == n) {
-        src[o] = 0.0;
-        return;
-    }
+    __shared__ SrcPlanes S;
+    __shared__ float Fx[kSrcTY][kSrcTX + 1];  // Fx[y][x + 1]: face (x, x+1), x = -1 .. 31
+    __shared__ float Fy[kSrcTY + 1][kSrcTX];  // Fy[y + 1][x]: face (y, y+1), y = -1 .. 7
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kSrcTX + tx;
+    const int i0 = blockIdx.x * kSrcTX, j0 = blockIdx.y * kSrcTY;
+    const int k0 = blockIdx.z * kSrcKC;
+    const int k1 = min(k0 + kSrcKC, n + 1);
     const long long P = n + 1;
-    const long long S[3] = {1, P, P * P};
-    const float q4 = 0.25f * inv_h;
-    float acc = 0.0f;
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            const long long oP = side == 0 ? o : o - S[ax];
-            const long long oQ = oP + S[ax];
-            const float dn = (float)(phi[oQ] - phi[oP]);
-            const float gn = dn * inv_h;
-            float g2 = gn * gn;
-#pragma unroll
-            for (int bx = 0; bx < 3; ++bx) {
-                if (bx == ax) continue;
-                const float cP = (float)(phi[oP + S[bx]] - phi[oP - S[bx]]);
-                const float cQ = (float)(phi[oQ + S[bx]] - phi[oQ - S[bx]]);
-                const float gt = (cP + cQ) * q4;
-                g2 += gt * gt;
-            }
-            if (g2 > 0.0f) {
-                const float nu = 0.5f * (1.0f + sqrtf(1.0f + four_a0 * rsqrtf(g2)));
-                acc += side == 0 ? nu * dn : -nu * dn;
-            }
+
+    // plane k of the tile (with halo) into slot `slot`; outside the grid -> 0
+    auto load_plane = [&](int k, int slot) {
+        for (int t = tid; t < kSrcPX * kSrcPY; t += kSrcTX * kSrcTY) {
+            const int lx = t % kSrcPX, ly = t / kSrcPX;
+            const int gi = i0 - 1 + lx, gj = j0 - 1 + ly;
+            float h = 0.0f, l = 0.0f;
+            if (k >= 0 && k <= n && gi >= 0 && gi <= n && gj >= 0 && gj <= n)
+                split_hi_lo(phi[gi + P * (gj + P * (long long)k)], h, l);
+            S.hi[slot][ly][lx] = h;
+            S.lo[slot][ly][lx] = l;
         }
+    };
+
+    const int x = tx + 1, y = ty + 1;
+    const int i = i0 + tx, j = j0 + ty;
+    load_plane(k0 - 1, 0);
+    load_plane(k0, 1);
+    __syncthreads();
+    // flux through the -z face of plane k0 (between k0-1 and k0)
+    float fz_prev = flux_z(S, 0, 1, y, x, inv_h, four_a0);
+    int pm = 0, pc = 1, pp = 2;  // slots of planes k-1, k, k+1
+    for (int k = k0; k < k1; ++k) {
+        __syncthreads();  // everyone is done with the slot about to be overwritten
+        load_plane(k + 1, pp);
+        __syncthreads();
+        Fx[ty][tx + 1] = flux_x(S, pm, pc, pp, y, x, inv_h, four_a0);
+        if (tx == 0) Fx[ty][0] = flux_x(S, pm, pc, pp, y, x - 1, inv_h, four_a0);
+        Fy[ty + 1][tx] = flux_y(S, pm, pc, pp, y, x, inv_h, four_a0);
+        if (ty == 0) Fy[0][tx] = flux_y(S, pm, pc, pp, y - 1, x, inv_h, four_a0);
+        const float fz = flux_z(S, pc, pp, y, x, inv_h, four_a0);
+        __syncthreads();
+        if (i <= n && j <= n) {
+            const bool inner = i > 0 && i < n && j > 0 && j < n && k > 0 && k < n;
+            const float v = inner ? ((Fx[ty][tx + 1] - Fx[ty][tx]) + (Fy[ty + 1][tx] - Fy[ty][tx]) + (fz - fz_prev)) * inv_h2
+                                  : 0.0f;
+            src[i + P * (j + P * (long long)k)] = f32_to_f64(v);
+        }
+        fz_prev = fz;
+        const int t = pm;
+        pm = pc;
+        pc = pp;
+        pp = t;
     }
-    src[o] = (double)(acc * inv_h2);
 }
+#undef SRC_D
 
 // ---------------------------------------------------------------------------
 // Forces at points: finest box whose containing cell has 8 interior corners.
@@ -307,8 +419,8 @@ void launch_boundary_from_parent(const double* parent, double* u, int n, int rat
 
 void launch_source(const double* phi, double* src, int n, double h, double a0, cudaStream_t s)
 {
-    const dim3 grid(cdiv(n + 1, kSrcBX), cdiv(n + 1, kSrcBY), (unsigned)(n + 1));
-    source_kernel<<<grid, dim3(kSrcBX, kSrcBY), 0, s>>>(phi, src, n, (float)(1.0 / h), (float)(4.0 * a0),
+    const dim3 grid(cdiv(n + 1, kSrcTX), cdiv(n + 1, kSrcTY), cdiv(n + 1, kSrcKC));
+    source_kernel<<<grid, dim3(kSrcTX, kSrcTY), 0, s>>>(phi, src, n, (float)(1.0 / h), (float)(4.0 * a0),
                                                         (float)(1.0 / (h * h)));
 }
 

@@ -429,9 +429,10 @@ residual_outer_kernel(const double* __restrict__ u, const double* __restrict__ r
 // (so only a few thousand partial sums need reducing).
 constexpr int kResidBlocksPerSM = 16;
 constexpr int kResidMaxBlocks = 152 * kResidBlocksPerSM;
+constexpr int kRowThreads = 128;
 
 template <typename T>
-__global__ void __launch_bounds__(kOuterThreads)
+__global__ void __launch_bounds__(kRowThreads)
 residual_rows_kernel(const double* __restrict__ u, const double* __restrict__ rhs, double coef, int n, double ih2,
                      T* __restrict__ r, LevelView v, double* __restrict__ partials)
 {
@@ -440,7 +441,7 @@ residual_rows_kernel(const double* __restrict__ u, const double* __restrict__ rh
     double rr = 0.0, ff = 0.0;
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
         const int j = row % (n - 1) + 1, k = row / (n - 1) + 1;
-        for (int i = threadIdx.x + 1; i < n; i += kOuterThreads) {
+        for (int i = threadIdx.x + 1; i < n; i += kRowThreads) {
             const long long o = nat(n, i, j, k);
             const double s = (u[o + 1] + u[o - 1]) + (u[o + P] + u[o - P]) + (u[o + Q] + u[o - Q]);
             const double fv = coef * rhs[o];
@@ -454,7 +455,7 @@ residual_rows_kernel(const double* __restrict__ u, const double* __restrict__ rh
         rr += __shfl_down_sync(0xffffffffu, rr, off);
         ff += __shfl_down_sync(0xffffffffu, ff, off);
     }
-    __shared__ double sr[kOuterThreads / 32], sf[kOuterThreads / 32];
+    __shared__ double sr[kRowThreads / 32], sf[kRowThreads / 32];
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
         sr[w] = rr;
@@ -463,7 +464,7 @@ residual_rows_kernel(const double* __restrict__ u, const double* __restrict__ rh
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0.0, b = 0.0;
-        for (int q = 0; q < kOuterThreads / 32; ++q) {
+        for (int q = 0; q < kRowThreads / 32; ++q) {
             a += sr[q];
             b += sf[q];
         }
@@ -514,16 +515,27 @@ decide_kernel(const double* __restrict__ partials, int nblocks, SolveState* __re
         a += partials[2 * t];
         b += partials[2 * t + 1];
     }
-    __shared__ double sa[kReduceThreads], sb[kReduceThreads];
-    sa[threadIdx.x] = a;
-    sb[threadIdx.x] = b;
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, off);
+        b += __shfl_down_sync(0xffffffffu, b, off);
+    }
+    __shared__ double sa[kReduceThreads / 32], sb[kReduceThreads / 32];
+    if ((threadIdx.x & 31) == 0) {
+        sa[threadIdx.x >> 5] = a;
+        sb[threadIdx.x >> 5] = b;
+    }
     __syncthreads();
-    for (int s = kReduceThreads / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            sa[threadIdx.x] += sa[threadIdx.x + s];
-            sb[threadIdx.x] += sb[threadIdx.x + s];
+    if (threadIdx.x < 32) {
+        a = sa[threadIdx.x];
+        b = sb[threadIdx.x];
+        for (int off = 16; off > 0; off >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, off);
+            b += __shfl_down_sync(0xffffffffu, b, off);
         }
-        __syncthreads();
+        if (threadIdx.x == 0) {
+            sa[0] = a;
+            sb[0] = b;
+        }
     }
     if (threadIdx.x == 0) {
         if (first) {
@@ -655,7 +667,7 @@ int launch_residual_rows(const double* u, const double* rhs, double coef, int n,
                          double* partials, cudaStream_t s)
 {
     const int nb = residual_rows_blocks(n);
-    residual_rows_kernel<T><<<nb, kOuterThreads, 0, s>>>(u, rhs, coef, n, 1.0 / (h * h), r, v, partials);
+    residual_rows_kernel<T><<<nb, kRowThreads, 0, s>>>(u, rhs, coef, n, 1.0 / (h * h), r, v, partials);
     return nb;
 }
 
