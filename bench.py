@@ -291,28 +291,37 @@ def run_ours(args):
     e2e_ms = max_over_ranks(e0.elapsed_time(e1))
     e2e_value = ws * args.steps / (e2e_ms / 1000.0)
 
-    # --- plain FP64 full multigrid at the same final residual ------------------------------
+    # --- the other arithmetic modes at the same final residual -------------------------
+    def time_mode(precision, nsteps):
+        cx, pp = new_pipeline(precision)
+        step(pp)
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record()
+        for _ in range(nsteps):
+            step(pp)
+        f1.record()
+        barrier()
+        pms = max_over_ranks(f0.elapsed_time(f1)) / nsteps
+        cx.close()
+        return pms
+
     plain = None
+    fp64_dc = None
     if not args.no_plain and prec != q.QUMOND_PREC_FP64:
         ctx.close()
         del pipe
         torch.cuda.empty_cache()
-        ctx64, pipe64 = new_pipeline(q.QUMOND_PREC_FP64)
-        step(pipe64)
-        barrier()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
         nplain = max(1, min(args.steps, 3))
-        f0.record()
-        for _ in range(nplain):
-            step(pipe64)
-        f1.record()
-        barrier()
-        pms = max_over_ranks(f0.elapsed_time(f1)) / nplain
+        pms = time_mode(q.QUMOND_PREC_FP64, nplain)
         plain = {"value": ws * 1000.0 / pms, "unit": UNIT, "ms_per_step": pms, "steps": nplain,
-                 "precision": "FP64 smoothing, residual and correction (same kernels, same tolerance)",
+                 "precision": PRECISION_NAMES["fp64"] + " (same kernels, same tolerance)",
                  "speedup_of_value": value / (ws * 1000.0 / pms)}
-        ctx64.close()
+        if prec == q.QUMOND_PREC_MIXED_FIXED:
+            mms = time_mode(q.QUMOND_PREC_MIXED, nplain)
+            fp64_dc = {"value": ws * 1000.0 / mms, "unit": UNIT, "ms_per_step": mms, "steps": nplain,
+                       "precision": PRECISION_NAMES["mixed"]}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -335,6 +344,7 @@ def run_ours(args):
             "gpu_launches_per_step": launches / args.steps,
             "vcycles_after_fmg_per_solve": vcycles,
             "plain_fmg": plain,
+            "fp32_smoothing_fp64_defect_correction": fp64_dc,
             "kernels": kernels,
             "clocks": clk,
             "cpu_baseline": cpu,
@@ -407,7 +417,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fixed", "mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["fixed", "mixed", "fp64"], default="fixed")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 FMG comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip timing the oracle on the host")
     args = ap.parse_args()
