@@ -140,26 +140,18 @@ def measured_peaks():
         return None
 
 
-def kernel_source_hash():
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1201_3185_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".h", ".cuh")):
-            h.update(open(os.path.join(csrc, name), "rb").read())
-    return h.hexdigest()[:16]
-
-
 def ncu_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None when the summary is missing or the kernels changed since."""
+    None when there is none or the kernel's source file changed since."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
     except (OSError, ValueError):
         return None
-    if t.get("kernel_source_hash") != kernel_source_hash():
-        return None
     k = t.get("kernels", {}).get(kernel)
     if not k:
+        return None
+    src = os.path.join(ROOT, k["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != k.get("source_hash"):
         return None
     return k.get("dram_bytes_per_launch_full_size")
 
@@ -197,7 +189,8 @@ def run_ours(args):
 
     def new_pipeline(precision):
         ctx = q.Context(n=w["n"], nboxes=w["nboxes"], L0=w["L0"], rel_tol=w["rel_tol"], max_vcycles=w["max_vcycles"],
-                        ncycle=w["ncycle"], npre=w["npre"], npost=w["npost"], precision=precision)
+                        ncycle=w["ncycle"], npre=w["npre"], npost=w["npost"], precision=precision,
+                        use_graphs=0 if args.no_graphs else 1)
         return ctx, q.Pipeline(ctx, dev)
 
     ctx, pipe = new_pipeline(prec)
@@ -215,7 +208,27 @@ def run_ours(args):
     vcycles = [s.vcycles for s in st_check[0] + st_check[1]]
     torch.cuda.synchronize()
 
-    # --- timed region: inputs resident in HBM; each solve is one CUDA graph ---------------
+    # --- per-kernel breakdown: the same steps with every kernel launched on its own and
+    # bracketed by CUDA events on its stream (host launch latency can inflate short kernels) ---
+    ctx.qumond_trace_read(reset=True)
+    ctx.qumond_trace_timing(True)
+    barrier()
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    r0.record()
+    for _ in range(args.steps):
+        step()
+    r1.record()
+    barrier()
+    replay_ms = r0.elapsed_time(r1) / args.steps
+    kstats, _, _ = ctx.qumond_trace_read(reset=True)
+    ctx.qumond_trace_timing(False)
+    dom_name = max(kstats.values(), key=lambda k: k.ms).name
+
+    # --- timed region: inputs resident in HBM; each solve is one CUDA graph, whose FMG
+    # part carries event-record nodes around the dominant kernel class -------------------
+    ctx.qumond_trace_timing(True, only=dom_name)
+    step()  # captures the instrumented graphs
     ctx.qumond_trace_read(reset=True)
     clocks = ClockSampler(local)
     barrier()
@@ -229,38 +242,26 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     ms_total = max_over_ranks(s0.elapsed_time(s1))
-    _, launches, cell_updates = ctx.qumond_trace_read(reset=True)
+    live, launches, cell_updates = ctx.qumond_trace_read(reset=True)
+    ctx.qumond_trace_timing(False)
     ms_step = ms_total / args.steps
     value = ws * args.steps / (ms_total / 1000.0)
 
-    # --- per-kernel CUDA-event timing: the same steps replayed with every kernel
-    # launched one by one and bracketed by events on its stream -------------------------
-    ctx.qumond_trace_timing(True)
-    barrier()
-    r0 = torch.cuda.Event(enable_timing=True)
-    r1 = torch.cuda.Event(enable_timing=True)
-    r0.record()
-    for _ in range(args.steps):
-        step()
-    r1.record()
-    barrier()
-    replay_ms = r0.elapsed_time(r1) / args.steps
-    kstats, _, _ = ctx.qumond_trace_read(reset=True)
-    ctx.qumond_trace_timing(False)
-
-    # dominant kernel and its roofline
-    dom = max(kstats.values(), key=lambda k: k.ms)
+    # dominant kernel and its roofline (live: event nodes inside the timed graphs)
+    dom = live[dom_name]
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    achieved = (dom.bytes / dom.launches) / (dom.ms / dom.timed) / 1e6 if dom.timed else None  # GB/s
+    bytes_per_launch = dom.bytes / max(dom.launches, 1)
+    avg_ms = dom.ms / dom.timed if dom.timed else None
+    achieved = bytes_per_launch / avg_ms / 1e6 if avg_ms else None  # GB/s
     roofline = {"bound": "hbm", "kernel": dom.name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None,
                 "traffic": ncu_traffic(dom.name),
-                "algorithmic_bytes_per_launch": dom.bytes / max(dom.launches, 1),
-                "avg_launch_ms": dom.ms / max(dom.timed, 1),
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "avg_launch_ms": avg_ms, "timed_launches": dom.timed,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s",
-                "timing": "CUDA events around each launch on its stream, over a replay of the timed steps with "
-                          "kernels launched one by one (the timed region runs each solve as one CUDA graph)"}
+                "timing": "CUDA event-record nodes around this kernel class's launches in the FMG part of each "
+                          "solve's graph, read after each solve of the timed region"}
     total_kernel_ms = sum(k.ms for k in kstats.values())
     total_bytes = sum(k.bytes for k in kstats.values())
     kernels = {k.name: {"launches_per_step": k.launches / args.steps, "ms_per_step": k.ms / args.steps,
@@ -336,7 +337,7 @@ def run_ours(args):
             "data": "synthetic", "config": workload_config(PRECISION_NAMES[args.precision]),
             "cell_updates_per_s": ws * cell_updates / (ms_total / 1000.0),
             "hbm_algorithmic_GBps_all_kernels": total_bytes / (total_kernel_ms * 1e6) if total_kernel_ms else None,
-            "kernel_ms_per_step": total_kernel_ms / args.steps,
+            "kernel_ms_per_step_one_by_one": total_kernel_ms / args.steps,
             "replay_ms_per_step_one_by_one": replay_ms,
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -411,6 +412,43 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(args):
+    """One box of the workload solved once, then a single V-cycle of defect
+    correction from that solution with every kernel launched on its own,
+    between cudaProfilerStart and cudaProfilerStop: the launches ncu sees
+    with --profile-from-start off are the finest-level ones first."""
+    import torch
+
+    import paper_1201_3185_gb300 as q
+    w = WORKLOAD
+    prec = {"fp64": q.QUMOND_PREC_FP64, "mixed": q.QUMOND_PREC_MIXED, "fixed": q.QUMOND_PREC_MIXED_FIXED}[args.precision]
+    p = make_particles()
+    dev = torch.device("cuda", 0)
+    x, y, z, m = (torch.from_numpy(a).to(dev) for a in (p.x, p.y, p.z, p.m))
+    common = dict(n=w["n"], nboxes=1, L0=w["L0"], npre=w["npre"], npost=w["npost"], ncycle=w["ncycle"],
+                  precision=prec, use_graphs=0)
+    ctx = q.Context(rel_tol=w["rel_tol"], max_vcycles=w["max_vcycles"], **common)
+    nodes = ctx.nodes
+    qf = torch.empty(nodes, dtype=torch.int64, device=dev)
+    rho = torch.empty(nodes, dtype=torch.float64, device=dev)
+    phi = torch.zeros(nodes, dtype=torch.float64, device=dev)
+    ctx.qumond_deposit(0, x, y, z, m, qf, rho)
+    ctx.qumond_solve_newton(0, rho, None, phi)
+    ctx2 = q.Context(rel_tol=1e-300, max_vcycles=1, warm_start=1, **common)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    try:
+        ctx2.qumond_solve_newton(0, rho, None, phi)
+    except q.NotConverged:
+        pass
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    ctx.close()
+    ctx2.close()
+    print(json.dumps({"profile_case": "box 0 of the workload, one warm-start V-cycle", "n": w["n"],
+                      "precision": args.precision}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -420,10 +458,15 @@ def main():
     ap.add_argument("--precision", choices=["fixed", "mixed", "fp64"], default="fixed")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 FMG comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip timing the oracle on the host")
+    ap.add_argument("--no-graphs", action="store_true", help="launch kernels one by one (for profilers)")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run one profiled V-cycle on one box instead of the benchmark (for ncu)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.profile_case:
+        profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -216,10 +216,18 @@ typedef struct {
 /* Number of kernel classes (size of the array qumond_trace_read fills). */
 QUMOND_API int qumond_trace_classes(void);
 
-/* Start (on != 0) or stop bracketing every launch with CUDA events on its
-   stream (at most 32768 launches per start; later ones are counted but not
-   timed).  Starting discards earlier timings.  Counters are always kept. */
-QUMOND_API qumond_status qumond_trace_timing(qumond_ctx* ctx, int on);
+/* Start (on != 0) or stop timing kernels with CUDA events on their stream.
+   only_class = -1: every launch is bracketed and the solves launch their
+   kernels one by one (graphs off); at most 32768 launches per start are
+   timed, later ones are only counted.
+   only_class = k (an index into qumond_trace_read's array): only launches of
+   class k are bracketed, and the solves keep running as CUDA graphs: their
+   graphs are captured with event-record nodes around the class-k launches of
+   the preamble (boundary values, FMG, first residual check; a conditional
+   loop body cannot hold event nodes), and each solve with residual checks
+   adds those events' times after its final synchronisation.
+   Starting discards earlier timings.  Counters are always kept. */
+QUMOND_API qumond_status qumond_trace_timing(qumond_ctx* ctx, int on, int only_class);
 
 /* Copies the per-class statistics into out[0 .. min(cap, classes)-1] and the
    totals into *totals (either may be NULL).  Synchronises the device when

@@ -50,7 +50,11 @@ struct Tracer {
     double ms[K_COUNT] = {};
     long long timed[K_COUNT] = {};
     long long cell_updates = 0;
-    Phase* sink = nullptr;  // while capturing: counts go here, nothing is timed
+    int only = -1;          // timing on: -1 every class (launches one by one), else this class only
+    Phase* sink = nullptr;  // while capturing: counts go here
+    // while capturing a preamble with timing on: event pairs recorded into the graph
+    std::vector<cudaEvent_t>* cap_events = nullptr;
+    std::vector<int>* cap_kinds = nullptr;
 
     void add(const Phase& ph, long long times)
     {
@@ -76,6 +80,9 @@ struct SolveGraph {
     cudaGraphExec_t exec = nullptr;
     Phase pre, body;
     unsigned long long last_use = 0;
+    int timed_class = -1;             // class bracketed by event nodes in the preamble, or -1
+    std::vector<cudaEvent_t> events;  // 2 per bracketed launch
+    std::vector<int> event_kinds;
 };
 constexpr size_t kMaxGraphs = 32;
 
@@ -197,13 +204,24 @@ void run(qumond_ctx* c, int kind, double bytes, cudaStream_t s, Launch&& launch)
 {
     Tracer& t = c->tr;
     if (t.sink) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        const bool rec = t.cap_events && kind == t.only && cudaEventCreate(&e0) == cudaSuccess &&
+                         cudaEventCreate(&e1) == cudaSuccess;
+        // "external" records become event-record nodes of the captured graph
+        if (rec) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
         launch();
+        if (rec) {
+            cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+            t.cap_events->push_back(e0);
+            t.cap_events->push_back(e1);
+            t.cap_kinds->push_back(kind);
+        }
         t.sink->launches[kind] += 1;
         t.sink->bytes[kind] += bytes;
         return;
     }
     const size_t slot = t.kind_of.size();
-    const bool rec = t.on && slot < (size_t)kMaxTimed;
+    const bool rec = t.on && (t.only < 0 || kind == t.only) && slot < (size_t)kMaxTimed;
     if (rec) cudaEventRecord(t.ev[2 * slot], s);
     launch();
     if (rec) {
@@ -415,8 +433,10 @@ cudaError_t enqueue_body(qumond_ctx* c, int box, const double* rhs, double coef,
 SolveGraph* find_graph(qumond_ctx* c, int kind, int box, const double* rhs, const double* parent, double* u,
                        bool norms)
 {
+    const int timed_class = c->tr.on ? c->tr.only : -1;
     for (auto& g : c->graphs)
-        if (g.kind == kind && g.box == box && g.rhs == rhs && g.parent == parent && g.u == u && g.norms == norms)
+        if (g.kind == kind && g.box == box && g.rhs == rhs && g.parent == parent && g.u == u && g.norms == norms &&
+            g.timed_class == timed_class)
             return &g;
     return nullptr;
 }
@@ -425,6 +445,9 @@ void destroy_graph(SolveGraph& g)
 {
     if (g.exec) cudaGraphExecDestroy(g.exec);
     if (g.graph) cudaGraphDestroy(g.graph);
+    for (cudaEvent_t e : g.events) cudaEventDestroy(e);
+    g.events.clear();
+    g.event_kinds.clear();
     g.exec = nullptr;
     g.graph = nullptr;
 }
@@ -453,9 +476,16 @@ qumond_status capture(qumond_ctx* c, int kind, int box, const double* rhs, doubl
                                                                 cudaStreamCaptureModeThreadLocal);
     if (err == cudaSuccess) {
         c->tr.sink = &g.pre;
+        g.timed_class = c->tr.on ? c->tr.only : -1;
+        if (g.timed_class >= 0) {
+            c->tr.cap_events = &g.events;
+            c->tr.cap_kinds = &g.event_kinds;
+        }
         cudaError_t e1 = enqueue_preamble<T>(c, box, rhs, coef, parent, u, norms, refine ? &handle : nullptr, cs);
         if (e1 == cudaSuccess && !refine && norms) e1 = enqueue_post<T>(c, u, cs);
         c->tr.sink = nullptr;
+        c->tr.cap_events = nullptr;
+        c->tr.cap_kinds = nullptr;
         if (refine && e1 == cudaSuccess) {
             cudaStreamCaptureStatus cst;
             const cudaGraphNode_t* deps = nullptr;
@@ -525,7 +555,7 @@ qumond_status solve_t(qumond_ctx* c, int kind, int box, const double* rhs, doubl
     const qumond_params& p = c->p;
     const bool refine = p.rel_tol > 0.0 && p.max_vcycles > 0;
     const bool norms = refine || st != nullptr;
-    if (p.use_graphs && !c->tr.on) {
+    if (p.use_graphs && !(c->tr.on && c->tr.only < 0)) {
         SolveGraph* g = find_graph(c, kind, box, rhs, parent, u, norms);
         if (!g) {
             if (c->graphs.size() >= kMaxGraphs) {
@@ -549,6 +579,12 @@ qumond_status solve_t(qumond_ctx* c, int kind, int box, const double* rhs, doubl
         CUDA_TRY(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, s), "state copy");
         CUDA_TRY(c, cudaStreamSynchronize(s), "solve");
         c->tr.add(g->body, c->h_state->it);
+        for (size_t q = 0; q < g->event_kinds.size(); ++q) {
+            float ms = 0.0f;
+            CUDA_TRY(c, cudaEventElapsedTime(&ms, g->events[2 * q], g->events[2 * q + 1]), "trace: elapsed");
+            c->tr.ms[g->event_kinds[q]] += ms;
+            c->tr.timed[g->event_kinds[q]] += 1;
+        }
     } else {
         CUDA_TRY(c, enqueue_preamble<T>(c, box, rhs, coef, parent, u, norms, nullptr, s), "solve launch");
         if (!norms) return QUMOND_OK;
@@ -825,11 +861,13 @@ qumond_status qumond_rotation_curve(qumond_ctx* c, const double* const* phi_boxe
 
 int qumond_trace_classes(void) { return K_COUNT; }
 
-qumond_status qumond_trace_timing(qumond_ctx* c, int on)
+qumond_status qumond_trace_timing(qumond_ctx* c, int on, int only_class)
 {
     if (!c) return QUMOND_ERR_INVALID_ARG;
     c->err.clear();
+    if (only_class < -1 || only_class >= K_COUNT) return fail(c, QUMOND_ERR_INVALID_ARG, "trace: no class %d", only_class);
     Tracer& t = c->tr;
+    t.only = only_class;
     if (on) {
         if (t.ev.empty()) {
             t.ev.resize(2 * (size_t)kMaxTimed);

@@ -110,7 +110,7 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
         "qumond_forces": (_I, [_P, _P, _P, _P, _P, _L, _P, _P, _P, _P]),
         "qumond_rotation_curve": (_I, [_P, _P, _I, _D, _I, _P, _P, _P]),
         "qumond_trace_classes": (_I, []),
-        "qumond_trace_timing": (_I, [_P, _I]),
+        "qumond_trace_timing": (_I, [_P, _I, _I]),
         "qumond_trace_read": (_I, [_P, ctypes.POINTER(qumond_kernel_stat), _I, ctypes.POINTER(qumond_counters), _I]),
         "qumond_solve_mond_noalloc": (_I, [ctypes.POINTER(qumond_params), _I, _P, _P, _P, ctypes.POINTER(qumond_stats),
                                            _P, ctypes.c_char_p, ctypes.c_size_t]),
@@ -306,8 +306,22 @@ class Context:
                                                _stream(stream)))
 
     # -- tracing ------------------------------------------------------------------
-    def qumond_trace_timing(self, on: bool):
-        self._check(_lib.qumond_trace_timing(self._ptr, 1 if on else 0))
+    def qumond_trace_timing(self, on: bool, only: str | None = None):
+        """Kernel timing with CUDA events; only=None times every launch (kernels
+        launched one by one), only=<class name> times that class inside the graphs."""
+        idx = -1
+        if only is not None:
+            names = self.trace_class_names()
+            if only not in names:
+                raise ValueError("unknown kernel class %r" % only)
+            idx = names.index(only)
+        self._check(_lib.qumond_trace_timing(self._ptr, 1 if on else 0, idx))
+
+    def trace_class_names(self):
+        k = _lib.qumond_trace_classes()
+        arr = (qumond_kernel_stat * k)()
+        self._check(_lib.qumond_trace_read(self._ptr, arr, k, None, 0))
+        return [a.name.decode() for a in arr]
 
     def qumond_trace_read(self, reset: bool = False):
         """Returns ({class name: KernelStat}, total launches, cell updates)."""
