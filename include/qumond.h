@@ -206,6 +206,7 @@ typedef struct {
     double ms;            /* summed CUDA-event time of the launches that were
                              bracketed while timing was on (0 otherwise) */
     int64_t timed;        /* how many launches were bracketed */
+    double timed_bytes;   /* algorithmic bytes of the bracketed launches */
 } qumond_kernel_stat;
 
 typedef struct {
@@ -221,11 +222,12 @@ QUMOND_API int qumond_trace_classes(void);
    kernels one by one (graphs off); at most 32768 launches per start are
    timed, later ones are only counted.
    only_class = k (an index into qumond_trace_read's array): only launches of
-   class k are bracketed, and the solves keep running as CUDA graphs: their
-   graphs are captured with event-record nodes around the class-k launches of
-   the preamble (boundary values, FMG, first residual check; a conditional
-   loop body cannot hold event nodes), and each solve with residual checks
-   adds those events' times after its final synchronisation.
+   class k are timed, and the solves keep running as CUDA graphs: their
+   graphs are captured with one pair of event-record nodes around each run of
+   consecutive class-k launches in the preamble (boundary values, FMG, first
+   residual check; a conditional loop body cannot hold event nodes), and each
+   solve with residual checks adds those intervals and the launches they
+   cover after its final synchronisation.
    Starting discards earlier timings.  Counters are always kept. */
 QUMOND_API qumond_status qumond_trace_timing(qumond_ctx* ctx, int on, int only_class);
 

@@ -19,6 +19,7 @@ struct Level {
     LevelView v;
     void* e = nullptr;  // iterate / correction, 2 colours
     void* f = nullptr;  // right-hand side, 2 colours
+    RbMaps maps;        // TMA descriptors of e (FP32 levels with n >= 64)
 };
 
 // Kernel classes of the tracer.
@@ -49,12 +50,18 @@ struct Tracer {
     double bytes[K_COUNT] = {};
     double ms[K_COUNT] = {};
     long long timed[K_COUNT] = {};
+    double timed_bytes[K_COUNT] = {};
+    std::vector<double> kind_bytes;  // per timed launch (one-by-one mode)
     long long cell_updates = 0;
     int only = -1;          // timing on: -1 every class (launches one by one), else this class only
     Phase* sink = nullptr;  // while capturing: counts go here
     // while capturing a preamble with timing on: event pairs recorded into the graph
     std::vector<cudaEvent_t>* cap_events = nullptr;
-    std::vector<int>* cap_kinds = nullptr;
+    std::vector<int>* cap_kinds = nullptr;  // per event pair: number of launches it brackets
+    std::vector<double>* cap_bytes = nullptr;  // per event pair: algorithmic bytes it brackets
+    bool run_open = false;
+    int run_count = 0;
+    double run_bytes = 0.0;
 
     void add(const Phase& ph, long long times)
     {
@@ -81,8 +88,9 @@ struct SolveGraph {
     Phase pre, body;
     unsigned long long last_use = 0;
     int timed_class = -1;             // class bracketed by event nodes in the preamble, or -1
-    std::vector<cudaEvent_t> events;  // 2 per bracketed launch
-    std::vector<int> event_kinds;
+    std::vector<cudaEvent_t> events;  // 2 per bracketed run of timed_class launches
+    std::vector<int> event_kinds;     // launches in each run
+    std::vector<double> event_bytes;  // algorithmic bytes of each run
 };
 constexpr size_t kMaxGraphs = 32;
 
@@ -103,6 +111,7 @@ struct qumond_ctx {
     int64_t* Ufix = nullptr;        // fixed-point master iterate (QUMOND_PREC_MIXED_FIXED)
     int64_t* Ffix = nullptr;        // fixed-point right-hand side
     unsigned* maxbits = nullptr;
+    int* fault = nullptr;           // set by kernels whose bounded waits ran out
     cudaStream_t cap_stream = nullptr;
     std::vector<SolveGraph> graphs;
     unsigned long long use_clock = 0;
@@ -197,6 +206,20 @@ inline double level_h(const qumond_ctx* c, int box, int l) { return box_h(c, box
 
 inline double cube(int n) { return (double)(n + 1) * (double)(n + 1) * (double)(n + 1); }
 
+inline void close_run(Tracer& t, cudaStream_t s)
+{
+    cudaEvent_t e1 = nullptr;
+    if (cudaEventCreate(&e1) == cudaSuccess) {
+        cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+        t.cap_events->push_back(e1);
+        t.cap_kinds->push_back(t.run_count);
+        t.cap_bytes->push_back(t.run_bytes);
+    } else {
+        t.cap_events->pop_back();
+    }
+    t.run_open = false;
+}
+
 // Every launch goes through here: counted, and bracketed by events while
 // timing is on.
 template <class Launch>
@@ -204,17 +227,27 @@ void run(qumond_ctx* c, int kind, double bytes, cudaStream_t s, Launch&& launch)
 {
     Tracer& t = c->tr;
     if (t.sink) {
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        const bool rec = t.cap_events && kind == t.only && cudaEventCreate(&e0) == cudaSuccess &&
-                         cudaEventCreate(&e1) == cudaSuccess;
-        // "external" records become event-record nodes of the captured graph
-        if (rec) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
+        // timing one class inside a captured graph: one event pair per run of
+        // consecutive launches of that class (event-record nodes cost several
+        // microseconds each, so they bracket runs rather than single launches)
+        if (t.cap_events) {
+            if (kind == t.only && !t.run_open) {
+                cudaEvent_t e0 = nullptr;
+                if (cudaEventCreate(&e0) == cudaSuccess) {
+                    cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);  // becomes an event-record node
+                    t.cap_events->push_back(e0);
+                    t.run_open = true;
+                    t.run_count = 0;
+                    t.run_bytes = 0.0;
+                }
+            } else if (kind != t.only && t.run_open) {
+                close_run(t, s);
+            }
+        }
         launch();
-        if (rec) {
-            cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
-            t.cap_events->push_back(e0);
-            t.cap_events->push_back(e1);
-            t.cap_kinds->push_back(kind);
+        if (t.run_open && kind == t.only) {
+            t.run_count += 1;
+            t.run_bytes += bytes;
         }
         t.sink->launches[kind] += 1;
         t.sink->bytes[kind] += bytes;
@@ -227,6 +260,7 @@ void run(qumond_ctx* c, int kind, double bytes, cudaStream_t s, Launch&& launch)
     if (rec) {
         cudaEventRecord(t.ev[2 * slot + 1], s);
         t.kind_of.push_back(kind);
+        t.kind_bytes.push_back(bytes);
     }
     t.launches[kind] += 1;
     t.bytes[kind] += bytes;
@@ -244,8 +278,13 @@ void rb(qumond_ctx* c, int l, int colour, bool zero, double h, cudaStream_t s)
     const int n = c->lev[l].v.n;
     const double nodes = cube(n);
     count_cells(c, ((long long)(n - 1) * (n - 1) * (n - 1) + (colour == 0 ? 1 : 0)) / 2);
-    run(c, l == c->L ? K_RB_FINEST : K_RB_COARSER, (zero ? 1.0 : 1.5) * nodes * sizeof(T), s,
-        [&] { launch_rb_half<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, colour, zero, h, s); });
+    run(c, l == c->L ? K_RB_FINEST : K_RB_COARSER, (zero ? 1.0 : 1.5) * nodes * sizeof(T), s, [&] {
+        if (sizeof(T) == sizeof(float) && !zero && c->lev[l].maps.ok)
+            launch_rb_half_tma(reinterpret_cast<float*>(E<T>(c, l)), reinterpret_cast<const float*>(F<T>(c, l)),
+                               c->lev[l].v, colour, c->lev[l].maps, h, c->fault, s);
+        else
+            launch_rb_half<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, colour, zero, h, s);
+    });
 }
 
 template <typename T>
@@ -359,7 +398,7 @@ void check(qumond_ctx* c, int box, const double* rhs, double coef, const double*
     }
     run(c, K_REDUCE, 16.0 * nb, s, [&] {
         launch_decide(c->partials, nb, c->d_state, p.rel_tol, p.max_vcycles, first, p.rel_tol > 0.0 && p.max_vcycles > 0,
-                      handle, s);
+                      handle, c->fault, s);
     });
 }
 
@@ -448,6 +487,7 @@ void destroy_graph(SolveGraph& g)
     for (cudaEvent_t e : g.events) cudaEventDestroy(e);
     g.events.clear();
     g.event_kinds.clear();
+    g.event_bytes.clear();
     g.exec = nullptr;
     g.graph = nullptr;
 }
@@ -480,12 +520,15 @@ qumond_status capture(qumond_ctx* c, int kind, int box, const double* rhs, doubl
         if (g.timed_class >= 0) {
             c->tr.cap_events = &g.events;
             c->tr.cap_kinds = &g.event_kinds;
+            c->tr.cap_bytes = &g.event_bytes;
         }
         cudaError_t e1 = enqueue_preamble<T>(c, box, rhs, coef, parent, u, norms, refine ? &handle : nullptr, cs);
         if (e1 == cudaSuccess && !refine && norms) e1 = enqueue_post<T>(c, u, cs);
+        if (c->tr.run_open) close_run(c->tr, cs);
         c->tr.sink = nullptr;
         c->tr.cap_events = nullptr;
         c->tr.cap_kinds = nullptr;
+        c->tr.cap_bytes = nullptr;
         if (refine && e1 == cudaSuccess) {
             cudaStreamCaptureStatus cst;
             const cudaGraphNode_t* deps = nullptr;
@@ -579,11 +622,12 @@ qumond_status solve_t(qumond_ctx* c, int kind, int box, const double* rhs, doubl
         CUDA_TRY(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, s), "state copy");
         CUDA_TRY(c, cudaStreamSynchronize(s), "solve");
         c->tr.add(g->body, c->h_state->it);
-        for (size_t q = 0; q < g->event_kinds.size(); ++q) {
+        for (size_t q = 0; q < g->event_kinds.size(); ++q) {  // one pair per run of g->timed_class launches
             float ms = 0.0f;
             CUDA_TRY(c, cudaEventElapsedTime(&ms, g->events[2 * q], g->events[2 * q + 1]), "trace: elapsed");
-            c->tr.ms[g->event_kinds[q]] += ms;
-            c->tr.timed[g->event_kinds[q]] += 1;
+            c->tr.ms[g->timed_class] += ms;
+            c->tr.timed[g->timed_class] += g->event_kinds[q];
+            c->tr.timed_bytes[g->timed_class] += g->event_bytes[q];
         }
     } else {
         CUDA_TRY(c, enqueue_preamble<T>(c, box, rhs, coef, parent, u, norms, nullptr, s), "solve launch");
@@ -598,6 +642,8 @@ qumond_status solve_t(qumond_ctx* c, int kind, int box, const double* rhs, doubl
         CUDA_TRY(c, enqueue_post<T>(c, u, s), "output launch");
     }
     const SolveState& r = *c->h_state;
+    if (r.fault)
+        return fail(c, QUMOND_ERR_TIMEOUT, "box %d: a kernel gave up waiting for its shared-memory pipeline", box);
     if (st) {
         st->vcycles = r.it;
         st->converged = r.converged;
@@ -722,7 +768,12 @@ qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
              cudaMallocHost(&c->h_state, sizeof(SolveState)) == cudaSuccess &&
              cudaMemset(c->d_state, 0, sizeof(SolveState)) == cudaSuccess &&
              cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaMalloc(&c->fault, sizeof(int)) == cudaSuccess && cudaMemset(c->fault, 0, sizeof(int)) == cudaSuccess &&
              prepare_kernels() == cudaSuccess;
+        if (ok && c->elt == sizeof(float))
+            for (int l = lc; l <= L; ++l)
+                make_rb_maps(static_cast<float*>(c->lev[l].e), static_cast<float*>(c->lev[l].f), c->lev[l].v,
+                             &c->lev[l].maps);
         if (ok && p->precision == QUMOND_PREC_MIXED_FIXED) {
             const size_t nn = (size_t)(p->n + 1) * (p->n + 1) * (p->n + 1);
             const int nfix = fixed_residual_blocks(p->n > 2 ? p->n : 2);
@@ -754,6 +805,7 @@ void qumond_destroy(qumond_ctx* c)
     if (c->d_norms) cudaFree(c->d_norms);
     if (c->h_norms) cudaFreeHost(c->h_norms);
     if (c->d_state) cudaFree(c->d_state);
+    if (c->fault) cudaFree(c->fault);
     if (c->Ufix) cudaFree(c->Ufix);
     if (c->Ffix) cudaFree(c->Ffix);
     if (c->maxbits) cudaFree(c->maxbits);
@@ -876,9 +928,11 @@ qumond_status qumond_trace_timing(qumond_ctx* c, int on, int only_class)
         }
         CUDA_TRY(c, cudaDeviceSynchronize(), "trace: start");
         t.kind_of.clear();
+        t.kind_bytes.clear();
         for (int k = 0; k < K_COUNT; ++k) {
             t.ms[k] = 0.0;
             t.timed[k] = 0;
+            t.timed_bytes[k] = 0.0;
         }
     }
     t.on = on != 0;
@@ -897,8 +951,10 @@ qumond_status qumond_trace_read(qumond_ctx* c, qumond_kernel_stat* out, int cap,
             CUDA_TRY(c, cudaEventElapsedTime(&ms, t.ev[2 * q], t.ev[2 * q + 1]), "trace: elapsed");
             t.ms[t.kind_of[q]] += ms;
             t.timed[t.kind_of[q]] += 1;
+            t.timed_bytes[t.kind_of[q]] += t.kind_bytes[q];
         }
         t.kind_of.clear();
+        t.kind_bytes.clear();
     }
     long long total = 0;
     for (int k = 0; k < K_COUNT; ++k) total += t.launches[k];
@@ -909,6 +965,7 @@ qumond_status qumond_trace_read(qumond_ctx* c, qumond_kernel_stat* out, int cap,
             out[k].bytes = t.bytes[k];
             out[k].ms = t.ms[k];
             out[k].timed = t.timed[k];
+            out[k].timed_bytes = t.timed_bytes[k];
         }
     if (totals) {
         totals->launches = total;
@@ -920,6 +977,7 @@ qumond_status qumond_trace_read(qumond_ctx* c, qumond_kernel_stat* out, int cap,
             t.bytes[k] = 0.0;
             t.ms[k] = 0.0;
             t.timed[k] = 0;
+            t.timed_bytes[k] = 0.0;
         }
         t.cell_updates = 0;
     }

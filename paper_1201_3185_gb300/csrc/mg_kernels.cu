@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_norms_kernel(const doub
 template <bool GRAPH>
 __global__ void __launch_bounds__(kReduceThreads)
 decide_kernel(const double* __restrict__ partials, int nblocks, SolveState* __restrict__ st, double tol, int max_it,
-              int first, int refine, cudaGraphConditionalHandle handle)
+              int first, int refine, cudaGraphConditionalHandle handle, int* __restrict__ fault)
 {
     double a = 0.0, b = 0.0;
     for (int t = threadIdx.x; t < nblocks; t += kReduceThreads) {
@@ -548,8 +548,14 @@ decide_kernel(const double* __restrict__ partials, int nblocks, SolveState* __re
         if (first) st->rel0 = rel;
         st->rel = rel;
         const bool finite = isfinite(rel);
-        st->converged = (finite && (!refine || rel <= tol)) ? 1 : 0;
-        const int cont = (refine && finite && rel > tol && st->it < max_it) ? 1 : 0;
+        const int faulted = (fault && *fault) ? 1 : 0;
+        if (first) st->fault = 0;
+        if (faulted) {
+            st->fault = 1;
+            *fault = 0;
+        }
+        st->converged = (finite && !st->fault && (!refine || rel <= tol)) ? 1 : 0;
+        const int cont = (refine && finite && !st->fault && rel > tol && st->it < max_it) ? 1 : 0;
         st->cont = cont;
         if (GRAPH) cudaGraphSetConditional(handle, (unsigned)cont);
     }
@@ -672,12 +678,13 @@ int launch_residual_rows(const double* u, const double* rhs, double coef, int n,
 }
 
 void launch_decide(const double* partials, int nblocks, SolveState* st, double tol, int max_it, bool first,
-                   bool refine, const cudaGraphConditionalHandle* handle, cudaStream_t s)
+                   bool refine, const cudaGraphConditionalHandle* handle, int* fault, cudaStream_t s)
 {
     if (handle)
-        decide_kernel<true><<<1, kReduceThreads, 0, s>>>(partials, nblocks, st, tol, max_it, first, refine, *handle);
+        decide_kernel<true><<<1, kReduceThreads, 0, s>>>(partials, nblocks, st, tol, max_it, first, refine, *handle,
+                                                         fault);
     else
-        decide_kernel<false><<<1, kReduceThreads, 0, s>>>(partials, nblocks, st, tol, max_it, first, refine, 0);
+        decide_kernel<false><<<1, kReduceThreads, 0, s>>>(partials, nblocks, st, tol, max_it, first, refine, 0, fault);
 }
 
 cudaError_t prepare_kernels()

@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libqumond.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -85,11 +86,23 @@ struct SolveState {
     int cont;      // 1: another V-cycle is needed
     int converged; // 1: rel <= tol (or no tolerance) and finite
     int scale_exp; // fixed-point outer loop: U = u * 2^scale_exp
+    int fault;     // 1: a kernel gave up waiting (bounded spin) since the last check
+    int pad;
 };
 // Reduces the partial norms and decides whether to continue; with a
 // non-null handle it also sets the graph's WHILE condition.
 void launch_decide(const double* partials, int nblocks, SolveState* st, double tol, int max_it, bool first,
-                   bool refine, const cudaGraphConditionalHandle* handle, cudaStream_t s);
+                   bool refine, const cudaGraphConditionalHandle* handle, int* fault, cudaStream_t s);
+
+// --- TMA-staged half-sweep for FP32 levels with n >= 64 (rb_tma.cu) ----------
+struct RbMaps {
+    CUtensorMap map[2];   // colour c of the iterate as a 3-D tensor (m, j, k), tile + halo boxes
+    CUtensorMap fmap[2];  // colour c of the right-hand side, tile boxes
+    bool ok = false;
+};
+bool make_rb_maps(float* e, float* f, const LevelView& v, RbMaps* out);
+void launch_rb_half_tma(float* e, const float* f, const LevelView& v, int colour, const RbMaps& maps, double h,
+                        int* fault, cudaStream_t s);
 // Sets kernel attributes (shared memory of the coarse-grid kernel); call
 // before any stream capture.
 cudaError_t prepare_kernels();

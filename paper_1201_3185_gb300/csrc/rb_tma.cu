@@ -1,0 +1,203 @@
+// Red-black half-sweep with TMA-staged neighbour planes (FP32 levels, n >= 64).
+//
+// Same update as rb_half_kernel -- every interior node of `colour` becomes
+// (sum of its 6 other-colour neighbours - h^2 f) / 6 -- but organised for the
+// memory system: a CTA owns a tile of 32 row entries (m) x 8 rows (j) of the
+// colour-split level and walks a chunk of k-planes.  The other colour's
+// planes k-1, k, k+1 (tile plus a one-row halo in j and the x-neighbours in m)
+// are brought into shared memory by the tensor-memory accelerator, one 3-D box
+// per plane, into a ring of four slots completed through mbarriers, so each
+// other-colour value crosses HBM once and the six neighbour reads hit shared
+// memory; f comes through the TMA unit with the same planes (both boxes
+// complete one mbarrier) and the result is written straight to global memory.
+//
+// The box starts at m0 - 4 so that its innermost coordinate is a multiple of
+// 16 bytes; entries before row start (m0 = 0) are filled with zeros by the
+// TMA unit and are never used by an interior node.  Waits are bounded: after
+// kSpinLimit failed polls a CTA records a fault (reported by the solve as a
+// timeout) and carries on instead of hanging.
+#include "qumond_internal.h"
+
+namespace qumond {
+
+namespace {
+
+constexpr int kTM = 32;
+constexpr int kTJ = 8;
+constexpr int kBoxX = kTM + 8;  // m0-4 .. m0+35
+constexpr int kBoxY = kTJ + 2;  // j0-1 .. j0+8
+constexpr int kSlots = 6;
+constexpr int kKC = 16;  // planes per CTA
+constexpr unsigned kPlaneBytes = kBoxX * kBoxY * sizeof(float);  // other colour, tile + halo
+constexpr unsigned kFBytes = kTM * kTJ * sizeof(float);           // own right-hand side, tile
+// TMA writes a box densely at a 128-byte aligned shared-memory address: pad each part.
+constexpr int kPlaneFloats = ((kPlaneBytes + 127) / 128) * 128 / sizeof(float);
+constexpr int kSlotFloats = kPlaneFloats + kFBytes / sizeof(float);
+constexpr long long kSpinLimit = 1LL << 24;
+// Levels below this size have too few planes per CTA column for the ring to pay off.
+constexpr int kTmaMinN = 256;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__global__ void __launch_bounds__(kTM * kTJ)
+rb_tma_kernel(const __grid_constant__ CUtensorMap other_map, const __grid_constant__ CUtensorMap f_map,
+              float* __restrict__ own, LevelView v, int colour, float h2, float sixth, int* __restrict__ fault)
+{
+    __shared__ __align__(128) float plane[kSlots][kSlotFloats];
+    __shared__ __align__(8) unsigned long long bar[kSlots];
+    __shared__ int abort_flag;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int m0 = blockIdx.x * kTM, j0 = 1 + blockIdx.y * kTJ;
+    const int kb = 1 + blockIdx.z * kKC;
+    const int ke = min(kb + kKC, v.n);  // output planes kb .. ke-1; planes kb-1 .. ke are read
+    const bool leader = tx == 0 && ty == 0;
+    if (leader) {
+        abort_flag = 0;
+        for (int q = 0; q < kSlots; ++q) mbar_init(&bar[q], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int q) {  // plane q into its slot (leader only)
+        const int u = q - (kb - 1);
+        float* dst = &plane[u % kSlots][0];
+        float* fdst = dst + kPlaneFloats;
+        if (((smem_u32(dst) | smem_u32(fdst)) & 127u) != 0u) {  // never issue a copy the TMA unit would reject
+            atomicExch(fault, 2);
+            atomicExch(&abort_flag, 1);
+            return;
+        }
+        mbar_expect_tx(&bar[u % kSlots], kPlaneBytes + kFBytes);
+        tma_load_3d(dst, &other_map, m0 - 4, j0 - 1, q, &bar[u % kSlots]);
+        tma_load_3d(fdst, &f_map, m0, j0, q, &bar[u % kSlots]);
+    };
+    if (leader)
+        for (int q = kb - 1; q < kb + kSlots - 1 && q <= ke; ++q) issue(q);
+    bool ok = true;
+    auto wait = [&](int q) {
+        const int u = q - (kb - 1);
+        long long spins = 0;
+        while (ok && !mbar_try_wait(&bar[u % kSlots], (unsigned)((u / kSlots) & 1))) {
+            if (++spins > kSpinLimit || *(volatile int*)&abort_flag) {
+                ok = false;
+                atomicExch(fault, 1);
+            }
+        }
+    };
+    const int m = m0 + tx, j = j0 + ty;
+    const int half = v.n >> 1;
+    const long long P = v.M;
+    const int xx = tx + 4, yy = ty + 1;
+    for (int k = kb; k < ke; ++k) {
+        const int p = (colour + j + k) & 1;
+        const bool valid = m < half && j < v.n && (p == 1 || m >= 1);
+        const long long row = ((long long)k * (v.n + 1) + j) * P;
+        if (k == kb) {
+            wait(k - 1);
+            wait(k);
+        }
+        wait(k + 1);
+        const int u = k - (kb - 1);
+        const int sm = (u - 1) % kSlots, s0 = u % kSlots, sp = (u + 1) % kSlots;
+        if (valid) {
+            const float fv = plane[s0][kPlaneFloats + ty * kTM + tx];
+            const float* c0 = &plane[s0][yy * kBoxX + xx];
+            const float s = (c0[p - 1] + c0[p]) + (c0[-kBoxX] + c0[kBoxX]) +
+                            (plane[sm][yy * kBoxX + xx] + plane[sp][yy * kBoxX + xx]);
+            own[row + m] = (s - h2 * fv) * sixth;
+        }
+        __syncthreads();  // slot of plane k-1 is free
+        if (leader && k + kSlots - 1 <= ke) issue(k + kSlots - 1);
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            (void)cudaGetLastError();
+    }
+    return fn;
+}
+
+}  // namespace
+
+bool make_rb_maps(float* e, float* f, const LevelView& v, RbMaps* out)
+{
+    out->ok = false;
+    if (v.n < kTmaMinN) return false;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)v.M, (cuuint64_t)(v.n + 1), (cuuint64_t)(v.n + 1)};
+    const cuuint64_t strides[2] = {(cuuint64_t)v.M * sizeof(float), (cuuint64_t)v.M * (v.n + 1) * sizeof(float)};
+    const cuuint32_t box[3] = {kBoxX, kBoxY, 1};
+    const cuuint32_t fbox[3] = {kTM, kTJ, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    for (int c = 0; c < 2; ++c) {
+        if (enc(&out->map[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, e + (long long)c * v.cs, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+        if (enc(&out->fmap[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, f + (long long)c * v.cs, dims, strides, fbox, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    out->ok = true;
+    return true;
+}
+
+void launch_rb_half_tma(float* e, const float* f, const LevelView& v, int colour, const RbMaps& maps, double h,
+                        int* fault, cudaStream_t s)
+{
+    const dim3 grid((unsigned)((v.n / 2 + kTM - 1) / kTM), (unsigned)((v.n - 1 + kTJ - 1) / kTJ),
+                    (unsigned)((v.n - 1 + kKC - 1) / kKC));
+    (void)f;
+    rb_tma_kernel<<<grid, dim3(kTM, kTJ), 0, s>>>(maps.map[colour ^ 1], maps.fmap[colour], e + (long long)colour * v.cs,
+                                                  v, colour, (float)(h * h), 1.0f / 6.0f, fault);
+}
+
+}  // namespace qumond

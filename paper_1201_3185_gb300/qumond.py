@@ -81,6 +81,7 @@ class qumond_kernel_stat(ctypes.Structure):
         ("bytes", ctypes.c_double),
         ("ms", ctypes.c_double),
         ("timed", ctypes.c_int64),
+        ("timed_bytes", ctypes.c_double),
     ]
 
 
@@ -194,6 +195,7 @@ class KernelStat:
     bytes: float
     ms: float
     timed: int
+    timed_bytes: float
 
 
 @dataclass
@@ -329,5 +331,6 @@ class Context:
         arr = (qumond_kernel_stat * k)()
         tot = qumond_counters()
         self._check(_lib.qumond_trace_read(self._ptr, arr, k, ctypes.byref(tot), 1 if reset else 0))
-        stats = {a.name.decode(): KernelStat(a.name.decode(), a.launches, a.bytes, a.ms, a.timed) for a in arr}
+        stats = {a.name.decode(): KernelStat(a.name.decode(), a.launches, a.bytes, a.ms, a.timed, a.timed_bytes)
+                 for a in arr}
         return stats, tot.launches, tot.cell_updates
