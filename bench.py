@@ -39,18 +39,28 @@ PRECISION_NAMES = {
 }
 UNIT = "solves/s"
 
-WORKLOAD = dict(
-    n=256, nboxes=3, L0=120000.0, particles=2_000_000, seed=1, rel_tol=1e-10, max_vcycles=40, ncycle=1,
-    npre=2, npost=2, nbins=50, rmax=30000.0, nphi=64,
-)
+WORKLOADS = {
+    # the metric's configuration: 256^3 intervals, 3 nested boxes, two-disk galaxy
+    "two-disk": dict(n=256, nboxes=3, L0=120000.0, particles=2_000_000, seed=1, rel_tol=1e-10, max_vcycles=40,
+                     ncycle=1, npre=2, npost=2, nbins=50, rmax=30000.0, nphi=64, kind="two-disk"),
+    # the large grid: 512^3 intervals, 4 nested boxes (240/120/60/30 kpc), disks + Hernquist bulge
+    "large": dict(n=512, nboxes=4, L0=240000.0, particles=20_000_000, seed=1, rel_tol=1e-10, max_vcycles=40,
+                  ncycle=1, npre=2, npost=2, nbins=50, rmax=30000.0, nphi=64, kind="large"),
+}
+WORKLOAD = dict(WORKLOADS["two-disk"])
 
 
 def workload_config(precision="FP32 smoothing + FP64 defect correction"):
     w = WORKLOAD
+    sides = "/".join("%g" % (w["L0"] / 1000.0 / 2 ** b) for b in range(w["nboxes"]))
+    galaxy = ("two-disk galaxy (stellar exponential disk Sigma0=500 Msun/pc^2, R_d=3 kpc, sech^2 h_* drawn in "
+              "[0.3,0.6] kpc; gas disk 1e9 Msun, R_g=8 kpc, h_g=0.1 kpc)")
+    if w["kind"] == "large":
+        galaxy = ("stellar + gas exponential disks as the two-disk galaxy plus a Hernquist bulge (M_b=1e10 Msun, "
+                  "a_b=0.5 kpc), a third of the particles each")
     return {
-        "workload": "two-disk galaxy (stellar exponential disk Sigma0=500 Msun/pc^2, R_d=3 kpc, sech^2 "
-                    "h_* drawn in [0.3,0.6] kpc; gas disk 1e9 Msun, R_g=8 kpc, h_g=0.1 kpc), %d particles, "
-                    "%d^3 nodes x %d nested boxes of 120/60/30 kpc" % (w["particles"], w["n"] + 1, w["nboxes"]),
+        "workload": "%s, %d particles, %d^3 nodes x %d nested boxes of %s kpc" % (galaxy, w["particles"], w["n"] + 1,
+                                                                                   w["nboxes"], sides),
         "n_intervals": w["n"],
         "boxes_kpc": [w["L0"] / 1000.0 / 2 ** b for b in range(w["nboxes"])],
         "particles": w["particles"],
@@ -69,6 +79,8 @@ def make_particles():
     import synth
     w = WORKLOAD
     lim = 0.45 * w["L0"]
+    if w["kind"] == "large":
+        return synth.large_galaxy(w["particles"], seed=w["seed"], rmax=lim)
     return synth.two_component_disk(w["particles"], seed=w["seed"], rmax=lim, zmax=lim)
 
 
@@ -158,30 +170,16 @@ def ncu_traffic(kernel: str):
 
 # --- our arm -------------------------------------------------------------------------
 def run_ours(args):
-    import numpy as np
     import torch
-    import torch.distributed as dist
 
     import paper_1201_3185_gb300 as q
 
-    ws, rank, local = dist_env()
-    if ws > 1:
-        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-
-    def barrier():
-        if ws > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def max_over_ranks(v):
-        if ws == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    from paper_1201_3185_gb300.replicas import Replicas
+    rep = Replicas.from_env()
+    ws, rank, local = rep.world_size, rep.rank, rep.local_rank
+    dev = rep.device
+    barrier = rep.barrier
+    max_over_ranks = rep.max
 
     w = WORKLOAD
     p = make_particles()
@@ -353,8 +351,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
-    if ws > 1:
-        dist.destroy_process_group()
+    rep.close()
 
 
 # --- the oracle (CPU) ------------------------------------------------------------------
@@ -461,9 +458,13 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 FMG comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip timing the oracle on the host")
     ap.add_argument("--no-graphs", action="store_true", help="launch kernels one by one (for profilers)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="two-disk",
+                    help="two-disk: the metric's 256^3 x 3-box configuration; large: 512^3 x 4 boxes")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one profiled V-cycle on one box instead of the benchmark (for ncu)")
     args = ap.parse_args()
+    WORKLOAD.clear()
+    WORKLOAD.update(WORKLOADS[args.workload])
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.profile_case:

@@ -2,7 +2,7 @@
 //
 // Same update as rb_half_kernel -- every interior node of `colour` becomes
 // (sum of its 6 other-colour neighbours - h^2 f) / 6 -- but organised for the
-// memory system: a CTA owns a tile of 32 row entries (m) x 8 rows (j) of the
+// memory system: a CTA owns a tile of 64 row entries (m) x 8 rows (j) of the
 // colour-split level and walks a chunk of k-planes.  The other colour's
 // planes k-1, k, k+1 (tile plus a one-row halo in j and the x-neighbours in m)
 // are brought into shared memory by the tensor-memory accelerator, one 3-D box
@@ -22,9 +22,10 @@ namespace qumond {
 
 namespace {
 
-constexpr int kTM = 32;
+constexpr int kTM = 64;          // two row entries per thread: m0 + tx and m0 + 32 + tx
 constexpr int kTJ = 8;
-constexpr int kBoxX = kTM + 8;  // m0-4 .. m0+35
+constexpr int kThreadsX = 32;
+constexpr int kBoxX = kTM + 8;  // m0-4 .. m0+67
 constexpr int kBoxY = kTJ + 2;  // j0-1 .. j0+8
 constexpr int kSlots = 6;
 constexpr int kKC = 16;  // planes per CTA
@@ -72,7 +73,7 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-__global__ void __launch_bounds__(kTM * kTJ)
+__global__ void __launch_bounds__(kThreadsX * kTJ)
 rb_tma_kernel(const __grid_constant__ CUtensorMap other_map, const __grid_constant__ CUtensorMap f_map,
               float* __restrict__ own, LevelView v, int colour, float h2, float sixth, int* __restrict__ fault)
 {
@@ -106,23 +107,26 @@ rb_tma_kernel(const __grid_constant__ CUtensorMap other_map, const __grid_consta
     if (leader)
         for (int q = kb - 1; q < kb + kSlots - 1 && q <= ke; ++q) issue(q);
     bool ok = true;
+    // lane 0 of each warp polls; __syncwarp passes the completed phase on to the warp
     auto wait = [&](int q) {
-        const int u = q - (kb - 1);
-        long long spins = 0;
-        while (ok && !mbar_try_wait(&bar[u % kSlots], (unsigned)((u / kSlots) & 1))) {
-            if (++spins > kSpinLimit || *(volatile int*)&abort_flag) {
-                ok = false;
-                atomicExch(fault, 1);
+        if ((tx & 31) == 0) {
+            const int u = q - (kb - 1);
+            long long spins = 0;
+            while (ok && !mbar_try_wait(&bar[u % kSlots], (unsigned)((u / kSlots) & 1))) {
+                if (++spins > kSpinLimit || *(volatile int*)&abort_flag) {
+                    ok = false;
+                    atomicExch(fault, 1);
+                }
             }
         }
+        __syncwarp();
     };
-    const int m = m0 + tx, j = j0 + ty;
+    const int j = j0 + ty;
     const int half = v.n >> 1;
     const long long P = v.M;
-    const int xx = tx + 4, yy = ty + 1;
+    const int yy = ty + 1;
     for (int k = kb; k < ke; ++k) {
         const int p = (colour + j + k) & 1;
-        const bool valid = m < half && j < v.n && (p == 1 || m >= 1);
         const long long row = ((long long)k * (v.n + 1) + j) * P;
         if (k == kb) {
             wait(k - 1);
@@ -130,13 +134,20 @@ rb_tma_kernel(const __grid_constant__ CUtensorMap other_map, const __grid_consta
         }
         wait(k + 1);
         const int u = k - (kb - 1);
-        const int sm = (u - 1) % kSlots, s0 = u % kSlots, sp = (u + 1) % kSlots;
-        if (valid) {
-            const float fv = plane[s0][kPlaneFloats + ty * kTM + tx];
-            const float* c0 = &plane[s0][yy * kBoxX + xx];
-            const float s = (c0[p - 1] + c0[p]) + (c0[-kBoxX] + c0[kBoxX]) +
-                            (plane[sm][yy * kBoxX + xx] + plane[sp][yy * kBoxX + xx]);
-            own[row + m] = (s - h2 * fv) * sixth;
+        const float* pm = &plane[(u - 1) % kSlots][0];
+        const float* p0 = &plane[u % kSlots][0];
+        const float* pp = &plane[(u + 1) % kSlots][0];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int t = tx + h * kThreadsX;  // entry within the tile
+            const int m = m0 + t;
+            const bool valid = m < half && j < v.n && (p == 1 || m >= 1);
+            if (valid) {
+                const int c = yy * kBoxX + t + 4;
+                const float fv = p0[kPlaneFloats + ty * kTM + t];
+                const float s = (p0[c - 1 + p] + p0[c + p]) + (p0[c - kBoxX] + p0[c + kBoxX]) + (pm[c] + pp[c]);
+                own[row + m] = (s - h2 * fv) * sixth;
+            }
         }
         __syncthreads();  // slot of plane k-1 is free
         if (leader && k + kSlots - 1 <= ke) issue(k + kSlots - 1);
@@ -196,7 +207,7 @@ void launch_rb_half_tma(float* e, const float* f, const LevelView& v, int colour
     const dim3 grid((unsigned)((v.n / 2 + kTM - 1) / kTM), (unsigned)((v.n - 1 + kTJ - 1) / kTJ),
                     (unsigned)((v.n - 1 + kKC - 1) / kKC));
     (void)f;
-    rb_tma_kernel<<<grid, dim3(kTM, kTJ), 0, s>>>(maps.map[colour ^ 1], maps.fmap[colour], e + (long long)colour * v.cs,
+    rb_tma_kernel<<<grid, dim3(kThreadsX, kTJ), 0, s>>>(maps.map[colour ^ 1], maps.fmap[colour], e + (long long)colour * v.cs,
                                                   v, colour, (float)(h * h), 1.0f / 6.0f, fault);
 }
 
