@@ -123,34 +123,41 @@ rb_tma_kernel(const __grid_constant__ CUtensorMap other_map, const __grid_consta
     };
     const int j = j0 + ty;
     const int half = v.n >> 1;
-    const long long P = v.M;
-    const int yy = ty + 1;
+    const long long plane_stride = (long long)(v.n + 1) * v.M;
+    // per-thread constants: the two entries' smem offsets, validity, global row
+    const int c0 = (ty + 1) * kBoxX + tx + 4, c1 = c0 + kThreadsX;
+    const int f0 = kPlaneFloats + ty * kTM + tx, f1 = f0 + kThreadsX;
+    const int mA = m0 + tx, mB = m0 + kThreadsX + tx;
+    const bool rowok = j < v.n;
+    const bool okA = rowok && mA < half, okB = rowok && mB < half;
+    long long row = ((long long)kb * (v.n + 1) + j) * v.M;
+    int p = (colour + j + kb) & 1;
+    int sm = 0, s0 = 1, sp = 2;  // slots of planes k-1, k, k+1
     for (int k = kb; k < ke; ++k) {
-        const int p = (colour + j + k) & 1;
-        const long long row = ((long long)k * (v.n + 1) + j) * P;
         if (k == kb) {
             wait(k - 1);
             wait(k);
         }
         wait(k + 1);
-        const int u = k - (kb - 1);
-        const float* pm = &plane[(u - 1) % kSlots][0];
-        const float* p0 = &plane[u % kSlots][0];
-        const float* pp = &plane[(u + 1) % kSlots][0];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int t = tx + h * kThreadsX;  // entry within the tile
-            const int m = m0 + t;
-            const bool valid = m < half && j < v.n && (p == 1 || m >= 1);
-            if (valid) {
-                const int c = yy * kBoxX + t + 4;
-                const float fv = p0[kPlaneFloats + ty * kTM + t];
-                const float s = (p0[c - 1 + p] + p0[c + p]) + (p0[c - kBoxX] + p0[c + kBoxX]) + (pm[c] + pp[c]);
-                own[row + m] = (s - h2 * fv) * sixth;
-            }
+        const float* pm = &plane[sm][0];
+        const float* p0 = &plane[s0][0];
+        const float* pp = &plane[sp][0];
+        if (okA && (p == 1 || mA >= 1)) {
+            const float s = (p0[c0 - 1 + p] + p0[c0 + p]) + (p0[c0 - kBoxX] + p0[c0 + kBoxX]) + (pm[c0] + pp[c0]);
+            own[row + mA] = (s - h2 * p0[f0]) * sixth;
+        }
+        if (okB) {  // mB >= 32: never the row's first entry
+            const float s = (p0[c1 - 1 + p] + p0[c1 + p]) + (p0[c1 - kBoxX] + p0[c1 + kBoxX]) + (pm[c1] + pp[c1]);
+            own[row + mB] = (s - h2 * p0[f1]) * sixth;
         }
         __syncthreads();  // slot of plane k-1 is free
         if (leader && k + kSlots - 1 <= ke) issue(k + kSlots - 1);
+        row += plane_stride;
+        p ^= 1;
+        const int t = sm;
+        sm = s0;
+        s0 = sp;
+        sp = t + 3 < kSlots ? t + 3 : t + 3 - kSlots;  // slot of plane k+2 = (slot of k-1) + 3
     }
 }
 
