@@ -168,6 +168,39 @@ def ncu_traffic(kernel: str):
     return k.get("dram_bytes_per_launch_full_size")
 
 
+class Contexts:
+    """The contexts of a pipeline, read and driven as one (tracer counters merged)."""
+
+    def __init__(self, ctxs):
+        self.ctxs = ctxs
+
+    def qumond_trace_timing(self, on, only=None):
+        for c in self.ctxs:
+            c.qumond_trace_timing(on, only=only)
+
+    def qumond_trace_read(self, reset=False):
+        merged, launches, cells = {}, 0, 0
+        for c in self.ctxs:
+            st, l, cu = c.qumond_trace_read(reset=reset)
+            launches += l
+            cells += cu
+            for name, k in st.items():
+                if name in merged:
+                    a = merged[name]
+                    a.launches += k.launches
+                    a.bytes += k.bytes
+                    a.ms += k.ms
+                    a.timed += k.timed
+                    a.timed_bytes += k.timed_bytes
+                else:
+                    merged[name] = k
+        return merged, launches, cells
+
+    def close(self):
+        for c in self.ctxs:
+            c.close()
+
+
 # --- our arm -------------------------------------------------------------------------
 def run_ours(args):
     import torch
@@ -186,10 +219,14 @@ def run_ours(args):
     prec = {"fp64": q.QUMOND_PREC_FP64, "mixed": q.QUMOND_PREC_MIXED, "fixed": q.QUMOND_PREC_MIXED_FIXED}[args.precision]
 
     def new_pipeline(precision):
-        ctx = q.Context(n=w["n"], nboxes=w["nboxes"], L0=w["L0"], rel_tol=w["rel_tol"], max_vcycles=w["max_vcycles"],
-                        ncycle=w["ncycle"], npre=w["npre"], npost=w["npost"], precision=precision,
-                        use_graphs=0 if args.no_graphs else 1)
-        return ctx, q.Pipeline(ctx, dev)
+        """A pipeline and its contexts: with two chains, the QUMOND solves run on their
+        own context and stream, concurrently with the next box's Newtonian solve."""
+        def make():
+            return q.Context(n=w["n"], nboxes=w["nboxes"], L0=w["L0"], rel_tol=w["rel_tol"],
+                             max_vcycles=w["max_vcycles"], ncycle=w["ncycle"], npre=w["npre"], npost=w["npost"],
+                             precision=precision, use_graphs=0 if args.no_graphs else 1)
+        cs = [make() for _ in range(args.chains)]
+        return Contexts(cs), q.Pipeline(cs[0], dev, ctx_mond=cs[1] if len(cs) > 1 else None)
 
     ctx, pipe = new_pipeline(prec)
     xd, yd, zd, md = (torch.from_numpy(a).to(dev) for a in (p.x, p.y, p.z, p.m))
@@ -221,12 +258,8 @@ def run_ours(args):
     replay_ms = r0.elapsed_time(r1) / args.steps
     kstats, _, _ = ctx.qumond_trace_read(reset=True)
     ctx.qumond_trace_timing(False)
-    dom_name = max(kstats.values(), key=lambda k: k.ms).name
 
-    # --- timed region: inputs resident in HBM; each solve is one CUDA graph, whose FMG
-    # part carries event-record nodes around the dominant kernel class -------------------
-    ctx.qumond_trace_timing(True, only=dom_name)
-    step()  # captures the instrumented graphs
+    # --- timed region: inputs resident in HBM; each solve is one CUDA graph -------------
     ctx.qumond_trace_read(reset=True)
     clocks = ClockSampler(local)
     barrier()
@@ -240,12 +273,45 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     ms_total = max_over_ranks(s0.elapsed_time(s1))
-    live, launches, cell_updates = ctx.qumond_trace_read(reset=True)
-    ctx.qumond_trace_timing(False)
+    timed_stats, launches, cell_updates = ctx.qumond_trace_read(reset=True)
+    step_bytes = sum(k.bytes for k in timed_stats.values()) / args.steps
     ms_step = ms_total / args.steps
     value = ws * args.steps / (ms_total / 1000.0)
 
-    # dominant kernel and its roofline (live: event nodes inside the timed graphs)
+    # --- kernels timed live: the same steps with one chain (no concurrent solve sharing
+    # the GPU), the graphs carrying event-record nodes around each run of consecutive
+    # launches of one kernel class in the FMG part of every solve.  The three classes
+    # with the most replay time are timed this way (one timed region each); the
+    # dominant kernel is the one with the most live time per step. ----------------------
+    pipe1 = q.Pipeline(ctx.ctxs[0], dev)
+    ctx1 = Contexts(ctx.ctxs[:1])
+    candidates = [k.name for k in sorted(kstats.values(), key=lambda k: -k.ms)[:3]]
+    live_by = {}
+    one_chain_ms = None
+    for name in candidates:
+        ctx1.qumond_trace_timing(True, only=name)
+        step(pipe1)  # captures the instrumented graphs
+        ctx1.qumond_trace_read(reset=True)
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(args.steps):
+            step(pipe1)
+        t1.record()
+        barrier()
+        ms1 = max_over_ranks(t0.elapsed_time(t1)) / args.steps
+        one_chain_ms = ms1 if one_chain_ms is None else min(one_chain_ms, ms1)
+        st1, _, _ = ctx1.qumond_trace_read(reset=True)
+        ctx1.qumond_trace_timing(False)
+        k = st1[name]
+        per_launch = k.ms / k.timed if k.timed else 0.0
+        live_by[name] = (k, per_launch * k.launches / args.steps)
+    dom_name = max(live_by, key=lambda nm: live_by[nm][1])
+    live = {dom_name: live_by[dom_name][0]}
+    live_ms_per_step = {nm: v[1] for nm, v in live_by.items()}
+
+    # dominant kernel and its roofline
     dom = live[dom_name]
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
@@ -260,8 +326,9 @@ def run_ours(args):
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s",
                 "timing": "CUDA event-record nodes around each run of consecutive launches of this kernel class in "
                           "the FMG part of each solve's graph (e.g. the four half-sweeps of a pre-smoothing), read "
-                          "after each solve of the timed region; achieved = algorithmic bytes of the timed launches / "
-                          "their time"}
+                          "after each solve, over %d timed steps of the same workload run with one chain; achieved = "
+                          "algorithmic bytes of the timed launches / their time" % args.steps,
+                "live_ms_per_step_of_candidates": live_ms_per_step}
     total_kernel_ms = sum(k.ms for k in kstats.values())
     total_bytes = sum(k.bytes for k in kstats.values())
     kernels = {k.name: {"launches_per_step": k.launches / args.steps, "ms_per_step": k.ms / args.steps,
@@ -305,12 +372,14 @@ def run_ours(args):
         f1.record()
         barrier()
         pms = max_over_ranks(f0.elapsed_time(f1)) / nsteps
+        pp.close()
         cx.close()
         return pms
 
     plain = None
     fp64_dc = None
     if not args.no_plain and prec != q.QUMOND_PREC_FP64:
+        pipe.close()
         ctx.close()
         del pipe
         torch.cuda.empty_cache()
@@ -336,13 +405,16 @@ def run_ours(args):
                                             q.QUMOND_PREC_FP64: "f64"}[prec],
             "data": "synthetic", "config": workload_config(PRECISION_NAMES[args.precision]),
             "cell_updates_per_s": ws * cell_updates / (ms_total / 1000.0),
-            "hbm_algorithmic_GBps_all_kernels": total_bytes / (total_kernel_ms * 1e6) if total_kernel_ms else None,
+            "algorithmic_bytes_per_step": step_bytes,
+            "algorithmic_GBps_whole_step": step_bytes / (ms_step * 1e6),
             "kernel_ms_per_step_one_by_one": total_kernel_ms / args.steps,
             "replay_ms_per_step_one_by_one": replay_ms,
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "gpu_launches_per_step": launches / args.steps,
+            "chains": args.chains,
+            "one_chain": {"value": ws * 1000.0 / one_chain_ms, "unit": UNIT, "ms_per_step": one_chain_ms},
             "vcycles_after_fmg_per_solve": vcycles,
             "plain_fmg": plain,
             "fp32_smoothing_fp64_defect_correction": fp64_dc,
@@ -458,6 +530,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 FMG comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip timing the oracle on the host")
     ap.add_argument("--no-graphs", action="store_true", help="launch kernels one by one (for profilers)")
+    ap.add_argument("--chains", type=int, choices=[1, 2], default=2,
+                    help="2: QUMOND solves on a second context and stream, concurrent with the Newtonian chain")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="two-disk",
                     help="two-disk: the metric's 256^3 x 3-box configuration; large: 512^3 x 4 boxes")
     ap.add_argument("--profile-case", action="store_true",

@@ -5,9 +5,22 @@ QUMOND source -> QUMOND solve, each box taking its boundary values from the
 previous one; then the forces at the particles and the rotation curve.
 Every step is a call into libqumond; this class only owns the device
 buffers and orders the calls.
+
+Concurrency: the QUMOND solve of box b needs box b's source and box b-1's
+QUMOND potential, the Newtonian solve of box b+1 needs box b's Newtonian
+potential -- so the two are independent.  With a second context
+(`ctx_mond`), the Newtonian chain (deposits, Newtonian solves, sources) runs
+on one stream from the calling thread and the QUMOND chain on another stream
+from a worker thread, the source of each box handed over with a CUDA event.
+Each solve spends a large part of its time on small multigrid levels that
+leave most of the GPU idle, and the other chain fills it.  The kernels and
+their order within each chain are unchanged, so the results are the same
+bits as the sequential order.
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
+import threading
 from dataclasses import dataclass, field
 
 import torch
@@ -24,20 +37,34 @@ class PipelineResult:
 
 
 class Pipeline:
-    def __init__(self, ctx: Context, device=None):
+    def __init__(self, ctx: Context, device=None, ctx_mond: Context | None = None):
         self.ctx = ctx
+        self.ctx_mond = ctx_mond
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         nodes = ctx.nodes
         nb = ctx.params.nboxes
         self.device = dev
         self.rho_fixed = torch.empty(nodes, dtype=torch.int64, device=dev)
         self.rho = torch.empty(nodes, dtype=torch.float64, device=dev)
-        self.src = torch.empty(nodes, dtype=torch.float64, device=dev)
+        nsrc = nb if ctx_mond is not None else 1  # concurrent chains: one source buffer per box
+        self.srcs = [torch.empty(nodes, dtype=torch.float64, device=dev) for _ in range(nsrc)]
+        self.src = self.srcs[0]
         self.phiN = [torch.zeros(nodes, dtype=torch.float64, device=dev) for _ in range(nb)]
         self.phi = [torch.zeros(nodes, dtype=torch.float64, device=dev) for _ in range(nb)]
+        if ctx_mond is not None:
+            if ctx_mond.nodes != nodes or ctx_mond.params.nboxes != nb:
+                raise ValueError("the two contexts must describe the same boxes")
+            self._streams = (torch.cuda.Stream(dev), torch.cuda.Stream(dev))
+            self._pool = cf.ThreadPoolExecutor(max_workers=1, thread_name_prefix="qumond-mond")
+
+    def close(self):
+        if self.ctx_mond is not None:
+            self._pool.shutdown(wait=True)
 
     def potentials(self, x, y, z, m, stats=False, stream=None):
         """Steps 1-4 for every box; fills self.phiN and self.phi."""
+        if self.ctx_mond is not None:
+            return self._potentials_concurrent(x, y, z, m, stats, stream)
         c = self.ctx
         ns, ms = [], []
         for b in range(c.params.nboxes):
@@ -47,6 +74,55 @@ class Pipeline:
             ns.append(c.qumond_solve_newton(b, self.rho, par_n, self.phiN[b], stats=stats, stream=stream))
             c.qumond_source(b, self.phiN[b], self.src, stream=stream)
             ms.append(c.qumond_solve_mond(b, self.src, par_m, self.phi[b], stats=stats, stream=stream))
+        return ns, ms
+
+    def _potentials_concurrent(self, x, y, z, m, stats, stream):
+        caller = stream if stream is not None else torch.cuda.current_stream(self.device)
+        sa, sb = self._streams
+        nb = self.ctx.params.nboxes
+        start = torch.cuda.Event()
+        start.record(caller)
+        sa.wait_event(start)
+        sb.wait_event(start)
+        ready = [threading.Event() for _ in range(nb)]
+        src_done = [torch.cuda.Event() for _ in range(nb)]
+        failed = []
+
+        def mond_chain():
+            out = []
+            with torch.cuda.device(self.device):
+                for b in range(nb):
+                    ready[b].wait()
+                    if failed:
+                        return out
+                    sb.wait_event(src_done[b])
+                    par = self.phi[b - 1] if b > 0 else None
+                    out.append(self.ctx_mond.qumond_solve_mond(b, self.srcs[b], par, self.phi[b], stats=stats,
+                                                               stream=sb))
+            return out
+
+        fut = self._pool.submit(mond_chain)
+        ns = []
+        try:
+            for b in range(nb):
+                self.ctx.qumond_deposit(b, x, y, z, m, self.rho_fixed, self.rho, stream=sa)
+                par = self.phiN[b - 1] if b > 0 else None
+                ns.append(self.ctx.qumond_solve_newton(b, self.rho, par, self.phiN[b], stats=stats, stream=sa))
+                self.ctx.qumond_source(b, self.phiN[b], self.srcs[b], stream=sa)
+                src_done[b].record(sa)
+                ready[b].set()
+        except Exception:
+            failed.append(True)
+            for e in ready:
+                e.set()
+            fut.result()
+            raise
+        ms = fut.result()
+        end_a, end_b = torch.cuda.Event(), torch.cuda.Event()
+        end_a.record(sa)
+        end_b.record(sb)
+        caller.wait_event(end_a)
+        caller.wait_event(end_b)
         return ns, ms
 
     def run(self, x, y, z, m, *, nbins=50, rmax=30000.0, nphi=64, forces=None, stats=False, stream=None):

@@ -300,6 +300,29 @@ def test_graph_and_one_by_one_launches_agree(q, prec):
     assert np.array_equal(a["vc"], b["vc"])
 
 
+def test_concurrent_chains_give_the_same_bits(q):
+    # the QUMOND chain on its own context and stream, concurrent with the
+    # Newtonian chain: the same kernels in the same order within each chain
+    p = synth.two_component_disk(50_000, seed=9, rmax=54000.0, zmax=54000.0)
+    kw = dict(n=64, nboxes=3, L0=120000.0, rel_tol=1e-10, max_vcycles=40, precision=q.QUMOND_PREC_MIXED_FIXED)
+    x, y, z, m = (to_dev(a) for a in (p.x, p.y, p.z, p.m))
+    c1 = q.Context(**kw)
+    seq = q.Pipeline(c1)
+    a = seq.run(x, y, z, m, nbins=30, rmax=20000.0, stats=True)
+    ca, cb = q.Context(**kw), q.Context(**kw)
+    con = q.Pipeline(ca, ctx_mond=cb)
+    for _ in range(2):  # second pass relaunches the cached graphs
+        b = con.run(x, y, z, m, nbins=30, rmax=20000.0, stats=True)
+    torch.cuda.synchronize()
+    for u, v in zip(seq.phiN + seq.phi, con.phiN + con.phi):
+        assert torch.equal(u, v)
+    assert torch.equal(a.vc, b.vc)
+    assert [s.vcycles for s in a.mond_stats] == [s.vcycles for s in b.mond_stats]
+    con.close()
+    for c in (c1, ca, cb):
+        c.close()
+
+
 def test_graph_paper_mode_and_relaunch(q, ora):
     # paper mode (no residual checks) as a graph, launched twice on the same arrays
     p = synth.two_component_disk(50_000, seed=6, rmax=54000.0, zmax=54000.0)
