@@ -47,6 +47,12 @@ WORKLOADS = {
     "large": dict(n=512, nboxes=4, L0=240000.0, particles=20_000_000, seed=1, rel_tol=1e-10, max_vcycles=40,
                   ncycle=1, npre=2, npost=2, nbins=50, rmax=30000.0, nphi=64, kind="large"),
 }
+# the fit sweep (Section 3.5): 64 parameter sets of the two-disk galaxy, 129^3 nodes x 2 boxes (80/40 kpc),
+# 5e5 particles each, chi^2 against the oracle-made target curve; one step = the whole sweep
+SWEEP = dict(n=128, nboxes=2, L0=80000.0, particles=500_000, galaxy_seed=11, sets=64, param_seed=2012,
+             rel_tol=1e-8, max_vcycles=40, ncycle=1, npre=2, npost=2, nbins=40, rmax=24000.0, nphi=64, kind="sweep",
+             target="tests/golden/sweep_target_two_disk_129cube.json")
+WORKLOADS["sweep"] = SWEEP
 WORKLOAD = dict(WORKLOADS["two-disk"])
 
 
@@ -72,6 +78,30 @@ def workload_config(precision="FP32 smoothing + FP64 defect correction"):
         "seed": w["seed"],
         "l2": "inputs larger than L2: each 257^3 FP64 grid is 136 MB and one step streams tens of GB",
         "data": "synthetic (seeded generator)",
+    }
+
+
+def sweep_config(precision, workers):
+    w = WORKLOAD
+    return {
+        "workload": "fit sweep: %d parameter sets (distance scale 0.8-1.2, stellar M/L 0.3-1.2, stellar h 0.2-1.0 kpc, "
+                    "gas h 0.05-0.5 kpc; uniform, seed %d) of the two-disk galaxy (stellar disk I0=500 Lsun/pc^2, "
+                    "R_d=3 kpc; gas 1e9 Msun, R_g=8 kpc), %d particles per set, %d^3 nodes x %d nested boxes of "
+                    "%g/%g kpc, reduced chi^2 of each %d-bin rotation curve against a synthetic target with 3%% "
+                    "Gaussian errors" % (w["sets"], w["param_seed"], w["particles"], w["n"] + 1, w["nboxes"],
+                                         w["L0"] / 1000.0, w["L0"] / 2000.0, w["nbins"]),
+        "sets_per_step": w["sets"],
+        "n_intervals": w["n"],
+        "particles_per_set": w["particles"],
+        "precision": precision,
+        "rel_tol": w["rel_tol"],
+        "fmg_vcycles_per_level": w["ncycle"],
+        "npre_npost": [w["npre"], w["npost"]],
+        "workers": workers,
+        "rotation_curve": "%d bins to %g kpc x distance factor, %d azimuths" % (w["nbins"], w["rmax"] / 1000.0,
+                                                                                w["nphi"]),
+        "l2": "inputs larger than L2: 64 sets x 5e5 particles x 32 B = 1 GB of particles, ~10 GB of grids per step",
+        "data": "synthetic (seeded generator; target curve written by the oracle)",
     }
 
 
@@ -426,7 +456,229 @@ def run_ours(args):
     rep.close()
 
 
+# --- the fit sweep -----------------------------------------------------------------------
+def sweep_inputs():
+    import numpy as np
+
+    import synth
+    w = WORKLOAD
+    doc = json.load(open(os.path.join(ROOT, w["target"])))
+    gal = synth.SweepGalaxy(w["particles"], w["galaxy_seed"])
+    params = synth.fit_sweep_parameters(w["sets"], seed=w["param_seed"])
+    return gal, params, np.array(doc["v_obs"]), np.array(doc["sigma"])
+
+
+def run_sweep(args):
+    import numpy as np
+    import torch
+
+    import paper_1201_3185_gb300 as q
+    from paper_1201_3185_gb300.replicas import Replicas
+    rep = Replicas.from_env()
+    ws, rank, local = rep.world_size, rep.rank, rep.local_rank
+    dev = rep.device
+    w = WORKLOAD
+    prec = {"fp64": q.QUMOND_PREC_FP64, "mixed": q.QUMOND_PREC_MIXED, "fixed": q.QUMOND_PREC_MIXED_FIXED}[args.precision]
+
+    def params(precision):
+        return q.default_params(n=w["n"], nboxes=w["nboxes"], L0=w["L0"], rel_tol=w["rel_tol"],
+                                max_vcycles=w["max_vcycles"], ncycle=w["ncycle"], npre=w["npre"], npost=w["npost"],
+                                precision=precision, use_graphs=0 if args.no_graphs else 1)
+
+    gal, prm, v_obs_h, sigma_h = sweep_inputs()
+    host_sets = [gal.particles(r) for r in prm]
+    sets = [tuple(torch.from_numpy(a).to(dev) for a in (p.x, p.y, p.z, p.m)) for p in host_sets]
+    dist = [float(r[0]) for r in prm]
+    v_obs = torch.from_numpy(v_obs_h).to(dev)
+    sigma = torch.from_numpy(sigma_h).to(dev)
+    kw = dict(nbins=w["nbins"], rmax=w["rmax"], nphi=w["nphi"], device=dev)
+
+    if args.workers:
+        workers, tune = args.workers, None
+    else:
+        workers, tune = q.tune_workers(params(prec), sets, dist, v_obs, sigma, **kw)
+    sw = q.FitSweep(params(prec), workers=workers, **kw)
+    ctx = Contexts(sw.ctxs)
+    for _ in range(args.warmup):
+        sw.run(sets, dist, v_obs, sigma)
+    chk = sw.run(sets, dist, v_obs, sigma, stats=True)
+    torch.cuda.synchronize()
+    vcyc = [[a.vcycles, b.vcycles] for st in chk.stats for a, b in st]
+    chi2 = chk.chi2.cpu().numpy()
+
+    # timed region: particles resident in HBM
+    ctx.qumond_trace_read(reset=True)
+    clocks = ClockSampler(local)
+    rep.barrier()
+    clocks.start()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for _ in range(args.steps):
+        sw.run(sets, dist, v_obs, sigma)
+    s1.record()
+    rep.barrier()
+    clk = clocks.stop()
+    ms_total = rep.max(s0.elapsed_time(s1))
+    tstats, launches, cells = ctx.qumond_trace_read(reset=True)
+    step_bytes = sum(k.bytes for k in tstats.values()) / args.steps
+    ms_step = ms_total / args.steps
+    value = ws * w["sets"] * args.steps / (ms_total / 1000.0)
+
+    # dominant kernel: classes timed live inside one worker's graphs (one set at a time)
+    one = q.FitSweep(params(prec), workers=1, **kw)
+    c1 = Contexts(one.ctxs)
+    sub = sets[:8]
+    live = {}
+    for name in ("rb_half_finest", "rb_half_coarser", "restrict_resid_red", "residual_outer"):
+        c1.qumond_trace_timing(True, only=name)
+        one.run(sub, dist[:8], v_obs, sigma)
+        c1.qumond_trace_read(reset=True)
+        one.run(sub, dist[:8], v_obs, sigma)
+        torch.cuda.synchronize()
+        st1, _, _ = c1.qumond_trace_read(reset=True)
+        c1.qumond_trace_timing(False)
+        k = st1[name]
+        if k.timed:
+            live[name] = (k, k.ms / k.timed * k.launches / len(sub))
+    one.close()
+    dom_name = max(live, key=lambda nm: live[nm][1])
+    dom = live[dom_name][0]
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = dom.timed_bytes / dom.ms / 1e6 if dom.ms else None
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "algorithmic_bytes_per_launch": dom.timed_bytes / dom.timed, "avg_launch_ms": dom.ms / dom.timed,
+                "timed_launches": dom.timed,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s",
+                "timing": "CUDA event-record nodes around runs of this class's launches in the FMG part of each "
+                          "solve's graph, one worker, 8 sets; the 129^3 grids (8.6 MB per FP32 field) are largely "
+                          "L2-resident, so achieved can exceed what HBM alone would give",
+                "live_ms_per_set": {nm: v[1] for nm, v in live.items()}}
+
+    # end to end: every set's particles copied from pinned host memory, chi^2 and curves read back
+    host = [[torch.from_numpy(a).pin_memory() for a in (p.x, p.y, p.z, p.m)] for p in host_sets]
+    out_vc = torch.empty(w["sets"], w["nbins"], dtype=torch.float64).pin_memory()
+    out_chi2 = torch.empty(w["sets"], dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for hs in host for t in hs)
+    d2h = out_vc.numel() * 8 + out_chi2.numel() * 8
+    rep.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        dsets = [tuple(t.to(dev, non_blocking=True) for t in hs) for hs in host]
+        res = sw.run(dsets, dist, v_obs, sigma)
+        out_vc.copy_(res.vc, non_blocking=True)
+        out_chi2.copy_(res.chi2, non_blocking=True)
+    e1.record()
+    rep.barrier()
+    e2e_ms = rep.max(e0.elapsed_time(e1))
+    e2e_value = ws * w["sets"] * args.steps / (e2e_ms / 1000.0)
+    sw.close()
+
+    # the same sweep, one set after another (one worker), same precision and in plain FP64
+    def sequential(precision):
+        one = q.FitSweep(params(precision), workers=1, **kw)
+        one.run(sets[:1], dist[:1], v_obs, sigma)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record()
+        one.run(sets, dist, v_obs, sigma)
+        f1.record()
+        rep.barrier()
+        t = rep.max(f0.elapsed_time(f1))
+        one.close()
+        return {"value": ws * w["sets"] / (t / 1000.0), "unit": "sets/s", "ms_per_step": t, "steps": 1}
+
+    seq_same = plain = None
+    if not args.no_plain:
+        seq_same = sequential(prec)
+        plain = sequential(q.QUMOND_PREC_FP64)
+        plain["precision"] = PRECISION_NAMES["fp64"] + " (same kernels, same tolerance), one set at a time"
+        plain["speedup_of_value"] = value / plain["value"]
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        ns = 4
+        t = oracle_sweep_sample(gal, prm[:ns], v_obs_h, sigma_h)
+        cpu = {"value": ns / t, "unit": "sets/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": "the first %d of the %d sets (galaxy realisation excluded), %.1f s" % (ns, w["sets"], t)}
+
+    if rank == 0:
+        best = int(np.argmin(chi2))
+        line = {
+            "metric": METRIC, "value": value, "unit": "sets/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {q.QUMOND_PREC_MIXED: "f32+f64", q.QUMOND_PREC_MIXED_FIXED: "f32+int64",
+                                            q.QUMOND_PREC_FP64: "f64"}[prec],
+            "data": "synthetic", "config": sweep_config(PRECISION_NAMES[args.precision], workers),
+            "solves_per_s": 2 * w["nboxes"] * value,
+            "cell_updates_per_s": ws * cells / (ms_total / 1000.0),
+            "algorithmic_bytes_per_step": step_bytes,
+            "algorithmic_GBps_whole_step": step_bytes / (ms_step * 1e6),
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": "sets/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "gpu_launches_per_step": launches / args.steps,
+            "workers_tuning_ms_per_sweep": tune,
+            "vcycles_after_fmg_per_set_max": max(max(v) for v in vcyc),
+            "best_set": {"index": best, "chi2": float(chi2[best]), "params": [float(v) for v in prm[best]]},
+            "sequential_same_precision": seq_same,
+            "plain_fmg": plain,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    rep.close()
+
+
 # --- the oracle (CPU) ------------------------------------------------------------------
+def oracle_sweep_sample(gal, prm, v_obs, sigma):
+    """The sweep's path for the given parameter sets with the FP64 oracle:
+    both solves of both boxes, the rotation curve and chi^2; returns seconds."""
+    import oracle
+    oracle.build()
+    w = WORKLOAD
+    t0 = time.perf_counter()
+    for r_ in prm:
+        p = gal.particles(r_)
+        boxes = oracle.pipeline(p, w["n"], w["L0"], w["nboxes"], ncycle=w["ncycle"], npre=w["npre"],
+                                npost=w["npost"], tol=w["rel_tol"], max_vcycles=w["max_vcycles"])
+        _, vc_o = oracle.rotation_curve(w["n"], w["L0"], (0.0, 0.0, 0.0), [b.phi for b in boxes], w["nbins"],
+                                        w["rmax"] * r_[0], w["nphi"])
+        oracle.chi2(vc_o, v_obs, sigma)
+    return time.perf_counter() - t0
+
+
+def run_reference_sweep(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    w = WORKLOAD
+    gal, prm, v_obs, sigma = sweep_inputs()
+    oracle_sweep_sample(gal, prm[:1], v_obs, sigma)  # builds the oracle
+    for i in range(args.warmup - 1):
+        oracle_sweep_sample(gal, prm[i + 1:i + 2], v_obs, sigma)
+    per = 2
+    times = [oracle_sweep_sample(gal, prm[per * i:per * i + per], v_obs, sigma) for i in range(args.steps)]
+    value = per * len(times) / sum(times)
+    sample = "each step: %d of the %d sets at full size (galaxy realisation included), whole sweep = %d sets" % (
+        per, w["sets"], w["sets"])
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "sets/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": w["sets"] * 1000.0 / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": sweep_config("FP64 CPU oracle", 1),
+        "cpu_baseline": {"kind": "oracle", "cores": cpu_cores(), "sample": sample, "value": value, "unit": "sets/s"},
+        "e2e": {"value": value, "unit": "sets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def oracle_sample(p, sample_boxes):
     """Steps 1-4 for the first `sample_boxes` boxes of the workload with the
     FP64 oracle, plus the rotation curve (over the boxes solved)."""
@@ -533,7 +785,10 @@ def main():
     ap.add_argument("--chains", type=int, choices=[1, 2], default=2,
                     help="2: QUMOND solves on a second context and stream, concurrent with the Newtonian chain")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="two-disk",
-                    help="two-disk: the metric's 256^3 x 3-box configuration; large: 512^3 x 4 boxes")
+                    help="two-disk: the metric's 256^3 x 3-box configuration; large: 512^3 x 4 boxes; "
+                         "sweep: the 64-set rotation-curve fit sweep at 128^3 x 2 boxes")
+    ap.add_argument("--workers", type=int, default=0,
+                    help="sweep: concurrent workers (0: pick by timing)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one profiled V-cycle on one box instead of the benchmark (for ncu)")
     args = ap.parse_args()
@@ -544,7 +799,9 @@ def main():
     if args.profile_case:
         profile_case(args)
     elif args.impl == "reference":
-        run_reference(args)
+        run_reference_sweep(args) if args.workload == "sweep" else run_reference(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_ours(args)
 

@@ -195,6 +195,16 @@ QUMOND_API qumond_status qumond_forces(qumond_ctx* ctx, const double* const* phi
 QUMOND_API qumond_status qumond_rotation_curve(qumond_ctx* ctx, const double* const* phi_boxes, int nbins, double rmax,
                                     int nphi, double* r_out, double* vc_out, void* stream);
 
+/* Quality of a rotation-curve fit (Section 3.5): for each of nsets curves,
+     chi2[s] = (1/nbins) * sum_i ((vc[s*nbins + i] - v_obs[i]) / sigma[i])^2
+   (the reduced chi^2 the paper minimises over distance, M/L and scale
+   heights).  vc: nsets x nbins doubles, row-major; v_obs, sigma: nbins
+   doubles; chi2: nsets doubles; all device pointers, owned by the caller.
+   sigma must be non-zero (a zero gives inf or nan).  nsets = 0 does nothing.
+   Errors: QUMOND_ERR_INVALID_ARG for nbins < 1, nsets < 0 or a host pointer. */
+QUMOND_API qumond_status qumond_chi2(qumond_ctx* ctx, const double* vc, const double* v_obs, const double* sigma,
+                                     int nbins, int nsets, double* chi2, void* stream);
+
 /* --- tracing (not part of the method: instrumentation of the kernels) ------ */
 
 /* Per-kernel-class counters of a context since it was created or last reset. */
@@ -202,7 +212,7 @@ typedef struct {
     const char* name;     /* kernel class, e.g. "rb_half_finest" (static storage) */
     int64_t launches;     /* kernels of this class launched */
     double bytes;         /* algorithmic HBM bytes of those launches (the minimum
-                             each kernel must read and write; see DESIGN.md) */
+                             each kernel must read and write) */
     double ms;            /* summed CUDA-event time of the launches that were
                              bracketed while timing was on (0 otherwise) */
     int64_t timed;        /* how many launches were bracketed */

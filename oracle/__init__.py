@@ -25,6 +25,7 @@ from .core import (  # noqa: F401
     boundary_fill,
     forces,
     rotation_curve,
+    chi2,
     Box,
     pipeline,
     grid_index,

@@ -59,6 +59,7 @@ def _load():
         "ora_boundary_fill": (None, [_I, _D, _D, _D, _D, _P, _D, _D, _D, _D, _P]),
         "ora_forces": (_L, [_I, _I, _D, _I, _D, _D, _D, _P, _P, _P, _P, _L, _P, _P, _P]),
         "ora_rotation_curve": (None, [_I, _I, _D, _I, _D, _D, _D, _P, _I, _D, _I, _D, _P, _P]),
+        "ora_chi2": (None, [_P, _P, _P, _I, _I, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -189,6 +190,15 @@ def rotation_curve(n, L0, center, phis, nbins, rmax, nphi=64, frac=0.2, ratio=2)
     _load().ora_rotation_curve(len(phis), n, L0, ratio, center[0], center[1], center[2], ctypes.cast(pa, _P),
                                nbins, rmax, nphi, frac, _ptr(r), _ptr(vc))
     return r, vc
+
+
+def chi2(vc, v_obs, sigma):
+    """Reduced chi^2 of each row of vc against (v_obs, sigma) (Section 3.5)."""
+    vc = np.ascontiguousarray(np.atleast_2d(vc), dtype=np.float64)
+    v_obs, sigma = _f64(v_obs), _f64(sigma)
+    out = np.empty(vc.shape[0])
+    _load().ora_chi2(_ptr(vc), _ptr(v_obs), _ptr(sigma), vc.shape[1], vc.shape[0], _ptr(out))
+    return out
 
 
 # --- the whole path, Section 2 ---------------------------------------------------

@@ -503,3 +503,18 @@ void ora_rotation_curve(int nboxes, int n, double L0, int ratio, double cx, doub
         vc_out[kb] = v2 >= 0.0 ? sqrt(v2) : -sqrt(-v2);
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Quality of a fit (Section 3.5): chi^2/n = (1/n) sum_i (V_fit(R_i) - V_obs(R_i))^2 / sigma_obs(R_i)^2,
+ * for nsets rotation curves of nbins points each (vc row-major [set][bin]). */
+void ora_chi2(const double* vc, const double* v_obs, const double* sigma, int nbins, int nsets, double* chi2)
+{
+    for (int s = 0; s < nsets; ++s) {
+        double acc = 0.0;
+        for (int i = 0; i < nbins; ++i) {
+            double d = (vc[(size_t)s * nbins + i] - v_obs[i]) / sigma[i];
+            acc += d * d;
+        }
+        chi2[s] = acc / (double)nbins;
+    }
+}

@@ -17,3 +17,4 @@ from .qumond import (  # noqa: F401
     EXPORTED,
 )
 from .pipeline import Pipeline, PipelineResult  # noqa: F401
+from .sweep import FitSweep, SweepResult, tune_workers  # noqa: F401

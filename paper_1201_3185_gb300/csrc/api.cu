@@ -26,12 +26,12 @@ struct Level {
 enum Kind {
     K_DEPOSIT, K_FIXED_TO_RHO, K_BOUNDARY, K_CONVERT_RHS, K_RESTRICT_FULL, K_COARSE, K_RB_FINEST, K_RB_COARSER,
     K_RESTRICT_RESID, K_PROLONG, K_SET_BOUNDARY, K_ASSIGN_OUTER, K_RESIDUAL_OUTER, K_REDUCE, K_SOURCE, K_FORCES,
-    K_ROTATION_CURVE, K_FIXED_SETUP, K_FIXED_OUTPUT, K_COUNT
+    K_ROTATION_CURVE, K_FIXED_SETUP, K_FIXED_OUTPUT, K_CHI2, K_COUNT
 };
 const char* const kKindNames[K_COUNT] = {
     "cic_deposit", "fixed_to_rho", "boundary_fill", "convert_rhs", "restrict_full", "coarse_solver",
     "rb_half_finest", "rb_half_coarser", "restrict_resid_red", "prolong_black", "set_boundary", "update_outer",
-    "residual_outer", "reduce_norms", "qumond_source", "forces", "rotation_curve", "fixed_setup", "fixed_output",
+    "residual_outer", "reduce_norms", "qumond_source", "forces", "rotation_curve", "fixed_setup", "fixed_output", "chi2",
 };
 constexpr int kMaxTimed = 32768;
 
@@ -908,6 +908,21 @@ qumond_status qumond_rotation_curve(qumond_ctx* c, const double* const* phi_boxe
                               nphi, c->p.rc_box_frac, r_out, vc_out, S(stream));
     });
     CUDA_TRY(c, cudaGetLastError(), "rotation_curve launch");
+    return QUMOND_OK;
+}
+
+qumond_status qumond_chi2(qumond_ctx* c, const double* vc, const double* v_obs, const double* sigma, int nbins,
+                          int nsets, double* chi2, void* stream)
+{
+    if (!c) return QUMOND_ERR_INVALID_ARG;
+    c->err.clear();
+    if (nbins < 1 || nsets < 0) return fail(c, QUMOND_ERR_INVALID_ARG, "chi2: need nbins >= 1 and nsets >= 0");
+    if (nsets == 0) return QUMOND_OK;
+    if (!device_ptr(vc) || !device_ptr(v_obs) || !device_ptr(sigma) || !device_ptr(chi2))
+        return fail(c, QUMOND_ERR_INVALID_ARG, "chi2: every array must be a device pointer");
+    run(c, K_CHI2, 8.0 * ((double)nbins * (nsets + 2) + nsets), S(stream),
+        [&] { launch_chi2(vc, v_obs, sigma, nbins, nsets, chi2, S(stream)); });
+    CUDA_TRY(c, cudaGetLastError(), "chi2 launch");
     return QUMOND_OK;
 }
 

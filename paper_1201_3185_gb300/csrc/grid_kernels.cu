@@ -437,4 +437,31 @@ void launch_rotation_curve(const BoxSet& boxes, double cx, double cy, double cz,
     rotation_curve_kernel<<<nbins, 128, 0, s>>>(boxes, cx, cy, cz, nbins, rmax, nphi, frac, r_out, vc_out);
 }
 
+// Quality of fit (Section 3.5): chi2[s] = (1/nbins) sum_i ((vc[s][i] - v_obs[i]) / sigma[i])^2.
+// One warp per parameter set; lane l sums bins l, l+32, ... and the warp adds
+// the 32 partial sums by a fixed shuffle tree, so the result does not depend
+// on scheduling.
+__global__ void chi2_kernel(const double* __restrict__ vc, const double* __restrict__ v_obs,
+                            const double* __restrict__ sigma, int nbins, int nsets, double* __restrict__ chi2)
+{
+    const int set = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (set >= nsets) return;
+    const double* row = vc + (long long)set * nbins;
+    double acc = 0.0;
+    for (int i = lane; i < nbins; i += 32) {
+        const double d = (row[i] - v_obs[i]) / sigma[i];
+        acc += d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) chi2[set] = acc / (double)nbins;
+}
+
+void launch_chi2(const double* vc, const double* v_obs, const double* sigma, int nbins, int nsets, double* chi2,
+                 cudaStream_t s)
+{
+    const int warps = 4;
+    chi2_kernel<<<(nsets + warps - 1) / warps, 32 * warps, 0, s>>>(vc, v_obs, sigma, nbins, nsets, chi2);
+}
+
 }  // namespace qumond

@@ -144,5 +144,7 @@ void launch_forces(const BoxSet& boxes, const double* qx, const double* qy, cons
                    double* gx, double* gy, double* gz, cudaStream_t s);
 void launch_rotation_curve(const BoxSet& boxes, double cx, double cy, double cz, int nbins, double rmax, int nphi,
                            double frac, double* r_out, double* vc_out, cudaStream_t s);
+void launch_chi2(const double* vc, const double* v_obs, const double* sigma, int nbins, int nsets, double* chi2,
+                 cudaStream_t s);
 
 }  // namespace qumond

@@ -37,7 +37,7 @@ QUMOND_BC_GIVEN = 1
 EXPORTED = (
     "qumond_default_params", "qumond_create", "qumond_destroy", "qumond_last_error", "qumond_deposit",
     "qumond_solve_newton", "qumond_source", "qumond_solve_mond", "qumond_forces", "qumond_rotation_curve",
-    "qumond_trace_classes", "qumond_trace_timing", "qumond_trace_read", "qumond_solve_mond_noalloc",
+    "qumond_chi2", "qumond_trace_classes", "qumond_trace_timing", "qumond_trace_read", "qumond_solve_mond_noalloc",
 )
 NOALLOC_MAX_N = 64
 
@@ -110,6 +110,7 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
         "qumond_solve_mond": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(qumond_stats), _P]),
         "qumond_forces": (_I, [_P, _P, _P, _P, _P, _L, _P, _P, _P, _P]),
         "qumond_rotation_curve": (_I, [_P, _P, _I, _D, _I, _P, _P, _P]),
+        "qumond_chi2": (_I, [_P, _P, _P, _P, _I, _I, _P, _P]),
         "qumond_trace_classes": (_I, []),
         "qumond_trace_timing": (_I, [_P, _I, _I]),
         "qumond_trace_read": (_I, [_P, ctypes.POINTER(qumond_kernel_stat), _I, ctypes.POINTER(qumond_counters), _I]),
@@ -306,6 +307,15 @@ class Context:
         v = _dev(vc_out, torch.float64, nbins, "vc_out")
         self._check(_lib.qumond_rotation_curve(self._ptr, ctypes.cast(arr, _P), nbins, float(rmax), nphi, r, v,
                                                _stream(stream)))
+
+    def qumond_chi2(self, vc, v_obs, sigma, chi2_out, stream=None):
+        """Reduced chi^2 of each row of vc (nsets x nbins) against v_obs, sigma."""
+        nsets, nbins = (vc.shape[0], vc.shape[1]) if vc.dim() == 2 else (1, vc.numel())
+        a = _dev(vc, torch.float64, nsets * nbins, "vc")
+        b = _dev(v_obs, torch.float64, nbins, "v_obs")
+        c = _dev(sigma, torch.float64, nbins, "sigma")
+        d = _dev(chi2_out, torch.float64, nsets, "chi2")
+        self._check(_lib.qumond_chi2(self._ptr, a, b, c, nbins, nsets, d, _stream(stream)))
 
     # -- tracing ------------------------------------------------------------------
     def qumond_trace_timing(self, on: bool, only: str | None = None):

@@ -15,4 +15,5 @@ from .galaxies import (  # noqa: F401
     two_component_disk,
     large_galaxy,
     fit_sweep_parameters,
+    SweepGalaxy,
 )

@@ -3,13 +3,16 @@
 * Kuzmin disk (Section 3.1): enclosed mass M(1 - a/sqrt(R^2+a^2)), so a mass
   fraction f sits inside R = a sqrt((1-f)^-2 - 1); azimuth uniform; z = 0.
 * Exponential disk with sech^2 vertical profile (Sections 3.3-3.4): radius
-  from the enclosed-mass fraction 1 - (1+x) e^-x, x = R/R_d (solved by
-  bisection, which draws exactly the distribution the paper's rejection
-  sampler draws); z = h atanh(2u - 1) for rho ~ sech^2(z/h).
+  from the enclosed-mass fraction 1 - (1+x) e^-x, x = R/R_d (inverted on a
+  fine table, which draws the distribution the paper's rejection sampler
+  draws); z = h atanh(2u - 1) for rho ~ sech^2(z/h).
 * Hernquist bulge: M(<r) = M r^2/(r+a)^2, so r = a sqrt(u)/(1 - sqrt(u)),
   isotropic direction.
 * Two components (Section 3.4): stars and gas each get half of the particles,
   each particle weighted by its component's total mass.
+* Fit sweeps (Section 3.5): every parameter set (distance, stellar M/L,
+  stellar and gas scale heights) rescales one seeded set of draws (common
+  random numbers), so the sets differ only through their parameters.
 """
 from __future__ import annotations
 
@@ -58,18 +61,21 @@ def kuzmin_disk(n: int, M: float, a: float, seed=0, stratified: bool = False) ->
 
 def _exp_radius(u: np.ndarray, Rd: float, rmax: float) -> np.ndarray:
     """Radius whose enclosed-mass fraction of an exponential disk truncated at
-    rmax equals u (bisection, 80 halvings)."""
+    rmax equals u: the fraction is inverted by bisection (60 halvings) on a
+    table of 2^16+1 points and interpolated linearly in between."""
     xmax = rmax / Rd
     norm = 1.0 - (1.0 + xmax) * np.exp(-xmax)
-    target = u * norm
-    lo = np.zeros_like(u)
-    hi = np.full_like(u, xmax)
-    for _ in range(80):
+    ut = np.linspace(0.0, 1.0, (1 << 16) + 1)
+    target = ut * norm
+    lo = np.zeros_like(ut)
+    hi = np.full_like(ut, xmax)
+    for _ in range(60):
         mid = 0.5 * (lo + hi)
         below = (1.0 - (1.0 + mid) * np.exp(-mid)) < target
         lo = np.where(below, mid, lo)
         hi = np.where(below, hi, mid)
-    return 0.5 * (lo + hi) * Rd
+    xt = 0.5 * (lo + hi)
+    return np.interp(u, ut, xt) * Rd
 
 
 def _sech2_height(u: np.ndarray, h: float, zmax: float) -> np.ndarray:
@@ -143,3 +149,42 @@ def fit_sweep_parameters(nsets: int, seed=0) -> np.ndarray:
     lo = np.array([0.8, 0.3, 200.0, 50.0])
     hi = np.array([1.2, 1.2, 1000.0, 500.0])
     return lo + (hi - lo) * u
+
+
+class SweepGalaxy:
+    """Two-component disk of a rotation-curve fit (Section 3.5) for any
+    parameter set (distance scale d, stellar M/L, stellar scale height h_star
+    pc, gas scale height h_gas pc), from draws made once with `seed`.
+
+    The fitted galaxy is the observed one seen at a distance d times the
+    nominal one: every in-plane length scales by d (scale lengths, truncation
+    radius), the stellar luminosity and the gas mass by d^2; the stellar mass
+    is M/L times the luminosity 2 pi I0 (d Rd)^2.  Scale heights are free
+    parameters in pc.  Half of the particles are stars, half gas."""
+
+    def __init__(self, n_total: int, seed=0, *, I0: float = 500.0, Rd: float = 3000.0, M_gas: float = 1.0e9,
+                 Rg: float = 8000.0, rmax: float = 30000.0, zmax: float = 5000.0):
+        rng = _rng(seed)
+        self.ns = n_total // 2
+        self.ng = n_total - self.ns
+        self.I0, self.Rd, self.M_gas, self.Rg, self.rmax, self.zmax = I0, Rd, M_gas, Rg, rmax, zmax
+        # radii in units of the scale length at d = 1 (the truncation scales with d as well)
+        self.Xs = _exp_radius(rng.random(self.ns), 1.0, rmax / Rd)
+        ps = 2.0 * np.pi * rng.random(self.ns)
+        self.us = rng.random(self.ns)
+        self.Xg = _exp_radius(rng.random(self.ng), 1.0, rmax / Rg)
+        pg = 2.0 * np.pi * rng.random(self.ng)
+        self.ug = rng.random(self.ng)
+        self.cs, self.ss = np.cos(ps), np.sin(ps)
+        self.cg, self.sg = np.cos(pg), np.sin(pg)
+
+    def particles(self, params) -> Particles:
+        d, ml, h_star, h_gas = (float(v) for v in params)
+        M_star = ml * 2.0 * np.pi * self.I0 * (d * self.Rd) ** 2
+        Rs = self.Xs * (d * self.Rd)
+        Rg = self.Xg * (d * self.Rg)
+        x = np.concatenate([Rs * self.cs, Rg * self.cg])
+        y = np.concatenate([Rs * self.ss, Rg * self.sg])
+        z = np.concatenate([_sech2_height(self.us, h_star, self.zmax), _sech2_height(self.ug, h_gas, self.zmax)])
+        m = np.concatenate([np.full(self.ns, M_star / self.ns), np.full(self.ng, d * d * self.M_gas / self.ng)])
+        return Particles(x, y, z, m)

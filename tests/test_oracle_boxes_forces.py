@@ -43,3 +43,14 @@ def test_rotation_curve_of_harmonic_potential(ora):
     r, vc = ora.rotation_curve(n, L0, c, phis, 40, 20000.0, 64)
     assert np.allclose(r, (np.arange(40) + 0.5) * 500.0)
     assert np.max(np.abs(vc - om * r)) < 1e-9 * np.max(vc)
+
+
+def test_chi2_definition(ora):
+    # Section 3.5: chi^2/n; zero for a perfect fit, 1 when every point is off by one sigma
+    v_obs = np.array([100.0, 120.0, 130.0, 135.0])
+    sigma = 0.03 * v_obs
+    vc = np.stack([v_obs, v_obs + sigma, v_obs - 2.0 * sigma])
+    got = ora.chi2(vc, v_obs, sigma)
+    assert got[0] == 0.0
+    assert got[1] == pytest.approx(1.0, rel=1e-14)
+    assert got[2] == pytest.approx(4.0, rel=1e-14)
