@@ -5,6 +5,7 @@ raises ImportError if the library is missing.  There is no CPU fallback.
 """
 from .qumond import (  # noqa: F401
     Context,
+    Guess,
     NotConverged,
     QumondError,
     SolveStats,

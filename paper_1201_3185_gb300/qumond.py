@@ -38,6 +38,9 @@ EXPORTED = (
     "qumond_default_params", "qumond_create", "qumond_destroy", "qumond_last_error", "qumond_deposit",
     "qumond_solve_newton", "qumond_source", "qumond_solve_mond", "qumond_forces", "qumond_rotation_curve",
     "qumond_chi2", "qumond_trace_classes", "qumond_trace_timing", "qumond_trace_read", "qumond_solve_mond_noalloc",
+    "qumond_guess_num_params", "qumond_guess_create", "qumond_guess_destroy", "qumond_guess_last_error",
+    "qumond_guess_set_params", "qumond_guess_get_params", "qumond_guess_make_sample", "qumond_guess_forward",
+    "qumond_guess_gradients", "qumond_guess_train_step", "qumond_guess_apply",
 )
 NOALLOC_MAX_N = 64
 
@@ -116,6 +119,17 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
         "qumond_trace_read": (_I, [_P, ctypes.POINTER(qumond_kernel_stat), _I, ctypes.POINTER(qumond_counters), _I]),
         "qumond_solve_mond_noalloc": (_I, [ctypes.POINTER(qumond_params), _I, _P, _P, _P, ctypes.POINTER(qumond_stats),
                                            _P, ctypes.c_char_p, ctypes.c_size_t]),
+        "qumond_guess_num_params": (ctypes.c_int64, []),
+        "qumond_guess_create": (_I, [_I, _D, ctypes.POINTER(_P)]),
+        "qumond_guess_destroy": (None, [_P]),
+        "qumond_guess_last_error": (ctypes.c_char_p, [_P]),
+        "qumond_guess_set_params": (_I, [_P, _P, _P]),
+        "qumond_guess_get_params": (_I, [_P, _P, _P]),
+        "qumond_guess_make_sample": (_I, [_P, _D, _P, _P, _P, _P, _P]),
+        "qumond_guess_forward": (_I, [_P, _P, ctypes.c_float, _P, _P]),
+        "qumond_guess_gradients": (_I, [_P, _P, _P, _I, _P, _P, _P]),
+        "qumond_guess_train_step": (_I, [_P, _P, _P, _I, ctypes.c_float, _P, _P]),
+        "qumond_guess_apply": (_I, [_P, _D, ctypes.c_float, _P, _P, _P, _P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -344,3 +358,87 @@ class Context:
         stats = {a.name.decode(): KernelStat(a.name.decode(), a.launches, a.bytes, a.ms, a.timed, a.timed_bytes)
                  for a in arr}
         return stats, tot.launches, tot.cell_updates
+
+
+# --- the learned initial guess (include/qumond_guess.h) ---------------------------------
+class Guess:
+    """A qumond_guess: the U-Net that maps (rho, Phi_N) of a box to Phi - Phi_N."""
+
+    def __init__(self, S: int, phi_scale: float):
+        self.S = int(S)
+        self.phi_scale = float(phi_scale)
+        self._ptr = ctypes.c_void_p()
+        st = _lib.qumond_guess_create(self.S, self.phi_scale, ctypes.byref(self._ptr))
+        if st != QUMOND_OK:
+            raise QumondError(st, "qumond_guess_create failed (S must be a multiple of 16 in [16, 512]; "
+                                  "or out of memory)")
+
+    @staticmethod
+    def num_params() -> int:
+        return int(_lib.qumond_guess_num_params())
+
+    @property
+    def voxels(self) -> int:
+        return self.S ** 3
+
+    def close(self):
+        if self._ptr:
+            _lib.qumond_guess_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != QUMOND_OK:
+            raise QumondError(st, _lib.qumond_guess_last_error(self._ptr).decode())
+
+    def qumond_guess_set_params(self, params, stream=None):
+        self._check(_lib.qumond_guess_set_params(self._ptr, _dev(params, torch.float32, self.num_params(), "params"),
+                                                 _stream(stream)))
+
+    def qumond_guess_get_params(self, params, stream=None):
+        self._check(_lib.qumond_guess_get_params(self._ptr, _dev(params, torch.float32, self.num_params(), "params"),
+                                                 _stream(stream)))
+
+    def qumond_guess_make_sample(self, rho_scale, rho, phiN, phi, sample, stream=None):
+        n = (self.S + 1) ** 3
+        self._check(_lib.qumond_guess_make_sample(
+            self._ptr, float(rho_scale), _dev(rho, torch.float64, n, "rho"), _dev(phiN, torch.float64, n, "phiN"),
+            _dev(phi, torch.float64, n, "phi"), _dev(sample, torch.bfloat16, 3 * self.voxels, "sample"),
+            _stream(stream)))
+
+    def qumond_guess_forward(self, sample, box_flag, y, stream=None):
+        self._check(_lib.qumond_guess_forward(self._ptr, _dev(sample, torch.bfloat16, 3 * self.voxels, "sample"),
+                                              float(box_flag), _dev(y, torch.float32, self.voxels, "y"),
+                                              _stream(stream)))
+
+    def _batch(self, samples, flags):
+        if len(samples) != len(flags) or not samples:
+            raise ValueError("need one box flag per sample, at least one sample")
+        ptrs = (ctypes.c_void_p * len(samples))(
+            *[_dev(t, torch.bfloat16, 3 * self.voxels, "sample").value for t in samples])
+        fl = (ctypes.c_float * len(flags))(*[float(f) for f in flags])
+        return ptrs, fl
+
+    def qumond_guess_gradients(self, samples, flags, grads, loss=None, stream=None):
+        ptrs, fl = self._batch(samples, flags)
+        lp = _dev(loss, torch.float32, 1, "loss") if loss is not None else None
+        self._check(_lib.qumond_guess_gradients(self._ptr, ctypes.cast(ptrs, _P), ctypes.cast(fl, _P), len(samples),
+                                                _dev(grads, torch.float32, self.num_params(), "grads"), lp,
+                                                _stream(stream)))
+
+    def qumond_guess_train_step(self, samples, flags, lr, loss=None, stream=None):
+        ptrs, fl = self._batch(samples, flags)
+        lp = _dev(loss, torch.float32, 1, "loss") if loss is not None else None
+        self._check(_lib.qumond_guess_train_step(self._ptr, ctypes.cast(ptrs, _P), ctypes.cast(fl, _P), len(samples),
+                                                 float(lr), lp, _stream(stream)))
+
+    def qumond_guess_apply(self, rho_scale, box_flag, rho, phiN, phi, stream=None):
+        n = (self.S + 1) ** 3
+        self._check(_lib.qumond_guess_apply(self._ptr, float(rho_scale), float(box_flag),
+                                            _dev(rho, torch.float64, n, "rho"), _dev(phiN, torch.float64, n, "phiN"),
+                                            _dev(phi, torch.float64, n, "phi"), _stream(stream)))

@@ -1,4 +1,4 @@
-"""The C ABI library loads and exports every entry point include/qumond.h declares (no GPU needed)."""
+"""The C ABI library loads and exports every entry point include/*.h declares (no GPU needed)."""
 import ctypes
 import os
 import re
@@ -9,7 +9,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_symbols():
-    text = open(os.path.join(ROOT, "include", "qumond.h")).read()
+    text = "".join(open(os.path.join(ROOT, "include", f)).read() for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+                   if f.endswith(".h"))
     return sorted(set(re.findall(r"QUMOND_API\s+[\w\s\*]+?\b(qumond_\w+)\s*\(", text)))
 
 
@@ -36,3 +37,10 @@ def test_params_struct_matches_defaults():
     assert (p.n, p.ncycle, p.npre, p.npost) == (256, 6, 2, 2)
     assert p.G == pytest.approx(4.30e-3) and p.a0 == pytest.approx(3.6)
     assert p.deposit_shift == 24 and p.rc_box_frac == pytest.approx(0.2)
+
+
+def test_guess_parameter_count():
+    import paper_1201_3185_gb300 as q
+    layers = [(16, 16), (16, 16), (16, 32), (32, 32), (32, 64), (64, 64), (64, 128), (128, 128), (192, 64), (64, 64),
+              (96, 32), (32, 32), (48, 16), (16, 16)]
+    assert q.Guess.num_params() == sum(27 * a * b + b for a, b in layers) + 17 == 1466065
