@@ -53,6 +53,12 @@ SWEEP = dict(n=128, nboxes=2, L0=80000.0, particles=500_000, galaxy_seed=11, set
              rel_tol=1e-8, max_vcycles=40, ncycle=1, npre=2, npost=2, nbins=40, rmax=24000.0, nphi=64, kind="sweep",
              target="tests/golden/sweep_target_two_disk_129cube.json")
 WORKLOADS["sweep"] = SWEEP
+# the learned initial guess: two-disk galaxies (stellar h in [0.3, 0.6] kpc) on 129^3 x 2 boxes (80/40 kpc),
+# 2e5 particles; one step = the whole path of one galaxy with the QUMOND solves started from the network's
+# guess, solves to rel. residual 1e-8
+LEARNED = dict(n=128, nboxes=2, L0=80000.0, particles=200_000, galaxies=8, seed=7919, rel_tol=1e-8, max_vcycles=60,
+               ncycle=1, npre=2, npost=2, nbins=40, rmax=24000.0, nphi=64, kind="learned")
+WORKLOADS["learned"] = LEARNED
 WORKLOAD = dict(WORKLOADS["two-disk"])
 
 
@@ -635,6 +641,150 @@ def run_sweep(args):
     rep.close()
 
 
+# --- the learned initial guess -------------------------------------------------------------
+def learned_config(precision):
+    w = WORKLOAD
+    return {
+        "workload": "learned initial guess: two-disk galaxies (stellar disk Sigma0=500 Msun/pc^2, R_d=3 kpc, sech^2 "
+                    "h_* uniform in [0.3,0.6] kpc; gas 1e9 Msun, R_g=8 kpc, h_g=0.1 kpc), %d particles, %d^3 nodes "
+                    "x %d nested boxes of %g/%g kpc; whole path per galaxy with each QUMOND solve started from "
+                    "Phi_N + U-Net(rho, Phi_N) (BF16, 4 levels 16-32-64-128 channels) and V-cycles to rel. residual "
+                    "%g" % (w["particles"], w["n"] + 1, w["nboxes"], w["L0"] / 1000.0, w["L0"] / 2000.0, w["rel_tol"]),
+        "galaxies": w["galaxies"],
+        "precision": precision,
+        "rel_tol": w["rel_tol"],
+        "weights": "paper_1201_3185_gb300/weights/unet_two_disk_129cube.npy (trained on the GPU by "
+                   "python -m paper_1201_3185_gb300.learned train)",
+        "l2": "inputs larger than L2: 8 galaxies x 2e5 particles; every step writes ~10 129^3 FP64 grids",
+        "data": "synthetic (seeded generator), evaluation galaxies disjoint from the training draws",
+    }
+
+
+def run_learned(args):
+    import numpy as np
+    import torch
+
+    import paper_1201_3185_gb300 as q
+    from paper_1201_3185_gb300 import learned as L
+    from paper_1201_3185_gb300.replicas import Replicas
+    rep = Replicas.from_env()
+    ws, rank, local = rep.world_size, rep.rank, rep.local_rank
+    dev = rep.device
+    w = WORKLOAD
+    prec = {"fp64": q.QUMOND_PREC_FP64, "mixed": q.QUMOND_PREC_MIXED, "fixed": q.QUMOND_PREC_MIXED_FIXED}[args.precision]
+    work = L.Workload(n=w["n"], L0=w["L0"], nboxes=w["nboxes"], particles=w["particles"], seed=w["seed"] + rank,
+                      device=dev)
+    gals = [work.galaxy()[0] for _ in range(w["galaxies"])]
+
+    def ctx(precision, warm=0):
+        return q.Context(q.default_params(n=w["n"], nboxes=w["nboxes"], L0=w["L0"], rel_tol=w["rel_tol"],
+                                          max_vcycles=w["max_vcycles"], ncycle=w["ncycle"], npre=w["npre"],
+                                          npost=w["npost"], precision=precision, warm_start=warm))
+
+    guess = q.Guess(w["n"], L.PHI_SCALE)
+    guess.qumond_guess_set_params(torch.from_numpy(L.load_weights()).to(dev))
+    c_fmg, c_warm = ctx(prec), ctx(prec, 1)
+    p_learn = q.Pipeline(c_fmg, dev, guess=guess, ctx_warm=c_warm)
+    p_fmg = q.Pipeline(ctx(prec), dev)
+
+    def run(pipe, n_steps):
+        for k in range(n_steps):
+            x, y, z, m = gals[k % len(gals)]
+            pipe.potentials(x, y, z, m)
+
+    def timed(pipe, n_steps):
+        run(pipe, min(args.warmup, len(gals)))
+        rep.barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        run(pipe, n_steps)
+        t1.record()
+        rep.barrier()
+        return rep.max(t0.elapsed_time(t1)) / n_steps
+
+    vcyc = {"learned": [], "fmg": []}
+    for pipe, key in ((p_learn, "learned"), (p_fmg, "fmg")):
+        for k in range(len(gals)):
+            _, ms = pipe.potentials(*gals[k], stats=True)
+            vcyc[key] += [s.vcycles for s in ms]
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_learn = timed(p_learn, args.steps)
+    clk = clocks.stop()
+    ms_fmg = timed(p_fmg, args.steps)
+    value = ws * 1000.0 / ms_learn
+
+    # plain FP64 FMG, same path and tolerance
+    plain = None
+    if not args.no_plain:
+        pp = q.Pipeline(ctx(q.QUMOND_PREC_FP64), dev)
+        ms_plain = timed(pp, max(1, min(args.steps, 8)))
+        plain = {"value": ws * 1000.0 / ms_plain, "unit": UNIT, "ms_per_step": ms_plain,
+                 "precision": PRECISION_NAMES["fp64"] + " FMG start (same path, same tolerance)",
+                 "speedup_of_value": ms_plain / ms_learn}
+
+    # the network alone: one inference (14 convolutions + pooling/upsampling + head) timed with events
+    S = w["n"]
+    layers = [(16, 16), (16, 16), (16, 32), (32, 32), (32, 64), (64, 64), (64, 128), (128, 128), (192, 64),
+              (64, 64), (96, 32), (32, 32), (48, 16), (16, 16)]
+    lev = [0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0]
+    flops = float(sum(2 * 27 * ci * co * (S >> l) ** 3 for (ci, co), l in zip(layers, lev)))
+    smp = torch.empty(3 * S ** 3, dtype=torch.bfloat16, device=dev)
+    p_fmg.potentials(*gals[0])
+    guess.qumond_guess_make_sample(p_learn.rho_scale(0), p_fmg.rho, p_fmg.phiN[-1], p_fmg.phi[-1], smp)
+    yv = torch.empty(S ** 3, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        guess.qumond_guess_forward(smp, 1.0, yv)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(10):
+        guess.qumond_guess_forward(smp, 1.0, yv)
+    f1.record()
+    f1.synchronize()
+    inf_ms = f0.elapsed_time(f1) / 10
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    f0.record()
+    for _ in range(5):
+        guess.qumond_guess_gradients([smp], [1.0], torch.empty(q.Guess.num_params(), dtype=torch.float32,
+                                                               device=dev), loss)
+    f1.record()
+    f1.synchronize()
+    grad_ms = f0.elapsed_time(f1) / 5
+    peaks = measured_peaks()
+    peak = peaks["bf16_tflops"] if peaks else 1900.0
+    achieved = flops / (inf_ms * 1e9)
+    roofline = {"bound": "tensor", "kernel": "conv3_kernel (the 14 convolutions of one network inference)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "algorithmic_flops_per_inference": flops, "inference_ms": inf_ms,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst, measured)" if peaks else "fallback",
+                "note": "mma.sync m16n8k16 BF16 tensor-core path; the time includes pooling, upsampling and head "
+                        "launches"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_learn, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16+f32+int64", "data": "synthetic",
+            "config": learned_config(PRECISION_NAMES[args.precision]),
+            "fmg_start_same_precision": {"value": ws * 1000.0 / ms_fmg, "unit": UNIT, "ms_per_step": ms_fmg,
+                                         "speedup_of_value": ms_fmg / ms_learn},
+            "plain_fmg": plain,
+            "mean_vcycles_per_mond_solve": {k: float(np.mean(v)) for k, v in vcyc.items()},
+            "roofline": roofline,
+            "training_step_ms_per_sample": grad_ms,
+            "training_tflops": 3.0 * flops / (grad_ms * 1e9),
+            "e2e": None,
+            "gpu_launches": None,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    rep.close()
+
+
 # --- the oracle (CPU) ------------------------------------------------------------------
 def oracle_sweep_sample(gal, prm, v_obs, sigma):
     """The sweep's path for the given parameter sets with the FP64 oracle:
@@ -786,7 +936,8 @@ def main():
                     help="2: QUMOND solves on a second context and stream, concurrent with the Newtonian chain")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="two-disk",
                     help="two-disk: the metric's 256^3 x 3-box configuration; large: 512^3 x 4 boxes; "
-                         "sweep: the 64-set rotation-curve fit sweep at 128^3 x 2 boxes")
+                         "sweep: the 64-set rotation-curve fit sweep at 128^3 x 2 boxes; "
+                         "learned: the whole path with the QUMOND solves started from the U-Net guess")
     ap.add_argument("--workers", type=int, default=0,
                     help="sweep: concurrent workers (0: pick by timing)")
     ap.add_argument("--profile-case", action="store_true",
@@ -802,6 +953,8 @@ def main():
         run_reference_sweep(args) if args.workload == "sweep" else run_reference(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 

@@ -12,7 +12,8 @@ of the Newtonian equation in units of the potential per cell), channel 1 =
 Phi_N / phi_scale; phi_scale = 1e5 (km/s)^2, the depth of the two-disk
 galaxies' potentials.
 
-    python -m paper_1201_3185_gb300.learned train --galaxies 4000 --epochs 4 --out weights.npy
+    python -m paper_1201_3185_gb300.learned train --galaxies 4000 --epochs 3 --out weights.npy
+    python -m paper_1201_3185_gb300.learned evaluate --eval-galaxies 8
 """
 from __future__ import annotations
 
@@ -169,11 +170,15 @@ def train(guess: Guess, samples, *, epochs=1, batch=4, lr=1e-3, lr_final=1e-4, s
     return losses[:step].cpu().numpy()
 
 
+STARTS = ("fmg", "learned", "phiN")
+
+
 def evaluate(work: Workload, guess: Guess, ngal: int, rel_tol=1e-8):
     """For ngal fresh galaxies, every box: the QUMOND solve to rel_tol started
-    from (a) FMG, (b) the network's guess, (c) Phi_N, (d) zero; V-cycles after
-    the start, the start's relative residual, and CUDA-event times of the
-    solve (with the guess's inference for (b))."""
+    from (a) FMG, (b) the network's guess, (c) Phi_N; V-cycles after the
+    start, the start's relative residual, and CUDA-event times of the solve
+    (with the guess's inference for (b)).  (A zero start is not offered: the
+    fixed-point defect correction takes its scale from the starting iterate.)"""
     dev = work.device
     base = work.context(rel_tol=1e-10)
     fmg = work.context(rel_tol=rel_tol)
@@ -188,14 +193,10 @@ def evaluate(work: Workload, guess: Guess, ngal: int, rel_tol=1e-8):
             sol.mond(b, stats=False)  # parent values for the next box come from an accurate solve
             keep = sol.phi[b].clone()
             row = {"box": b, "h_star": h}
-            for name in ("fmg", "learned", "phiN", "zero"):
+            for name in STARTS:
                 ctx = fmg if name == "fmg" else warm
-                if name == "learned":
+                if name != "fmg":
                     sol.phi[b].copy_(sol.phiN[b])
-                elif name == "phiN":
-                    sol.phi[b].copy_(sol.phiN[b])
-                elif name == "zero":
-                    sol.phi[b].zero_()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 torch.cuda.synchronize()
                 e0.record()
@@ -216,7 +217,7 @@ def evaluate(work: Workload, guess: Guess, ngal: int, rel_tol=1e-8):
 
 def summarize(rows):
     out = {}
-    for name in ("fmg", "learned", "phiN", "zero"):
+    for name in STARTS:
         out[name] = {"mean_vcycles": float(np.mean([r[name]["vcycles"] for r in rows])),
                      "mean_ms": float(np.mean([r[name]["ms"] for r in rows])),
                      "median_rel_residual_start": float(np.median([r[name]["rel_residual_start"] for r in rows]))}
@@ -225,7 +226,7 @@ def summarize(rows):
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("cmd", choices=["train"])
+    ap.add_argument("cmd", choices=["train", "evaluate"])
     ap.add_argument("--galaxies", type=int, default=4000)
     ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--batch", type=int, default=4)
@@ -237,10 +238,21 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default="weights.npy")
     ap.add_argument("--report", default=None)
+    ap.add_argument("--weights", default=WEIGHTS, help="evaluate: the parameter file")
     args = ap.parse_args()
     dev = torch.device("cuda", 0)
-    work = Workload(n=args.n, particles=args.particles, seed=args.seed, device=dev)
     guess = Guess(args.n, PHI_SCALE)
+    if args.cmd == "evaluate":
+        guess.qumond_guess_set_params(torch.from_numpy(load_weights(args.weights)).to(dev))
+        ev = Workload(n=args.n, particles=args.particles, seed=args.seed + 7919, device=dev)
+        rows = evaluate(ev, guess, args.eval_galaxies)
+        rep = {"weights": args.weights, "eval": summarize(rows)}
+        print(json.dumps(rep), flush=True)
+        if args.report:
+            with open(args.report, "w") as f:
+                json.dump({"report": rep, "rows": rows}, f)
+        return
+    work = Workload(n=args.n, particles=args.particles, seed=args.seed, device=dev)
     p0 = torch.from_numpy(he_init(args.seed)).to(dev)
     guess.qumond_guess_set_params(p0)
     t0 = time.time()

@@ -16,6 +16,10 @@ Each solve spends a large part of its time on small multigrid levels that
 leave most of the GPU idle, and the other chain fills it.  The kernels and
 their order within each chain are unchanged, so the results are the same
 bits as the sequential order.
+
+Learned initial guess: with `guess` (a Guess for S = n) and `ctx_warm` (a
+context with warm_start = 1), the QUMOND solve of each box starts from
+Phi_N + the network's output instead of FMG (sequential order only).
 """
 from __future__ import annotations
 
@@ -23,9 +27,11 @@ import concurrent.futures as cf
 import threading
 from dataclasses import dataclass, field
 
+import math
+
 import torch
 
-from .qumond import Context
+from .qumond import Context, Guess
 
 
 @dataclass
@@ -37,9 +43,19 @@ class PipelineResult:
 
 
 class Pipeline:
-    def __init__(self, ctx: Context, device=None, ctx_mond: Context | None = None):
+    def __init__(self, ctx: Context, device=None, ctx_mond: Context | None = None, guess: Guess | None = None,
+                 ctx_warm: Context | None = None):
         self.ctx = ctx
         self.ctx_mond = ctx_mond
+        if (guess is None) != (ctx_warm is None):
+            raise ValueError("a learned guess needs both the network and a warm-start context")
+        if guess is not None:
+            if ctx_mond is not None:
+                raise ValueError("the learned guess runs in the sequential order only")
+            if guess.S != ctx.params.n or not ctx_warm.params.warm_start:
+                raise ValueError("the network must match n and ctx_warm must have warm_start = 1")
+        self.guess = guess
+        self.ctx_warm = ctx_warm
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         nodes = ctx.nodes
         nb = ctx.params.nboxes
@@ -73,8 +89,20 @@ class Pipeline:
             par_m = self.phi[b - 1] if b > 0 else None
             ns.append(c.qumond_solve_newton(b, self.rho, par_n, self.phiN[b], stats=stats, stream=stream))
             c.qumond_source(b, self.phiN[b], self.src, stream=stream)
-            ms.append(c.qumond_solve_mond(b, self.src, par_m, self.phi[b], stats=stats, stream=stream))
+            if self.guess is not None:
+                self.guess.qumond_guess_apply(self.rho_scale(b), float(b > 0), self.rho, self.phiN[b], self.phi[b],
+                                              stream=stream)
+                ms.append(self.ctx_warm.qumond_solve_mond(b, self.src, par_m, self.phi[b], stats=stats,
+                                                          stream=stream))
+            else:
+                ms.append(c.qumond_solve_mond(b, self.src, par_m, self.phi[b], stats=stats, stream=stream))
         return ns, ms
+
+    def rho_scale(self, b):
+        """Density channel scale of the network for box b: 4 pi G h_b^2 / phi_scale."""
+        p = self.ctx.params
+        h = self.ctx.box_side(b) / p.n
+        return 4.0 * math.pi * p.G * h * h / self.guess.phi_scale
 
     def _potentials_concurrent(self, x, y, z, m, stats, stream):
         caller = stream if stream is not None else torch.cuda.current_stream(self.device)
