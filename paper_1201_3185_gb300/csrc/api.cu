@@ -108,7 +108,8 @@ struct qumond_ctx {
     double* h_norms = nullptr;  // pinned
     SolveState* d_state = nullptr;
     SolveState* h_state = nullptr;  // pinned
-    int64_t* Ufix = nullptr;        // fixed-point master iterate (QUMOND_PREC_MIXED_FIXED)
+    int64_t* Ufix = nullptr;        // fixed-point master iterate (QUMOND_PREC_MIXED_FIXED), buffer 0
+    int64_t* Ufix2 = nullptr;       // its second buffer (the iterate alternates: current = buffer it & 1)
     int64_t* Ffix = nullptr;        // fixed-point right-hand side
     unsigned* maxbits = nullptr;
     int* fault = nullptr;           // set by kernels whose bounded waits ran out
@@ -432,7 +433,7 @@ cudaError_t enqueue_preamble(qumond_ctx* c, int box, const double* rhs, double c
         run(c, K_FIXED_SETUP, nodes * 32.0, s, [&] {
             launch_fixed_scale(eL, c->lev[c->L].v, u, n, p.warm_start != 0, c->maxbits, c->d_state, s);
             launch_fixed_init(eL, c->lev[c->L].v, u, rhs, coef, box_h(c, box), n, p.warm_start != 0, c->d_state,
-                              c->Ufix, c->Ffix, s);
+                              c->Ufix, c->Ufix2, c->Ffix, s);
         });
     }
     if (!p.warm_start) set_bnd<T>(c, c->L, nullptr, s);
@@ -445,7 +446,8 @@ template <typename T>
 cudaError_t enqueue_post(qumond_ctx* c, double* u, cudaStream_t s)
 {
     if (!fixed_mode(c)) return cudaSuccess;
-    run(c, K_FIXED_OUTPUT, cube(c->p.n) * 16.0, s, [&] { launch_fixed_output(c->Ufix, u, c->p.n, c->d_state, s); });
+    run(c, K_FIXED_OUTPUT, cube(c->p.n) * 16.0, s,
+        [&] { launch_fixed_output(c->Ufix, c->Ufix2, u, c->p.n, c->d_state, s); });
     return cudaGetLastError();
 }
 
@@ -458,13 +460,23 @@ cudaError_t enqueue_body(qumond_ctx* c, int box, const double* rhs, double coef,
     const int n = c->p.n;
     cudaError_t err = vcycle<T>(c, box, c->L, true, s);
     if (err != cudaSuccess) return err;
-    if (fixed_mode(c))
-        run(c, K_ASSIGN_OUTER, cube(n) * 20.0, s, [&] {
-            launch_fixed_update(c->Ufix, reinterpret_cast<const float*>(E<T>(c, c->L)), c->lev[c->L].v, n, c->d_state, s);
+    if (fixed_mode(c)) {
+        // update and residual in one pass (U' into the other buffer), then the decision
+        int nb = 0;
+        run(c, K_RESIDUAL_OUTER, cube(n) * 32.0, s, [&] {
+            nb = launch_fixed_update_residual(c->Ufix, c->Ufix2, c->Ffix, reinterpret_cast<const float*>(E<T>(c, c->L)),
+                                              n, box_h(c, box), c->d_state, reinterpret_cast<float*>(F<T>(c, c->L)),
+                                              c->lev[c->L].v, c->partials, s);
         });
-    else
-        run(c, K_ASSIGN_OUTER, cube(n) * (16.0 + sizeof(T)), s,
-            [&] { launch_assign_outer<T>(u, n, E<T>(c, c->L), c->lev[c->L].v, true, s); });
+        const qumond_params& p = c->p;
+        run(c, K_REDUCE, 16.0 * nb, s, [&] {
+            launch_decide(c->partials, nb, c->d_state, p.rel_tol, p.max_vcycles, false,
+                          p.rel_tol > 0.0 && p.max_vcycles > 0, handle, c->fault, s);
+        });
+        return cudaGetLastError();
+    }
+    run(c, K_ASSIGN_OUTER, cube(n) * (16.0 + sizeof(T)), s,
+        [&] { launch_assign_outer<T>(u, n, E<T>(c, c->L), c->lev[c->L].v, true, s); });
     check<T>(c, box, rhs, coef, u, false, handle, s);
     return cudaGetLastError();
 }
@@ -779,6 +791,7 @@ qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
             const int nfix = fixed_residual_blocks(p->n > 2 ? p->n : 2);
             if (nfix > c->max_partials) ok = false;  // partial buffer sized above covers it
             ok = ok && cudaMalloc(&c->Ufix, nn * sizeof(int64_t)) == cudaSuccess &&
+                 cudaMalloc(&c->Ufix2, nn * sizeof(int64_t)) == cudaSuccess &&
                  cudaMalloc(&c->Ffix, nn * sizeof(int64_t)) == cudaSuccess &&
                  cudaMalloc(&c->maxbits, sizeof(unsigned)) == cudaSuccess &&
                  cudaMemset(c->maxbits, 0, sizeof(unsigned)) == cudaSuccess;
@@ -807,6 +820,7 @@ void qumond_destroy(qumond_ctx* c)
     if (c->d_state) cudaFree(c->d_state);
     if (c->fault) cudaFree(c->fault);
     if (c->Ufix) cudaFree(c->Ufix);
+    if (c->Ufix2) cudaFree(c->Ufix2);
     if (c->Ffix) cudaFree(c->Ffix);
     if (c->maxbits) cudaFree(c->maxbits);
     if (c->h_state) cudaFreeHost(c->h_state);

@@ -102,12 +102,14 @@ __global__ void choose_scale_kernel(unsigned* __restrict__ maxbits, SolveState* 
 }
 
 // U = round(u * 2^S) on every node (interior from the FP32 FMG result or the
-// caller's warm start, boundary from the caller's FP64 values) and
-// F = round(coef * rhs * h^2 * 2^S) on interior nodes.
+// caller's warm start, boundary from the caller's FP64 values), into both
+// buffers of the iterate, and F = round(coef * rhs * h^2 * 2^S) on interior
+// nodes.
 __global__ void __launch_bounds__(kThreads)
 fixed_init_kernel(const float* __restrict__ e, LevelView v, const double* __restrict__ u64,
                   const double* __restrict__ rhs, double coef_h2, int n, int from_u64,
-                  const SolveState* __restrict__ st, long long* __restrict__ U, long long* __restrict__ F)
+                  const SolveState* __restrict__ st, long long* __restrict__ U, long long* __restrict__ U2,
+                  long long* __restrict__ F)
 {
     const int S = st->scale_exp;
     const double sc = pow2d(S);
@@ -120,8 +122,10 @@ fixed_init_kernel(const float* __restrict__ e, LevelView v, const double* __rest
         for (int i = threadIdx.x; i <= n; i += kThreads) {
             const long long o = nat(n, i, j, k);
             const bool bnd = brow || i == 0 || i == n;
-            if (bnd || from_u64) U[o] = __double2ll_rn(u64[o] * sc);
-            else U[o] = f32_to_i64(e[node_off(v, i, j, k)] * scf);
+            const long long val =
+                (bnd || from_u64) ? __double2ll_rn(u64[o] * sc) : f32_to_i64(e[node_off(v, i, j, k)] * scf);
+            U[o] = val;
+            U2[o] = val;  // the second buffer of the iterate needs the boundary values too
             F[o] = bnd ? 0LL : __double2ll_rn(rhs[o] * kf);
         }
     }
@@ -181,23 +185,131 @@ fixed_residual_kernel(const long long* __restrict__ U, const long long* __restri
     }
 }
 
-// U += round(e 2^S) on interior nodes.
-__global__ void __launch_bounds__(kThreads)
-fixed_update_kernel(long long* __restrict__ U, const float* __restrict__ e, LevelView v, int n,
-                    const SolveState* __restrict__ st)
+// One defect-correction iteration after its V-cycle, in one pass:
+//   U' = U + round(e 2^S) on interior nodes (U' = U on the boundary),
+//   R = F - (sum of the 6 neighbours of U' - 6 U'),  r = R 2^-S / h^2,
+// the same integers as updating every interior node and then running
+// fixed_residual_kernel.
+// A CTA owns a 32 x 8 tile of (i, j) columns and a chunk of k-planes; it forms
+// U' on each plane of the tile and its one-node halo in shared memory (a ring
+// of three planes) and writes U' for its own nodes.  Since a CTA reads the
+// old values of its halo while the neighbouring CTA writes their new ones,
+// the iterate alternates between two buffers: the current one is buffer
+// (it & 1), it = V-cycles made so far (advanced by the decide kernel after).
+constexpr int kFTI = 32, kFTJ = 8, kFKC = 16;
+constexpr int kFW = kFTI + 2, kFH = kFTJ + 2;
+
+__global__ void __launch_bounds__(kFTI * kFTJ)
+fixed_update_residual_kernel(long long* Ua, long long* Ub, const long long* __restrict__ F,
+                             const float* __restrict__ e, int n, float ih2, const SolveState* __restrict__ st,
+                             float* __restrict__ r, LevelView v, double* __restrict__ partials)
 {
-    const float scf = pow2f(st->scale_exp);
-    const int rows = (n - 1) * (n - 1);
-    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int j = row % (n - 1) + 1, k = row / (n - 1) + 1;
-        for (int i = threadIdx.x + 1; i < n; i += kThreads) U[nat(n, i, j, k)] += f32_to_i64(e[node_off(v, i, j, k)] * scf);
+    __shared__ long long pl[3][kFH][kFW];
+    const bool odd = (st->it & 1) != 0;
+    const long long* __restrict__ cur = odd ? Ub : Ua;
+    long long* __restrict__ nxt = odd ? Ua : Ub;
+    const int S = st->scale_exp;
+    const float scf = pow2f(S);
+    const float k = pow2f(-S) * ih2;
+    constexpr float kDown = 9.313225746154785e-10f;  // 2^-30
+    const long long P = n + 1, Q = P * P;
+    const long long plane_e = (long long)(n + 1) * v.M;  // one plane of one colour array of the level
+    const int ni = (n - 1 + kFTI - 1) / kFTI, nj = (n - 1 + kFTJ - 1) / kFTJ, nk = (n - 1 + kFKC - 1) / kFKC;
+    const int items = ni * nj * nk;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kFTI + tx;
+    constexpr int kEnt = 2;  // halo entries per thread per plane: tid and tid + 256 (34 x 10 = 340 entries)
+    float rr = 0.0f;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int i0 = 1 + (item % ni) * kFTI, j0 = 1 + ((item / ni) % nj) * kFTJ, kb = 1 + (item / (ni * nj)) * kFKC;
+        const int ke = kb + kFKC < n ? kb + kFKC : n;  // residual planes kb .. ke-1; planes kb-1 .. ke are formed
+        // per entry: position, validity, and the parts of its offsets that do not depend on the plane
+        int hi[kEnt], hj[kEnt], ii[kEnt];
+        bool valid[kEnt], inner[kEnt], own[kEnt];
+        long long ob[kEnt], eb[kEnt];
+#pragma unroll
+        for (int q = 0; q < kEnt; ++q) {
+            const int t = tid + q * kFTI * kFTJ;
+            hi[q] = t % kFW;
+            hj[q] = t / kFW;
+            const int i = i0 - 1 + hi[q], j = j0 - 1 + hj[q];  // >= 0 since i0, j0 >= 1
+            ii[q] = i + j;
+            valid[q] = t < kFW * kFH && i <= n && j <= n;
+            inner[q] = valid[q] && i >= 1 && i < n && j >= 1 && j < n;
+            own[q] = inner[q] && hi[q] >= 1 && hi[q] <= kFTI && hj[q] >= 1 && hj[q] <= kFTJ;
+            ob[q] = (long long)i + P * (long long)j;
+            eb[q] = (long long)j * v.M + (i >> 1);
+        }
+        const int ri = i0 + tx, rj = j0 + ty;
+        const bool rok = ri < n && rj < n;
+        const long long rb = (long long)ri + P * (long long)rj;
+        long long ru[kEnt];
+        float re[kEnt];
+        auto fetch = [&](int q) {  // raw U and e of plane q for this thread's entries
+            const bool qin = q >= 1 && q < n;
+#pragma unroll
+            for (int m = 0; m < kEnt; ++m) {
+                ru[m] = valid[m] ? cur[ob[m] + Q * q] : 0LL;
+                re[m] = (inner[m] && qin) ? e[(long long)((ii[m] + q) & 1) * v.cs + q * plane_e + eb[m]] : 0.0f;
+            }
+        };
+        fetch(kb - 1);
+        long long fcur = 0;
+        for (int q = kb - 1; q <= ke; ++q) {
+            const bool qin = q >= 1 && q < n, qown = q >= kb && q < ke;
+            long long(*dst)[kFW] = pl[q % 3];
+#pragma unroll
+            for (int m = 0; m < kEnt; ++m) {
+                if (tid + m * kFTI * kFTJ < kFW * kFH) {
+                    long long val = ru[m];
+                    if (inner[m] && qin) {
+                        val += f32_to_i64(re[m] * scf);
+                        if (own[m] && qown) nxt[ob[m] + Q * q] = val;
+                    }
+                    dst[hj[m]][hi[m]] = val;
+                }
+            }
+            // loads for the next plane and the right-hand side of the next residual plane, in flight
+            // across the barrier and this plane's residual
+            if (q + 1 <= ke) fetch(q + 1);
+            const long long fnext = (rok && qown) ? F[rb + Q * q] : 0LL;
+            __syncthreads();
+            const int kk = q - 1;
+            if (kk >= kb && rok) {
+                const long long(*pm)[kFW] = pl[(kk - 1) % 3];
+                const long long(*p0)[kFW] = pl[kk % 3];
+                const long long(*pp)[kFW] = pl[(kk + 1) % 3];
+                const int hx = tx + 1, hy = ty + 1;
+                const long long sum = (p0[hy][hx + 1] + p0[hy][hx - 1]) + (p0[hy + 1][hx] + p0[hy - 1][hx]) +
+                                      (pp[hy][hx] + pm[hy][hx]) - 6 * p0[hy][hx];
+                const float R = i64_to_f32(fcur - sum);
+                r[node_off(v, ri, rj, kk)] = R * k;
+                const float Rs = R * kDown;
+                rr = fmaf(Rs, Rs, rr);
+            }
+            fcur = fnext;
+            __syncthreads();
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) rr += __shfl_down_sync(0xffffffffu, rr, off);
+    __shared__ double sr[kFTI * kFTJ / 32];
+    if ((tid & 31) == 0) sr[tid >> 5] = rr;
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0;
+        for (int q = 0; q < kFTI * kFTJ / 32; ++q) a += sr[q];
+        const double up = ldexp((double)k, 30);
+        partials[2 * blockIdx.x] = a * up * up;
+        partials[2 * blockIdx.x + 1] = 0.0;
     }
 }
 
-// u = U 2^-S on interior nodes (the boundary values are left as given).
+// u = U 2^-S on interior nodes (the boundary values are left as given); U is
+// the current buffer of the iterate, buffer (it & 1).
 __global__ void __launch_bounds__(kThreads)
-fixed_output_kernel(const long long* __restrict__ U, double* __restrict__ u, int n, const SolveState* __restrict__ st)
+fixed_output_kernel(const long long* Ua, const long long* Ub, double* __restrict__ u, int n,
+                    const SolveState* __restrict__ st)
 {
+    const long long* __restrict__ U = (st->it & 1) ? Ub : Ua;
     const double isc = pow2d(-st->scale_exp);
     const int rows = (n - 1) * (n - 1);
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
@@ -222,11 +334,24 @@ void launch_fixed_scale(const float* e, const LevelView& v, const double* u64, i
 }
 
 void launch_fixed_init(const float* e, const LevelView& v, const double* u64, const double* rhs, double coef, double h,
-                       int n, bool from_u64, const SolveState* st, int64_t* U, int64_t* F, cudaStream_t s)
+                       int n, bool from_u64, const SolveState* st, int64_t* U, int64_t* U2, int64_t* F, cudaStream_t s)
 {
     fixed_init_kernel<<<blocks_for_rows((long long)(n + 1) * (n + 1)), kThreads, 0, s>>>(
         e, v, u64, rhs, coef * h * h, n, from_u64 ? 1 : 0, st, reinterpret_cast<long long*>(U),
-        reinterpret_cast<long long*>(F));
+        reinterpret_cast<long long*>(U2), reinterpret_cast<long long*>(F));
+}
+
+int launch_fixed_update_residual(int64_t* U, int64_t* U2, const int64_t* F, const float* e, int n, double h,
+                                 const SolveState* st, float* r, const LevelView& v, double* partials, cudaStream_t s)
+{
+    const long long items = (long long)((n - 1 + kFTI - 1) / kFTI) * ((n - 1 + kFTJ - 1) / kFTJ) *
+                            ((n - 1 + kFKC - 1) / kFKC);
+    const int cap = fixed_residual_blocks(n);
+    const int nb = (int)(items < cap ? items : cap);
+    fixed_update_residual_kernel<<<nb, dim3(kFTI, kFTJ), 0, s>>>(
+        reinterpret_cast<long long*>(U), reinterpret_cast<long long*>(U2), reinterpret_cast<const long long*>(F), e, n,
+        (float)(1.0 / (h * h)), st, r, v, partials);
+    return nb;
 }
 
 int fixed_residual_blocks(int n) { return blocks_for_rows((long long)(n - 1) * (n - 1)); }
@@ -241,14 +366,10 @@ int launch_fixed_residual(const int64_t* U, const int64_t* F, int n, double h, c
     return nb;
 }
 
-void launch_fixed_update(int64_t* U, const float* e, const LevelView& v, int n, const SolveState* st, cudaStream_t s)
+void launch_fixed_output(const int64_t* U, const int64_t* U2, double* u, int n, const SolveState* st, cudaStream_t s)
 {
-    fixed_update_kernel<<<fixed_residual_blocks(n), kThreads, 0, s>>>(reinterpret_cast<long long*>(U), e, v, n, st);
-}
-
-void launch_fixed_output(const int64_t* U, double* u, int n, const SolveState* st, cudaStream_t s)
-{
-    fixed_output_kernel<<<fixed_residual_blocks(n), kThreads, 0, s>>>(reinterpret_cast<const long long*>(U), u, n, st);
+    fixed_output_kernel<<<fixed_residual_blocks(n), kThreads, 0, s>>>(reinterpret_cast<const long long*>(U),
+                                                                       reinterpret_cast<const long long*>(U2), u, n, st);
 }
 
 }  // namespace qumond

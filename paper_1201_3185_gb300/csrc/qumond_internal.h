@@ -111,12 +111,14 @@ cudaError_t prepare_kernels();
 void launch_fixed_scale(const float* e, const LevelView& v, const double* u64, int n, bool from_u64, unsigned* maxbits,
                         SolveState* st, cudaStream_t s);
 void launch_fixed_init(const float* e, const LevelView& v, const double* u64, const double* rhs, double coef, double h,
-                       int n, bool from_u64, const SolveState* st, int64_t* U, int64_t* F, cudaStream_t s);
+                       int n, bool from_u64, const SolveState* st, int64_t* U, int64_t* U2, int64_t* F, cudaStream_t s);
 int fixed_residual_blocks(int n);
 int launch_fixed_residual(const int64_t* U, const int64_t* F, int n, double h, const SolveState* st, bool want_f,
                           float* r, const LevelView& v, double* partials, cudaStream_t s);
-void launch_fixed_update(int64_t* U, const float* e, const LevelView& v, int n, const SolveState* st, cudaStream_t s);
-void launch_fixed_output(const int64_t* U, double* u, int n, const SolveState* st, cudaStream_t s);
+void launch_fixed_output(const int64_t* U, const int64_t* U2, double* u, int n, const SolveState* st, cudaStream_t s);
+// U' = U + round(e 2^S) into the other buffer and the residual of U' (one pass); returns the blocks written
+int launch_fixed_update_residual(int64_t* U, int64_t* U2, const int64_t* F, const float* e, int n, double h,
+                                 const SolveState* st, float* r, const LevelView& v, double* partials, cudaStream_t s);
 
 // --- grid kernels (grid_kernels.cu) ------------------------------------------
 void launch_cic_deposit(const double* x, const double* y, const double* z, const double* m, long long np, int n,
