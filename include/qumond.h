@@ -195,6 +195,28 @@ QUMOND_API qumond_status qumond_forces(qumond_ctx* ctx, const double* const* phi
 QUMOND_API qumond_status qumond_rotation_curve(qumond_ctx* ctx, const double* const* phi_boxes, int nbins, double rmax,
                                     int nphi, double* r_out, double* vc_out, void* stream);
 
+/* Algebraic MOND rotation curve (Eq. 3, compared with the QUMOND curve in
+   Section 3.3): the tracers and box rule of qumond_rotation_curve, applied
+   to the NEWTONIAN potentials, with the field at each tracer taken as
+   nu(|g_N|/a0) g_N, nu(y) = 1/2 + 1/2 sqrt(1 + 4/y) (a tracer with g_N = 0
+   adds 0); v_c = sign(s) sqrt(|s|), s = R_k * mean of -(g . R^).
+   phiN_boxes: HOST array of ctx->nboxes DEVICE pointers; r_out, vc_out:
+   nbins doubles (device).  Errors as qumond_rotation_curve. */
+QUMOND_API qumond_status qumond_rotation_curve_algebraic(qumond_ctx* ctx, const double* const* phiN_boxes, int nbins,
+                                                         double rmax, int nphi, double* r_out, double* vc_out,
+                                                         void* stream);
+
+/* Vertical velocity dispersion of an isothermal stellar layer (Section 5.6):
+   sigma_z^2 = -dPhi/dz * rho_s / (d rho_s/dz).  For the sech^2(z/h) layers of
+   the realisations, rho_s / (d rho_s/dz) = -h / (2 tanh(z/h)); with tracers
+   at height z_eval above the plane (radii, azimuths and box rule of
+   qumond_rotation_curve), sigma_out[k] = sign(s) sqrt(|s|),
+   s = (mean of dPhi/dz) * h / (2 tanh(z_eval/h)).  z_eval, h > 0 (pc).
+   r_out, sigma_out: nbins doubles (device). */
+QUMOND_API qumond_status qumond_sigma_z(qumond_ctx* ctx, const double* const* phi_boxes, int nbins, double rmax,
+                                        int nphi, double z_eval, double h, double* r_out, double* sigma_out,
+                                        void* stream);
+
 /* Quality of a rotation-curve fit (Section 3.5): for each of nsets curves,
      chi2[s] = (1/nbins) * sum_i ((vc[s*nbins + i] - v_obs[i]) / sigma[i])^2
    (the reduced chi^2 the paper minimises over distance, M/L and scale

@@ -60,6 +60,20 @@ QUMOND_API qumond_status qumond_guess_create(int S, double phi_scale, qumond_gue
 QUMOND_API void qumond_guess_destroy(qumond_guess* g);
 QUMOND_API const char* qumond_guess_last_error(qumond_guess* g);
 
+/* Convolution path: mode 1 (the default when available) runs the 3x3x3
+   convolutions of levels with S >= 16 on the tcgen05 tensor cores with TMEM
+   accumulators; mode 0 runs every convolution with mma.sync.  The tcgen05
+   path is available when a one-MMA self-test at the first create reproduced
+   a CPU product; mode 1 is rejected (QUMOND_ERR_INVALID_ARG) otherwise.
+   Both give FP32-accumulated BF16 results (they differ in summation order). */
+QUMOND_API qumond_status qumond_guess_tensor_path(qumond_guess* g, int mode);
+QUMOND_API int qumond_guess_tensor_path_available(qumond_guess* g);
+
+/* Synchronises `stream` and reports QUMOND_ERR_TIMEOUT (and clears the flag)
+   if a tensor-core convolution gave up a bounded wait since the last call;
+   the outputs of such calls are undefined. */
+QUMOND_API qumond_status qumond_guess_status(qumond_guess* g, void* stream);
+
 /* Copies num_params FP32 values from / to a device array; setting also
    resets the Adam state. */
 QUMOND_API qumond_status qumond_guess_set_params(qumond_guess* g, const float* params, void* stream);

@@ -26,6 +26,8 @@ from .core import (  # noqa: F401
     forces,
     rotation_curve,
     chi2,
+    rotation_curve_algebraic,
+    sigma_z,
     Box,
     pipeline,
     grid_index,

@@ -60,6 +60,8 @@ def _load():
         "ora_forces": (_L, [_I, _I, _D, _I, _D, _D, _D, _P, _P, _P, _P, _L, _P, _P, _P]),
         "ora_rotation_curve": (None, [_I, _I, _D, _I, _D, _D, _D, _P, _I, _D, _I, _D, _P, _P]),
         "ora_chi2": (None, [_P, _P, _P, _I, _I, _P]),
+        "ora_rotation_curve_algebraic": (None, [_I, _I, _D, _I, _D, _D, _D, _P, _I, _D, _I, _D, _D, _P, _P]),
+        "ora_sigma_z": (None, [_I, _I, _D, _I, _D, _D, _D, _P, _I, _D, _I, _D, _D, _D, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -190,6 +192,26 @@ def rotation_curve(n, L0, center, phis, nbins, rmax, nphi=64, frac=0.2, ratio=2)
     _load().ora_rotation_curve(len(phis), n, L0, ratio, center[0], center[1], center[2], ctypes.cast(pa, _P),
                                nbins, rmax, nphi, frac, _ptr(r), _ptr(vc))
     return r, vc
+
+
+def rotation_curve_algebraic(n, L0, center, phiNs, nbins, rmax, nphi=64, frac=0.2, ratio=2, a0=3.6):
+    """Rotation curve of the algebraic MOND relation (Eq. 3) from the Newtonian potentials."""
+    r = np.empty(nbins, dtype=np.float64)
+    vc = np.empty(nbins, dtype=np.float64)
+    pa = _ptr_array(phiNs)
+    _load().ora_rotation_curve_algebraic(len(phiNs), n, L0, ratio, center[0], center[1], center[2],
+                                         ctypes.cast(pa, _P), nbins, rmax, nphi, frac, a0, _ptr(r), _ptr(vc))
+    return r, vc
+
+
+def sigma_z(n, L0, center, phis, nbins, rmax, z_eval, h, nphi=64, frac=0.2, ratio=2):
+    """Vertical velocity dispersion of an isothermal sech^2(z/h) layer (Section 5.6)."""
+    r = np.empty(nbins, dtype=np.float64)
+    sg = np.empty(nbins, dtype=np.float64)
+    pa = _ptr_array(phis)
+    _load().ora_sigma_z(len(phis), n, L0, ratio, center[0], center[1], center[2], ctypes.cast(pa, _P), nbins, rmax,
+                        nphi, frac, z_eval, h, _ptr(r), _ptr(sg))
+    return r, sg
 
 
 def chi2(vc, v_obs, sigma):

@@ -518,3 +518,82 @@ void ora_chi2(const double* vc, const double* v_obs, const double* sigma, int nb
         chi2[s] = acc / (double)nbins;
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Science extras on a solved set of boxes (tracers and box rule as
+ * ora_rotation_curve).
+ *
+ * Algebraic MOND rotation curve (Eq. 3, compared with QUMOND in Section 3.3):
+ * the field at a tracer is taken as nu(|g_N|/a0) g_N, g_N = -grad Phi_N
+ * interpolated as for the forces, nu(y) = 1/2 + 1/2 sqrt(1 + 4/y); a tracer
+ * with |g_N| = 0 contributes 0.  v_c^2 = R * mean over azimuths of -(g . R^). */
+void ora_rotation_curve_algebraic(int nboxes, int n, double L0, int ratio, double cx, double cy, double cz,
+                                  const double* const* phiN, int nbins, double rmax, int nphi, double frac,
+                                  double a0, double* r_out, double* vc_out)
+{
+    const double twopi = 6.283185307179586476925286766559;
+    for (int kb = 0; kb < nbins; ++kb) {
+        double R = ((double)kb + 0.5) * rmax / (double)nbins;
+        int b0 = 0;
+        for (int b = nboxes - 1; b >= 0; --b)
+            if (R < frac * (L0 / pow((double)ratio, (double)b))) { b0 = b; break; }
+        double sum = 0.0;
+        for (int m = 0; m < nphi; ++m) {
+            double ph = twopi * (double)m / (double)nphi;
+            double c = cos(ph), s = sin(ph);
+            double g[3] = {0.0, 0.0, 0.0};
+            for (int b = b0; b >= 0; --b) {
+                double L = L0 / pow((double)ratio, (double)b);
+                int ijk[3];
+                double d[3];
+                if (find_cell(n, L, cx, cy, cz, cx + R * c, cy + R * s, cz, ijk, d)) {
+                    grad_at(n, L, phiN[b], ijk, d, g);
+                    break;
+                }
+            }
+            double gm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+            double nu = gm > 0.0 ? 0.5 + 0.5 * sqrt(1.0 + 4.0 * a0 / gm) : 0.0;
+            sum += -nu * (g[0] * c + g[1] * s);
+        }
+        double v2 = R * (sum / (double)nphi);
+        r_out[kb] = R;
+        vc_out[kb] = v2 >= 0.0 ? sqrt(v2) : -sqrt(-v2);
+    }
+}
+
+/* Vertical velocity dispersion of an isothermal stellar layer (Section 5.6):
+ * sigma_z^2 = -dPhi/dz * rho_s / (d rho_s/dz), rho_s the stellar density.  For
+ * rho_s ~ sech^2(z/h), rho_s / (d rho_s/dz) = -h / (2 tanh(z/h)), so at height z_eval above the plane
+ * sigma_z^2(R) = <dPhi/dz>(R, z_eval) * h / (2 tanh(z_eval/h)), the mean of
+ * dPhi/dz = -g_z over the nphi azimuths.  sig_out = sign(s) sqrt(|s|). */
+void ora_sigma_z(int nboxes, int n, double L0, int ratio, double cx, double cy, double cz, const double* const* phi,
+                 int nbins, double rmax, int nphi, double frac, double z_eval, double h, double* r_out,
+                 double* sig_out)
+{
+    const double twopi = 6.283185307179586476925286766559;
+    for (int kb = 0; kb < nbins; ++kb) {
+        double R = ((double)kb + 0.5) * rmax / (double)nbins;
+        int b0 = 0;
+        for (int b = nboxes - 1; b >= 0; --b)
+            if (R < frac * (L0 / pow((double)ratio, (double)b))) { b0 = b; break; }
+        double sum = 0.0;
+        for (int m = 0; m < nphi; ++m) {
+            double ph = twopi * (double)m / (double)nphi;
+            double c = cos(ph), s = sin(ph);
+            double g[3] = {0.0, 0.0, 0.0};
+            for (int b = b0; b >= 0; --b) {
+                double L = L0 / pow((double)ratio, (double)b);
+                int ijk[3];
+                double d[3];
+                if (find_cell(n, L, cx, cy, cz, cx + R * c, cy + R * s, cz + z_eval, ijk, d)) {
+                    grad_at(n, L, phi[b], ijk, d, g);
+                    break;
+                }
+            }
+            sum += -g[2];
+        }
+        double s2 = (sum / (double)nphi) * h / (2.0 * tanh(z_eval / h));
+        r_out[kb] = R;
+        sig_out[kb] = s2 >= 0.0 ? sqrt(s2) : -sqrt(-s2);
+    }
+}

@@ -26,12 +26,12 @@ struct Level {
 enum Kind {
     K_DEPOSIT, K_FIXED_TO_RHO, K_BOUNDARY, K_CONVERT_RHS, K_RESTRICT_FULL, K_COARSE, K_RB_FINEST, K_RB_COARSER,
     K_RESTRICT_RESID, K_PROLONG, K_SET_BOUNDARY, K_ASSIGN_OUTER, K_RESIDUAL_OUTER, K_REDUCE, K_SOURCE, K_FORCES,
-    K_ROTATION_CURVE, K_FIXED_SETUP, K_FIXED_OUTPUT, K_CHI2, K_COUNT
+    K_ROTATION_CURVE, K_FIXED_SETUP, K_FIXED_OUTPUT, K_CHI2, K_PROFILE, K_COUNT
 };
 const char* const kKindNames[K_COUNT] = {
     "cic_deposit", "fixed_to_rho", "boundary_fill", "convert_rhs", "restrict_full", "coarse_solver",
     "rb_half_finest", "rb_half_coarser", "restrict_resid_red", "prolong_black", "set_boundary", "update_outer",
-    "residual_outer", "reduce_norms", "qumond_source", "forces", "rotation_curve", "fixed_setup", "fixed_output", "chi2",
+    "residual_outer", "reduce_norms", "qumond_source", "forces", "rotation_curve", "fixed_setup", "fixed_output", "chi2", "profile",
 };
 constexpr int kMaxTimed = 32768;
 
@@ -923,6 +923,42 @@ qumond_status qumond_rotation_curve(qumond_ctx* c, const double* const* phi_boxe
     });
     CUDA_TRY(c, cudaGetLastError(), "rotation_curve launch");
     return QUMOND_OK;
+}
+
+namespace {
+qumond_status profile(qumond_ctx* c, const double* const* phi_boxes, int nbins, double rmax, int nphi, int mode,
+                      double z_eval, double h, double* r_out, double* out, void* stream, const char* what)
+{
+    if (!c) return QUMOND_ERR_INVALID_ARG;
+    c->err.clear();
+    qumond_status st = check_phis(c, phi_boxes, what);
+    if (st != QUMOND_OK) return st;
+    if (nbins < 1 || nbins > 65535) return fail(c, QUMOND_ERR_INVALID_ARG, "%s: nbins must be in [1, 65535]", what);
+    if (nphi < 1 || nphi > 1024) return fail(c, QUMOND_ERR_INVALID_ARG, "%s: nphi must be in [1, 1024]", what);
+    if (!(rmax > 0.0) || !std::isfinite(rmax)) return fail(c, QUMOND_ERR_INVALID_ARG, "%s: rmax must be positive", what);
+    if (mode == 1 && (!(z_eval > 0.0) || !(h > 0.0) || !std::isfinite(z_eval) || !std::isfinite(h)))
+        return fail(c, QUMOND_ERR_INVALID_ARG, "%s: z_eval and h must be positive", what);
+    if (!device_ptr(r_out) || !device_ptr(out))
+        return fail(c, QUMOND_ERR_INVALID_ARG, "%s: outputs must be device pointers", what);
+    run(c, K_PROFILE, 16.0 * nbins, S(stream), [&] {
+        launch_profile(box_set(c, phi_boxes), c->p.center[0], c->p.center[1], c->p.center[2], nbins, rmax, nphi,
+                       c->p.rc_box_frac, mode, c->p.a0, z_eval, h, r_out, out, S(stream));
+    });
+    CUDA_TRY(c, cudaGetLastError(), what);
+    return QUMOND_OK;
+}
+}  // namespace
+
+qumond_status qumond_rotation_curve_algebraic(qumond_ctx* c, const double* const* phiN_boxes, int nbins, double rmax,
+                                              int nphi, double* r_out, double* vc_out, void* stream)
+{
+    return profile(c, phiN_boxes, nbins, rmax, nphi, 0, 0.0, 1.0, r_out, vc_out, stream, "rotation_curve_algebraic");
+}
+
+qumond_status qumond_sigma_z(qumond_ctx* c, const double* const* phi_boxes, int nbins, double rmax, int nphi,
+                             double z_eval, double h, double* r_out, double* sigma_out, void* stream)
+{
+    return profile(c, phi_boxes, nbins, rmax, nphi, 1, z_eval, h, r_out, sigma_out, stream, "sigma_z");
 }
 
 qumond_status qumond_chi2(qumond_ctx* c, const double* vc, const double* v_obs, const double* sigma, int nbins,

@@ -390,6 +390,58 @@ __global__ void rotation_curve_kernel(BoxSet boxes, double cx, double cy, double
     }
 }
 
+// Science extras on the same tracers and box rule as the rotation curve.
+// mode 0 (Eq. 3, algebraic MOND): the field at a tracer is nu(|g_N|/a0) g_N
+//   from the Newtonian potentials (a tracer with g_N = 0 adds 0), out = sign(s) sqrt(|s|),
+//   s = R * mean of -(g . R^);
+// mode 1 (Section 5.6, isothermal sech^2(z/h) stellar layer): tracers at height z_eval,
+//   s = mean of dPhi/dz * h / (2 tanh(z_eval / h)), out = sign(s) sqrt(|s|) = sigma_z.
+__global__ void profile_kernel(BoxSet boxes, double cx, double cy, double cz, int nbins, double rmax, int nphi,
+                               double frac, int mode, double a0, double z_eval, double h, double* __restrict__ r_out,
+                               double* __restrict__ out)
+{
+    __shared__ double val[kMaxPhi];
+    const int kb = blockIdx.x;
+    const double R = ((double)kb + 0.5) * rmax / (double)nbins;
+    int b0 = 0;
+    for (int b = boxes.nboxes - 1; b >= 0; --b)
+        if (R < frac * boxes.b[b].L) {
+            b0 = b;
+            break;
+        }
+    const double zt = mode == 1 ? cz + z_eval : cz;
+    for (int m = threadIdx.x; m < nphi; m += blockDim.x) {
+        const double ph = 6.283185307179586476925286766559 * (double)m / (double)nphi;
+        double s, c;
+        sincos(ph, &s, &c);
+        double g[3] = {0.0, 0.0, 0.0};
+        for (int b = b0; b >= 0; --b) {
+            int ijk[3];
+            double d[3];
+            if (find_cell(boxes.b[b], boxes.n, cx + R * c, cy + R * s, zt, ijk, d)) {
+                grad_at(boxes.b[b], boxes.n, ijk, d, g);
+                break;
+            }
+        }
+        if (mode == 0) {
+            const double gm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+            const double nu = gm > 0.0 ? 0.5 + 0.5 * sqrt(1.0 + 4.0 * a0 / gm) : 0.0;
+            val[m] = -nu * (g[0] * c + g[1] * s);
+        } else {
+            val[m] = -g[2];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int m = 0; m < nphi; ++m) sum += val[m];
+        const double mean = sum / (double)nphi;
+        const double v2 = mode == 0 ? R * mean : mean * h / (2.0 * tanh(z_eval / h));
+        r_out[kb] = R;
+        out[kb] = v2 >= 0.0 ? sqrt(v2) : -sqrt(-v2);
+    }
+}
+
 }  // namespace
 
 // --- launchers ----------------------------------------------------------------
@@ -435,6 +487,12 @@ void launch_rotation_curve(const BoxSet& boxes, double cx, double cy, double cz,
                            double frac, double* r_out, double* vc_out, cudaStream_t s)
 {
     rotation_curve_kernel<<<nbins, 128, 0, s>>>(boxes, cx, cy, cz, nbins, rmax, nphi, frac, r_out, vc_out);
+}
+
+void launch_profile(const BoxSet& boxes, double cx, double cy, double cz, int nbins, double rmax, int nphi, double frac,
+                    int mode, double a0, double z_eval, double h, double* r_out, double* out, cudaStream_t s)
+{
+    profile_kernel<<<nbins, 128, 0, s>>>(boxes, cx, cy, cz, nbins, rmax, nphi, frac, mode, a0, z_eval, h, r_out, out);
 }
 
 // Quality of fit (Section 3.5): chi2[s] = (1/nbins) sum_i ((vc[s][i] - v_obs[i]) / sigma[i])^2.

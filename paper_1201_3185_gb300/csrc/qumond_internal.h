@@ -148,5 +148,7 @@ void launch_rotation_curve(const BoxSet& boxes, double cx, double cy, double cz,
                            double frac, double* r_out, double* vc_out, cudaStream_t s);
 void launch_chi2(const double* vc, const double* v_obs, const double* sigma, int nbins, int nsets, double* chi2,
                  cudaStream_t s);
+void launch_profile(const BoxSet& boxes, double cx, double cy, double cz, int nbins, double rmax, int nphi, double frac,
+                    int mode, double a0, double z_eval, double h, double* r_out, double* out, cudaStream_t s);
 
 }  // namespace qumond

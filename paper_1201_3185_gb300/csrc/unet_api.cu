@@ -59,6 +59,9 @@ struct qumond_guess {
     float* cpart = nullptr;
     float* hpart = nullptr;
     int cblocks = 0, hblocks = 0;
+    int tc_swap = -1;     // tcgen05 convolutions: descriptor reading found by the self-test, -1 unavailable
+    int use_tc = 0;       // 1: tcgen05 convolutions where they apply, 0: mma.sync everywhere
+    int* fault = nullptr; // bounded waits of the tcgen05 path
     std::vector<void*> allocs;
 };
 
@@ -164,6 +167,8 @@ void conv(qumond_guess* g, int l, cudaStream_t s)
     a.out = w.out, a.ld_out = w.ld_out, a.out_off = w.out_off, a.cout = kLayers[l].cout;
     a.relu = 1;
     a.S = g->S >> kLayers[l].level;
+    a.tc_swap = g->use_tc ? g->tc_swap : -1;
+    a.fault = g->fault;
     launch_conv3(a, s);
 }
 
@@ -209,6 +214,8 @@ void backward(qumond_guess* g, const __nv_bfloat16* target, float k, float loss_
         ConvArgs a{};
         a.in = g->G[l], a.ld_in = cout, a.in_off = 0, a.cin = cout;
         a.w = g->wd[l], a.bias = nullptr, a.relu = 0, a.cout = cin, a.S = S;
+        a.tc_swap = g->use_tc ? g->tc_swap : -1;
+        a.fault = g->fault;
         const bool from_pool = (l == 2 || l == 4 || l == 6);
         const bool from_cat = (l == 8 || l == 10 || l == 12);
         if (from_pool) {
@@ -322,7 +329,8 @@ qumond_status qumond_guess_create(int S, double phi_scale, qumond_guess** out)
     g->cblocks = 2 * g->sms;
     g->hblocks = 2 * g->sms;
     ok = ok && alloc(g, &g->wpart, wp) && alloc(g, &g->cpart, (size_t)g->cblocks * 128) &&
-         alloc(g, &g->hpart, (size_t)g->hblocks * 18);
+         alloc(g, &g->hpart, (size_t)g->hblocks * 18) && alloc(g, &g->fault, 1) &&
+         cudaMemset(g->fault, 0, sizeof(int)) == cudaSuccess;
     ok = ok && cudaMemset(g->params, 0, g->nparams * sizeof(float)) == cudaSuccess &&
          cudaMemset(g->adam_m, 0, g->nparams * sizeof(float)) == cudaSuccess &&
          cudaMemset(g->adam_v, 0, g->nparams * sizeof(float)) == cudaSuccess;
@@ -333,6 +341,14 @@ qumond_status qumond_guess_create(int S, double phi_scale, qumond_guess** out)
     }
     prepare_conv3();
     prepare_wgrad();
+    prepare_conv3_tc();
+    {
+        // once per process: which reading of the tcgen05 shared-memory descriptor reproduces a CPU product
+        static int tc = -2;
+        if (tc == -2) tc = tc_selftest();
+        g->tc_swap = tc;
+        g->use_tc = tc >= 0 ? 1 : 0;
+    }
     refresh_bf16(g, nullptr);
     if (cudaDeviceSynchronize() != cudaSuccess) {
         (void)cudaGetLastError();
@@ -349,6 +365,33 @@ void qumond_guess_destroy(qumond_guess* g)
     cudaDeviceSynchronize();
     for (void* p : g->allocs) cudaFree(p);
     delete g;
+}
+
+qumond_status qumond_guess_tensor_path(qumond_guess* g, int mode)
+{
+    if (!g) return QUMOND_ERR_INVALID_ARG;
+    g->err.clear();
+    if (mode != 0 && mode != 1) return fail(g, QUMOND_ERR_INVALID_ARG, "tensor_path: mode must be 0 or 1");
+    if (mode == 1 && g->tc_swap < 0)
+        return fail(g, QUMOND_ERR_INVALID_ARG, "tensor_path: the tcgen05 path failed its self-test on this device");
+    g->use_tc = mode;
+    return QUMOND_OK;
+}
+
+int qumond_guess_tensor_path_available(qumond_guess* g) { return g && g->tc_swap >= 0 ? 1 : 0; }
+
+qumond_status qumond_guess_status(qumond_guess* g, void* stream)
+{
+    if (!g) return QUMOND_ERR_INVALID_ARG;
+    g->err.clear();
+    int f = 0;
+    GTRY(g, cudaMemcpyAsync(&f, g->fault, sizeof(int), cudaMemcpyDeviceToHost, S_(stream)), "status");
+    GTRY(g, cudaStreamSynchronize(S_(stream)), "status");
+    if (f) {
+        GTRY(g, cudaMemset(g->fault, 0, sizeof(int)), "status");
+        return fail(g, QUMOND_ERR_TIMEOUT, "a tensor-core convolution gave up waiting for its MMAs");
+    }
+    return QUMOND_OK;
 }
 
 qumond_status qumond_guess_set_params(qumond_guess* g, const float* params, void* stream)

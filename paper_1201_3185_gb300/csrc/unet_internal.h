@@ -27,6 +27,8 @@ struct ConvArgs {
     int relu;
     int S;
     Brick brick;  // set by the launcher
+    int tc_swap;  // tcgen05 path: which descriptor field holds the K stride (0/1, from tc_selftest); -1: mma.sync
+    int* fault;   // set to 3 when a bounded wait of the tcgen05 path gave up
 };
 
 // Weight gradient of a 3^3 convolution: dW[co][tap][ci] = sum_v g[v, co] x[v + off(tap), ci].
@@ -45,6 +47,13 @@ size_t conv3_smem_bytes(int cout_tile);
 int conv3_tile(int cout);
 void prepare_conv3();
 void launch_conv3(ConvArgs a, cudaStream_t s);
+
+// tcgen05 path (unet_tc.cu)
+int tc_selftest();
+bool conv3_tc_applies(const ConvArgs& a);
+size_t conv3_tc_smem_bytes(int nt);
+void prepare_conv3_tc();
+void launch_conv3_tc(const ConvArgs& a, cudaStream_t s);
 
 int wgrad_mt(int cout);
 size_t wgrad_smem_bytes(int mt, const Brick& b);

@@ -213,6 +213,10 @@ void prepare_conv3()
 
 void launch_conv3(ConvArgs a, cudaStream_t s)
 {
+    if (conv3_tc_applies(a)) {
+        launch_conv3_tc(a, s);
+        return;
+    }
     a.brick = brick_for(a.S);
     const int bricks = (a.S / a.brick.bx) * (a.S / a.brick.by) * (a.S / a.brick.bz);
     switch (conv3_tile(a.cout)) {

@@ -37,10 +37,11 @@ QUMOND_BC_GIVEN = 1
 EXPORTED = (
     "qumond_default_params", "qumond_create", "qumond_destroy", "qumond_last_error", "qumond_deposit",
     "qumond_solve_newton", "qumond_source", "qumond_solve_mond", "qumond_forces", "qumond_rotation_curve",
-    "qumond_chi2", "qumond_trace_classes", "qumond_trace_timing", "qumond_trace_read", "qumond_solve_mond_noalloc",
+    "qumond_chi2", "qumond_rotation_curve_algebraic", "qumond_sigma_z", "qumond_trace_classes", "qumond_trace_timing", "qumond_trace_read", "qumond_solve_mond_noalloc",
     "qumond_guess_num_params", "qumond_guess_create", "qumond_guess_destroy", "qumond_guess_last_error",
     "qumond_guess_set_params", "qumond_guess_get_params", "qumond_guess_make_sample", "qumond_guess_forward",
-    "qumond_guess_gradients", "qumond_guess_train_step", "qumond_guess_apply",
+    "qumond_guess_gradients", "qumond_guess_train_step", "qumond_guess_apply", "qumond_guess_tensor_path",
+    "qumond_guess_tensor_path_available", "qumond_guess_status",
 )
 NOALLOC_MAX_N = 64
 
@@ -114,6 +115,8 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
         "qumond_forces": (_I, [_P, _P, _P, _P, _P, _L, _P, _P, _P, _P]),
         "qumond_rotation_curve": (_I, [_P, _P, _I, _D, _I, _P, _P, _P]),
         "qumond_chi2": (_I, [_P, _P, _P, _P, _I, _I, _P, _P]),
+        "qumond_rotation_curve_algebraic": (_I, [_P, _P, _I, _D, _I, _P, _P, _P]),
+        "qumond_sigma_z": (_I, [_P, _P, _I, _D, _I, _D, _D, _P, _P, _P]),
         "qumond_trace_classes": (_I, []),
         "qumond_trace_timing": (_I, [_P, _I, _I]),
         "qumond_trace_read": (_I, [_P, ctypes.POINTER(qumond_kernel_stat), _I, ctypes.POINTER(qumond_counters), _I]),
@@ -130,6 +133,9 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
         "qumond_guess_gradients": (_I, [_P, _P, _P, _I, _P, _P, _P]),
         "qumond_guess_train_step": (_I, [_P, _P, _P, _I, ctypes.c_float, _P, _P]),
         "qumond_guess_apply": (_I, [_P, _D, ctypes.c_float, _P, _P, _P, _P]),
+        "qumond_guess_tensor_path": (_I, [_P, _I]),
+        "qumond_guess_tensor_path_available": (_I, [_P]),
+        "qumond_guess_status": (_I, [_P, _P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -322,6 +328,20 @@ class Context:
         self._check(_lib.qumond_rotation_curve(self._ptr, ctypes.cast(arr, _P), nbins, float(rmax), nphi, r, v,
                                                _stream(stream)))
 
+    def qumond_rotation_curve_algebraic(self, phiNs, nbins, rmax, nphi, r_out, vc_out, stream=None):
+        arr = self._phis(phiNs)
+        r = _dev(r_out, torch.float64, nbins, "r_out")
+        v = _dev(vc_out, torch.float64, nbins, "vc_out")
+        self._check(_lib.qumond_rotation_curve_algebraic(self._ptr, ctypes.cast(arr, _P), nbins, float(rmax), nphi, r,
+                                                         v, _stream(stream)))
+
+    def qumond_sigma_z(self, phis, nbins, rmax, nphi, z_eval, h, r_out, sigma_out, stream=None):
+        arr = self._phis(phis)
+        r = _dev(r_out, torch.float64, nbins, "r_out")
+        v = _dev(sigma_out, torch.float64, nbins, "sigma_out")
+        self._check(_lib.qumond_sigma_z(self._ptr, ctypes.cast(arr, _P), nbins, float(rmax), nphi, float(z_eval),
+                                        float(h), r, v, _stream(stream)))
+
     def qumond_chi2(self, vc, v_obs, sigma, chi2_out, stream=None):
         """Reduced chi^2 of each row of vc (nsets x nbins) against v_obs, sigma."""
         nsets, nbins = (vc.shape[0], vc.shape[1]) if vc.dim() == 2 else (1, vc.numel())
@@ -395,6 +415,16 @@ class Guess:
     def _check(self, st: int):
         if st != QUMOND_OK:
             raise QumondError(st, _lib.qumond_guess_last_error(self._ptr).decode())
+
+    def qumond_guess_tensor_path(self, mode: int):
+        """1: tcgen05 convolutions where they apply (the default when available), 0: mma.sync everywhere."""
+        self._check(_lib.qumond_guess_tensor_path(self._ptr, int(mode)))
+
+    def qumond_guess_tensor_path_available(self) -> bool:
+        return bool(_lib.qumond_guess_tensor_path_available(self._ptr))
+
+    def qumond_guess_status(self, stream=None):
+        self._check(_lib.qumond_guess_status(self._ptr, _stream(stream)))
 
     def qumond_guess_set_params(self, params, stream=None):
         self._check(_lib.qumond_guess_set_params(self._ptr, _dev(params, torch.float32, self.num_params(), "params"),

@@ -160,3 +160,30 @@ def test_invalid_arguments(q):
     with pytest.raises(q.QumondError):
         g.qumond_guess_train_step([torch.zeros(3 * 16 ** 3, dtype=torch.bfloat16, device="cuda")], [0.0], -1.0)
     g.close()
+
+
+def test_tcgen05_path_available(q):
+    g = q.Guess(16, 1e5)
+    assert g.qumond_guess_tensor_path_available(), "the tcgen05 self-test did not reproduce the CPU product"
+    g.close()
+
+
+@pytest.mark.parametrize("S", [64, 128])
+def test_tcgen05_matches_mma_sync(q, S):
+    """The two convolution paths on the same inputs: the same FP32-accumulated
+    products in a different order, so the outputs agree to a few BF16 roundings."""
+    rng = np.random.default_rng(S + 1)
+    g = q.Guess(S, 1e5)
+    g.qumond_guess_set_params(to_dev(he(S + 1), torch.float32))
+    smp = random_sample(rng, S).cuda()
+    ys = []
+    for mode in (1, 0):
+        g.qumond_guess_tensor_path(mode)
+        y = torch.empty(S ** 3, dtype=torch.float32, device="cuda")
+        g.qumond_guess_forward(smp, 1.0, y)
+        g.qumond_guess_status()
+        ys.append(y.cpu().numpy().astype(np.float64))
+    err = rel_l2(ys[0], ys[1])
+    print("tcgen05 vs mma.sync S=%d rel L2 %.3e" % (S, err))
+    assert err < 1e-2
+    g.close()

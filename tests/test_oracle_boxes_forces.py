@@ -54,3 +54,32 @@ def test_chi2_definition(ora):
     assert got[0] == 0.0
     assert got[1] == pytest.approx(1.0, rel=1e-14)
     assert got[2] == pytest.approx(4.0, rel=1e-14)
+
+
+def test_algebraic_curve_of_harmonic_potential(ora):
+    # Eq. 3 on Phi_N = Omega^2 R^2 / 2: |g_N| = Omega^2 R in the plane, so
+    # v_c^2 = R nu(Omega^2 R / a0) Omega^2 R exactly (the gradient is exact on a quadratic)
+    n, L0, nb, c, a0 = 32, 64000.0, 3, (0.0, 0.0, 0.0), 3.6
+    om = 0.01
+    phis = [0.5 * om * om * (x * x + y * y) + 1e-6 * z * z
+            for x, y, z in (node_coords(n, L0 / 2 ** b, c) for b in range(nb))]
+    r, vc = ora.rotation_curve_algebraic(n, L0, c, phis, 40, 20000.0, 64, a0=a0)
+    g = om * om * r
+    nu = 0.5 + 0.5 * np.sqrt(1.0 + 4.0 * a0 / g)
+    np.testing.assert_allclose(vc, np.sqrt(r * nu * g), rtol=1e-9)
+    # a0 -> 0 is Newtonian: the plain rotation curve
+    _, vN = ora.rotation_curve_algebraic(n, L0, c, phis, 40, 20000.0, 64, a0=0.0)
+    np.testing.assert_allclose(vN, om * r, rtol=1e-9)
+
+
+def test_sigma_z_of_vertical_harmonic_potential(ora):
+    # Section 5.6: sigma_z^2 = -dPhi/dz rho/(d rho/dz); for Phi = k^2 z^2 / 2 and a
+    # sech^2(z/h) layer at height z: sigma_z^2 = k^2 z h / (2 tanh(z/h))
+    n, L0, nb, c = 32, 64000.0, 3, (0.0, 0.0, 0.0)
+    k2 = 2e-3
+    phis = [0.5 * k2 * z * z + 3e-5 * (x * x + y * y)
+            for x, y, z in (node_coords(n, L0 / 2 ** b, c) for b in range(nb))]
+    for z_eval, h in ((300.0, 300.0), (450.0, 600.0)):
+        r, sg = ora.sigma_z(n, L0, c, phis, 30, 15000.0, z_eval, h, 64)
+        want = np.sqrt(k2 * z_eval * h / (2.0 * np.tanh(z_eval / h)))
+        np.testing.assert_allclose(sg, want, rtol=1e-9)

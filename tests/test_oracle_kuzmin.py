@@ -65,6 +65,25 @@ def test_algebraic_relation_holds_for_kuzmin(ora):
 
 
 @pytest.mark.slow
+def test_algebraic_curve_converges_for_kuzmin(ora):
+    # Eq. 3 in the mid-plane of a thin Kuzmin disk: the vertical field vanishes
+    # there by symmetry, so the algebraic curve is v^2 = R nu(g_R/a0) g_R with
+    # g_R = G M R / (R^2 + a^2)^(3/2); the grid curve converges to it at second
+    # order (the QUMOND curve of the same runs converges to F'(r'), a different
+    # quantity: Section 3.3's comparison)
+    M, a = 1e10, 2000.0
+    errs = []
+    for n in (32, 64):
+        boxes, r, _, _ = _kuzmin_run(ora, n)
+        _, vA = ora.rotation_curve_algebraic(n, 160000.0, (0.0, 0.0, 0.0), [b.phiN for b in boxes], 50, 20000.0,
+                                             a0=A0)
+        gR = G * M * r / (r * r + a * a) ** 1.5
+        want = np.sqrt(r * an.nu(gR / A0) * gR)
+        sel = r > 3000.0
+        errs.append(np.max(np.abs(vA[sel] / want[sel] - 1.0)))
+    assert errs[1] < 0.04 and errs[0] / errs[1] > 4.0, errs
+
+
 def test_paper_kuzmin_accuracy_claim(ora):
     """The paper's printed accuracy for its Kuzmin disk, in its own setup."""
     gold = json.load(open(os.path.join(HERE, "golden", "kuzmin_paper_accuracy.json")))
