@@ -102,9 +102,9 @@ __global__ void choose_scale_kernel(unsigned* __restrict__ maxbits, SolveState* 
 }
 
 // U = round(u * 2^S) on every node (interior from the FP32 FMG result or the
-// caller's warm start, boundary from the caller's FP64 values), into both
-// buffers of the iterate, and F = round(coef * rhs * h^2 * 2^S) on interior
-// nodes.
+// caller's warm start, boundary from the caller's FP64 values), the boundary
+// values also into the iterate's second buffer, and
+// F = round(coef * rhs * h^2 * 2^S) on interior nodes.
 __global__ void __launch_bounds__(kThreads)
 fixed_init_kernel(const float* __restrict__ e, LevelView v, const double* __restrict__ u64,
                   const double* __restrict__ rhs, double coef_h2, int n, int from_u64,
@@ -125,7 +125,7 @@ fixed_init_kernel(const float* __restrict__ e, LevelView v, const double* __rest
             const long long val =
                 (bnd || from_u64) ? __double2ll_rn(u64[o] * sc) : f32_to_i64(e[node_off(v, i, j, k)] * scf);
             U[o] = val;
-            U2[o] = val;  // the second buffer of the iterate needs the boundary values too
+            if (bnd) U2[o] = val;  // the second buffer's interior is written before it is read
             F[o] = bnd ? 0LL : __double2ll_rn(rhs[o] * kf);
         }
     }

@@ -183,77 +183,83 @@ struct CoarseSmem {
     T* r[kMaxCoarseLevels];
 };
 
-template <typename T>
-__device__ void sm_relax(T* u, const T* f, int n, T h2, int colour)
+// Every level size is a compile-time constant (N = 2 << L), so the index
+// arithmetic below is shifts and multiplications.
+// One colour of the interior of an N-level: row (j, k) holds that colour's
+// nodes at i = first, first + 2, ... (first = 1 or 2), N/2 slots per row.
+template <typename T, int N>
+__device__ void sm_relax(T* u, const T* f, T h2, int colour)
 {
-    const int m = n - 1, P = n + 1;
-    const int tot = m * m * m;
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-        const int i = t % m + 1, j = (t / m) % m + 1, k = t / (m * m) + 1;
-        if (((i + j + k) & 1) != colour) continue;
+    constexpr int M = N - 1, P = N + 1, H = N / 2, TOT = M * M * H;
+    for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) {
+        const int sl = t % H, row = t / H;
+        const int j = row % M + 1, k = row / M + 1;
+        const int i = 1 + (((1 + j + k) & 1) != colour ? 1 : 0) + 2 * sl;
+        if (i > M) continue;
         const int o = i + P * (j + P * k);
-        const T s = (u[o + 1] + u[o - 1]) + (u[o + P] + u[o - P]) + (u[o + P * P] + u[o - P * P]);
-        u[o] = (s - h2 * f[o]) * (T(1) / T(6));
+        const T sum = (u[o + 1] + u[o - 1]) + (u[o + P] + u[o - P]) + (u[o + P * P] + u[o - P * P]);
+        u[o] = (sum - h2 * f[o]) * (T(1) / T(6));
     }
     __syncthreads();
 }
 
-template <typename T>
-__device__ void sm_residual(const T* u, const T* f, T* r, int n, T ih2)
+template <typename T, int N>
+__device__ void sm_residual(const T* u, const T* f, T* r, T ih2)
 {
-    const int m = n - 1, P = n + 1;
-    const int tot = m * m * m;
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-        const int i = t % m + 1, j = (t / m) % m + 1, k = t / (m * m) + 1;
+    constexpr int M = N - 1, P = N + 1, TOT = M * M * M;
+    for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) {
+        const int i = t % M + 1, j = (t / M) % M + 1, k = t / (M * M) + 1;
         const int o = i + P * (j + P * k);
-        const T s = (u[o + 1] + u[o - 1]) + (u[o + P] + u[o - P]) + (u[o + P * P] + u[o - P * P]);
-        r[o] = f[o] - (s - T(6) * u[o]) * ih2;
+        const T sum = (u[o + 1] + u[o - 1]) + (u[o + P] + u[o - P]) + (u[o + P * P] + u[o - P * P]);
+        r[o] = f[o] - (sum - T(6) * u[o]) * ih2;
     }
     __syncthreads();
 }
 
-template <typename T>
-__device__ void sm_restrict(const T* fine, int nf, T* coarse)
+template <typename T, int NF>
+__device__ void sm_restrict(const T* fine, T* coarse)
 {
-    const int nc = nf / 2, mc = nc - 1, Pf = nf + 1, Pc = nc + 1;
-    const int tot = mc * mc * mc;
-    const T w[3] = {T(0.25), T(0.5), T(0.25)};
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-        const int I = t % mc + 1, J = (t / mc) % mc + 1, K = t / (mc * mc) + 1;
+    constexpr int NC = NF / 2, MC = NC - 1, PF = NF + 1, PC = NC + 1, TOT = MC * MC * MC;
+    for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) {
+        const int I = t % MC + 1, J = (t / MC) % MC + 1, K = t / (MC * MC) + 1;
         T acc = T(0);
+#pragma unroll
         for (int c = -1; c <= 1; ++c)
+#pragma unroll
             for (int b = -1; b <= 1; ++b)
-                for (int a = -1; a <= 1; ++a)
-                    acc += (w[a + 1] * w[b + 1] * w[c + 1]) * fine[(2 * I + a) + Pf * ((2 * J + b) + Pf * (2 * K + c))];
-        coarse[I + Pc * (J + Pc * K)] = acc;
+#pragma unroll
+                for (int a = -1; a <= 1; ++a) {
+                    const T w = T(0.125) * T(a == 0 ? 2 : 1) * T(b == 0 ? 2 : 1) * T(c == 0 ? 2 : 1) * T(0.125);
+                    acc += w * fine[(2 * I + a) + PF * ((2 * J + b) + PF * (2 * K + c))];
+                }
+        coarse[I + PC * (J + PC * K)] = acc;
     }
     __syncthreads();
 }
 
-template <typename T>
-__device__ void sm_prolong(const T* coarse, int nc, T* fine, bool add)
+template <typename T, int NC>
+__device__ void sm_prolong(const T* coarse, T* fine, bool add)
 {
-    const int nf = 2 * nc, m = nf - 1, Pf = nf + 1, Pc = nc + 1;
-    const int tot = m * m * m;
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-        const int i = t % m + 1, j = (t / m) % m + 1, k = t / (m * m) + 1;
+    constexpr int NF = 2 * NC, M = NF - 1, PF = NF + 1, PC = NC + 1, TOT = M * M * M;
+    for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) {
+        const int i = t % M + 1, j = (t / M) % M + 1, k = t / (M * M) + 1;
         const int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = j >> 1, J1 = (j + 1) >> 1, K0 = k >> 1, K1 = (k + 1) >> 1;
-        T s = (coarse[I0 + Pc * (J0 + Pc * K0)] + coarse[I1 + Pc * (J0 + Pc * K0)])
-            + (coarse[I0 + Pc * (J1 + Pc * K0)] + coarse[I1 + Pc * (J1 + Pc * K0)]);
-        s += (coarse[I0 + Pc * (J0 + Pc * K1)] + coarse[I1 + Pc * (J0 + Pc * K1)])
-           + (coarse[I0 + Pc * (J1 + Pc * K1)] + coarse[I1 + Pc * (J1 + Pc * K1)]);
-        s *= T(0.125);
-        const int o = i + Pf * (j + Pf * k);
-        fine[o] = add ? fine[o] + s : s;
+        T sum = (coarse[I0 + PC * (J0 + PC * K0)] + coarse[I1 + PC * (J0 + PC * K0)])
+              + (coarse[I0 + PC * (J1 + PC * K0)] + coarse[I1 + PC * (J1 + PC * K0)]);
+        sum += (coarse[I0 + PC * (J0 + PC * K1)] + coarse[I1 + PC * (J0 + PC * K1)])
+             + (coarse[I0 + PC * (J1 + PC * K1)] + coarse[I1 + PC * (J1 + PC * K1)]);
+        sum *= T(0.125);
+        const int o = i + PF * (j + PF * k);
+        fine[o] = add ? fine[o] + sum : sum;
     }
     __syncthreads();
 }
 
-template <typename T>
-__device__ void sm_fill(T* a, int n, T val)
+template <typename T, int N>
+__device__ void sm_fill(T* a, T val)
 {
-    const int tot = cube(n);
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) a[t] = val;
+    constexpr int TOT = (N + 1) * (N + 1) * (N + 1);
+    for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) a[t] = val;
     __syncthreads();
 }
 
@@ -262,92 +268,117 @@ template <typename T>
 __device__ void sm_coarsest(T* u, const T* f, T h)
 {
     if (threadIdx.x == 0) {
-        const T s = (u[14] + u[12]) + (u[16] + u[10]) + (u[22] + u[4]);
-        u[13] = (s - h * h * f[13]) * (T(1) / T(6));
+        const T sum = (u[14] + u[12]) + (u[16] + u[10]) + (u[22] + u[4]);
+        u[13] = (sum - h * h * f[13]) * (T(1) / T(6));
     }
     __syncthreads();
 }
 
-template <typename T>
-__device__ void sm_vcycle(CoarseSmem<T>& S, int top, T htop, int npre, int npost)
+// V(npre, npost) cycle from level L down to the 3^3 grid; the coarser levels
+// start from zero (zero boundary values), level L from what u[L] holds.
+template <typename T, int L>
+__device__ void sm_vcycle(CoarseSmem<T>& S, T h, int npre, int npost)
 {
-    for (int l = top; l >= 1; --l) {
-        const int n = 2 << l;
-        const T h = htop * T(1 << (top - l));
-        if (l < top) sm_fill(S.u[l], n, T(0));
-        for (int s = 0; s < npre; ++s) {
-            sm_relax(S.u[l], S.f[l], n, h * h, 0);
-            sm_relax(S.u[l], S.f[l], n, h * h, 1);
+    constexpr int N = 2 << L;
+    if constexpr (L == 0) {
+        sm_coarsest(S.u[0], S.f[0], h);
+    } else {
+        for (int q = 0; q < npre; ++q) {
+            sm_relax<T, N>(S.u[L], S.f[L], h * h, 0);
+            sm_relax<T, N>(S.u[L], S.f[L], h * h, 1);
         }
-        sm_residual(S.u[l], S.f[l], S.r[l], n, T(1) / (h * h));
-        sm_restrict(S.r[l], n, S.f[l - 1]);
-    }
-    if (top >= 1) sm_fill(S.u[0], 2, T(0));
-    sm_coarsest(S.u[0], S.f[0], htop * T(1 << top));
-    for (int l = 1; l <= top; ++l) {
-        const int n = 2 << l;
-        const T h = htop * T(1 << (top - l));
-        sm_prolong(S.u[l - 1], n / 2, S.u[l], true);
-        for (int s = 0; s < npost; ++s) {
-            sm_relax(S.u[l], S.f[l], n, h * h, 0);
-            sm_relax(S.u[l], S.f[l], n, h * h, 1);
+        sm_residual<T, N>(S.u[L], S.f[L], S.r[L], T(1) / (h * h));
+        sm_restrict<T, N>(S.r[L], S.f[L - 1]);
+        sm_fill<T, N / 2>(S.u[L - 1], T(0));
+        sm_vcycle<T, L - 1>(S, h * T(2), npre, npost);
+        sm_prolong<T, N / 2>(S.u[L - 1], S.u[L], true);
+        for (int q = 0; q < npost; ++q) {
+            sm_relax<T, N>(S.u[L], S.f[L], h * h, 0);
+            sm_relax<T, N>(S.u[L], S.f[L], h * h, 1);
         }
     }
 }
 
-template <typename T>
+// f restricted from level L down to level 0
+template <typename T, int L>
+__device__ void sm_restrict_down(CoarseSmem<T>& S)
+{
+    if constexpr (L > 0) {
+        sm_restrict<T, (2 << L)>(S.f[L], S.f[L - 1]);
+        sm_restrict_down<T, L - 1>(S);
+    }
+}
+
+// boundary values of level L (and below): injected from the finest grid (nfine intervals), or zero
+template <typename T, int L>
+__device__ void sm_inject(CoarseSmem<T>& S, const double* __restrict__ u64, int nfine)
+{
+    constexpr int N = 2 << L, P = N + 1, TOT = P * P * P;
+    const int st = u64 ? nfine / N : 0;
+    const long long PF = nfine + 1;
+    for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) {
+        const int i = t % P, j = (t / P) % P, k = t / (P * P);
+        const bool inner = i > 0 && i < N && j > 0 && j < N && k > 0 && k < N;
+        T val = T(0);
+        if (!inner && u64) val = (T)u64[(long long)i * st + PF * ((long long)j * st + PF * (long long)k * st)];
+        S.u[L][t] = val;
+    }
+    if constexpr (L > 0) sm_inject<T, L - 1>(S, u64, nfine);
+}
+
+// FMG from the 3^3 grid up to level L: prolong, then ncycle V-cycles per level
+template <typename T, int L>
+__device__ void sm_fmg_up(CoarseSmem<T>& S, T h0, int ncycle, int npre, int npost)
+{
+    if constexpr (L == 0) {
+        sm_coarsest(S.u[0], S.f[0], h0);
+    } else {
+        sm_fmg_up<T, L - 1>(S, h0, ncycle, npre, npost);
+        const T h = h0 / T(1 << L);
+        sm_prolong<T, (2 << (L - 1))>(S.u[L - 1], S.u[L], false);
+        for (int c = 0; c < ncycle; ++c) sm_vcycle<T, L>(S, h, npre, npost);
+    }
+}
+
+template <typename T, int TOP>
 __global__ void __launch_bounds__(kCoarseThreads)
 coarse_kernel(int fmg, T* __restrict__ e, const T* __restrict__ f, LevelView v, T htop, const double* __restrict__ u64,
               int nfine, int ncycle, int npre, int npost)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* base = reinterpret_cast<T*>(smem_raw);
-    int top = 0;
-    while ((2 << top) < v.n) ++top;
     CoarseSmem<T> S;
-    for (int l = 0; l <= top; ++l) {
+#pragma unroll
+    for (int l = 0; l <= TOP; ++l) {
         const int c = cube(2 << l);
         S.u[l] = base;
         S.f[l] = base + c;
         S.r[l] = base + 2 * c;
         base += 3 * c;
     }
-    const int n = v.n, P = n + 1;
+    constexpr int N = 2 << TOP, P = N + 1, TOT = P * P * P;
     // right-hand side of the top level (interior), zero elsewhere
-    for (int t = threadIdx.x; t < cube(n); t += blockDim.x) {
+#pragma unroll 5
+    for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) {
         const int i = t % P, j = (t / P) % P, k = t / (P * P);
-        const bool inner = i > 0 && i < n && j > 0 && j < n && k > 0 && k < n;
-        S.f[top][t] = inner ? f[node_off(v, i, j, k)] : T(0);
+        const bool inner = i > 0 && i < N && j > 0 && j < N && k > 0 && k < N;
+        S.f[TOP][t] = inner ? f[node_off(v, i, j, k)] : T(0);
     }
-    __syncthreads();
     if (fmg) {
-        for (int l = top - 1; l >= 0; --l) sm_restrict(S.f[l + 1], 2 << (l + 1), S.f[l]);
-        // boundary values of every level: injected from the finest grid
-        for (int l = 0; l <= top; ++l) {
-            const int nl = 2 << l, Pl = nl + 1;
-            const int s = u64 ? nfine / nl : 0;
-            const long long PF = nfine + 1;
-            for (int t = threadIdx.x; t < cube(nl); t += blockDim.x) {
-                const int i = t % Pl, j = (t / Pl) % Pl, k = t / (Pl * Pl);
-                const bool inner = i > 0 && i < nl && j > 0 && j < nl && k > 0 && k < nl;
-                T val = T(0);
-                if (!inner && u64) val = (T)u64[(long long)i * s + PF * ((long long)j * s + PF * (long long)k * s)];
-                S.u[l][t] = val;
-            }
-        }
         __syncthreads();
-        sm_coarsest(S.u[0], S.f[0], htop * T(1 << top));
-        for (int l = 1; l <= top; ++l) {
-            sm_prolong(S.u[l - 1], 1 << l, S.u[l], false);
-            for (int c = 0; c < ncycle; ++c) sm_vcycle(S, l, htop * T(1 << (top - l)), npre, npost);
-        }
+        sm_restrict_down<T, TOP>(S);
+        sm_inject<T, TOP>(S, u64, nfine);
+        __syncthreads();
+        sm_fmg_up<T, TOP>(S, htop * T(1 << TOP), ncycle, npre, npost);
     } else {
-        sm_fill(S.u[top], n, T(0));
-        sm_vcycle(S, top, htop, npre, npost);
+        for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) S.u[TOP][t] = T(0);
+        __syncthreads();
+        sm_vcycle<T, TOP>(S, htop, npre, npost);
     }
-    for (int t = threadIdx.x; t < cube(n); t += blockDim.x) {
+#pragma unroll 5
+    for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) {
         const int i = t % P, j = (t / P) % P, k = t / (P * P);
-        e[node_off(v, i, j, k)] = S.u[top][t];
+        e[node_off(v, i, j, k)] = S.u[TOP][t];
     }
 }
 
@@ -622,14 +653,13 @@ cudaError_t launch_coarse(int fmg, T* e, const T* f, const LevelView& v, double 
                           int ncycle, int npre, int npost, cudaStream_t s)
 {
     const size_t bytes = coarse_smem_bytes<T>(v.n);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t err = cudaFuncSetAttribute(coarse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)coarse_smem_bytes<T>(kCoarseN));
-        if (err != cudaSuccess) return err;
-        attr_set = true;
+    switch (v.n) {
+    case 2: coarse_kernel<T, 0><<<1, kCoarseThreads, bytes, s>>>(fmg, e, f, v, (T)h, u64, nfine, ncycle, npre, npost); break;
+    case 4: coarse_kernel<T, 1><<<1, kCoarseThreads, bytes, s>>>(fmg, e, f, v, (T)h, u64, nfine, ncycle, npre, npost); break;
+    case 8: coarse_kernel<T, 2><<<1, kCoarseThreads, bytes, s>>>(fmg, e, f, v, (T)h, u64, nfine, ncycle, npre, npost); break;
+    case 16: coarse_kernel<T, 3><<<1, kCoarseThreads, bytes, s>>>(fmg, e, f, v, (T)h, u64, nfine, ncycle, npre, npost); break;
+    default: return cudaErrorInvalidValue;  // the coarse solver covers the levels n = 2 .. 16
     }
-    coarse_kernel<T><<<1, kCoarseThreads, bytes, s>>>(fmg, e, f, v, (T)h, u64, nfine, ncycle, npre, npost);
     return cudaSuccess;
 }
 
@@ -689,10 +719,10 @@ void launch_decide(const double* partials, int nblocks, SolveState* st, double t
 
 cudaError_t prepare_kernels()
 {
-    cudaError_t e = cudaFuncSetAttribute(coarse_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(coarse_kernel<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)coarse_smem_bytes<float>(kCoarseN));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(coarse_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(coarse_kernel<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)coarse_smem_bytes<double>(kCoarseN));
 }
 
