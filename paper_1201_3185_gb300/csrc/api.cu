@@ -110,6 +110,7 @@ struct qumond_ctx {
     SolveState* h_state = nullptr;  // pinned
     int64_t* Ufix = nullptr;        // fixed-point master iterate (QUMOND_PREC_MIXED_FIXED), buffer 0
     int64_t* Ufix2 = nullptr;       // its second buffer (the iterate alternates: current = buffer it & 1)
+    FixedMaps fmaps{};              // TMA descriptors of the fixed-point arrays (n >= 128)
     int64_t* Ffix = nullptr;        // fixed-point right-hand side
     unsigned* maxbits = nullptr;
     int* fault = nullptr;           // set by kernels whose bounded waits ran out
@@ -464,9 +465,15 @@ cudaError_t enqueue_body(qumond_ctx* c, int box, const double* rhs, double coef,
         // update and residual in one pass (U' into the other buffer), then the decision
         int nb = 0;
         run(c, K_RESIDUAL_OUTER, cube(n) * 32.0, s, [&] {
-            nb = launch_fixed_update_residual(c->Ufix, c->Ufix2, c->Ffix, reinterpret_cast<const float*>(E<T>(c, c->L)),
-                                              n, box_h(c, box), c->d_state, reinterpret_cast<float*>(F<T>(c, c->L)),
-                                              c->lev[c->L].v, c->partials, s);
+            if (c->fmaps.ok)
+                nb = launch_fixed_update_residual_tma(c->Ufix, c->Ufix2, c->fmaps, n, box_h(c, box), c->d_state,
+                                                      reinterpret_cast<float*>(F<T>(c, c->L)), c->lev[c->L].v,
+                                                      c->partials, c->fault, s);
+            else
+                nb = launch_fixed_update_residual(c->Ufix, c->Ufix2, c->Ffix,
+                                                  reinterpret_cast<const float*>(E<T>(c, c->L)), n, box_h(c, box),
+                                                  c->d_state, reinterpret_cast<float*>(F<T>(c, c->L)), c->lev[c->L].v,
+                                                  c->partials, s);
         });
         const qumond_params& p = c->p;
         run(c, K_REDUCE, 16.0 * nb, s, [&] {
@@ -787,14 +794,24 @@ qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
                 make_rb_maps(static_cast<float*>(c->lev[l].e), static_cast<float*>(c->lev[l].f), c->lev[l].v,
                              &c->lev[l].maps);
         if (ok && p->precision == QUMOND_PREC_MIXED_FIXED) {
-            const size_t nn = (size_t)(p->n + 1) * (p->n + 1) * (p->n + 1);
+            const size_t nn = fixed_elems(p->n);
             const int nfix = fixed_residual_blocks(p->n > 2 ? p->n : 2);
             if (nfix > c->max_partials) ok = false;  // partial buffer sized above covers it
             ok = ok && cudaMalloc(&c->Ufix, nn * sizeof(int64_t)) == cudaSuccess &&
                  cudaMalloc(&c->Ufix2, nn * sizeof(int64_t)) == cudaSuccess &&
                  cudaMalloc(&c->Ffix, nn * sizeof(int64_t)) == cudaSuccess &&
+                 cudaMemset(c->Ufix, 0, nn * sizeof(int64_t)) == cudaSuccess &&
+                 cudaMemset(c->Ufix2, 0, nn * sizeof(int64_t)) == cudaSuccess &&
+                 cudaMemset(c->Ffix, 0, nn * sizeof(int64_t)) == cudaSuccess &&
                  cudaMalloc(&c->maxbits, sizeof(unsigned)) == cudaSuccess &&
                  cudaMemset(c->maxbits, 0, sizeof(unsigned)) == cudaSuccess;
+            if (ok && c->elt == sizeof(float)) {
+                const int n = p->n;
+                const long long items = (long long)((n - 1 + 31) / 32) * ((n - 1 + 7) / 8) * ((n - 1 + 15) / 16);
+                if (items <= c->max_partials)
+                    make_fixed_maps(c->Ufix, c->Ufix2, c->Ffix, static_cast<float*>(c->lev[L].e), c->lev[L].v,
+                                    &c->fmaps);
+            }
         }
     }
     if (!ok) {

@@ -29,6 +29,14 @@ __device__ __forceinline__ long long nat(int n, int i, int j, int k)
     return (long long)i + P * ((long long)j + P * (long long)k);
 }
 
+// The fixed-point arrays (U, its second buffer, F) have rows of n + 2 entries
+// (one unused), so that a row is a multiple of 16 bytes and the arrays can be
+// described to the tensor-memory accelerator.
+__device__ __forceinline__ long long fix(int n, int i, int j, int k)
+{
+    return (long long)i + (long long)(n + 2) * ((long long)j + (long long)(n + 1) * (long long)k);
+}
+
 // int64 -> FP32 through its two 32-bit halves (within one FP32 rounding of
 // the exact value); integer and FP32 pipes only.
 __device__ __forceinline__ float i64_to_f32(long long x)
@@ -120,13 +128,13 @@ fixed_init_kernel(const float* __restrict__ e, LevelView v, const double* __rest
         const int j = row % (n + 1), k = row / (n + 1);
         const bool brow = j == 0 || j == n || k == 0 || k == n;
         for (int i = threadIdx.x; i <= n; i += kThreads) {
-            const long long o = nat(n, i, j, k);
+            const long long o = nat(n, i, j, k), of = fix(n, i, j, k);
             const bool bnd = brow || i == 0 || i == n;
             const long long val =
                 (bnd || from_u64) ? __double2ll_rn(u64[o] * sc) : f32_to_i64(e[node_off(v, i, j, k)] * scf);
-            U[o] = val;
-            if (bnd) U2[o] = val;  // the second buffer's interior is written before it is read
-            F[o] = bnd ? 0LL : __double2ll_rn(rhs[o] * kf);
+            U[of] = val;
+            if (bnd) U2[of] = val;  // the second buffer's interior is written before it is read
+            F[of] = bnd ? 0LL : __double2ll_rn(rhs[o] * kf);
         }
     }
 }
@@ -141,7 +149,7 @@ fixed_residual_kernel(const long long* __restrict__ U, const long long* __restri
                       const SolveState* __restrict__ st, int want_f, float* __restrict__ r, LevelView v,
                       double* __restrict__ partials)
 {
-    const long long P = n + 1, Q = P * P;
+    const long long P = n + 2, Q = P * (n + 1);
     const float k = pow2f(-st->scale_exp) * ih2;
     const int rows = (n - 1) * (n - 1);
     float rr = 0.0f, ff = 0.0f;
@@ -149,7 +157,7 @@ fixed_residual_kernel(const long long* __restrict__ U, const long long* __restri
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
         const int j = row % (n - 1) + 1, kk = row / (n - 1) + 1;
         for (int i = threadIdx.x + 1; i < n; i += kThreads) {
-            const long long o = nat(n, i, j, kk);
+            const long long o = fix(n, i, j, kk);
             const long long s = (U[o + 1] + U[o - 1]) + (U[o + P] + U[o - P]) + (U[o + Q] + U[o - Q]) - 6 * U[o];
             const long long fv = F[o];
             const float R = i64_to_f32(fv - s);
@@ -212,7 +220,7 @@ fixed_update_residual_kernel(long long* Ua, long long* Ub, const long long* __re
     const float scf = pow2f(S);
     const float k = pow2f(-S) * ih2;
     constexpr float kDown = 9.313225746154785e-10f;  // 2^-30
-    const long long P = n + 1, Q = P * P;
+    const long long P = n + 2, Q = P * (n + 1);          // padded rows of the fixed-point arrays
     const long long plane_e = (long long)(n + 1) * v.M;  // one plane of one colour array of the level
     const int ni = (n - 1 + kFTI - 1) / kFTI, nj = (n - 1 + kFTJ - 1) / kFTJ, nk = (n - 1 + kFKC - 1) / kFKC;
     const int items = ni * nj * nk;
@@ -314,10 +322,7 @@ fixed_output_kernel(const long long* Ua, const long long* Ub, double* __restrict
     const int rows = (n - 1) * (n - 1);
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
         const int j = row % (n - 1) + 1, k = row / (n - 1) + 1;
-        for (int i = threadIdx.x + 1; i < n; i += kThreads) {
-            const long long o = nat(n, i, j, k);
-            u[o] = __ll2double_rn(U[o]) * isc;
-        }
+        for (int i = threadIdx.x + 1; i < n; i += kThreads) u[nat(n, i, j, k)] = __ll2double_rn(U[fix(n, i, j, k)]) * isc;
     }
 }
 
@@ -355,6 +360,8 @@ int launch_fixed_update_residual(int64_t* U, int64_t* U2, const int64_t* F, cons
 }
 
 int fixed_residual_blocks(int n) { return blocks_for_rows((long long)(n - 1) * (n - 1)); }
+
+size_t fixed_elems(int n) { return (size_t)(n + 2) * (n + 1) * (n + 1); }
 
 int launch_fixed_residual(const int64_t* U, const int64_t* F, int n, double h, const SolveState* st, bool want_f,
                           float* r, const LevelView& v, double* partials, cudaStream_t s)

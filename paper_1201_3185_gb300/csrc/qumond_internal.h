@@ -117,6 +117,20 @@ int launch_fixed_residual(const int64_t* U, const int64_t* F, int n, double h, c
                           float* r, const LevelView& v, double* partials, cudaStream_t s);
 void launch_fixed_output(const int64_t* U, const int64_t* U2, double* u, int n, const SolveState* st, cudaStream_t s);
 // U' = U + round(e 2^S) into the other buffer and the residual of U' (one pass); returns the blocks written
+// elements of a fixed-point array (rows padded to n + 2 entries)
+size_t fixed_elems(int n);
+// TMA descriptors of the fixed-point arrays (both buffers of U, F) and of the finest level's e (two colours)
+struct FixedMaps {
+    CUtensorMap u[2];
+    CUtensorMap f;
+    CUtensorMap e[2];
+    bool ok;
+};
+bool make_fixed_maps(int64_t* U, int64_t* U2, int64_t* F, float* e, const LevelView& v, FixedMaps* out);
+// the fused update + residual with TMA-staged planes (n >= 128); returns the blocks written
+int launch_fixed_update_residual_tma(int64_t* U, int64_t* U2, const FixedMaps& maps, int n, double h,
+                                     const SolveState* st, float* r, const LevelView& v, double* partials, int* fault,
+                                     cudaStream_t s);
 int launch_fixed_update_residual(int64_t* U, int64_t* U2, const int64_t* F, const float* e, int n, double h,
                                  const SolveState* st, float* r, const LevelView& v, double* partials, cudaStream_t s);
 
