@@ -111,6 +111,14 @@ typedef struct {
     int use_graphs;     /* 1: each solve runs as one cached CUDA graph (FMG and
                            the whole tolerance loop, decided on the device);
                            0: kernels are launched one by one */
+    int persistent_vcycle; /* 1: the part of each V-cycle on the levels with
+                           n <= 64 below the finest runs as one cooperative
+                           kernel with grid barriers (when the device supports
+                           cooperative launches); 0 (default): one launch per
+                           step.  The results are the same bits.  On GB300 the
+                           cooperative form is not faster (a grid barrier costs
+                           about what a graph launch does) and it serialises
+                           concurrent solves, so it is off by default. */
 } qumond_params;
 
 /* Per-solve report (host struct). */
@@ -126,7 +134,7 @@ typedef struct qumond_ctx qumond_ctx;
 /* Paper defaults: n = 256, one box of 120 kpc, G = 4.30e-3, a0 = 3.6,
    npre = npost = 2, ncycle = 6, rel_tol = 0 (paper mode), max_vcycles = 50,
    QUMOND_PREC_MIXED, QUMOND_BC_ZERO, warm_start = 0, deposit_shift = 24,
-   rc_box_frac = 0.2, box_ratio = 2, use_graphs = 1. */
+   rc_box_frac = 0.2, box_ratio = 2, use_graphs = 1, persistent_vcycle = 0. */
 QUMOND_API void qumond_default_params(qumond_params* p);
 
 /* Validates p and allocates the context's device scratch on the current

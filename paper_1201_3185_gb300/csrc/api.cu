@@ -26,12 +26,12 @@ struct Level {
 enum Kind {
     K_DEPOSIT, K_FIXED_TO_RHO, K_BOUNDARY, K_CONVERT_RHS, K_RESTRICT_FULL, K_COARSE, K_RB_FINEST, K_RB_COARSER,
     K_RESTRICT_RESID, K_PROLONG, K_SET_BOUNDARY, K_ASSIGN_OUTER, K_RESIDUAL_OUTER, K_REDUCE, K_SOURCE, K_FORCES,
-    K_ROTATION_CURVE, K_FIXED_SETUP, K_FIXED_OUTPUT, K_CHI2, K_PROFILE, K_COUNT
+    K_ROTATION_CURVE, K_FIXED_SETUP, K_FIXED_OUTPUT, K_CHI2, K_PROFILE, K_VSUB, K_COUNT
 };
 const char* const kKindNames[K_COUNT] = {
     "cic_deposit", "fixed_to_rho", "boundary_fill", "convert_rhs", "restrict_full", "coarse_solver",
     "rb_half_finest", "rb_half_coarser", "restrict_resid_red", "prolong_black", "set_boundary", "update_outer",
-    "residual_outer", "reduce_norms", "qumond_source", "forces", "rotation_curve", "fixed_setup", "fixed_output", "chi2", "profile",
+    "residual_outer", "reduce_norms", "qumond_source", "forces", "rotation_curve", "fixed_setup", "fixed_output", "chi2", "profile", "vcycle_small_levels",
 };
 constexpr int kMaxTimed = 32768;
 
@@ -111,6 +111,9 @@ struct qumond_ctx {
     int64_t* Ufix = nullptr;        // fixed-point master iterate (QUMOND_PREC_MIXED_FIXED), buffer 0
     int64_t* Ufix2 = nullptr;       // its second buffer (the iterate alternates: current = buffer it & 1)
     FixedMaps fmaps{};              // TMA descriptors of the fixed-point arrays (n >= 128)
+    int vtop = -1;                  // top level of the cooperative small-level V-cycle kernel, -1: not used
+    int vgrid = 0;                  // its CTAs (one per SM)
+    unsigned* vbar = nullptr;       // its grid-barrier counter
     int64_t* Ffix = nullptr;        // fixed-point right-hand side
     unsigned* maxbits = nullptr;
     int* fault = nullptr;           // set by kernels whose bounded waits ran out
@@ -188,6 +191,8 @@ qumond_status check_params(qumond_ctx* c, const qumond_params* p)
     if (p->box_ratio != 2 && p->box_ratio != 4 && p->box_ratio != 8)
         return fail(c, QUMOND_ERR_INVALID_ARG, "box_ratio must be 2, 4 or 8");
     if (p->use_graphs != 0 && p->use_graphs != 1) return fail(c, QUMOND_ERR_INVALID_ARG, "use_graphs must be 0 or 1");
+    if (p->persistent_vcycle != 0 && p->persistent_vcycle != 1)
+        return fail(c, QUMOND_ERR_INVALID_ARG, "persistent_vcycle must be 0 or 1");
     if (p->nboxes > 1 && p->n < 2 * p->box_ratio)
         return fail(c, QUMOND_ERR_INVALID_ARG, "n=%d too small for nested boxes of ratio %d", p->n, p->box_ratio);
     return QUMOND_OK;
@@ -321,6 +326,39 @@ cudaError_t coarse(qumond_ctx* c, int box, int fmg_mode, const double* u64, cuda
     return err;
 }
 
+// The V-cycle from level vtop down, as one cooperative kernel.
+template <typename T>
+cudaError_t vsub(qumond_ctx* c, int box, bool zero_top, cudaStream_t s)
+{
+    const qumond_params& p = c->p;
+    T* e[8];
+    T* f[8];
+    LevelView v[8];
+    double h[8];
+    double bytes = 2.0 * cube(c->lev[c->lc].v.n) * sizeof(T);
+    long long upd = 0;
+    for (int m = 4; m <= c->lev[c->lc].v.n; m *= 2) upd += (long long)(p.npre + p.npost) * (m - 1) * (m - 1) * (m - 1);
+    const int nlev = c->vtop - c->lc + 1;
+    for (int q = 0; q < nlev; ++q) {
+        const int l = c->lc + q;
+        e[q] = E<T>(c, l);
+        f[q] = F<T>(c, l);
+        v[q] = c->lev[l].v;
+        h[q] = level_h(c, box, l);
+        if (q > 0) {
+            const double nodes = cube(v[q].n);
+            bytes += ((3.0 * (p.npre + p.npost) - 0.5) + 1.625 + 1.125) * nodes * sizeof(T);
+            upd += (long long)(p.npre + p.npost) * (v[q].n - 1) * (v[q].n - 1) * (v[q].n - 1);
+        }
+    }
+    count_cells(c, upd);
+    cudaError_t err = cudaSuccess;
+    run(c, K_VSUB, bytes, s, [&] {
+        err = launch_vsub<T>(e, f, v, h, nlev, zero_top ? 1 : 0, p.npre, p.npost, c->vbar, c->fault, c->vgrid, s);
+    });
+    return err;
+}
+
 // One V-cycle at level l on the correction problem held in lev[l] (for l <
 // L the initial guess is zero; at l = L the caller says so).
 template <typename T>
@@ -329,6 +367,7 @@ cudaError_t vcycle(qumond_ctx* c, int box, int l, bool zero_guess, cudaStream_t 
     const qumond_params& p = c->p;
     const double h = level_h(c, box, l);
     if (l <= c->lc) return coarse<T>(c, box, 0, nullptr, s);
+    if (l == c->vtop) return vsub<T>(c, box, zero_guess, s);
     for (int q = 0; q < p.npre; ++q) {
         rb<T>(c, l, 0, zero_guess && q == 0, h, s);
         rb<T>(c, l, 1, false, h, s);
@@ -741,6 +780,7 @@ void qumond_default_params(qumond_params* p)
     p->rc_box_frac = 0.2;
     p->box_ratio = 2;
     p->use_graphs = 1;
+    p->persistent_vcycle = 0;
 }
 
 qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
@@ -814,6 +854,23 @@ qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
             }
         }
     }
+    if (ok && p->persistent_vcycle) {
+        // levels lc+1 .. vtop (n <= 64, below the finest) in one cooperative kernel
+        int dev = 0, coop = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int top = -1;
+        for (int l = c->lc + 1; l < L; ++l)
+            if (c->lev[l].v.n <= 64) top = l;
+        if (coop && sms > 0 && top > c->lc && top - c->lc + 1 <= 6) {
+            ok = cudaMalloc(&c->vbar, sizeof(unsigned)) == cudaSuccess;
+            if (ok) {
+                c->vtop = top;
+                c->vgrid = vsub_grid(sms);
+            }
+        }
+    }
     if (!ok) {
         (void)cudaGetLastError();
         qumond_destroy(c);
@@ -838,6 +895,7 @@ void qumond_destroy(qumond_ctx* c)
     if (c->fault) cudaFree(c->fault);
     if (c->Ufix) cudaFree(c->Ufix);
     if (c->Ufix2) cudaFree(c->Ufix2);
+    if (c->vbar) cudaFree(c->vbar);
     if (c->Ffix) cudaFree(c->Ffix);
     if (c->maxbits) cudaFree(c->maxbits);
     if (c->h_state) cudaFreeHost(c->h_state);

@@ -31,15 +31,9 @@ inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) /
 // its neighbours all being of the other colour.  ZERO: the neighbours are
 // known to be zero (first sweep of a correction that starts from zero).
 template <typename T, bool ZERO>
-__global__ void __launch_bounds__(kBX * kBY)
-rb_half_kernel(T* __restrict__ own, const T* __restrict__ other, const T* __restrict__ f, LevelView v, int colour,
-               T h2, T sixth)
+__device__ __forceinline__ void rb_node(T* __restrict__ own, const T* __restrict__ other, const T* __restrict__ f,
+                                        const LevelView& v, int colour, T h2, T sixth, int m, int j, int k)
 {
-    const int half = v.n >> 1;
-    const int m = blockIdx.x * kBX + threadIdx.x;
-    const int j = blockIdx.y * kBY + threadIdx.y + 1;
-    const int k = blockIdx.z + 1;
-    if (m >= half || j >= v.n) return;
     const int p = (colour + j + k) & 1;  // parity of i in this row
     if (p == 0 && m == 0) return;        // i = 0 is a boundary node
     const long long row = ((long long)k * (v.n + 1) + j) * v.M;
@@ -50,6 +44,19 @@ rb_half_kernel(T* __restrict__ own, const T* __restrict__ other, const T* __rest
         s = (o[m - 1 + p] + o[m + p]) + (o[m - P] + o[m + P]) + (o[m - Q] + o[m + Q]);
     }
     own[row + m] = (s - h2 * f[row + m]) * sixth;
+}
+
+template <typename T, bool ZERO>
+__global__ void __launch_bounds__(kBX * kBY)
+rb_half_kernel(T* __restrict__ own, const T* __restrict__ other, const T* __restrict__ f, LevelView v, int colour,
+               T h2, T sixth)
+{
+    const int half = v.n >> 1;
+    const int m = blockIdx.x * kBX + threadIdx.x;
+    const int j = blockIdx.y * kBY + threadIdx.y + 1;
+    const int k = blockIdx.z + 1;
+    if (m >= half || j >= v.n) return;
+    rb_node<T, ZERO>(own, other, f, v, colour, h2, sixth, m, j, k);
 }
 
 // Residual f - L u at the red node (i, j, k) of a level.
@@ -70,14 +77,9 @@ __device__ __forceinline__ T red_residual(const T* __restrict__ e, const T* __re
 // weight 1/8 at the coinciding fine node and 1/32 at its 12 edge neighbours
 // (the other 14 fine nodes of the stencil are black, residual zero).
 template <typename T>
-__global__ void __launch_bounds__(kBX * kBY)
-restrict_resid_red_kernel(const T* __restrict__ ef, const T* __restrict__ ff, LevelView vf, T* __restrict__ fc,
-                          LevelView vc, T ih2)
+__device__ __forceinline__ void restrict_node(const T* __restrict__ ef, const T* __restrict__ ff, const LevelView& vf,
+                                              T* __restrict__ fc, const LevelView& vc, T ih2, int I, int J, int K)
 {
-    const int I = blockIdx.x * kBX + threadIdx.x + 1;
-    const int J = blockIdx.y * kBY + threadIdx.y + 1;
-    const int K = blockIdx.z + 1;
-    if (I >= vc.n || J >= vc.n) return;
     const int i = 2 * I, j = 2 * J, k = 2 * K;
     T edge = (red_residual(ef, ff, vf, i + 1, j + 1, k, ih2) + red_residual(ef, ff, vf, i - 1, j + 1, k, ih2))
            + (red_residual(ef, ff, vf, i + 1, j - 1, k, ih2) + red_residual(ef, ff, vf, i - 1, j - 1, k, ih2));
@@ -87,6 +89,18 @@ restrict_resid_red_kernel(const T* __restrict__ ef, const T* __restrict__ ff, Le
           + (red_residual(ef, ff, vf, i, j + 1, k - 1, ih2) + red_residual(ef, ff, vf, i, j - 1, k - 1, ih2));
     const T centre = red_residual(ef, ff, vf, i, j, k, ih2);
     fc[node_off(vc, I, J, K)] = T(0.125) * centre + T(0.03125) * edge;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBX * kBY)
+restrict_resid_red_kernel(const T* __restrict__ ef, const T* __restrict__ ff, LevelView vf, T* __restrict__ fc,
+                          LevelView vc, T ih2)
+{
+    const int I = blockIdx.x * kBX + threadIdx.x + 1;
+    const int J = blockIdx.y * kBY + threadIdx.y + 1;
+    const int K = blockIdx.z + 1;
+    if (I >= vc.n || J >= vc.n) return;
+    restrict_node<T>(ef, ff, vf, fc, vc, ih2, I, J, K);
 }
 
 // Full weighting of a right-hand side (both colours) onto coarse interior nodes.
@@ -110,14 +124,9 @@ restrict_full_kernel(const T* __restrict__ ff, LevelView vf, T* __restrict__ fc,
 // Trilinear prolongation of a coarse array to the black interior nodes of the
 // next finer level: assign (FMG interpolation) or add (coarse-grid correction).
 template <typename T, bool ADD>
-__global__ void __launch_bounds__(kBX * kBY)
-prolong_black_kernel(const T* __restrict__ ec, LevelView vc, T* __restrict__ ef, LevelView vf)
+__device__ __forceinline__ void prolong_node(const T* __restrict__ ec, const LevelView& vc, T* __restrict__ ef,
+                                             const LevelView& vf, int m, int j, int k)
 {
-    const int half = vf.n >> 1;
-    const int m = blockIdx.x * kBX + threadIdx.x;
-    const int j = blockIdx.y * kBY + threadIdx.y + 1;
-    const int k = blockIdx.z + 1;
-    if (m >= half || j >= vf.n) return;
     const int p = (1 + j + k) & 1;
     const int i = 2 * m + p;
     if (i < 1) return;
@@ -129,6 +138,18 @@ prolong_black_kernel(const T* __restrict__ ec, LevelView vc, T* __restrict__ ef,
     s *= T(0.125);
     const long long o = vf.cs + ((long long)k * (vf.n + 1) + j) * vf.M + m;
     ef[o] = ADD ? ef[o] + s : s;
+}
+
+template <typename T, bool ADD>
+__global__ void __launch_bounds__(kBX * kBY)
+prolong_black_kernel(const T* __restrict__ ec, LevelView vc, T* __restrict__ ef, LevelView vf)
+{
+    const int half = vf.n >> 1;
+    const int m = blockIdx.x * kBX + threadIdx.x;
+    const int j = blockIdx.y * kBY + threadIdx.y + 1;
+    const int k = blockIdx.z + 1;
+    if (m >= half || j >= vf.n) return;
+    prolong_node<T, ADD>(ec, vc, ef, vf, m, j, k);
 }
 
 // Boundary nodes of a level <- the finest boundary values at the same
@@ -341,11 +362,9 @@ __device__ void sm_fmg_up(CoarseSmem<T>& S, T h0, int ncycle, int npre, int npos
 }
 
 template <typename T, int TOP>
-__global__ void __launch_bounds__(kCoarseThreads)
-coarse_kernel(int fmg, T* __restrict__ e, const T* __restrict__ f, LevelView v, T htop, const double* __restrict__ u64,
-              int nfine, int ncycle, int npre, int npost)
+__device__ void coarse_run(unsigned char* smem_raw, int fmg, T* __restrict__ e, const T* __restrict__ f, LevelView v,
+                           T htop, const double* __restrict__ u64, int nfine, int ncycle, int npre, int npost)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T* base = reinterpret_cast<T*>(smem_raw);
     CoarseSmem<T> S;
 #pragma unroll
@@ -379,6 +398,152 @@ coarse_kernel(int fmg, T* __restrict__ e, const T* __restrict__ f, LevelView v, 
     for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) {
         const int i = t % P, j = (t / P) % P, k = t / (P * P);
         e[node_off(v, i, j, k)] = S.u[TOP][t];
+    }
+}
+
+template <typename T, int TOP>
+__global__ void __launch_bounds__(kCoarseThreads)
+coarse_kernel(int fmg, T* __restrict__ e, const T* __restrict__ f, LevelView v, T htop, const double* __restrict__ u64,
+              int nfine, int ncycle, int npre, int npost)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    coarse_run<T, TOP>(smem_raw, fmg, e, f, v, htop, u64, nfine, ncycle, npre, npost);
+}
+
+// ---------------------------------------------------------------------------
+// The V-cycle below a level, as one cooperative kernel: the levels top .. 1 of
+// a.lev (level 0 = the coarse-grid level) are smoothed, restricted and
+// corrected phase by phase, every CTA taking a grid-stride share of each
+// phase, with a grid barrier between phases; CTA 0 runs the coarse-grid solver
+// in shared memory.  Each node's arithmetic is that of the one-launch-per-step
+// kernels (rb_node, restrict_node, prolong_node, coarse_run), and nodes within
+// a phase are independent, so the result is the same bits.  The barrier
+// counter is zeroed before each launch; a barrier that waits too long records
+// a fault (reported by the solve as a timeout) and the kernel gives up.
+template <typename T>
+struct VsubLevel {
+    T* e;
+    T* f;
+    LevelView v;
+    T h;
+};
+
+constexpr int kVsubMaxLevels = 6;
+
+template <typename T>
+struct VsubArgs {
+    VsubLevel<T> lev[kVsubMaxLevels];
+    int top;        // index of the top level in lev
+    int zero_top;   // the top level's correction starts from zero
+    int npre, npost;
+    unsigned* bar;  // barrier counter (zeroed before the launch)
+    int* fault;
+};
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen, int* fault)
+{
+    __syncthreads();
+    __shared__ int give_up;
+    if (threadIdx.x == 0) {
+        give_up = 0;
+        gen += gridDim.x;
+        __threadfence();
+        atomicAdd(bar, 1u);
+        long long spins = 0;
+        while (*(volatile unsigned*)bar < gen) {
+            if (++spins > (1LL << 26)) {
+                atomicExch(fault, 4);
+                give_up = 1;
+                break;
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return give_up == 0;
+}
+
+template <typename T>
+__device__ void vsub_rb(const VsubLevel<T>& L, int colour, bool zero)
+{
+    const LevelView& v = L.v;
+    const int half = v.n >> 1, rows = v.n - 1;
+    const long long W = (long long)half * rows * rows;
+    const T h2 = L.h * L.h, sixth = T(1) / T(6);
+    T* own = L.e + (long long)colour * v.cs;
+    const T* other = L.e + (long long)(colour ^ 1) * v.cs;
+    const T* f = L.f + (long long)colour * v.cs;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < W; w += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(w % half);
+        const long long r = w / half;
+        const int j = (int)(r % rows) + 1, k = (int)(r / rows) + 1;
+        if (zero)
+            rb_node<T, true>(own, other, f, v, colour, h2, sixth, m, j, k);
+        else
+            rb_node<T, false>(own, other, f, v, colour, h2, sixth, m, j, k);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCoarseThreads) vsub_kernel(VsubArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned gen = 0;
+    bool ok = true;
+    // down: smooth, restrict
+    for (int l = a.top; l >= 1 && ok; --l) {
+        const VsubLevel<T>& L = a.lev[l];
+        for (int q = 0; q < a.npre && ok; ++q) {
+            vsub_rb(L, 0, q == 0 && (l < a.top || a.zero_top));
+            ok = grid_barrier(a.bar, gen, a.fault);
+            if (!ok) break;
+            vsub_rb(L, 1, false);
+            ok = grid_barrier(a.bar, gen, a.fault);
+        }
+        if (!ok) break;
+        const VsubLevel<T>& C = a.lev[l - 1];
+        const int mc = C.v.n - 1;
+        const long long W = (long long)mc * mc * mc;
+        const T ih2 = T(1) / (L.h * L.h);
+        for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < W;
+             w += (long long)gridDim.x * blockDim.x) {
+            const int I = (int)(w % mc) + 1, J = (int)((w / mc) % mc) + 1, K = (int)(w / ((long long)mc * mc)) + 1;
+            restrict_node<T>(L.e, L.f, L.v, C.f, C.v, ih2, I, J, K);
+        }
+        ok = grid_barrier(a.bar, gen, a.fault);
+    }
+    if (!ok) return;
+    // the coarse-grid level: one V-cycle from zero in CTA 0's shared memory
+    if (blockIdx.x == 0) {
+        const VsubLevel<T>& C = a.lev[0];
+        switch (C.v.n) {
+        case 2: coarse_run<T, 0>(smem_raw, 0, C.e, C.f, C.v, C.h, nullptr, 0, 0, a.npre, a.npost); break;
+        case 4: coarse_run<T, 1>(smem_raw, 0, C.e, C.f, C.v, C.h, nullptr, 0, 0, a.npre, a.npost); break;
+        case 8: coarse_run<T, 2>(smem_raw, 0, C.e, C.f, C.v, C.h, nullptr, 0, 0, a.npre, a.npost); break;
+        default: coarse_run<T, 3>(smem_raw, 0, C.e, C.f, C.v, C.h, nullptr, 0, 0, a.npre, a.npost); break;
+        }
+    }
+    ok = grid_barrier(a.bar, gen, a.fault);
+    // up: correct, smooth
+    for (int l = 1; l <= a.top && ok; ++l) {
+        const VsubLevel<T>& L = a.lev[l];
+        const VsubLevel<T>& C = a.lev[l - 1];
+        const int half = L.v.n >> 1, rows = L.v.n - 1;
+        const long long W = (long long)half * rows * rows;
+        for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < W;
+             w += (long long)gridDim.x * blockDim.x) {
+            const int m = (int)(w % half);
+            const long long r = w / half;
+            prolong_node<T, true>(C.e, C.v, L.e, L.v, m, (int)(r % rows) + 1, (int)(r / rows) + 1);
+        }
+        ok = grid_barrier(a.bar, gen, a.fault);
+        for (int q = 0; q < a.npost && ok; ++q) {
+            vsub_rb(L, 0, false);
+            ok = grid_barrier(a.bar, gen, a.fault);
+            if (!ok) break;
+            vsub_rb(L, 1, false);
+            if (l < a.top || q + 1 < a.npost) ok = grid_barrier(a.bar, gen, a.fault);
+        }
     }
 }
 
@@ -664,6 +829,40 @@ cudaError_t launch_coarse(int fmg, T* e, const T* f, const LevelView& v, double 
 }
 
 template <typename T>
+cudaError_t launch_vsub(T* const* e, T* const* f, const LevelView* v, const double* h, int nlev, int zero_top, int npre,
+                        int npost, unsigned* bar, int* fault, int grid, cudaStream_t s)
+{
+    if (nlev < 2 || nlev > kVsubMaxLevels || v[0].n > kCoarseN) return cudaErrorInvalidValue;
+    VsubArgs<T> a{};
+    for (int l = 0; l < nlev; ++l) a.lev[l] = VsubLevel<T>{e[l], f[l], v[l], (T)h[l]};
+    a.top = nlev - 1;
+    a.zero_top = zero_top;
+    a.npre = npre;
+    a.npost = npost;
+    a.bar = bar;
+    a.fault = fault;
+    cudaError_t err = cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
+    if (err != cudaSuccess) return err;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kCoarseThreads);
+    cfg.dynamicSmemBytes = coarse_smem_bytes<T>(v[0].n);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, vsub_kernel<T>, a);
+}
+
+int vsub_grid(int sms)
+{
+    // one CTA per SM: the kernel's shared memory (the coarse solver's) allows one or more per SM
+    return sms;
+}
+
+template <typename T>
 void launch_convert_rhs(const double* rhs, double coef, int n, T* f, const LevelView& v, cudaStream_t s)
 {
     convert_rhs_kernel<T><<<outer_grid(n), kOuterThreads, 0, s>>>(rhs, coef, n, f, v);
@@ -719,6 +918,11 @@ void launch_decide(const double* partials, int nblocks, SolveState* st, double t
 
 cudaError_t prepare_kernels()
 {
+    if (cudaFuncSetAttribute(vsub_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)coarse_smem_bytes<float>(kCoarseN)) != cudaSuccess ||
+        cudaFuncSetAttribute(vsub_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)coarse_smem_bytes<double>(kCoarseN)) != cudaSuccess)
+        return cudaGetLastError();
     cudaError_t e = cudaFuncSetAttribute(coarse_kernel<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)coarse_smem_bytes<float>(kCoarseN));
     if (e != cudaSuccess) return e;
@@ -738,6 +942,8 @@ void launch_reduce_norms(const double* partials, int nblocks, double* out, cudaS
     template void launch_restrict_full<T>(const T*, const LevelView&, T*, const LevelView&, cudaStream_t);            \
     template void launch_prolong_black<T>(const T*, const LevelView&, T*, const LevelView&, bool, cudaStream_t);      \
     template void launch_set_boundary<T>(T*, const LevelView&, const double*, int, cudaStream_t);                     \
+    template cudaError_t launch_vsub<T>(T* const*, T* const*, const LevelView*, const double*, int, int, int, int,     \
+                                        unsigned*, int*, int, cudaStream_t);                                          \
     template cudaError_t launch_coarse<T>(int, T*, const T*, const LevelView&, double, const double*, int, int, int,  \
                                           int, cudaStream_t);                                                          \
     template void launch_convert_rhs<T>(const double*, double, int, T*, const LevelView&, cudaStream_t);              \

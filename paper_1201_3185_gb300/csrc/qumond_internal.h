@@ -59,6 +59,11 @@ template <typename T> void launch_prolong_black(const T* ec, const LevelView& vc
                                                 bool add, cudaStream_t s);
 template <typename T> void launch_set_boundary(T* e, const LevelView& v, const double* u64, int nfine,
                                                cudaStream_t s);
+// the V-cycle on levels 0 .. nlev-1 (level 0 = the coarse-grid level) as one cooperative kernel
+template <typename T> cudaError_t launch_vsub(T* const* e, T* const* f, const LevelView* v, const double* h, int nlev,
+                                              int zero_top, int npre, int npost, unsigned* bar, int* fault, int grid,
+                                              cudaStream_t s);
+int vsub_grid(int sms);
 template <typename T> cudaError_t launch_coarse(int fmg, T* e, const T* f, const LevelView& v, double h,
                                                 const double* u64, int nfine, int ncycle, int npre, int npost,
                                                 cudaStream_t s);

@@ -66,6 +66,7 @@ class qumond_params(ctypes.Structure):
         ("rc_box_frac", ctypes.c_double),
         ("box_ratio", ctypes.c_int),
         ("use_graphs", ctypes.c_int),
+        ("persistent_vcycle", ctypes.c_int),
     ]
 
 

@@ -300,6 +300,23 @@ def test_graph_and_one_by_one_launches_agree(q, prec):
     assert np.array_equal(a["vc"], b["vc"])
 
 
+@pytest.mark.parametrize("prec_name,graphs", [("MIXED_FIXED", 1), ("MIXED_FIXED", 0), ("FP64", 1)])
+def test_cooperative_small_level_vcycle_gives_the_same_bits(q, prec_name, graphs):
+    # the V-cycle on the levels n <= 64 below the finest as one cooperative
+    # kernel with grid barriers, or one launch per step: the same node
+    # arithmetic, so the same bits (n = 128: levels 64 and 32 above the coarse grid)
+    prec = getattr(q, "QUMOND_PREC_" + prec_name)
+    p = synth.two_component_disk(50_000, seed=12, rmax=54000.0, zmax=54000.0)
+    a = gpu_pipeline(p, 128, 120000.0, 2, rel_tol=1e-10, max_vcycles=40, precision=prec, use_graphs=graphs,
+                     persistent_vcycle=1)
+    b = gpu_pipeline(p, 128, 120000.0, 2, rel_tol=1e-10, max_vcycles=40, precision=prec, use_graphs=graphs,
+                     persistent_vcycle=0)
+    for key in ("phiN", "phi"):
+        for x, y in zip(a[key], b[key]):
+            assert np.array_equal(x, y)
+    assert [s.vcycles for s in a["mond_stats"]] == [s.vcycles for s in b["mond_stats"]]
+
+
 def test_concurrent_chains_give_the_same_bits(q):
     # the QUMOND chain on its own context and stream, concurrent with the
     # Newtonian chain: the same kernels in the same order within each chain
