@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(ConvArgs a)
             commit(&bar);
         }
         // the MMAs have read this chunk's shared memory once the commit arrives
-        ok = mbar_wait(&bar, (unsigned)(c & 1), a.fault) && ok;
+        if (ok) ok = mbar_wait(&bar, (unsigned)(c & 1), a.fault);
         fence_after();
     }
     // epilogue: warp w holds TMEM lanes 32w..32w+31 = brick voxels 32w + lane
