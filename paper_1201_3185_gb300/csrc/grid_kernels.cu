@@ -259,13 +259,42 @@ source_kernel(const double* __restrict__ phi, double* __restrict__ src, int n, f
     const int i = i0 + tx, j = j0 + ty;
     load_plane(k0 - 1, 0);
     load_plane(k0, 1);
+    // the next plane's values are fetched into registers one plane ahead, so their loads are in flight
+    // while the current plane's fluxes are computed
+    constexpr int kEnt = (kSrcPX * kSrcPY + kSrcTX * kSrcTY - 1) / (kSrcTX * kSrcTY);  // 2
+    double pre[kEnt];
+    auto fetch = [&](int k) {
+#pragma unroll
+        for (int q = 0; q < kEnt; ++q) {
+            const int t = tid + q * kSrcTX * kSrcTY;
+            const int lx = t % kSrcPX, ly = t / kSrcPX;
+            const int gi = i0 - 1 + lx, gj = j0 - 1 + ly;
+            pre[q] = (t < kSrcPX * kSrcPY && k >= 0 && k <= n && gi >= 0 && gi <= n && gj >= 0 && gj <= n)
+                         ? phi[gi + P * (gj + P * (long long)k)]
+                         : 0.0;
+        }
+    };
+    auto store = [&](int slot) {  // the fetched plane into a slot, split into hi/lo
+#pragma unroll
+        for (int q = 0; q < kEnt; ++q) {
+            const int t = tid + q * kSrcTX * kSrcTY;
+            if (t >= kSrcPX * kSrcPY) continue;
+            const int lx = t % kSrcPX, ly = t / kSrcPX;
+            float h = 0.0f, l = 0.0f;
+            split_hi_lo(pre[q], h, l);  // zero -> (0, 0), as for nodes outside the grid
+            S.hi[slot][ly][lx] = h;
+            S.lo[slot][ly][lx] = l;
+        }
+    };
+    fetch(k0 + 1);
     __syncthreads();
     // flux through the -z face of plane k0 (between k0-1 and k0)
     float fz_prev = flux_z(S, 0, 1, y, x, inv_h, four_a0);
     int pm = 0, pc = 1, pp = 2;  // slots of planes k-1, k, k+1
     for (int k = k0; k < k1; ++k) {
         __syncthreads();  // everyone is done with the slot about to be overwritten
-        load_plane(k + 1, pp);
+        store(pp);        // plane k + 1
+        if (k + 1 < k1) fetch(k + 2);
         __syncthreads();
         Fx[ty][tx + 1] = flux_x(S, pm, pc, pp, y, x, inv_h, four_a0);
         if (tx == 0) Fx[ty][0] = flux_x(S, pm, pc, pp, y, x - 1, inv_h, four_a0);
