@@ -7,8 +7,8 @@
  * potential of a box to Phi - Phi_N, the QUMOND correction (Eq. 2), so that
  * the second solve of the box can start from Phi_N + (network output) and run
  * V-cycles to the tolerance instead of FMG (qumond_params.warm_start = 1).
- * FMG stays the default and the fallback; the network is judged by the
- * residual and the V-cycles it saves.
+ * FMG stays the default and the fallback; the network is measured by the
+ * residual it starts from and the V-cycles it saves.
  *
  * Network (fixed): input S^3 voxels x 16 channels, voxel (x,y,z) = node
  * (x,y,z) of the box's (S+1)^3 grid (S = n, a multiple of 16, >= 16):

@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Tolerances (derivations in the design doc):
+Tolerances:
 * deposit: bit-exact int64 grid, bit-exact FP64 density;
 * FP64 solves at a fixed number of V-cycles: 1e-11 of max|u| (same iterates,
   only the rounding order differs);
