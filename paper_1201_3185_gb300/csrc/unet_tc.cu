@@ -72,12 +72,27 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
     return ok != 0;
 }
 
-// bounded wait on an mbarrier phase; false (and *fault = 3) when it gave up
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait on an mbarrier phase: gives up after kSpinLimit polls or about a second, whichever comes first;
+// false (and *fault = 3) when it gave up
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int* fault)
 {
     long long spins = 0;
+    unsigned long long t0 = 0;
     while (!mbar_try_wait(bar, parity)) {
-        if (++spins > kSpinLimit) {
+        ++spins;
+        if ((spins & 1023) == 0) {
+            const unsigned long long now = global_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > 1000000000ull) spins = kSpinLimit + 1;
+        }
+        if (spins > kSpinLimit) {
             if (fault) atomicExch(fault, 3);
             return false;
         }
