@@ -10,6 +10,11 @@
 // other-colour value crosses HBM once and the six neighbour reads hit shared
 // memory; f comes through the TMA unit with the same planes (both boxes
 // complete one mbarrier) and the result is written straight to global memory.
+// A thread updates four consecutive entries of a row (the parity of i is the
+// same along a row): 16-byte shared-memory loads of the row and of its four
+// neighbour rows, two scalars for the x-neighbours past the ends, and one
+// 16-byte store, which keeps the kernel bound by memory rather than by
+// instruction issue.
 //
 // The box starts at m0 - 4 so that its innermost coordinate is a multiple of
 // 16 bytes; entries before row start (m0 = 0) are filled with zeros by the
@@ -22,9 +27,9 @@ namespace qumond {
 
 namespace {
 
-constexpr int kTM = 64;          // two row entries per thread: m0 + tx and m0 + 32 + tx
+constexpr int kTM = 64;          // four consecutive row entries per thread: m0 + 4 tx .. m0 + 4 tx + 3
 constexpr int kTJ = 8;
-constexpr int kThreadsX = 32;
+constexpr int kThreadsX = kTM / 4;
 constexpr int kBoxX = kTM + 8;  // m0-4 .. m0+67
 constexpr int kBoxY = kTJ + 2;  // j0-1 .. j0+8
 constexpr int kSlots = 6;
@@ -108,8 +113,9 @@ rb_tma_kernel(const __grid_constant__ CUtensorMap other_map, const __grid_consta
         for (int q = kb - 1; q < kb + kSlots - 1 && q <= ke; ++q) issue(q);
     bool ok = true;
     // lane 0 of each warp polls; __syncwarp passes the completed phase on to the warp
+    const bool lane0 = ((tx + ty * kThreadsX) & 31) == 0;
     auto wait = [&](int q) {
-        if ((tx & 31) == 0) {
+        if (lane0) {
             const int u = q - (kb - 1);
             long long spins = 0;
             while (ok && !mbar_try_wait(&bar[u % kSlots], (unsigned)((u / kSlots) & 1))) {
@@ -124,12 +130,15 @@ rb_tma_kernel(const __grid_constant__ CUtensorMap other_map, const __grid_consta
     const int j = j0 + ty;
     const int half = v.n >> 1;
     const long long plane_stride = (long long)(v.n + 1) * v.M;
-    // per-thread constants: the two entries' smem offsets, validity, global row
-    const int c0 = (ty + 1) * kBoxX + tx + 4, c1 = c0 + kThreadsX;
-    const int f0 = kPlaneFloats + ty * kTM + tx, f1 = f0 + kThreadsX;
-    const int mA = m0 + tx, mB = m0 + kThreadsX + tx;
+    // per-thread constants: smem offsets of the four entries (box column 4 + 4 tx) and of their f, the
+    // first entry, validity of each entry apart from the parity rule at m = 0
+    const int c = (ty + 1) * kBoxX + 4 + 4 * tx;
+    const int fo = kPlaneFloats + ty * kTM + 4 * tx;
+    const int mA = m0 + 4 * tx;
     const bool rowok = j < v.n;
-    const bool okA = rowok && mA < half, okB = rowok && mB < half;
+    bool ok4[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) ok4[e] = rowok && mA + e < half;
     long long row = ((long long)kb * (v.n + 1) + j) * v.M;
     int p = (colour + j + kb) & 1;
     int sm = 0, s0 = 1, sp = 2;  // slots of planes k-1, k, k+1
@@ -142,13 +151,35 @@ rb_tma_kernel(const __grid_constant__ CUtensorMap other_map, const __grid_consta
         const float* pm = &plane[sm][0];
         const float* p0 = &plane[s0][0];
         const float* pp = &plane[sp][0];
-        if (okA && (p == 1 || mA >= 1)) {
-            const float s = (p0[c0 - 1 + p] + p0[c0 + p]) + (p0[c0 - kBoxX] + p0[c0 + kBoxX]) + (pm[c0] + pp[c0]);
-            own[row + mA] = (s - h2 * p0[f0]) * sixth;
-        }
-        if (okB) {  // mB >= 32: never the row's first entry
-            const float s = (p0[c1 - 1 + p] + p0[c1 + p]) + (p0[c1 - kBoxX] + p0[c1 + kBoxX]) + (pm[c1] + pp[c1]);
-            own[row + mB] = (s - h2 * p0[f1]) * sixth;
+        if (rowok && mA < half) {
+            const float4 V = *reinterpret_cast<const float4*>(p0 + c);
+            const float x[6] = {p0[c - 1], V.x, V.y, V.z, V.w, p0[c + 4]};  // entries mA-1 .. mA+4
+            const float4 Y0 = *reinterpret_cast<const float4*>(p0 + c - kBoxX);
+            const float4 Y1 = *reinterpret_cast<const float4*>(p0 + c + kBoxX);
+            const float4 Zm = *reinterpret_cast<const float4*>(pm + c);
+            const float4 Zp = *reinterpret_cast<const float4*>(pp + c);
+            const float4 F = *reinterpret_cast<const float4*>(p0 + fo);
+            const float y0[4] = {Y0.x, Y0.y, Y0.z, Y0.w}, y1[4] = {Y1.x, Y1.y, Y1.z, Y1.w};
+            const float zm[4] = {Zm.x, Zm.y, Zm.z, Zm.w}, zp[4] = {Zp.x, Zp.y, Zp.z, Zp.w};
+            const float fv[4] = {F.x, F.y, F.z, F.w};
+            float r[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                // x-neighbours: entries m-1+p and m+p
+                const float lo = p ? x[e + 1] : x[e];
+                const float hi = p ? x[e + 2] : x[e + 1];
+                const float sum = (lo + hi) + (y0[e] + y1[e]) + (zm[e] + zp[e]);
+                r[e] = (sum - h2 * fv[e]) * sixth;
+            }
+            // i = 2m + p must lie in 1 .. n-1: only the row's first entry (m = 0, p = 0) is a boundary node
+            const bool first = p == 0 && mA == 0;
+            if (!first && ok4[3])
+                *reinterpret_cast<float4*>(own + row + mA) = make_float4(r[0], r[1], r[2], r[3]);
+            else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (ok4[e] && !(first && e == 0)) own[row + mA + e] = r[e];
+            }
         }
         __syncthreads();  // slot of plane k-1 is free
         if (leader && k + kSlots - 1 <= ke) issue(k + kSlots - 1);
