@@ -59,6 +59,57 @@ rb_half_kernel(T* __restrict__ own, const T* __restrict__ other, const T* __rest
     rb_node<T, ZERO>(own, other, f, v, colour, h2, sixth, m, j, k);
 }
 
+// The same half-sweep on FP32 levels with four consecutive entries of a row
+// per thread (the parity of i is the same along a row): 16-byte loads of the
+// row, its four neighbour rows and f, two scalars for the x-neighbours past
+// the ends, one 16-byte store; the node arithmetic is rb_node's, in the same
+// order.  half = n/2 is a multiple of 4, so a group lies wholly inside or
+// outside the row's entries; the scalar before entry 0 (read from the padding
+// at the end of the previous row) only feeds the boundary node i = 0, which
+// is not written.
+constexpr int kVX = 8, kVY = 16;  // threads: 32 entries x 16 rows per block
+
+template <bool ZERO>
+__global__ void __launch_bounds__(kVX * kVY)
+rb_half4_kernel(float* __restrict__ own, const float* __restrict__ other, const float* __restrict__ f, LevelView v,
+                int colour, float h2, float sixth)
+{
+    const int half = v.n >> 1;
+    const int mA = 4 * (blockIdx.x * kVX + threadIdx.x);
+    const int j = blockIdx.y * kVY + threadIdx.y + 1;
+    const int k = blockIdx.z + 1;
+    if (mA >= half || j >= v.n) return;
+    const int p = (colour + j + k) & 1;
+    const long long row = ((long long)k * (v.n + 1) + j) * v.M;
+    float sum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (!ZERO) {
+        const float* o = other + row + mA;
+        const long long P = v.M, Q = (long long)v.M * (v.n + 1);
+        const float4 V = *reinterpret_cast<const float4*>(o);
+        const float x[6] = {o[-1], V.x, V.y, V.z, V.w, o[4]};  // entries mA-1 .. mA+4
+        const float4 Y0 = *reinterpret_cast<const float4*>(o - P), Y1 = *reinterpret_cast<const float4*>(o + P);
+        const float4 Z0 = *reinterpret_cast<const float4*>(o - Q), Z1 = *reinterpret_cast<const float4*>(o + Q);
+        const float y0[4] = {Y0.x, Y0.y, Y0.z, Y0.w}, y1[4] = {Y1.x, Y1.y, Y1.z, Y1.w};
+        const float z0[4] = {Z0.x, Z0.y, Z0.z, Z0.w}, z1[4] = {Z1.x, Z1.y, Z1.z, Z1.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float lo = p ? x[e + 1] : x[e];
+            const float hi = p ? x[e + 2] : x[e + 1];
+            sum[e] = (lo + hi) + (y0[e] + y1[e]) + (z0[e] + z1[e]);
+        }
+    }
+    const float4 F = *reinterpret_cast<const float4*>(f + row + mA);
+    const float fv[4] = {F.x, F.y, F.z, F.w};
+    float r[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) r[e] = (sum[e] - h2 * fv[e]) * sixth;
+    if (p == 0 && mA == 0) {  // i = 0 is a boundary node
+        own[row + 1] = r[1], own[row + 2] = r[2], own[row + 3] = r[3];
+    } else {
+        *reinterpret_cast<float4*>(own + row + mA) = make_float4(r[0], r[1], r[2], r[3]);
+    }
+}
+
 // Residual f - L u at the red node (i, j, k) of a level.
 template <typename T>
 __device__ __forceinline__ T red_residual(const T* __restrict__ e, const T* __restrict__ f, const LevelView& v, int i,
@@ -779,6 +830,17 @@ void launch_rb_half(T* e, const T* f, const LevelView& v, int colour, bool zero_
     const T* other = e + (long long)(colour ^ 1) * v.cs;
     const T* fc = f + (long long)colour * v.cs;
     const dim3 blk(kBX, kBY);
+    if (sizeof(T) == sizeof(float) && v.n >= 8) {
+        const dim3 grid(cdiv(v.n / 2, 4 * kVX), cdiv(v.n - 1, kVY), (unsigned)(v.n - 1));
+        float* o4 = reinterpret_cast<float*>(own);
+        const float* x4 = reinterpret_cast<const float*>(other);
+        const float* f4 = reinterpret_cast<const float*>(fc);
+        if (zero_guess)
+            rb_half4_kernel<true><<<grid, dim3(kVX, kVY), 0, s>>>(o4, x4, f4, v, colour, (float)(h * h), 1.0f / 6.0f);
+        else
+            rb_half4_kernel<false><<<grid, dim3(kVX, kVY), 0, s>>>(o4, x4, f4, v, colour, (float)(h * h), 1.0f / 6.0f);
+        return;
+    }
     if (zero_guess)
         rb_half_kernel<T, true><<<half_grid(v.n), blk, 0, s>>>(own, other, fc, v, colour, (T)(h * h), T(1) / T(6));
     else
