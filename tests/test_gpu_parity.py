@@ -121,8 +121,8 @@ def test_fp64_extra_vcycles_match_oracle(q, ora, n):
 
 @pytest.mark.parametrize("n,prec", [(n, p) for n in (16, 64, 128) for p in (0, 1, 2)] + [(256, 1), (256, 2)])
 def test_tolerance_mode_matches_oracle(q, ora, n, prec):
-    # n = 256 runs the TMA-staged half-sweeps, the fused coarse-grid correction
-    # + red half-sweep and (prec 2) the TMA-staged fixed-point update + residual
+    # n = 256 runs the TMA-staged half-sweeps on the finest level and (prec 2)
+    # the TMA-staged fixed-point update + residual
     x, y, z = an.node_coords(n, 4000.0)
     f = np.exp(-(x * x + y * y + 4 * z * z) / 2e5) * 0.05
     bc = -1000.0 / np.sqrt(x * x + y * y + z * z + 1e6)
