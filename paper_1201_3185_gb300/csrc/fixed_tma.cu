@@ -6,11 +6,14 @@
 //   U' = U + round(e 2^S) on interior nodes, U' = U on the boundary,
 //   R = F - (sum of the 6 neighbours of U' - 6 U'),  r = R 2^-S / h^2,
 // U' written to the iterate's other buffer.  A CTA owns a 32 x 8 tile of
-// (i, j) columns and 16 k-planes; for every plane it needs, one thread issues
-// three 3-D boxes (U with a one-node halo, the two colour rows of e covering
-// the same nodes, F of the tile) into a four-slot shared-memory ring
-// completed by mbarriers, so each input byte crosses HBM once and the loads of
-// three planes are in flight while a plane is processed.  Waits are bounded:
+// (i, j) columns, i from a multiple of 32, and 16 k-planes; for every plane it
+// needs, one thread issues four 3-D boxes (U over i0-2 .. i0+33 and a one-row
+// halo, the two colour rows of e covering the same nodes, F of the tile) into
+// a four-slot shared-memory ring completed by mbarriers, so each input byte
+// crosses HBM once and the loads of three planes are in flight while a plane
+// is processed.  A thread works on a pair of consecutive nodes (i even, i+1):
+// the pairs start on 16-byte boundaries in every staged array, so the update
+// and the stencil use 16-byte shared-memory loads and stores.  Waits are bounded:
 // after kSpinLimit polls a CTA records a fault (reported by the solve as a
 // timeout) and finishes without waiting further.
 #include "qumond_internal.h"
@@ -20,12 +23,17 @@ namespace qumond {
 namespace {
 
 constexpr int kTI = 32, kTJ = 8, kKC = 16;
-constexpr int kW = kTI + 2, kH = kTJ + 2;            // U box: 34 x 10 nodes (int64)
-constexpr int kEW = 20;                              // e box: 20 row entries (17 used) x 10 rows (FP32)
-constexpr unsigned kUBytes = kW * kH * 8;            // 2720
-constexpr unsigned kEBytes = kEW * kH * 4;           // 800
-constexpr unsigned kFBytes = kW * kTJ * 8;           // 2176
-constexpr unsigned kOffE0 = 2816, kOffE1 = 3712, kOffF = 4608, kSlotBytes = 6784;  // 128-byte aligned parts
+constexpr int kPX = kTI / 2;                         // threads along i: one pair of nodes each
+constexpr int kW = kTI + 4, kH = kTJ + 2;            // U box: i0-2 .. i0+33 x j0-1 .. j0+8 (int64)
+constexpr int kEW = 24;                              // e box: entries i0/2-4 .. i0/2+19 (FP32)
+constexpr unsigned kUBytes = kW * kH * 8;            // 2880
+constexpr unsigned kEBytes = kEW * kH * 4;           // 960
+constexpr unsigned kFBytes = kTI * kTJ * 8;          // 2048
+constexpr unsigned kOffE0 = 2944, kOffE1 = 3968, kOffF = 4992, kSlotBytes = 7040;  // 128-byte aligned parts
+static_assert(kOffE0 >= kUBytes && kOffE1 >= kOffE0 + kEBytes && kOffF >= kOffE1 + kEBytes &&
+                  kSlotBytes >= kOffF + kFBytes && kOffE0 % 128 == 0 && kOffE1 % 128 == 0 && kOffF % 128 == 0 &&
+                  kSlotBytes % 128 == 0,
+              "slot parts are disjoint and 128-byte aligned");
 constexpr int kSlots = 4;
 constexpr long long kSpinLimit = 1LL << 24;
 constexpr int kMinN = 128;
@@ -82,7 +90,7 @@ __device__ __forceinline__ long long f32_to_i64(float v)
     return (bits >> 31) ? -m : m;
 }
 
-__global__ void __launch_bounds__(kTI * kTJ)
+__global__ void __launch_bounds__(kPX * kTJ)
 fixed_update_residual_tma_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_constant__ CUtensorMap map_u1,
                                  const __grid_constant__ CUtensorMap map_f, const __grid_constant__ CUtensorMap map_e0,
                                  const __grid_constant__ CUtensorMap map_e1, long long* Ua, long long* Ub, int n,
@@ -90,10 +98,10 @@ fixed_update_residual_tma_kernel(const __grid_constant__ CUtensorMap map_u0, con
                                  double* __restrict__ partials, int* __restrict__ fault)
 {
     __shared__ __align__(128) unsigned char slot[kSlots][kSlotBytes];
-    __shared__ long long pl[3][kH][kW];
+    __shared__ __align__(16) long long pl[3][kH][kW];
     __shared__ __align__(8) unsigned long long bar[kSlots];
     __shared__ int abort_flag;
-    __shared__ double sr[kTI * kTJ / 32];
+    __shared__ double sr[kPX * kTJ / 32];
     const bool odd = (st->it & 1) != 0;
     const CUtensorMap* mu = odd ? &map_u1 : &map_u0;
     long long* __restrict__ nxt = odd ? Ua : Ub;
@@ -102,12 +110,11 @@ fixed_update_residual_tma_kernel(const __grid_constant__ CUtensorMap map_u0, con
     const float k = ldexpf(1.0f, -S) * ih2;
     constexpr float kDown = 9.313225746154785e-10f;  // 2^-30
     const long long P = n + 2, Q = P * (n + 1);
-    const int ni = (n - 1 + kTI - 1) / kTI, nj = (n - 1 + kTJ - 1) / kTJ;
+    const int ni = n / kTI, nj = (n - 1 + kTJ - 1) / kTJ;
     const int item = blockIdx.x;
-    const int ti = item % ni;
-    const int i0 = 1 + ti * kTI, j0 = 1 + ((item / ni) % nj) * kTJ, kb = 1 + (item / (ni * nj)) * kKC;
+    const int i0 = (item % ni) * kTI, j0 = 1 + ((item / ni) % nj) * kTJ, kb = 1 + (item / (ni * nj)) * kKC;
     const int ke = kb + kKC < n ? kb + kKC : n;  // residual planes kb .. ke-1; planes kb-1 .. ke are staged
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTI + tx;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPX + tx;
     const bool leader = tid == 0;
     if (leader) {
         abort_flag = 0;
@@ -125,10 +132,10 @@ fixed_update_residual_tma_kernel(const __grid_constant__ CUtensorMap map_u0, con
         }
         unsigned long long* b = &bar[u % kSlots];
         mbar_expect_tx(b, kUBytes + 2 * kEBytes + kFBytes);
-        tma_load_3d(base, mu, i0 - 1, j0 - 1, q, b);
-        tma_load_3d(base + kOffE0, &map_e0, (i0 - 1) >> 1, j0 - 1, q, b);
-        tma_load_3d(base + kOffE1, &map_e1, (i0 - 1) >> 1, j0 - 1, q, b);
-        tma_load_3d(base + kOffF, &map_f, i0 - 1, j0, q, b);
+        tma_load_3d(base, mu, i0 - 2, j0 - 1, q, b);  // x: even int64 index, a 16-byte boundary
+        tma_load_3d(base + kOffE0, &map_e0, i0 / 2 - 4, j0 - 1, q, b);  // x: a multiple of 4 floats
+        tma_load_3d(base + kOffE1, &map_e1, i0 / 2 - 4, j0 - 1, q, b);
+        tma_load_3d(base + kOffF, &map_f, i0, j0, q, b);
     };
     if (leader)
         for (int q = kb - 1; q < kb - 1 + kSlots && q <= ke; ++q) issue(q);
@@ -146,26 +153,33 @@ fixed_update_residual_tma_kernel(const __grid_constant__ CUtensorMap map_u0, con
         }
         __syncwarp();
     };
-    // this thread's (up to) two halo entries of a plane
-    constexpr int kEnt = 2;
-    int hi[kEnt], hj[kEnt], isum[kEnt], em[kEnt];
-    bool inner[kEnt], own[kEnt], used[kEnt];
+    // this thread's (up to) two halo pairs of a plane: nodes (a, a+1), a = i0-2 + 2 hp, row j0-1 + hj
+    constexpr int kPairs = kW / 2 * kH;  // 180
+    constexpr int kEnt = (kPairs + kPX * kTJ - 1) / (kPX * kTJ);
+    int hp[kEnt], hj[kEnt], em[kEnt], ipar[kEnt];
+    bool used[kEnt], inner0[kEnt], inner1[kEnt], own[kEnt];
     long long ob[kEnt];
 #pragma unroll
     for (int m = 0; m < kEnt; ++m) {
-        const int t = tid + m * kTI * kTJ;
-        used[m] = t < kW * kH;
-        hi[m] = t % kW;
-        hj[m] = t / kW;
-        const int i = i0 - 1 + hi[m], j = j0 - 1 + hj[m];
-        inner[m] = used[m] && i >= 1 && i < n && j >= 1 && j < n;
-        own[m] = inner[m] && hi[m] >= 1 && hi[m] <= kTI && hj[m] >= 1 && hj[m] <= kTJ;
-        isum[m] = i + j;
-        em[m] = (i >> 1) - ((i0 - 1) >> 1);  // entry of the node in its colour row of the e box
-        ob[m] = (long long)i + P * (long long)j;
+        const int t = tid + m * kPX * kTJ;
+        used[m] = t < kPairs;
+        hp[m] = t % (kW / 2);
+        hj[m] = t / (kW / 2);
+        const int a = i0 - 2 + 2 * hp[m], j = j0 - 1 + hj[m];
+        const bool jin = used[m] && j >= 1 && j < n;
+        inner0[m] = jin && a >= 1 && a < n;
+        inner1[m] = jin && a + 1 >= 1 && a + 1 < n;
+        // the pair is stored when both nodes lie in the tile (a >= i0, rows of the tile); a boundary node
+        // (i = 0) is stored with its unchanged value, which the other buffer already holds
+        own[m] = jin && a >= i0 && a < i0 + kTI && hj[m] >= 1 && hj[m] <= kTJ;
+        ipar[m] = (a + j) & 1;                 // colour of node a in plane 0
+        em[m] = (a >> 1) - (i0 / 2 - 4);       // entry of both nodes in their colour rows of the e box
+        ob[m] = (long long)a + P * (long long)j;
     }
-    const int ri = i0 + tx, rj = j0 + ty;
-    const bool rok = ri < n && rj < n;
+    // the residual pair: nodes ri, ri+1 of row rj; ri = 0 is a boundary node
+    const int ri = i0 + 2 * tx, rj = j0 + ty;
+    const bool rok = rj < n;
+    const int hx = 2 * tx + 2, hy = ty + 1;
     float rr = 0.0f;
     for (int q = kb - 1; q <= ke; ++q) {
         const int u = q - (kb - 1);
@@ -179,29 +193,51 @@ fixed_update_residual_tma_kernel(const __grid_constant__ CUtensorMap map_u0, con
 #pragma unroll
         for (int m = 0; m < kEnt; ++m) {
             if (!used[m]) continue;
-            long long val = ub[hj[m]][hi[m]];  // zero beyond the array (TMA fill), as for i or j > n
-            if (inner[m] && qin) {
-                const float ev = ((isum[m] + q) & 1) ? e1[hj[m]][em[m]] : e0[hj[m]][em[m]];
-                val += f32_to_i64(ev * scf);
-                if (own[m] && qown) nxt[ob[m] + Q * q] = val;
+            const longlong2 uv = *reinterpret_cast<const longlong2*>(&ub[hj[m]][2 * hp[m]]);
+            long long v0 = uv.x, v1 = uv.y;  // zero beyond the array (TMA fill), as for i or j > n
+            if (qin && (inner0[m] || inner1[m])) {
+                // node a has colour (a + j + q) & 1, node a+1 the other one
+                const bool c0 = ((ipar[m] + q) & 1) != 0;
+                const float ea = c0 ? e1[hj[m]][em[m]] : e0[hj[m]][em[m]];
+                const float eb = c0 ? e0[hj[m]][em[m]] : e1[hj[m]][em[m]];
+                if (inner0[m]) v0 += f32_to_i64(ea * scf);
+                if (inner1[m]) v1 += f32_to_i64(eb * scf);
+                if (own[m] && qown) *reinterpret_cast<longlong2*>(nxt + ob[m] + Q * q) = make_longlong2(v0, v1);
             }
-            dst[hj[m]][hi[m]] = val;
+            *reinterpret_cast<longlong2*>(&dst[hj[m]][2 * hp[m]]) = make_longlong2(v0, v1);
         }
         __syncthreads();
         const int kk = q - 1;
         if (kk >= kb && rok && ok) {
-            const long long(*fb)[kW] =
-                reinterpret_cast<const long long(*)[kW]>(&slot[(u - 1) % kSlots][0] + kOffF);
+            const long long(*fb)[kTI] = reinterpret_cast<const long long(*)[kTI]>(&slot[(u - 1) % kSlots][0] + kOffF);
             const long long(*pm)[kW] = pl[(kk - 1) % 3];
             const long long(*p0)[kW] = pl[kk % 3];
             const long long(*pp)[kW] = pl[(kk + 1) % 3];
-            const int hx = tx + 1, hy = ty + 1;
-            const long long sum = (p0[hy][hx + 1] + p0[hy][hx - 1]) + (p0[hy + 1][hx] + p0[hy - 1][hx]) +
-                                  (pp[hy][hx] + pm[hy][hx]) - 6 * p0[hy][hx];
-            const float R = i64_to_f32(fb[ty][tx + 1] - sum);
-            r[node_off(v, ri, rj, kk)] = R * k;
-            const float Rs = R * kDown;
-            rr = fmaf(Rs, Rs, rr);
+            const longlong2 w0 = *reinterpret_cast<const longlong2*>(&p0[hy][hx - 2]);
+            const longlong2 w1 = *reinterpret_cast<const longlong2*>(&p0[hy][hx]);
+            const longlong2 w2 = *reinterpret_cast<const longlong2*>(&p0[hy][hx + 2]);
+            const longlong2 yn = *reinterpret_cast<const longlong2*>(&p0[hy - 1][hx]);
+            const longlong2 ys = *reinterpret_cast<const longlong2*>(&p0[hy + 1][hx]);
+            const longlong2 zm = *reinterpret_cast<const longlong2*>(&pm[hy][hx]);
+            const longlong2 zp = *reinterpret_cast<const longlong2*>(&pp[hy][hx]);
+            const longlong2 fv = *reinterpret_cast<const longlong2*>(&fb[ty][2 * tx]);
+            // the same sums, in the same order, as the single-node form
+            const long long s0 = (w1.y + w0.y) + (ys.x + yn.x) + (zp.x + zm.x) - 6 * w1.x;
+            const long long s1 = (w2.x + w1.x) + (ys.y + yn.y) + (zp.y + zm.y) - 6 * w1.y;
+            const long long rowb = ((long long)kk * (v.n + 1) + rj) * v.M + (ri >> 1);
+            const int c = (ri + rj + kk) & 1;  // colour of node ri; ri + 1 has the other one
+            if (ri >= 1) {
+                const float R0 = i64_to_f32(fv.x - s0);
+                r[(long long)c * v.cs + rowb] = R0 * k;
+                const float Rs = R0 * kDown;
+                rr = fmaf(Rs, Rs, rr);
+            }
+            {
+                const float R1 = i64_to_f32(fv.y - s1);
+                r[(long long)(c ^ 1) * v.cs + rowb] = R1 * k;
+                const float Rs = R1 * kDown;
+                rr = fmaf(Rs, Rs, rr);
+            }
         }
         __syncthreads();  // slot of plane q-1 is free
         if (leader && q >= kb && q + kSlots - 1 <= ke) issue(q + kSlots - 1);
@@ -211,7 +247,7 @@ fixed_update_residual_tma_kernel(const __grid_constant__ CUtensorMap map_u0, con
     __syncthreads();
     if (leader) {
         double a = 0.0;
-        for (int q = 0; q < kTI * kTJ / 32; ++q) a += sr[q];
+        for (int q = 0; q < kPX * kTJ / 32; ++q) a += sr[q];
         const double up = ldexp((double)k, 30);
         partials[2 * blockIdx.x] = a * up * up;
         partials[2 * blockIdx.x + 1] = 0.0;
@@ -262,7 +298,7 @@ bool make_fixed_maps(int64_t* U, int64_t* U2, int64_t* F, float* e, const LevelV
     const cuuint64_t erow = (cuuint64_t)v.M * 4, eplane = erow * (n + 1);
     bool ok = encode3(enc, &out->u[0], CU_TENSOR_MAP_DATA_TYPE_INT64, U, n + 2, n + 1, n + 1, rowb, planeb, kW, kH) &&
               encode3(enc, &out->u[1], CU_TENSOR_MAP_DATA_TYPE_INT64, U2, n + 2, n + 1, n + 1, rowb, planeb, kW, kH) &&
-              encode3(enc, &out->f, CU_TENSOR_MAP_DATA_TYPE_INT64, F, n + 2, n + 1, n + 1, rowb, planeb, kW, kTJ);
+              encode3(enc, &out->f, CU_TENSOR_MAP_DATA_TYPE_INT64, F, n + 2, n + 1, n + 1, rowb, planeb, kTI, kTJ);
     for (int c = 0; ok && c < 2; ++c)
         ok = encode3(enc, &out->e[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, e + (long long)c * v.cs, v.M, n + 1, n + 1, erow,
                      eplane, kEW, kH);
@@ -274,8 +310,8 @@ int launch_fixed_update_residual_tma(int64_t* U, int64_t* U2, const FixedMaps& m
                                      const SolveState* st, float* r, const LevelView& v, double* partials, int* fault,
                                      cudaStream_t s)
 {
-    const int items = ((n - 1 + kTI - 1) / kTI) * ((n - 1 + kTJ - 1) / kTJ) * ((n - 1 + kKC - 1) / kKC);
-    fixed_update_residual_tma_kernel<<<items, dim3(kTI, kTJ), 0, s>>>(
+    const int items = (n / kTI) * ((n - 1 + kTJ - 1) / kTJ) * ((n - 1 + kKC - 1) / kKC);
+    fixed_update_residual_tma_kernel<<<items, dim3(kPX, kTJ), 0, s>>>(
         maps.u[0], maps.u[1], maps.f, maps.e[0], maps.e[1], reinterpret_cast<long long*>(U),
         reinterpret_cast<long long*>(U2), n, (float)(1.0 / (h * h)), st, r, v, partials, fault);
     return items;
