@@ -710,12 +710,46 @@ def run_learned(args):
             vcyc[key] += [s.vcycles for s in ms]
     torch.cuda.synchronize()
 
+    run(p_learn, min(args.warmup, len(gals)))
+    for c in (c_fmg, c_warm):
+        c.qumond_trace_read(reset=True)
+    g0 = guess.qumond_guess_launches()
     clocks = ClockSampler(local)
+    rep.barrier()
     clocks.start()
-    ms_learn = timed(p_learn, args.steps)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    run(p_learn, args.steps)
+    t1.record()
+    rep.barrier()
     clk = clocks.stop()
+    ms_learn = rep.max(t0.elapsed_time(t1)) / args.steps
+    # kernels of the timed region: the solver contexts' and the network's
+    launches = sum(c.qumond_trace_read(reset=True)[1] for c in (c_fmg, c_warm)) + \
+        (guess.qumond_guess_launches() - g0)
     ms_fmg = timed(p_fmg, args.steps)
     value = ws * 1000.0 / ms_learn
+
+    # end to end: each step copies a galaxy's particles in from pinned host memory and the finest box's
+    # potential out
+    host = [[t.cpu().pin_memory() for t in gals[k]] for k in range(min(len(gals), 4))]
+    out_phi = torch.empty_like(p_learn.phi[-1], device="cpu").pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host[0])
+    d2h = out_phi.numel() * out_phi.element_size()
+    rep.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(args.steps):
+        xs, ys, zs, ms_ = (t.to(dev, non_blocking=True) for t in host[k % len(host)])
+        p_learn.potentials(xs, ys, zs, ms_)
+        out_phi.copy_(p_learn.phi[-1], non_blocking=True)
+    e1.record()
+    rep.barrier()
+    e2e_ms = rep.max(e0.elapsed_time(e1))
+    e2e = {"value": ws * args.steps / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
 
     # plain FP64 FMG, same path and tolerance
     plain = None
@@ -757,12 +791,16 @@ def run_learned(args):
     peaks = measured_peaks()
     peak = peaks["bf16_tflops"] if peaks else 1900.0
     achieved = flops / (inf_ms * 1e9)
-    roofline = {"bound": "tensor", "kernel": "conv3_kernel (the 14 convolutions of one network inference)",
+    tc = guess.qumond_guess_tensor_path_available()
+    roofline = {"bound": "tensor",
+                "kernel": ("conv3_tc_kernel" if tc else "conv3_kernel") +
+                          " (the 14 convolutions of one network inference)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "algorithmic_flops_per_inference": flops, "inference_ms": inf_ms,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst, measured)" if peaks else "fallback",
-                "note": "mma.sync m16n8k16 BF16 tensor-core path; the time includes pooling, upsampling and head "
-                        "launches"}
+                "note": ("tcgen05 MMAs with TMEM accumulators (BF16, FP32 accumulation)" if tc else
+                         "mma.sync m16n8k16 BF16 tensor-core path") +
+                        "; the time includes the input, pooling, upsampling and head launches"}
 
     if rank == 0:
         line = {
@@ -777,8 +815,9 @@ def run_learned(args):
             "roofline": roofline,
             "training_step_ms_per_sample": grad_ms,
             "training_tflops": 3.0 * flops / (grad_ms * 1e9),
-            "e2e": None,
-            "gpu_launches": None,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "gpu_launches_per_step": launches / args.steps,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

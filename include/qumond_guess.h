@@ -69,6 +69,10 @@ QUMOND_API const char* qumond_guess_last_error(qumond_guess* g);
 QUMOND_API qumond_status qumond_guess_tensor_path(qumond_guess* g, int mode);
 QUMOND_API int qumond_guess_tensor_path_available(qumond_guess* g);
 
+/* Kernels this object has enqueued since it was created: every call above
+   and below adds the kernels it launched (0 for a null object). */
+QUMOND_API int64_t qumond_guess_launches(qumond_guess* g);
+
 /* Synchronises `stream` and reports QUMOND_ERR_TIMEOUT (and clears the flag)
    if a tensor-core convolution gave up a bounded wait since the last call;
    the outputs of such calls are undefined. */

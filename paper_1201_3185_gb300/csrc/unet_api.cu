@@ -62,6 +62,7 @@ struct qumond_guess {
     int tc_swap = -1;     // tcgen05 convolutions: descriptor reading found by the self-test, -1 unavailable
     int use_tc = 0;       // 1: tcgen05 convolutions where they apply, 0: mma.sync everywhere
     int* fault = nullptr; // bounded waits of the tcgen05 path
+    long long launches = 0;  // kernels enqueued by the API calls (each launch_* helper's count at its call site)
     std::vector<void*> allocs;
 };
 
@@ -170,6 +171,7 @@ void conv(qumond_guess* g, int l, cudaStream_t s)
     a.tc_swap = g->use_tc ? g->tc_swap : -1;
     a.fault = g->fault;
     launch_conv3(a, s);
+    g->launches += 1;
 }
 
 void forward(qumond_guess* g, cudaStream_t s)
@@ -180,9 +182,11 @@ void forward(qumond_guess* g, cudaStream_t s)
         if (l == 2 || l == 4 || l == 6) {  // pool the previous level's skip output
             const int C = kLayers[l].cin;
             launch_pool(g->D[lev - 1], cat_channels(lev - 1), up_channels(lev - 1), C, S * 2, g->P[lev - 1], s);
+            g->launches += 1;
         }
         if (l == 8 || l == 10 || l == 12) {  // upsample the level below into the concatenation
             launch_up(g->A[l - 1], up_channels(lev), S, g->D[lev], cat_channels(lev), s);
+            g->launches += 1;
         }
         conv(g, l, s);
     }
@@ -193,6 +197,7 @@ void backward(qumond_guess* g, const __nv_bfloat16* target, float k, float loss_
               cudaStream_t s)
 {
     const long long n0 = vox(g, 0);
+    g->launches += 2;  // head + its reduction
     launch_head_train(g->A[13], g->params + g->head_off, target, n0, k, g->G[13], g->hpart, g->hblocks,
                       g->grads + g->head_off, accumulate, loss, loss_scale, s);
     for (int l = kNumLayers - 1; l >= 0; --l) {
@@ -207,6 +212,7 @@ void backward(qumond_guess* g, const __nv_bfloat16* target, float k, float loss_
         wa.part = g->wpart;
         wa.S = S;
         launch_wgrad(wa, wgrad_vblocks(S, cout, cin, g->sms), g->grads + g->woff[l], accumulate, s);
+        g->launches += 4;  // weight gradient + reduction, bias gradient + reduction
         launch_bias_grad(g->G[l], cout, 0, cout, vox(g, lev), g->cpart, g->cblocks, g->grads + g->boff[l], accumulate,
                          s);
         if (l == 0) break;
@@ -231,15 +237,18 @@ void backward(qumond_guess* g, const __nv_bfloat16* target, float k, float loss_
             a.mask = mp, a.ld_mask = ld, a.mask_off = off;
         }
         launch_conv3(a, s);
+        g->launches += 1;
         if (from_pool) {
             // layer l-1 (second encoder layer of the level above) gets the pooled gradient plus the skip gradient
             const int up = lev - 1;
             const int C = cin;
+            g->launches += 1;
             launch_pool_back(g->GP[up], g->GD[up], cat_channels(up), up_channels(up), g->D[up], cat_channels(up),
                              up_channels(up), C, S * 2, g->G[l - 1], s);
         } else if (from_cat) {
             // layer l-1 (the level below) gets the sum over the 8 children of the upsampled slice
             launch_up_back(g->GD[lev], cat_channels(lev), g->A[l - 1], up_channels(lev), S, g->G[l - 1], s);
+            g->launches += 1;
         }
     }
 }
@@ -248,6 +257,7 @@ void refresh_bf16(qumond_guess* g, cudaStream_t s)
 {
     for (int l = 0; l < kNumLayers; ++l)
         launch_weights_bf16(g->params + g->woff[l], kLayers[l].cout, kLayers[l].cin, g->wf[l], g->wd[l], s);
+    g->launches += kNumLayers;
 }
 
 qumond_status check_samples(qumond_guess* g, const uint16_t* const* samples, const float* flags, int nbatch)
@@ -267,6 +277,7 @@ qumond_status batch_gradients(qumond_guess* g, const uint16_t* const* samples, c
     for (int i = 0; i < nbatch; ++i) {
         const __nv_bfloat16* smp = reinterpret_cast<const __nv_bfloat16*>(samples[i]);
         launch_input_from_sample(smp, g->S, flags[i], g->X0, s);
+        g->launches += 1;
         forward(g, s);
         backward(g, smp + 2 * n0, k, ls, loss, i > 0, s);
     }
@@ -380,6 +391,8 @@ qumond_status qumond_guess_tensor_path(qumond_guess* g, int mode)
 
 int qumond_guess_tensor_path_available(qumond_guess* g) { return g && g->tc_swap >= 0 ? 1 : 0; }
 
+int64_t qumond_guess_launches(qumond_guess* g) { return g ? g->launches : 0; }
+
 qumond_status qumond_guess_status(qumond_guess* g, void* stream)
 {
     if (!g) return QUMOND_ERR_INVALID_ARG;
@@ -426,6 +439,7 @@ qumond_status qumond_guess_make_sample(qumond_guess* g, double rho_scale, const 
     g->err.clear();
     if (!dev_ptr(rho) || !dev_ptr(phiN) || !dev_ptr(phi) || !dev_ptr(sample))
         return fail(g, QUMOND_ERR_INVALID_ARG, "make_sample: every array must be a device pointer");
+    g->launches += 1;
     launch_make_sample(rho, phiN, phi, g->S, rho_scale, 1.0 / g->phi_scale, reinterpret_cast<__nv_bfloat16*>(sample),
                        S_(stream));
     GTRY(g, cudaGetLastError(), "make_sample");
@@ -441,6 +455,7 @@ qumond_status qumond_guess_forward(qumond_guess* g, const uint16_t* sample, floa
     launch_input_from_sample(reinterpret_cast<const __nv_bfloat16*>(sample), g->S, box_flag, g->X0, s);
     forward(g, s);
     launch_head(g->A[13], g->params + g->head_off, vox(g, 0), y, s);
+    g->launches += 2;
     GTRY(g, cudaGetLastError(), "forward");
     return QUMOND_OK;
 }
@@ -477,6 +492,7 @@ qumond_status qumond_guess_train_step(qumond_guess* g, const uint16_t* const* sa
     const float b1 = 0.9f, b2 = 0.999f;
     double p1 = 1.0, p2 = 1.0;
     for (int i = 0; i < g->step; ++i) p1 *= b1, p2 *= b2;
+    g->launches += 1;
     launch_adam(g->params, g->grads, g->adam_m, g->adam_v, g->nparams, lr, b1, b2, 1e-8f, (float)(1.0 / (1.0 - p1)),
                 (float)(1.0 / (1.0 - p2)), s);
     refresh_bf16(g, s);
@@ -496,6 +512,7 @@ qumond_status qumond_guess_apply(qumond_guess* g, double rho_scale, float box_fl
     forward(g, s);
     launch_head(g->A[13], g->params + g->head_off, vox(g, 0), g->yhat, s);
     launch_apply_guess(phiN, g->yhat, g->S, g->phi_scale, phi, s);
+    g->launches += 3;
     GTRY(g, cudaGetLastError(), "apply");
     return QUMOND_OK;
 }

@@ -41,7 +41,7 @@ EXPORTED = (
     "qumond_guess_num_params", "qumond_guess_create", "qumond_guess_destroy", "qumond_guess_last_error",
     "qumond_guess_set_params", "qumond_guess_get_params", "qumond_guess_make_sample", "qumond_guess_forward",
     "qumond_guess_gradients", "qumond_guess_train_step", "qumond_guess_apply", "qumond_guess_tensor_path",
-    "qumond_guess_tensor_path_available", "qumond_guess_status",
+    "qumond_guess_tensor_path_available", "qumond_guess_status", "qumond_guess_launches",
 )
 NOALLOC_MAX_N = 64
 
@@ -136,6 +136,7 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
         "qumond_guess_apply": (_I, [_P, _D, ctypes.c_float, _P, _P, _P, _P]),
         "qumond_guess_tensor_path": (_I, [_P, _I]),
         "qumond_guess_tensor_path_available": (_I, [_P]),
+        "qumond_guess_launches": (ctypes.c_int64, [_P]),
         "qumond_guess_status": (_I, [_P, _P]),
     }
     for name, (res, args) in sigs.items():
@@ -420,6 +421,10 @@ class Guess:
     def qumond_guess_tensor_path(self, mode: int):
         """1: tcgen05 convolutions where they apply (the default when available), 0: mma.sync everywhere."""
         self._check(_lib.qumond_guess_tensor_path(self._ptr, int(mode)))
+
+    def qumond_guess_launches(self) -> int:
+        """Kernels this network has enqueued since it was created."""
+        return int(_lib.qumond_guess_launches(self._ptr))
 
     def qumond_guess_tensor_path_available(self) -> bool:
         return bool(_lib.qumond_guess_tensor_path_available(self._ptr))

@@ -187,3 +187,21 @@ def test_tcgen05_matches_mma_sync(q, S):
     print("tcgen05 vs mma.sync S=%d rel L2 %.3e" % (S, err))
     assert err < 1e-2
     g.close()
+
+
+def test_launch_count(q):
+    """One inference (qumond_guess_apply) enqueues the input kernel, the 14
+    convolutions, 3 poolings, 3 upsamplings, the head and the apply kernel;
+    the object's counter (bench.py's gpu_launches) reports exactly those."""
+    S = 32
+    g = q.Guess(S, 1e5)
+    g.qumond_guess_set_params(to_dev(he(3), torch.float32))
+    n1 = (S + 1) ** 3
+    rho = torch.rand(n1, dtype=torch.float64, device="cuda")
+    phiN = torch.rand(n1, dtype=torch.float64, device="cuda")
+    phi = torch.zeros(n1, dtype=torch.float64, device="cuda")
+    l0 = g.qumond_guess_launches()
+    g.qumond_guess_apply(1.0, 0.0, rho, phiN, phi)
+    g.qumond_guess_status()
+    assert g.qumond_guess_launches() - l0 == 23
+    g.close()
