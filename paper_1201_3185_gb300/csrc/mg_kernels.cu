@@ -154,6 +154,139 @@ restrict_resid_red_kernel(const T* __restrict__ ef, const T* __restrict__ ff, Le
     restrict_node<T>(ef, ff, vf, fc, vc, ih2, I, J, K);
 }
 
+// The same restriction on FP32 levels without recomputation: a CTA owns a
+// tile of 32 x 8 coarse (I, J) columns and rk coarse planes (up to 8, fewer
+// when the level has too few tiles to fill the GPU), and marches over
+// the fine planes 2K0-1 .. 2K1-1.  For each fine plane it computes the red
+// residuals of the rows 2J0-1 .. 2J0+15 and entries I0-1 .. I0+34 once (four
+// consecutive entries per thread, 16-byte loads, red_residual's arithmetic in
+// its order) into a three-plane shared ring; after each odd plane 2K+1 it
+// full-weights coarse plane K from the ring with restrict_node's sums in their
+// order.  A red residual is evaluated once per CTA instead of by each of the
+// up to four coarse nodes that weight it.
+constexpr int kRI = 32, kRJ = 8, kRK = 8;  // coarse tile and the most planes per CTA
+constexpr int kRG = 9;                     // groups of four red entries per fine row (36 entries)
+constexpr int kRR = 2 * kRJ + 1;           // fine rows per tile
+static_assert(kRR * kRG <= kRI * kRJ, "one thread per residual group");
+
+__global__ void __launch_bounds__(kRI * kRJ)
+restrict_resid4_kernel(const float* __restrict__ ef, const float* __restrict__ ff, LevelView vf,
+                       float* __restrict__ fc, LevelView vc, float ih2, int rk)
+{
+    __shared__ __align__(16) float ring[3][kRR][kRG * 4];
+    const int n = vf.n, nc = vc.n;
+    const int I0 = 1 + blockIdx.x * kRI, J0 = 1 + blockIdx.y * kRJ, K0 = 1 + blockIdx.z * rk;
+    const int K1 = min(K0 + rk, nc);  // coarse planes K0 .. K1-1
+    const int t = threadIdx.x;
+    const int mbase = I0 - 1;          // a multiple of 32: the groups start on 16-byte boundaries
+    // residual phase: row rr, group rg of the fine tile
+    const int rr = t / kRG, rg = t % kRG;
+    const int jf = 2 * J0 - 1 + rr;
+    const int m0 = mbase + 4 * rg;
+    const bool ract = t < kRR * kRG && jf >= 1 && jf <= n - 1 && m0 < vf.M;
+    // coarse phase: node (I, J)
+    const int cI = t % kRI, cJ = t / kRI;
+    const int I = I0 + cI, J = J0 + cJ;
+    const bool cact = I <= nc - 1 && J <= nc - 1;
+    const long long P = vf.M, Q = (long long)vf.M * (n + 1);
+    for (int k = 2 * K0 - 1; k <= 2 * K1 - 1; ++k) {
+        if (ract) {
+            const int p = (jf + k) & 1;
+            const long long row = ((long long)k * (n + 1) + jf) * vf.M + m0;
+            const float* eb = ef + vf.cs + row;  // the black neighbours
+            const float4 V = *reinterpret_cast<const float4*>(eb);
+            const float x[6] = {eb[-1], V.x, V.y, V.z, V.w, eb[4]};
+            const float4 Y0 = *reinterpret_cast<const float4*>(eb - P), Y1 = *reinterpret_cast<const float4*>(eb + P);
+            const float4 Z0 = *reinterpret_cast<const float4*>(eb - Q), Z1 = *reinterpret_cast<const float4*>(eb + Q);
+            const float4 E = *reinterpret_cast<const float4*>(ef + row);
+            const float4 F = *reinterpret_cast<const float4*>(ff + row);
+            const float y0[4] = {Y0.x, Y0.y, Y0.z, Y0.w}, y1[4] = {Y1.x, Y1.y, Y1.z, Y1.w};
+            const float z0[4] = {Z0.x, Z0.y, Z0.z, Z0.w}, z1[4] = {Z1.x, Z1.y, Z1.z, Z1.w};
+            const float ev[4] = {E.x, E.y, E.z, E.w}, fv[4] = {F.x, F.y, F.z, F.w};
+            float r[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float lo = p ? x[e + 1] : x[e];
+                const float hi = p ? x[e + 2] : x[e + 1];
+                const float sum = (lo + hi) + (y0[e] + y1[e]) + (z0[e] + z1[e]);
+                r[e] = fv[e] - (sum - 6.0f * ev[e]) * ih2;
+            }
+            *reinterpret_cast<float4*>(&ring[k % 3][rr][4 * rg]) = make_float4(r[0], r[1], r[2], r[3]);
+        }
+        __syncthreads();
+        if ((k & 1) && k >= 2 * K0 + 1 && cact) {
+            const int K = (k - 1) >> 1;
+            const float(*pm)[kRG * 4] = ring[(k + 1) % 3];  // fine plane 2K-1
+            const float(*p0)[kRG * 4] = ring[(k + 2) % 3];  // 2K
+            const float(*pp)[kRG * 4] = ring[k % 3];        // 2K+1
+            // fine node (i, j) = (2I, 2J): row 2cJ+1 of the tile; entries I-1 (i-1) and I (i, i+1)
+            const int a = 2 * cJ + 1, lo = cI, hi = cI + 1;
+            float edge = (p0[a + 1][hi] + p0[a + 1][lo]) + (p0[a - 1][hi] + p0[a - 1][lo]);
+            edge += (pp[a][hi] + pp[a][lo]) + (pm[a][hi] + pm[a][lo]);
+            edge += (pp[a + 1][hi] + pp[a - 1][hi]) + (pm[a + 1][hi] + pm[a - 1][hi]);
+            const float centre = p0[a][hi];
+            fc[node_off(vc, I, J, K)] = 0.125f * centre + 0.03125f * edge;
+        }
+        __syncthreads();
+    }
+}
+
+// The coarse-grid correction / FMG interpolation on FP32 levels with four
+// consecutive black entries of a fine row per thread.  For a coarse row
+// (J', K') the nodes I = mA .. mA+4 alternate between the two colour arrays
+// (entries mA/2 .. mA/2+2 and mA/2 .. mA/2+1), read with 8-byte loads; the
+// sums are prolong_node's, in its order, and the fine row is read and
+// written with 16-byte accesses.
+template <bool ADD>
+__global__ void __launch_bounds__(kVX * kVY)
+prolong_black4_kernel(const float* __restrict__ ec, LevelView vc, float* __restrict__ ef, LevelView vf)
+{
+    const int half = vf.n >> 1;
+    const int mA = 4 * (blockIdx.x * kVX + threadIdx.x);
+    const int j = blockIdx.y * kVY + threadIdx.y + 1;
+    const int k = blockIdx.z + 1;
+    if (mA >= half || j >= vf.n) return;
+    const int p = (1 + j + k) & 1;  // parity of i of the black nodes in this row
+    const int J0 = j >> 1, J1 = (j + 1) >> 1, K0 = k >> 1, K1 = (k + 1) >> 1;
+    // coarse nodes I = mA + d (d = 0..4) of row (Jr, Kr)
+    auto row5 = [&](int Jr, int Kr, float* c) {
+        const int ca = (mA + Jr + Kr) & 1;  // colour of the even d
+        const long long base = ((long long)Kr * (vc.n + 1) + Jr) * vc.M + (mA >> 1);
+        const float* A = ec + (long long)ca * vc.cs + base;
+        const float* B = ec + (long long)(ca ^ 1) * vc.cs + base;
+        const float2 a2 = *reinterpret_cast<const float2*>(A);
+        const float2 b2 = *reinterpret_cast<const float2*>(B);
+        c[0] = a2.x, c[1] = b2.x, c[2] = a2.y, c[3] = b2.y, c[4] = A[2];
+    };
+    float c00[5], c10[5], c01[5], c11[5];  // (J0, K0), (J1, K0), (J0, K1), (J1, K1)
+    row5(J0, K0, c00);
+    row5(J1, K0, c10);
+    row5(J0, K1, c01);
+    row5(J1, K1, c11);
+    const long long o = vf.cs + ((long long)k * (vf.n + 1) + j) * vf.M + mA;
+    float4 cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (ADD) cur = *reinterpret_cast<const float4*>(ef + o);
+    const float cv[4] = {cur.x, cur.y, cur.z, cur.w};
+    float r[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        // I0 = mA + e, I1 = mA + e + p
+        const float a0 = c00[e], a1 = p ? c00[e + 1] : c00[e];
+        const float b0 = c10[e], b1 = p ? c10[e + 1] : c10[e];
+        const float d0 = c01[e], d1 = p ? c01[e + 1] : c01[e];
+        const float g0 = c11[e], g1 = p ? c11[e + 1] : c11[e];
+        float sv = (a0 + a1) + (b0 + b1);
+        sv += (d0 + d1) + (g0 + g1);
+        sv *= 0.125f;
+        r[e] = ADD ? cv[e] + sv : sv;
+    }
+    if (p == 0 && mA == 0) {  // i = 0 is a boundary node
+        ef[o + 1] = r[1], ef[o + 2] = r[2], ef[o + 3] = r[3];
+    } else {
+        *reinterpret_cast<float4*>(ef + o) = make_float4(r[0], r[1], r[2], r[3]);
+    }
+}
+
 // Full weighting of a right-hand side (both colours) onto coarse interior nodes.
 template <typename T>
 __global__ void __launch_bounds__(kBX * kBY)
@@ -851,6 +984,24 @@ template <typename T>
 void launch_restrict_resid_red(const T* ef, const T* ff, const LevelView& vf, T* fc, const LevelView& vc, double hf,
                                cudaStream_t s)
 {
+    if (sizeof(T) == sizeof(float) && vf.n >= 128) {
+        // planes per CTA: as many as keep about two CTAs per multiprocessor busy
+        static int sms = 0;
+        if (sms <= 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+        }
+        const int tiles = (int)(cdiv(vc.n - 1, kRI) * cdiv(vc.n - 1, kRJ));
+        int rk = kRK;
+        while (rk > 1 && tiles * (int)cdiv(vc.n - 1, rk) < 2 * sms) --rk;
+        const dim3 grid(cdiv(vc.n - 1, kRI), cdiv(vc.n - 1, kRJ), cdiv(vc.n - 1, rk));
+        restrict_resid4_kernel<<<grid, kRI * kRJ, 0, s>>>(reinterpret_cast<const float*>(ef),
+                                                           reinterpret_cast<const float*>(ff), vf,
+                                                           reinterpret_cast<float*>(fc), vc, (float)(1.0 / (hf * hf)),
+                                                           rk);
+        return;
+    }
     restrict_resid_red_kernel<T><<<inner_grid(vc.n), dim3(kBX, kBY), 0, s>>>(ef, ff, vf, fc, vc, (T)(1.0 / (hf * hf)));
 }
 
@@ -863,6 +1014,16 @@ void launch_restrict_full(const T* ff, const LevelView& vf, T* fc, const LevelVi
 template <typename T>
 void launch_prolong_black(const T* ec, const LevelView& vc, T* ef, const LevelView& vf, bool add, cudaStream_t s)
 {
+    if (sizeof(T) == sizeof(float) && vf.n >= 8) {
+        const dim3 grid(cdiv(vf.n / 2, 4 * kVX), cdiv(vf.n - 1, kVY), (unsigned)(vf.n - 1));
+        const float* c4 = reinterpret_cast<const float*>(ec);
+        float* f4 = reinterpret_cast<float*>(ef);
+        if (add)
+            prolong_black4_kernel<true><<<grid, dim3(kVX, kVY), 0, s>>>(c4, vc, f4, vf);
+        else
+            prolong_black4_kernel<false><<<grid, dim3(kVX, kVY), 0, s>>>(c4, vc, f4, vf);
+        return;
+    }
     if (add)
         prolong_black_kernel<T, true><<<half_grid(vf.n), dim3(kBX, kBY), 0, s>>>(ec, vc, ef, vf);
     else
