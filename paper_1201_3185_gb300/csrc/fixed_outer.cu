@@ -93,6 +93,29 @@ scan_max_kernel(const float* __restrict__ e, LevelView v, const double* __restri
     if ((threadIdx.x & 31) == 0) atomicMax(out, local);
 }
 
+// The same maximum after FMG (not a warm start), as one flat pass over the
+// finest FP32 level with 16-byte loads: its boundary entries hold the FP32
+// values of the boundary data (set before FMG interpolates into the level),
+// and the entries that are no node (beyond i = n, row padding) hold zero.
+__global__ void __launch_bounds__(256) scan_max_level_kernel(const float4* __restrict__ e, long long n4,
+                                                             unsigned* __restrict__ out)
+{
+    unsigned local = 0u;
+    for (long long q = blockIdx.x * 256LL + threadIdx.x; q < n4; q += (long long)gridDim.x * 256) {
+        const float4 x = e[q];
+        const unsigned a = __float_as_uint(fabsf(x.x)), b = __float_as_uint(fabsf(x.y));
+        const unsigned c = __float_as_uint(fabsf(x.z)), d = __float_as_uint(fabsf(x.w));
+        const unsigned m1 = a > b ? a : b, m2 = c > d ? c : d;
+        const unsigned m = m1 > m2 ? m1 : m2;
+        local = m > local ? m : local;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned o = __shfl_down_sync(0xffffffffu, local, off);
+        local = o > local ? o : local;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, local);
+}
+
 // S = 56 - ceil(log2(max|u|)), kept in [-60, 100] so that 2^S and 2^-S stay
 // normal FP32 numbers; also clears the max for the next solve.
 __global__ void choose_scale_kernel(unsigned* __restrict__ maxbits, SolveState* __restrict__ st)
@@ -110,33 +133,45 @@ __global__ void choose_scale_kernel(unsigned* __restrict__ maxbits, SolveState* 
 }
 
 // U = round(u * 2^S) on every node (interior from the FP32 FMG result or the
-// caller's warm start, boundary from the caller's FP64 values), the boundary
-// values also into the iterate's second buffer, and
-// F = round(coef * rhs * h^2 * 2^S) on interior nodes.
-__global__ void __launch_bounds__(kThreads)
-fixed_init_kernel(const float* __restrict__ e, LevelView v, const double* __restrict__ u64,
-                  const double* __restrict__ rhs, double coef_h2, int n, int from_u64,
-                  const SolveState* __restrict__ st, long long* __restrict__ U, long long* __restrict__ U2,
-                  long long* __restrict__ F)
+// caller's warm start, boundary from the boundary data), F = round(coef h^2 f
+// 2^S) on the interior (0 on the boundary); the boundary of the second buffer
+// too.  One thread per pair of nodes (i = 2a, 2a+1) of a row over a flat
+// grid; the pair is one 16-byte store in U and F (their rows start on 16-byte
+// boundaries), and the entry i = n+1 of a row (padding) is written as zero.
+__global__ void __launch_bounds__(256)
+fixed_init_pairs_kernel(const float* __restrict__ e, LevelView v, const double* __restrict__ u64,
+                        const double* __restrict__ rhs, double coef_h2, int n, int from_u64,
+                        const SolveState* __restrict__ st, long long* __restrict__ U, long long* __restrict__ U2,
+                        long long* __restrict__ F)
 {
+    const int pairs = n / 2 + 1;
+    const long long idx = blockIdx.x * 256LL + threadIdx.x;
+    if (idx >= (long long)pairs * (n + 1) * (n + 1)) return;
+    const int row = (int)(idx / pairs), a = (int)(idx - (long long)row * pairs);
+    const int j = row % (n + 1), k = row / (n + 1);
     const int S = st->scale_exp;
     const double sc = pow2d(S);
     const float scf = pow2f(S);
     const double kf = coef_h2 * sc;
-    const int rows = (n + 1) * (n + 1);
-    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int j = row % (n + 1), k = row / (n + 1);
-        const bool brow = j == 0 || j == n || k == 0 || k == n;
-        for (int i = threadIdx.x; i <= n; i += kThreads) {
-            const long long o = nat(n, i, j, k), of = fix(n, i, j, k);
-            const bool bnd = brow || i == 0 || i == n;
-            const long long val =
-                (bnd || from_u64) ? __double2ll_rn(u64[o] * sc) : f32_to_i64(e[node_off(v, i, j, k)] * scf);
-            U[of] = val;
-            if (bnd) U2[of] = val;  // the second buffer's interior is written before it is read
-            F[of] = bnd ? 0LL : __double2ll_rn(rhs[o] * kf);
-        }
+    const bool brow = j == 0 || j == n || k == 0 || k == n;
+    const int i0 = 2 * a;
+    const bool has1 = i0 + 1 <= n;
+    const bool b0 = brow || i0 == 0 || i0 == n, b1 = brow || i0 + 1 == n;
+    const long long o = nat(n, i0, j, k), of = fix(n, i0, j, k);
+    const int c0 = (i0 + j + k) & 1;
+    const long long er = ((long long)k * (n + 1) + j) * v.M + a;  // entry of both nodes in their colour rows
+    const long long v0 = (b0 || from_u64) ? __double2ll_rn(u64[o] * sc) : f32_to_i64(e[(long long)c0 * v.cs + er] * scf);
+    long long v1 = 0, f1 = 0;
+    if (has1) {
+        v1 = (b1 || from_u64) ? __double2ll_rn(u64[o + 1] * sc) : f32_to_i64(e[(long long)(c0 ^ 1) * v.cs + er] * scf);
+        f1 = b1 ? 0LL : __double2ll_rn(rhs[o + 1] * kf);
     }
+    const long long f0 = b0 ? 0LL : __double2ll_rn(rhs[o] * kf);
+    *reinterpret_cast<longlong2*>(U + of) = make_longlong2(v0, v1);
+    *reinterpret_cast<longlong2*>(F + of) = make_longlong2(f0, f1);
+    // the second buffer's interior is written before it is read
+    if (b0) U2[of] = v0;
+    if (has1 && b1) U2[of + 1] = v1;
 }
 
 // R = F - (sum of 6 neighbours - 6 U), exact; r = R 2^-S / h^2 in FP32 into
@@ -311,8 +346,6 @@ fixed_update_residual_kernel(long long* Ua, long long* Ub, const long long* __re
     }
 }
 
-// u = U 2^-S on interior nodes (the boundary values are left as given); U is
-// the current buffer of the iterate, buffer (it & 1).
 __global__ void __launch_bounds__(kThreads)
 fixed_output_kernel(const long long* Ua, const long long* Ub, double* __restrict__ u, int n,
                     const SolveState* __restrict__ st)
@@ -333,15 +366,18 @@ inline int blocks_for_rows(long long rows) { return (int)(rows < kMaxBlocks ? ro
 void launch_fixed_scale(const float* e, const LevelView& v, const double* u64, int n, bool from_u64, unsigned* maxbits,
                         SolveState* st, cudaStream_t s)
 {
-    scan_max_kernel<<<blocks_for_rows((long long)(n + 1) * (n + 1)), kThreads, 0, s>>>(e, v, u64, n, from_u64 ? 1 : 0,
-                                                                                     maxbits);
+    if (from_u64)
+        scan_max_kernel<<<blocks_for_rows((long long)(n + 1) * (n + 1)), kThreads, 0, s>>>(e, v, u64, n, 1, maxbits);
+    else
+        scan_max_level_kernel<<<kMaxBlocks, 256, 0, s>>>(reinterpret_cast<const float4*>(e), 2 * v.cs / 4, maxbits);
     choose_scale_kernel<<<1, 1, 0, s>>>(maxbits, st);
 }
 
 void launch_fixed_init(const float* e, const LevelView& v, const double* u64, const double* rhs, double coef, double h,
                        int n, bool from_u64, const SolveState* st, int64_t* U, int64_t* U2, int64_t* F, cudaStream_t s)
 {
-    fixed_init_kernel<<<blocks_for_rows((long long)(n + 1) * (n + 1)), kThreads, 0, s>>>(
+    const long long threads = (long long)(n / 2 + 1) * (n + 1) * (n + 1);
+    fixed_init_pairs_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
         e, v, u64, rhs, coef * h * h, n, from_u64 ? 1 : 0, st, reinterpret_cast<long long*>(U),
         reinterpret_cast<long long*>(U2), reinterpret_cast<long long*>(F));
 }
