@@ -163,7 +163,8 @@ restrict_resid_red_kernel(const T* __restrict__ ef, const T* __restrict__ ff, Le
 // its order) into a three-plane shared ring; after each odd plane 2K+1 it
 // full-weights coarse plane K from the ring with restrict_node's sums in their
 // order.  A red residual is evaluated once per CTA instead of by each of the
-// up to four coarse nodes that weight it.
+// up to four coarse nodes that weight it, and the loads of fine plane k+1 are
+// issued before the barriers of plane k.
 constexpr int kRI = 32, kRJ = 8, kRK = 8;  // coarse tile and the most planes per CTA
 constexpr int kRG = 9;                     // groups of four red entries per fine row (36 entries)
 constexpr int kRR = 2 * kRJ + 1;           // fine rows per tile
@@ -189,20 +190,31 @@ restrict_resid4_kernel(const float* __restrict__ ef, const float* __restrict__ f
     const int I = I0 + cI, J = J0 + cJ;
     const bool cact = I <= nc - 1 && J <= nc - 1;
     const long long P = vf.M, Q = (long long)vf.M * (n + 1);
+    // the inputs of one fine plane: the black row with its two outer neighbours, the black rows j-1, j+1
+    // and planes k-1, k+1, the red values and f
+    struct In {
+        float4 V, Y0, Y1, Z0, Z1, E, F;
+        float xl, xr;
+    };
+    auto load = [&](int k, In& d) {
+        const long long row = ((long long)k * (n + 1) + jf) * vf.M + m0;
+        const float* eb = ef + vf.cs + row;
+        d.V = *reinterpret_cast<const float4*>(eb);
+        d.xl = eb[-1], d.xr = eb[4];
+        d.Y0 = *reinterpret_cast<const float4*>(eb - P), d.Y1 = *reinterpret_cast<const float4*>(eb + P);
+        d.Z0 = *reinterpret_cast<const float4*>(eb - Q), d.Z1 = *reinterpret_cast<const float4*>(eb + Q);
+        d.E = *reinterpret_cast<const float4*>(ef + row);
+        d.F = *reinterpret_cast<const float4*>(ff + row);
+    };
+    In cur;
+    if (ract) load(2 * K0 - 1, cur);
     for (int k = 2 * K0 - 1; k <= 2 * K1 - 1; ++k) {
         if (ract) {
             const int p = (jf + k) & 1;
-            const long long row = ((long long)k * (n + 1) + jf) * vf.M + m0;
-            const float* eb = ef + vf.cs + row;  // the black neighbours
-            const float4 V = *reinterpret_cast<const float4*>(eb);
-            const float x[6] = {eb[-1], V.x, V.y, V.z, V.w, eb[4]};
-            const float4 Y0 = *reinterpret_cast<const float4*>(eb - P), Y1 = *reinterpret_cast<const float4*>(eb + P);
-            const float4 Z0 = *reinterpret_cast<const float4*>(eb - Q), Z1 = *reinterpret_cast<const float4*>(eb + Q);
-            const float4 E = *reinterpret_cast<const float4*>(ef + row);
-            const float4 F = *reinterpret_cast<const float4*>(ff + row);
-            const float y0[4] = {Y0.x, Y0.y, Y0.z, Y0.w}, y1[4] = {Y1.x, Y1.y, Y1.z, Y1.w};
-            const float z0[4] = {Z0.x, Z0.y, Z0.z, Z0.w}, z1[4] = {Z1.x, Z1.y, Z1.z, Z1.w};
-            const float ev[4] = {E.x, E.y, E.z, E.w}, fv[4] = {F.x, F.y, F.z, F.w};
+            const float x[6] = {cur.xl, cur.V.x, cur.V.y, cur.V.z, cur.V.w, cur.xr};
+            const float y0[4] = {cur.Y0.x, cur.Y0.y, cur.Y0.z, cur.Y0.w}, y1[4] = {cur.Y1.x, cur.Y1.y, cur.Y1.z, cur.Y1.w};
+            const float z0[4] = {cur.Z0.x, cur.Z0.y, cur.Z0.z, cur.Z0.w}, z1[4] = {cur.Z1.x, cur.Z1.y, cur.Z1.z, cur.Z1.w};
+            const float ev[4] = {cur.E.x, cur.E.y, cur.E.z, cur.E.w}, fv[4] = {cur.F.x, cur.F.y, cur.F.z, cur.F.w};
             float r[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -212,6 +224,8 @@ restrict_resid4_kernel(const float* __restrict__ ef, const float* __restrict__ f
                 r[e] = fv[e] - (sum - 6.0f * ev[e]) * ih2;
             }
             *reinterpret_cast<float4*>(&ring[k % 3][rr][4 * rg]) = make_float4(r[0], r[1], r[2], r[3]);
+            // the next plane's loads are in flight across the barriers and the coarse plane below
+            if (k < 2 * K1 - 1) load(k + 1, cur);
         }
         __syncthreads();
         if ((k & 1) && k >= 2 * K0 + 1 && cact) {
