@@ -14,10 +14,12 @@
 // ~2^-56 max|u|, finer than FP64's 2^-53 relative spacing near max|u|, and
 // |F| <= 12 max|U| < 2^60 cannot overflow for a solution of the problem.
 //
-// Only the once-per-solve conversions (FP64 right-hand side and boundary
-// values in, FP64 potential out) use the FP64 pipe; the per-V-cycle kernels
-// use integer and FP32 instructions only.
+// Only the once-per-solve scaling of the FP64 right-hand side uses the FP64
+// pipe (one multiply per node); the conversions between FP64 and int64 are
+// done on the integer pipe (fixed_conv.h), and the per-V-cycle kernels use
+// integer and FP32 instructions only.
 #include "qumond_internal.h"
+#include "fixed_conv.h"
 
 namespace qumond {
 
@@ -160,13 +162,14 @@ fixed_init_pairs_kernel(const float* __restrict__ e, LevelView v, const double* 
     const long long o = nat(n, i0, j, k), of = fix(n, i0, j, k);
     const int c0 = (i0 + j + k) & 1;
     const long long er = ((long long)k * (n + 1) + j) * v.M + a;  // entry of both nodes in their colour rows
-    const long long v0 = (b0 || from_u64) ? __double2ll_rn(u64[o] * sc) : f32_to_i64(e[(long long)c0 * v.cs + er] * scf);
+    // FP64 -> int64 on the integer pipe (round to nearest even, as the FP64 conversion instruction)
+    const long long v0 = (b0 || from_u64) ? f64_to_i64_rn(u64[o] * sc) : f32_to_i64(e[(long long)c0 * v.cs + er] * scf);
     long long v1 = 0, f1 = 0;
     if (has1) {
-        v1 = (b1 || from_u64) ? __double2ll_rn(u64[o + 1] * sc) : f32_to_i64(e[(long long)(c0 ^ 1) * v.cs + er] * scf);
-        f1 = b1 ? 0LL : __double2ll_rn(rhs[o + 1] * kf);
+        v1 = (b1 || from_u64) ? f64_to_i64_rn(u64[o + 1] * sc) : f32_to_i64(e[(long long)(c0 ^ 1) * v.cs + er] * scf);
+        f1 = b1 ? 0LL : f64_to_i64_rn(rhs[o + 1] * kf);
     }
-    const long long f0 = b0 ? 0LL : __double2ll_rn(rhs[o] * kf);
+    const long long f0 = b0 ? 0LL : f64_to_i64_rn(rhs[o] * kf);
     *reinterpret_cast<longlong2*>(U + of) = make_longlong2(v0, v1);
     *reinterpret_cast<longlong2*>(F + of) = make_longlong2(f0, f1);
     // the second buffer's interior is written before it is read
@@ -351,11 +354,12 @@ fixed_output_kernel(const long long* Ua, const long long* Ub, double* __restrict
                     const SolveState* __restrict__ st)
 {
     const long long* __restrict__ U = (st->it & 1) ? Ub : Ua;
-    const double isc = pow2d(-st->scale_exp);
+    const int S = st->scale_exp;
     const int rows = (n - 1) * (n - 1);
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
         const int j = row % (n - 1) + 1, k = row / (n - 1) + 1;
-        for (int i = threadIdx.x + 1; i < n; i += kThreads) u[nat(n, i, j, k)] = __ll2double_rn(U[fix(n, i, j, k)]) * isc;
+        // U 2^-S: int64 -> FP64 on the integer pipe (round to nearest even, then an exact power-of-two scale)
+        for (int i = threadIdx.x + 1; i < n; i += kThreads) u[nat(n, i, j, k)] = i64_to_f64_rn_scaled(U[fix(n, i, j, k)], -S);
     }
 }
 
