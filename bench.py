@@ -204,6 +204,34 @@ def ncu_traffic(kernel: str):
     return k.get("dram_bytes_per_launch_full_size")
 
 
+# kernel classes that belong to the solves (everything but the deposit, the source and the post-processing)
+NOT_SOLVE = {"cic_deposit", "fixed_to_rho", "qumond_source", "forces", "rotation_curve", "chi2", "profile"}
+
+
+def solve_roofline(pipe1, ctx1, step, steps, peak, barrier, max_over_ranks):
+    """Time every solve of `steps` whole steps run with one chain (the pipeline
+    records a CUDA event pair around each solve call on its stream) and relate
+    the solves' algorithmic bytes (the tracer's per-class counts of the solve
+    kernels) to their summed event time."""
+    import torch
+    ctx1.qumond_trace_read(reset=True)
+    pipe1.solve_events = []
+    barrier()
+    for _ in range(steps):
+        step(pipe1)
+    torch.cuda.synchronize()
+    events, pipe1.solve_events = pipe1.solve_events, None
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in events))
+    st, _, _ = ctx1.qumond_trace_read(reset=True)
+    nbytes = sum(k.bytes for name, k in st.items() if name not in NOT_SOLVE)
+    achieved = nbytes / ms / 1e6
+    return {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "solves": len(events), "ms_per_solve": ms / len(events), "algorithmic_bytes_per_solve": nbytes / len(events),
+            "timing": "CUDA events on the solve's stream around each qumond_solve_newton / qumond_solve_mond call "
+                      "(boundary values, FMG, defect correction to the tolerance, output) over %d steps run with "
+                      "one chain (no concurrent solve); bytes = the algorithmic bytes of the solve kernels" % steps}
+
+
 class Contexts:
     """The contexts of a pipeline, read and driven as one (tracer counters merged)."""
 
@@ -365,6 +393,12 @@ def run_ours(args):
                           "after each solve, over %d timed steps of the same workload run with one chain; achieved = "
                           "algorithmic bytes of the timed launches / their time" % args.steps,
                 "live_ms_per_step_of_candidates": live_ms_per_step}
+    # --- the solve-level roofline: every FMG solve of the step (boundary values, FMG and the defect correction
+    # to the tolerance) bracketed by CUDA events on its stream, with one chain so that no two solves overlap;
+    # achieved = the algorithmic bytes of the solves' kernels / the solves' summed event time ----------------
+    roofline["solve"] = {PRECISION_NAMES[args.precision]: solve_roofline(pipe1, ctx1, step, args.steps, peak, barrier,
+                                                                         max_over_ranks)}
+
     total_kernel_ms = sum(k.ms for k in kstats.values())
     total_bytes = sum(k.bytes for k in kstats.values())
     kernels = {k.name: {"launches_per_step": k.launches / args.steps, "ms_per_step": k.ms / args.steps,
@@ -428,10 +462,16 @@ def run_ours(args):
             mms = time_mode(q.QUMOND_PREC_MIXED, nplain)
             fp64_dc = {"value": ws * 1000.0 / mms, "unit": UNIT, "ms_per_step": mms, "steps": nplain,
                        "precision": PRECISION_NAMES["mixed"]}
+            cm, _ = new_pipeline(q.QUMOND_PREC_MIXED)
+            pm = q.Pipeline(cm.ctxs[0], dev)
+            step(pm)
+            roofline["solve"][PRECISION_NAMES["mixed"]] = solve_roofline(pm, Contexts(cm.ctxs[:1]), step,
+                                                                         args.steps, peak, barrier, max_over_ranks)
+            cm.close()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(p, sample_boxes=2)
+        cpu = cpu_baseline(p)
 
     if rank == 0:
         line = {
@@ -868,16 +908,23 @@ def run_reference_sweep(args):
     print(json.dumps(line), flush=True)
 
 
-def oracle_sample(p, sample_boxes):
-    """Steps 1-4 for the first `sample_boxes` boxes of the workload with the
-    FP64 oracle, plus the rotation curve (over the boxes solved)."""
+def oracle_step(p):
+    """One whole step of the workload with the FP64 oracle: for every box the
+    deposit, both FMG solves to the tolerance and the source, then the forces
+    at every particle and the rotation curve.  Returns seconds."""
     import oracle
     w = WORKLOAD
     t0 = time.perf_counter()
-    boxes = oracle.pipeline(p, w["n"], w["L0"], sample_boxes, ncycle=w["ncycle"], npre=w["npre"], npost=w["npost"],
+    boxes = oracle.pipeline(p, w["n"], w["L0"], w["nboxes"], ncycle=w["ncycle"], npre=w["npre"], npost=w["npost"],
                             tol=w["rel_tol"], max_vcycles=w["max_vcycles"])
-    oracle.rotation_curve(w["n"], w["L0"], (0.0, 0.0, 0.0), [b.phi for b in boxes], w["nbins"], w["rmax"], w["nphi"])
+    phis = [b.phi for b in boxes]
+    oracle.forces(w["n"], w["L0"], (0.0, 0.0, 0.0), phis, p.x, p.y, p.z)
+    oracle.rotation_curve(w["n"], w["L0"], (0.0, 0.0, 0.0), phis, w["nbins"], w["rmax"], w["nphi"])
     return time.perf_counter() - t0
+
+
+STEP_SAMPLE = ("the whole step at full size: for each of the %d boxes the deposit, both FMG solves to rel. residual "
+               "%g and the source, then the forces at every particle and the rotation curve")
 
 
 def cpu_cores():
@@ -885,17 +932,15 @@ def cpu_cores():
     return int(n) if n else (os.cpu_count() or 1)
 
 
-def cpu_baseline(p, sample_boxes=1):
+def cpu_baseline(p, steps=2):
     import oracle
     oracle.build()
-    t = oracle_sample(p, sample_boxes)
     w = WORKLOAD
-    value = sample_boxes / (w["nboxes"] * t)
+    times = [oracle_step(p) for _ in range(steps)]
+    value = 1.0 / statistics.mean(times)
     return {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-            "sample": "boxes 0..%d of %d (deposit, both FMG solves to rel. residual %g, source, rotation curve) "
-                      "in %.1f s, scaled by %d/%d to a whole %d-box solve" % (sample_boxes - 1, w["nboxes"],
-                                                                             w["rel_tol"], t, sample_boxes,
-                                                                             w["nboxes"], w["nboxes"])}
+            "sample": "%d steps, each %s (%.1f s per step)" % (steps, STEP_SAMPLE % (w["nboxes"], w["rel_tol"]),
+                                                             statistics.mean(times))}
 
 
 def run_reference(args):
@@ -908,12 +953,11 @@ def run_reference(args):
     p = make_particles()
     w = WORKLOAD
     for _ in range(args.warmup):
-        oracle_sample(p, 1)
-    times = [oracle_sample(p, 1) for _ in range(args.steps)]
-    per_solve = w["nboxes"] * statistics.mean(times)
+        oracle_step(p)
+    times = [oracle_step(p) for _ in range(args.steps)]
+    per_solve = statistics.mean(times)
     value = 1.0 / per_solve
-    sample = "each step: box 0 of %d at full size (deposit, both FMG solves, source, rotation curve), " \
-             "scaled by 1/%d" % (w["nboxes"], w["nboxes"])
+    sample = "each step: " + STEP_SAMPLE % (w["nboxes"], w["rel_tol"])
     config = workload_config("FP64 CPU oracle")
     if w["kind"] == "learned":  # the oracle has no network: it runs the same path with its FMG start
         config = learned_config("FP64 CPU oracle, FMG start")

@@ -235,6 +235,16 @@ QUMOND_API qumond_status qumond_sigma_z(qumond_ctx* ctx, const double* const* ph
 QUMOND_API qumond_status qumond_chi2(qumond_ctx* ctx, const double* vc, const double* v_obs, const double* sigma,
                                      int nbins, int nsets, double* chi2, void* stream);
 
+/* Bound on the polls of one grid barrier of the cooperative small-level
+   V-cycle kernel (persistent_vcycle = 1) before the barrier gives up; the
+   solve then stops its V-cycles and returns QUMOND_ERR_TIMEOUT (the output
+   holds no usable solution).  Default 2^26 polls (far beyond any barrier of
+   a healthy solve).  Not part of the method: it exists so that the timeout
+   path can be exercised (a limit of 1 makes the barriers give up).  Drops
+   the context's cached solve graphs (synchronises the device) when the
+   limit changes.  polls >= 1, else QUMOND_ERR_INVALID_ARG. */
+QUMOND_API qumond_status qumond_set_barrier_poll_limit(qumond_ctx* ctx, int64_t polls);
+
 /* --- tracing (not part of the method: instrumentation of the kernels) ------ */
 
 /* Per-kernel-class counters of a context since it was created or last reset. */
@@ -294,8 +304,14 @@ QUMOND_API qumond_status qumond_trace_read(qumond_ctx* ctx, qumond_kernel_stat* 
    bytes on failure.
 
    The call makes no cudaMalloc, cudaFree or other allocating call.  The first
-   call on each device looks up the array's device address (with that device
-   current) and caches it; make that first call before any stream capture.
+   call on each device does a one-time set-up with that device current: it
+   looks up the array's device address and caches it, and sets the kernel
+   attributes the solve needs (neither allocates).  Make that first call
+   before any stream capture.  The cached address assumes the device is not
+   reset: calling cudaDeviceReset in the same process and then this entry
+   point again is not supported.  When a tolerance is set (rel_tol > 0 and
+   max_vcycles > 0) or stats is non-NULL, the call copies residual norms to
+   a host buffer and synchronises `stream` after each residual check.
    All calls on a device share the array, which keeps the previous call's
    contents (each call clears it before use): calls whose GPU work overlaps,
    on different streams or host threads, race and give wrong results. */

@@ -97,25 +97,49 @@ def network_input(sample, flag):
     return x
 
 
-def forward(layers, head, x):
-    """Network output y [S][S][S] for input x [16][S][S][S]."""
+def bf16_acts(t):
+    """An activation stored in BF16 (round to nearest even), kept as float64."""
+    return t.to(torch.bfloat16).to(torch.float64)
+
+
+def forward(layers, head, x, store=None, terms=False):
+    """Network output y [S][S][S] for input x [16][S][S][S].
+
+    store: None keeps every activation in float64; bf16_acts stores each one in
+    BF16 at the points where the network's definition holds activations in
+    BF16 (every convolution's output after ReLU, every pooled level; the
+    upsampled copies and the concatenations are those values unchanged).
+    terms: also return T[z][y][x] = sum over the head's channels c of
+    |w_c d0_c|, the magnitude of the output's terms."""
+    keep = store if store is not None else (lambda t: t)
+
     def c(i, t):
-        return torch.relu(conv3(t, *layers[i]))
+        return keep(torch.relu(conv3(t, *layers[i])))
+
+    def p(t):
+        return keep(pool(t))
     e0 = c(1, c(0, x))
-    e1 = c(3, c(2, pool(e0)))
-    e2 = c(5, c(4, pool(e1)))
-    b3 = c(7, c(6, pool(e2)))
+    e1 = c(3, c(2, p(e0)))
+    e2 = c(5, c(4, p(e1)))
+    b3 = c(7, c(6, p(e2)))
     d2 = c(9, c(8, torch.cat([up(b3), e2])))
     d1 = c(11, c(10, torch.cat([up(d2), e1])))
     d0 = c(13, c(12, torch.cat([up(d1), e0])))
     hw, hb = head
-    return torch.einsum("c,czyx->zyx", hw, d0) + hb
+    y = torch.einsum("c,czyx->zyx", hw, d0) + hb
+    if terms:
+        return y, torch.einsum("c,czyx->zyx", hw.abs(), d0.abs())
+    return y
 
 
-def predict(params, sample, flag, round_weights=True):
+def predict(params, sample, flag, round_weights=True, store=None, terms=False):
+    """Output voxels (flat, x fastest); with terms=True also the per-voxel term magnitudes."""
     layers, head = unpack(params, round_weights)
     with torch.no_grad():
-        return forward(layers, head, network_input(sample, flag)).numpy().ravel()
+        out = forward(layers, head, network_input(sample, flag), store=store, terms=terms)
+    if terms:
+        return out[0].numpy().ravel(), out[1].numpy().ravel()
+    return out.numpy().ravel()
 
 
 def loss_and_gradients(params, samples, flags, round_weights=True):

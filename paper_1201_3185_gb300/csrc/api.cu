@@ -114,6 +114,7 @@ struct qumond_ctx {
     int vtop = -1;                  // top level of the cooperative small-level V-cycle kernel, -1: not used
     int vgrid = 0;                  // its CTAs (one per SM)
     unsigned* vbar = nullptr;       // its grid-barrier counter
+    long long barrier_polls = 1LL << 26;  // polls before one of its grid barriers gives up
     int64_t* Ffix = nullptr;        // fixed-point right-hand side
     unsigned* maxbits = nullptr;
     int* fault = nullptr;           // set by kernels whose bounded waits ran out
@@ -354,7 +355,8 @@ cudaError_t vsub(qumond_ctx* c, int box, bool zero_top, cudaStream_t s)
     count_cells(c, upd);
     cudaError_t err = cudaSuccess;
     run(c, K_VSUB, bytes, s, [&] {
-        err = launch_vsub<T>(e, f, v, h, nlev, zero_top ? 1 : 0, p.npre, p.npost, c->vbar, c->fault, c->vgrid, s);
+        err = launch_vsub<T>(e, f, v, h, nlev, zero_top ? 1 : 0, p.npre, p.npost, c->vbar, c->fault, c->barrier_polls,
+                             c->vgrid, s);
     });
     return err;
 }
@@ -1048,6 +1050,20 @@ qumond_status qumond_chi2(qumond_ctx* c, const double* vc, const double* v_obs, 
     run(c, K_CHI2, 8.0 * ((double)nbins * (nsets + 2) + nsets), S(stream),
         [&] { launch_chi2(vc, v_obs, sigma, nbins, nsets, chi2, S(stream)); });
     CUDA_TRY(c, cudaGetLastError(), "chi2 launch");
+    return QUMOND_OK;
+}
+
+qumond_status qumond_set_barrier_poll_limit(qumond_ctx* c, int64_t polls)
+{
+    if (!c) return QUMOND_ERR_INVALID_ARG;
+    c->err.clear();
+    if (polls < 1) return fail(c, QUMOND_ERR_INVALID_ARG, "barrier poll limit must be >= 1");
+    if (polls == c->barrier_polls) return QUMOND_OK;
+    // the limit is an argument of the captured kernels: drop the cached graphs
+    CUDA_TRY(c, cudaDeviceSynchronize(), "barrier poll limit");
+    for (auto& g : c->graphs) destroy_graph(g);
+    c->graphs.clear();
+    c->barrier_polls = polls;
     return QUMOND_OK;
 }
 

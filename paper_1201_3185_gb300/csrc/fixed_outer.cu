@@ -131,8 +131,12 @@ __global__ void choose_scale_kernel(unsigned* __restrict__ maxbits, SolveState* 
         S = S < -60 ? -60 : (S > 100 ? 100 : S);
     }
     st->scale_exp = S;
+    st->nonfinite = isfinite(m) ? 0 : 1;  // a NaN or infinity in the start: no integer iterate holds it
     *maxbits = 0u;
 }
+
+// The binary64 exponent field is all ones: an infinity or a NaN (integer pipe only).
+__device__ __forceinline__ bool f64_nonfinite(double x) { return ((f64_bits(x) >> 52) & 0x7ff) == 0x7ff; }
 
 // U = round(u * 2^S) on every node (interior from the FP32 FMG result or the
 // caller's warm start, boundary from the boundary data), F = round(coef h^2 f
@@ -143,7 +147,7 @@ __global__ void choose_scale_kernel(unsigned* __restrict__ maxbits, SolveState* 
 __global__ void __launch_bounds__(256)
 fixed_init_pairs_kernel(const float* __restrict__ e, LevelView v, const double* __restrict__ u64,
                         const double* __restrict__ rhs, double coef_h2, int n, int from_u64,
-                        const SolveState* __restrict__ st, long long* __restrict__ U, long long* __restrict__ U2,
+                        SolveState* __restrict__ st, long long* __restrict__ U, long long* __restrict__ U2,
                         long long* __restrict__ F)
 {
     const int pairs = n / 2 + 1;
@@ -170,6 +174,7 @@ fixed_init_pairs_kernel(const float* __restrict__ e, LevelView v, const double* 
         f1 = b1 ? 0LL : f64_to_i64_rn(rhs[o + 1] * kf);
     }
     const long long f0 = b0 ? 0LL : f64_to_i64_rn(rhs[o] * kf);
+    if ((!b0 && f64_nonfinite(rhs[o])) || (has1 && !b1 && f64_nonfinite(rhs[o + 1]))) st->nonfinite = 1;
     *reinterpret_cast<longlong2*>(U + of) = make_longlong2(v0, v1);
     *reinterpret_cast<longlong2*>(F + of) = make_longlong2(f0, f1);
     // the second buffer's interior is written before it is read
@@ -378,7 +383,7 @@ void launch_fixed_scale(const float* e, const LevelView& v, const double* u64, i
 }
 
 void launch_fixed_init(const float* e, const LevelView& v, const double* u64, const double* rhs, double coef, double h,
-                       int n, bool from_u64, const SolveState* st, int64_t* U, int64_t* U2, int64_t* F, cudaStream_t s)
+                       int n, bool from_u64, SolveState* st, int64_t* U, int64_t* U2, int64_t* F, cudaStream_t s)
 {
     const long long threads = (long long)(n / 2 + 1) * (n + 1) * (n + 1);
     fixed_init_pairs_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(

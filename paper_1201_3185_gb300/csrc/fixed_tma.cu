@@ -15,7 +15,8 @@
 // the pairs start on 16-byte boundaries in every staged array, so the update
 // and the stencil use 16-byte shared-memory loads and stores.  Waits are bounded:
 // after kSpinLimit polls a CTA records a fault (reported by the solve as a
-// timeout) and finishes without waiting further.
+// timeout), issues no further copies, waits (bounded) for the copies already
+// in flight, and finishes.
 #include "qumond_internal.h"
 
 namespace qumond {
@@ -122,7 +123,11 @@ fixed_update_residual_tma_kernel(const __grid_constant__ CUtensorMap map_u0, con
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    auto issue = [&](int q) {  // plane q into its slot (leader only)
+    // leader: planes kb-1 .. issued-1 have been issued; lane 0 of a warp: planes
+    // before `landed` have been seen complete
+    int issued = kb - 1, landed = kb - 1;
+    auto issue = [&](int q) {  // plane q into its slot (leader only); nothing more once a wait gave up
+        if (*(volatile int*)&abort_flag) return;
         const int u = q - (kb - 1);
         unsigned char* base = &slot[u % kSlots][0];
         if ((smem_u32(base) & 127u) != 0u) {  // never issue a copy the TMA unit would reject
@@ -136,6 +141,7 @@ fixed_update_residual_tma_kernel(const __grid_constant__ CUtensorMap map_u0, con
         tma_load_3d(base + kOffE0, &map_e0, i0 / 2 - 4, j0 - 1, q, b);  // x: a multiple of 4 floats
         tma_load_3d(base + kOffE1, &map_e1, i0 / 2 - 4, j0 - 1, q, b);
         tma_load_3d(base + kOffF, &map_f, i0, j0, q, b);
+        issued = q + 1;
     };
     if (leader)
         for (int q = kb - 1; q < kb - 1 + kSlots && q <= ke; ++q) issue(q);
@@ -148,8 +154,10 @@ fixed_update_residual_tma_kernel(const __grid_constant__ CUtensorMap map_u0, con
                 if (++spins > kSpinLimit || *(volatile int*)&abort_flag) {
                     ok = false;
                     atomicExch(fault, 1);
+                    *(volatile int*)&abort_flag = 1;  // the leader stops issuing copies
                 }
             }
+            if (ok) landed = q + 1;
         }
         __syncwarp();
     };
@@ -245,6 +253,16 @@ fixed_update_residual_tma_kernel(const __grid_constant__ CUtensorMap map_u0, con
     for (int off = 16; off > 0; off >>= 1) rr += __shfl_down_sync(0xffffffffu, rr, off);
     if ((tid & 31) == 0) sr[tid >> 5] = rr;
     __syncthreads();
+    if (leader && *(volatile int*)&abort_flag) {
+        // a wait gave up: copies issued earlier may still be landing in this CTA's shared memory, so wait
+        // for every plane in [landed, issued) before exiting (bounded again; the fault is recorded)
+        for (int q = landed; q < issued; ++q) {
+            const int u = q - (kb - 1);
+            long long spins = 0;
+            while (!mbar_try_wait(&bar[u % kSlots], (unsigned)((u / kSlots) & 1)) && ++spins <= kSpinLimit) {
+            }
+        }
+    }
     if (leader) {
         double a = 0.0;
         for (int q = 0; q < kPX * kTJ / 32; ++q) a += sr[q];

@@ -636,9 +636,10 @@ struct VsubArgs {
     int npre, npost;
     unsigned* bar;  // barrier counter (zeroed before the launch)
     int* fault;
+    long long polls;  // a barrier gives up after this many polls of the counter
 };
 
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen, int* fault)
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen, int* fault, long long polls)
 {
     __syncthreads();
     __shared__ int give_up;
@@ -649,7 +650,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen, int* 
         atomicAdd(bar, 1u);
         long long spins = 0;
         while (*(volatile unsigned*)bar < gen) {
-            if (++spins > (1LL << 26)) {
+            if (++spins > polls) {
                 atomicExch(fault, 4);
                 give_up = 1;
                 break;
@@ -693,10 +694,10 @@ __global__ void __launch_bounds__(kCoarseThreads) vsub_kernel(VsubArgs<T> a)
         const VsubLevel<T>& L = a.lev[l];
         for (int q = 0; q < a.npre && ok; ++q) {
             vsub_rb(L, 0, q == 0 && (l < a.top || a.zero_top));
-            ok = grid_barrier(a.bar, gen, a.fault);
+            ok = grid_barrier(a.bar, gen, a.fault, a.polls);
             if (!ok) break;
             vsub_rb(L, 1, false);
-            ok = grid_barrier(a.bar, gen, a.fault);
+            ok = grid_barrier(a.bar, gen, a.fault, a.polls);
         }
         if (!ok) break;
         const VsubLevel<T>& C = a.lev[l - 1];
@@ -708,7 +709,7 @@ __global__ void __launch_bounds__(kCoarseThreads) vsub_kernel(VsubArgs<T> a)
             const int I = (int)(w % mc) + 1, J = (int)((w / mc) % mc) + 1, K = (int)(w / ((long long)mc * mc)) + 1;
             restrict_node<T>(L.e, L.f, L.v, C.f, C.v, ih2, I, J, K);
         }
-        ok = grid_barrier(a.bar, gen, a.fault);
+        ok = grid_barrier(a.bar, gen, a.fault, a.polls);
     }
     if (!ok) return;
     // the coarse-grid level: one V-cycle from zero in CTA 0's shared memory
@@ -721,7 +722,7 @@ __global__ void __launch_bounds__(kCoarseThreads) vsub_kernel(VsubArgs<T> a)
         default: coarse_run<T, 3>(smem_raw, 0, C.e, C.f, C.v, C.h, nullptr, 0, 0, a.npre, a.npost); break;
         }
     }
-    ok = grid_barrier(a.bar, gen, a.fault);
+    ok = grid_barrier(a.bar, gen, a.fault, a.polls);
     // up: correct, smooth
     for (int l = 1; l <= a.top && ok; ++l) {
         const VsubLevel<T>& L = a.lev[l];
@@ -734,13 +735,13 @@ __global__ void __launch_bounds__(kCoarseThreads) vsub_kernel(VsubArgs<T> a)
             const long long r = w / half;
             prolong_node<T, true>(C.e, C.v, L.e, L.v, m, (int)(r % rows) + 1, (int)(r / rows) + 1);
         }
-        ok = grid_barrier(a.bar, gen, a.fault);
+        ok = grid_barrier(a.bar, gen, a.fault, a.polls);
         for (int q = 0; q < a.npost && ok; ++q) {
             vsub_rb(L, 0, false);
-            ok = grid_barrier(a.bar, gen, a.fault);
+            ok = grid_barrier(a.bar, gen, a.fault, a.polls);
             if (!ok) break;
             vsub_rb(L, 1, false);
-            if (l < a.top || q + 1 < a.npost) ok = grid_barrier(a.bar, gen, a.fault);
+            if (l < a.top || q + 1 < a.npost) ok = grid_barrier(a.bar, gen, a.fault, a.polls);
         }
     }
 }
@@ -941,7 +942,7 @@ decide_kernel(const double* __restrict__ partials, int nblocks, SolveState* __re
         const double rel = sqrt(sa[0]) / st->denom;
         if (first) st->rel0 = rel;
         st->rel = rel;
-        const bool finite = isfinite(rel);
+        const bool finite = isfinite(rel) && !st->nonfinite;
         const int faulted = (fault && *fault) ? 1 : 0;
         if (first) st->fault = 0;
         if (faulted) {
@@ -1067,7 +1068,7 @@ cudaError_t launch_coarse(int fmg, T* e, const T* f, const LevelView& v, double 
 
 template <typename T>
 cudaError_t launch_vsub(T* const* e, T* const* f, const LevelView* v, const double* h, int nlev, int zero_top, int npre,
-                        int npost, unsigned* bar, int* fault, int grid, cudaStream_t s)
+                        int npost, unsigned* bar, int* fault, long long polls, int grid, cudaStream_t s)
 {
     if (nlev < 2 || nlev > kVsubMaxLevels || v[0].n > kCoarseN) return cudaErrorInvalidValue;
     VsubArgs<T> a{};
@@ -1078,6 +1079,7 @@ cudaError_t launch_vsub(T* const* e, T* const* f, const LevelView* v, const doub
     a.npost = npost;
     a.bar = bar;
     a.fault = fault;
+    a.polls = polls;
     cudaError_t err = cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
     if (err != cudaSuccess) return err;
     cudaLaunchConfig_t cfg = {};
@@ -1180,7 +1182,7 @@ void launch_reduce_norms(const double* partials, int nblocks, double* out, cudaS
     template void launch_prolong_black<T>(const T*, const LevelView&, T*, const LevelView&, bool, cudaStream_t);      \
     template void launch_set_boundary<T>(T*, const LevelView&, const double*, int, cudaStream_t);                     \
     template cudaError_t launch_vsub<T>(T* const*, T* const*, const LevelView*, const double*, int, int, int, int,     \
-                                        unsigned*, int*, int, cudaStream_t);                                          \
+                                        unsigned*, int*, long long, int, cudaStream_t);                               \
     template cudaError_t launch_coarse<T>(int, T*, const T*, const LevelView&, double, const double*, int, int, int,  \
                                           int, cudaStream_t);                                                          \
     template void launch_convert_rhs<T>(const double*, double, int, T*, const LevelView&, cudaStream_t);              \

@@ -14,7 +14,9 @@
 // stays allocated on every device that loaded it until the process exits.
 // Only the device-side address is usable by kernels: in host code the array's
 // name is a host stand-in, so the first call on each device looks the address
-// up with cudaGetSymbolAddress (with that device current) and caches it.  All
+// up with cudaGetSymbolAddress (with that device current) and caches it; a
+// device reset (cudaDeviceReset) in the same process is not supported, since
+// the cached address would then be stale.  All
 // calls on a device share the array and it keeps the previous call's
 // contents, so every call clears it first; two calls whose work overlaps on
 // the GPU (different streams, or different host threads) race on it.
@@ -53,7 +55,11 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_dev[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device (looked up once per device).
+// Set-up of the current device, once per device: the device address of
+// g_scratch, and the kernel attributes the solve needs (the coarse-grid
+// kernel takes more than the default 48 KB of dynamic shared memory for
+// n >= 16).  Neither step allocates.  qumond_create sets the same attributes,
+// but a caller of this entry point may never create a context.
 cudaError_t scratch_address(void** out)
 {
     int dev = 0;
@@ -64,6 +70,8 @@ cudaError_t scratch_address(void** out)
     if (!g_scratch_dev[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess) return e;
+        e = prepare_kernels();
         if (e != cudaSuccess) return e;
         g_scratch_dev[dev] = p;
     }

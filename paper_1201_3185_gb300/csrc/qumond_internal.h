@@ -61,8 +61,8 @@ template <typename T> void launch_set_boundary(T* e, const LevelView& v, const d
                                                cudaStream_t s);
 // the V-cycle on levels 0 .. nlev-1 (level 0 = the coarse-grid level) as one cooperative kernel
 template <typename T> cudaError_t launch_vsub(T* const* e, T* const* f, const LevelView* v, const double* h, int nlev,
-                                              int zero_top, int npre, int npost, unsigned* bar, int* fault, int grid,
-                                              cudaStream_t s);
+                                              int zero_top, int npre, int npost, unsigned* bar, int* fault,
+                                              long long polls, int grid, cudaStream_t s);
 int vsub_grid(int sms);
 template <typename T> cudaError_t launch_coarse(int fmg, T* e, const T* f, const LevelView& v, double h,
                                                 const double* u64, int nfine, int ncycle, int npre, int npost,
@@ -92,7 +92,8 @@ struct SolveState {
     int converged; // 1: rel <= tol (or no tolerance) and finite
     int scale_exp; // fixed-point outer loop: U = u * 2^scale_exp
     int fault;     // 1: a kernel gave up waiting (bounded spin) since the last check
-    int pad;
+    int nonfinite; // fixed-point mode: the start (FMG result, boundary or warm-start values, right-hand
+                   // side) holds a NaN or an infinity, so no integer iterate represents it
 };
 // Reduces the partial norms and decides whether to continue; with a
 // non-null handle it also sets the graph's WHILE condition.
@@ -116,7 +117,7 @@ cudaError_t prepare_kernels();
 void launch_fixed_scale(const float* e, const LevelView& v, const double* u64, int n, bool from_u64, unsigned* maxbits,
                         SolveState* st, cudaStream_t s);
 void launch_fixed_init(const float* e, const LevelView& v, const double* u64, const double* rhs, double coef, double h,
-                       int n, bool from_u64, const SolveState* st, int64_t* U, int64_t* U2, int64_t* F, cudaStream_t s);
+                       int n, bool from_u64, SolveState* st, int64_t* U, int64_t* U2, int64_t* F, cudaStream_t s);
 int fixed_residual_blocks(int n);
 int launch_fixed_residual(const int64_t* U, const int64_t* F, int n, double h, const SolveState* st, bool want_f,
                           float* r, const LevelView& v, double* partials, cudaStream_t s);

@@ -20,7 +20,8 @@
 // 16 bytes; entries before row start (m0 = 0) are filled with zeros by the
 // TMA unit and are never used by an interior node.  Waits are bounded: after
 // kSpinLimit failed polls a CTA records a fault (reported by the solve as a
-// timeout) and carries on instead of hanging.
+// timeout), issues no further copies, waits (bounded) for the copies already
+// in flight, and finishes instead of hanging.
 #include "qumond_internal.h"
 
 namespace qumond {
@@ -78,6 +79,23 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// After a wait gave up, copies the leader issued may still be landing in this
+// CTA's shared memory: before the CTA exits, the leader waits for every plane
+// in [landed, issued) (bounded again; the fault is already recorded).  Only
+// the leader issues, so its own progress bounds what is in flight.
+__device__ __forceinline__ void drain_after_abort(bool leader, int* abort_flag, unsigned long long* bar, int first,
+                                                  int landed, int issued)
+{
+    __syncthreads();
+    if (!leader || !*(volatile int*)abort_flag) return;
+    for (int q = landed; q < issued; ++q) {
+        const int u = q - first;
+        long long spins = 0;
+        while (!mbar_try_wait(&bar[u % kSlots], (unsigned)((u / kSlots) & 1)) && ++spins <= kSpinLimit) {
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreadsX * kTJ)
 rb_tma_kernel(const __grid_constant__ CUtensorMap other_map, const __grid_constant__ CUtensorMap f_map,
               float* __restrict__ own, LevelView v, int colour, float h2, float sixth, int* __restrict__ fault)
@@ -96,7 +114,11 @@ rb_tma_kernel(const __grid_constant__ CUtensorMap other_map, const __grid_consta
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    auto issue = [&](int q) {  // plane q into its slot (leader only)
+    // leader: planes kb-1 .. issued-1 have been issued; lane 0 of a warp: planes
+    // before `landed` have been seen complete
+    int issued = kb - 1, landed = kb - 1;
+    auto issue = [&](int q) {  // plane q into its slot (leader only); nothing more once a wait gave up
+        if (*(volatile int*)&abort_flag) return;
         const int u = q - (kb - 1);
         float* dst = &plane[u % kSlots][0];
         float* fdst = dst + kPlaneFloats;
@@ -108,6 +130,7 @@ rb_tma_kernel(const __grid_constant__ CUtensorMap other_map, const __grid_consta
         mbar_expect_tx(&bar[u % kSlots], kPlaneBytes + kFBytes);
         tma_load_3d(dst, &other_map, m0 - 4, j0 - 1, q, &bar[u % kSlots]);
         tma_load_3d(fdst, &f_map, m0, j0, q, &bar[u % kSlots]);
+        issued = q + 1;
     };
     if (leader)
         for (int q = kb - 1; q < kb + kSlots - 1 && q <= ke; ++q) issue(q);
@@ -122,8 +145,10 @@ rb_tma_kernel(const __grid_constant__ CUtensorMap other_map, const __grid_consta
                 if (++spins > kSpinLimit || *(volatile int*)&abort_flag) {
                     ok = false;
                     atomicExch(fault, 1);
+                    *(volatile int*)&abort_flag = 1;  // the leader stops issuing copies
                 }
             }
+            if (ok) landed = q + 1;
         }
         __syncwarp();
     };
@@ -190,6 +215,7 @@ rb_tma_kernel(const __grid_constant__ CUtensorMap other_map, const __grid_consta
         s0 = sp;
         sp = t + 3 < kSlots ? t + 3 : t + 3 - kSlots;  // slot of plane k+2 = (slot of k-1) + 3
     }
+    drain_after_abort(leader, &abort_flag, bar, kb - 1, landed, issued);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,

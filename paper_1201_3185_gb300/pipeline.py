@@ -20,6 +20,10 @@ bits as the sequential order.
 Learned initial guess: with `guess` (a Guess for S = n) and `ctx_warm` (a
 context with warm_start = 1), the QUMOND solve of each box starts from
 Phi_N + the network's output instead of FMG (sequential order only).
+
+Solve timing (measurement only): when `solve_events` is a list, the
+sequential order appends one pair of CUDA timing events per solve, recorded
+on the solve's stream right before and right after the call.
 """
 from __future__ import annotations
 
@@ -56,6 +60,7 @@ class Pipeline:
                 raise ValueError("the network must match n and ctx_warm must have warm_start = 1")
         self.guess = guess
         self.ctx_warm = ctx_warm
+        self.solve_events = None
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         nodes = ctx.nodes
         nb = ctx.params.nboxes
@@ -83,19 +88,32 @@ class Pipeline:
             return self._potentials_concurrent(x, y, z, m, stats, stream)
         c = self.ctx
         ns, ms = [], []
+
+        def timed(call):
+            if self.solve_events is None:
+                return call()
+            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            ev[0].record(stream)
+            out = call()
+            ev[1].record(stream)
+            self.solve_events.append(ev)
+            return out
+
         for b in range(c.params.nboxes):
             c.qumond_deposit(b, x, y, z, m, self.rho_fixed, self.rho, stream=stream)
             par_n = self.phiN[b - 1] if b > 0 else None
             par_m = self.phi[b - 1] if b > 0 else None
-            ns.append(c.qumond_solve_newton(b, self.rho, par_n, self.phiN[b], stats=stats, stream=stream))
+            ns.append(timed(lambda: c.qumond_solve_newton(b, self.rho, par_n, self.phiN[b], stats=stats,
+                                                          stream=stream)))
             c.qumond_source(b, self.phiN[b], self.src, stream=stream)
             if self.guess is not None:
                 self.guess.qumond_guess_apply(self.rho_scale(b), float(b > 0), self.rho, self.phiN[b], self.phi[b],
                                               stream=stream)
-                ms.append(self.ctx_warm.qumond_solve_mond(b, self.src, par_m, self.phi[b], stats=stats,
-                                                          stream=stream))
+                ms.append(timed(lambda: self.ctx_warm.qumond_solve_mond(b, self.src, par_m, self.phi[b], stats=stats,
+                                                                        stream=stream)))
             else:
-                ms.append(c.qumond_solve_mond(b, self.src, par_m, self.phi[b], stats=stats, stream=stream))
+                ms.append(timed(lambda: c.qumond_solve_mond(b, self.src, par_m, self.phi[b], stats=stats,
+                                                            stream=stream)))
         return ns, ms
 
     def rho_scale(self, b):

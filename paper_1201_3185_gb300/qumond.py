@@ -38,6 +38,7 @@ EXPORTED = (
     "qumond_default_params", "qumond_create", "qumond_destroy", "qumond_last_error", "qumond_deposit",
     "qumond_solve_newton", "qumond_source", "qumond_solve_mond", "qumond_forces", "qumond_rotation_curve",
     "qumond_chi2", "qumond_rotation_curve_algebraic", "qumond_sigma_z", "qumond_trace_classes", "qumond_trace_timing", "qumond_trace_read", "qumond_solve_mond_noalloc",
+    "qumond_set_barrier_poll_limit",
     "qumond_guess_num_params", "qumond_guess_create", "qumond_guess_destroy", "qumond_guess_last_error",
     "qumond_guess_set_params", "qumond_guess_get_params", "qumond_guess_make_sample", "qumond_guess_forward",
     "qumond_guess_gradients", "qumond_guess_train_step", "qumond_guess_apply", "qumond_guess_tensor_path",
@@ -118,6 +119,7 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
         "qumond_chi2": (_I, [_P, _P, _P, _P, _I, _I, _P, _P]),
         "qumond_rotation_curve_algebraic": (_I, [_P, _P, _I, _D, _I, _P, _P, _P]),
         "qumond_sigma_z": (_I, [_P, _P, _I, _D, _I, _D, _D, _P, _P, _P]),
+        "qumond_set_barrier_poll_limit": (_I, [_P, _L]),
         "qumond_trace_classes": (_I, []),
         "qumond_trace_timing": (_I, [_P, _I, _I]),
         "qumond_trace_read": (_I, [_P, ctypes.POINTER(qumond_kernel_stat), _I, ctypes.POINTER(qumond_counters), _I]),
@@ -352,6 +354,11 @@ class Context:
         c = _dev(sigma, torch.float64, nbins, "sigma")
         d = _dev(chi2_out, torch.float64, nsets, "chi2")
         self._check(_lib.qumond_chi2(self._ptr, a, b, c, nbins, nsets, d, _stream(stream)))
+
+    def qumond_set_barrier_poll_limit(self, polls: int):
+        """Polls before a grid barrier of the cooperative small-level V-cycle
+        gives up (the solve then fails with QUMOND_ERR_TIMEOUT)."""
+        self._check(_lib.qumond_set_barrier_poll_limit(self._ptr, int(polls)))
 
     # -- tracing ------------------------------------------------------------------
     def qumond_trace_timing(self, on: bool, only: str | None = None):

@@ -102,3 +102,38 @@ def test_gradient_finite_differences():
         lm, _ = U.loss_and_gradients(pm, smp, flags, round_weights=False)
         fd = (lp - lm) / (2 * eps)
         assert fd == pytest.approx(g[i], rel=1e-5, abs=1e-9), (i, fd, g[i])
+
+
+def test_bf16_activation_storage_closed_form():
+    # all weights zero: every convolution outputs relu(bias), so the output is
+    # sum_c w_c relu(b13_c) + b_head with the last layer's activations stored
+    # in BF16 (1 + 2^-10 and 3 + 2^-7 are not BF16 values; 1 and 3 are)
+    p = np.zeros(U.num_params(), dtype=np.float32)
+    sl = dict(U.layer_slices())
+    b13 = np.zeros(16, dtype=np.float32)
+    b13[0], b13[1], b13[2] = 1.0 + 2.0 ** -10, 3.0 + 2.0 ** -7, -5.0
+    p[sl["b13"]] = b13
+    hw = np.zeros(16, dtype=np.float32)
+    hw[0], hw[1], hw[2] = 2.0, -0.5, 7.0
+    p[sl["head"]] = np.concatenate([hw, [0.25]])
+    smp = np.random.default_rng(5).standard_normal(3 * 8 ** 3)
+    y64, t64 = U.predict(p, smp, 1.0, terms=True)
+    yb, tb = U.predict(p, smp, 1.0, store=U.bf16_acts, terms=True)
+    exact = 2.0 * (1.0 + 2.0 ** -10) - 0.5 * (3.0 + 2.0 ** -7) + 0.25
+    assert np.allclose(y64, exact, rtol=0, atol=1e-12)
+    assert np.all(yb == 2.0 * 1.0 - 0.5 * 3.0 + 0.25)
+    assert np.all(tb == 2.0 * 1.0 + 0.5 * 3.0)
+    assert np.allclose(t64, 2.0 * (1.0 + 2.0 ** -10) + 0.5 * (3.0 + 2.0 ** -7), rtol=0, atol=1e-12)
+
+
+def test_bf16_activation_storage_stays_within_the_rounding_model():
+    # storing activations in BF16 (relative rounding <= 2^-8 per value) moves a
+    # random network's output by about a percent, never by more than a few
+    rng = np.random.default_rng(6)
+    p = he_params(6)
+    S = 16
+    smp = np.concatenate([rng.random(S ** 3), rng.standard_normal(S ** 3), rng.standard_normal(S ** 3)])
+    y64 = U.predict(p, smp, 0.0)
+    yb = U.predict(p, smp, 0.0, store=U.bf16_acts)
+    rel = np.linalg.norm(yb - y64) / np.linalg.norm(y64)
+    assert 1e-4 < rel < 3e-2
