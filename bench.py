@@ -88,7 +88,7 @@ def workload_config(precision="FP32 smoothing + FP64 defect correction"):
     }
 
 
-def sweep_config(precision, workers):
+def sweep_config(precision, choice):
     w = WORKLOAD
     return {
         "workload": "fit sweep: %d parameter sets (distance scale 0.8-1.2, stellar M/L 0.3-1.2, stellar h 0.2-1.0 kpc, "
@@ -104,7 +104,7 @@ def sweep_config(precision, workers):
         "rel_tol": w["rel_tol"],
         "fmg_vcycles_per_level": w["ncycle"],
         "npre_npost": [w["npre"], w["npost"]],
-        "workers": workers,
+        "batched_form": choice,
         "rotation_curve": "%d bins to %g kpc x distance factor, %d azimuths" % (w["nbins"], w["rmax"] / 1000.0,
                                                                                 w["nphi"]),
         "l2": "inputs larger than L2: 64 sets x 5e5 particles x 32 B = 1 GB of particles, ~10 GB of grids per step",
@@ -205,7 +205,8 @@ def ncu_traffic(kernel: str):
 
 
 # kernel classes that belong to the solves (everything but the deposit, the source and the post-processing)
-NOT_SOLVE = {"cic_deposit", "fixed_to_rho", "qumond_source", "forces", "rotation_curve", "chi2", "profile"}
+NOT_SOLVE = {"cic_deposit", "fixed_to_rho", "qumond_source", "forces", "rotation_curve", "chi2", "profile",
+             "far_field"}
 
 
 def solve_roofline(pipe1, ctx1, step, steps, peak, barrier, max_over_ranks):
@@ -526,24 +527,25 @@ def run_sweep(args):
     w = WORKLOAD
     prec = {"fp64": q.QUMOND_PREC_FP64, "mixed": q.QUMOND_PREC_MIXED, "fixed": q.QUMOND_PREC_MIXED_FIXED}[args.precision]
 
-    def params(precision):
+    def params(precision, tile=0):
         return q.default_params(n=w["n"], nboxes=w["nboxes"], L0=w["L0"], rel_tol=w["rel_tol"],
                                 max_vcycles=w["max_vcycles"], ncycle=w["ncycle"], npre=w["npre"], npost=w["npost"],
-                                precision=precision, use_graphs=0 if args.no_graphs else 1)
+                                precision=precision, use_graphs=0 if args.no_graphs else 1, tile_small=tile)
 
     gal, prm, v_obs_h, sigma_h = sweep_inputs()
     host_sets = [gal.particles(r) for r in prm]
-    sets = [tuple(torch.from_numpy(a).to(dev) for a in (p.x, p.y, p.z, p.m)) for p in host_sets]
+    # every set's particles, set after set, resident in HBM (a chunk of sets is then a view)
+    sets = tuple(torch.from_numpy(np.concatenate([getattr(p, a) for p in host_sets])).to(dev) for a in "xyzm")
     dist = [float(r[0]) for r in prm]
     v_obs = torch.from_numpy(v_obs_h).to(dev)
     sigma = torch.from_numpy(sigma_h).to(dev)
     kw = dict(nbins=w["nbins"], rmax=w["rmax"], nphi=w["nphi"], device=dev)
 
     if args.workers:
-        workers, tune = args.workers, None
+        choice, tune = {"batch": w["sets"], "lanes": args.workers, "tile_small": 0}, None
     else:
-        workers, tune = q.tune_workers(params(prec), sets, dist, v_obs, sigma, **kw)
-    sw = q.FitSweep(params(prec), workers=workers, **kw)
+        choice, tune = q.autotune(params(prec), sets, dist, v_obs, sigma, **kw)
+    sw = q.FitSweep(params(prec, choice["tile_small"]), batch=choice["batch"], lanes=choice["lanes"], **kw)
     ctx = Contexts(sw.ctxs)
     for _ in range(args.warmup):
         sw.run(sets, dist, v_obs, sigma)
@@ -571,22 +573,25 @@ def run_sweep(args):
     ms_step = ms_total / args.steps
     value = ws * w["sets"] * args.steps / (ms_total / 1000.0)
 
-    # dominant kernel: classes timed live inside one worker's graphs (one set at a time)
-    one = q.FitSweep(params(prec), workers=1, **kw)
+    # kernel classes timed live inside the batched graphs (the tuned batch, one lane): event-record nodes
+    # around each run of consecutive launches of the class in the FMG part of every solve
+    one = q.FitSweep(params(prec, choice["tile_small"]), batch=choice["batch"], lanes=1, **kw)
     c1 = Contexts(one.ctxs)
-    sub = sets[:8]
+    nsub = choice["batch"]
+    sub = tuple(a[:nsub * (a.numel() // w["sets"])] for a in sets)
     live = {}
-    for name in ("rb_half_finest", "rb_half_coarser", "restrict_resid_red", "residual_outer"):
+    for name in ("rb_half_finest", "rb_half_coarser", "restrict_resid_red", "prolong_black", "residual_outer",
+                 "coarse_solver"):
         c1.qumond_trace_timing(True, only=name)
-        one.run(sub, dist[:8], v_obs, sigma)
+        one.run(sub, dist[:nsub], v_obs, sigma)
         c1.qumond_trace_read(reset=True)
-        one.run(sub, dist[:8], v_obs, sigma)
+        one.run(sub, dist[:nsub], v_obs, sigma)
         torch.cuda.synchronize()
         st1, _, _ = c1.qumond_trace_read(reset=True)
         c1.qumond_trace_timing(False)
         k = st1[name]
         if k.timed:
-            live[name] = (k, k.ms / k.timed * k.launches / len(sub))
+            live[name] = (k, k.ms / k.timed * k.launches / nsub)
     one.close()
     dom_name = max(live, key=lambda nm: live[nm][1])
     dom = live[dom_name][0]
@@ -599,22 +604,22 @@ def run_sweep(args):
                 "timed_launches": dom.timed,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s",
                 "timing": "CUDA event-record nodes around runs of this class's launches in the FMG part of each "
-                          "solve's graph, one worker, 8 sets; the 129^3 grids (8.6 MB per FP32 field) are largely "
-                          "L2-resident, so achieved can exceed what HBM alone would give",
-                "live_ms_per_set": {nm: v[1] for nm, v in live.items()}}
+                          "solve's graph; one context holding %d sets (every launch covers all of them)" % nsub,
+                "live_ms_per_set": {nm: v[1] for nm, v in live.items()},
+                "live_GBps": {nm: v[0].timed_bytes / v[0].ms / 1e6 for nm, v in live.items() if v[0].ms}}
 
     # end to end: every set's particles copied from pinned host memory, chi^2 and curves read back
-    host = [[torch.from_numpy(a).pin_memory() for a in (p.x, p.y, p.z, p.m)] for p in host_sets]
+    host = [torch.from_numpy(np.concatenate([getattr(p, a) for p in host_sets])).pin_memory() for a in "xyzm"]
     out_vc = torch.empty(w["sets"], w["nbins"], dtype=torch.float64).pin_memory()
     out_chi2 = torch.empty(w["sets"], dtype=torch.float64).pin_memory()
-    h2d = sum(t.numel() * t.element_size() for hs in host for t in hs)
+    h2d = sum(t.numel() * t.element_size() for t in host)
     d2h = out_vc.numel() * 8 + out_chi2.numel() * 8
     rep.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        dsets = [tuple(t.to(dev, non_blocking=True) for t in hs) for hs in host]
+        dsets = tuple(t.to(dev, non_blocking=True) for t in host)
         res = sw.run(dsets, dist, v_obs, sigma)
         out_vc.copy_(res.vc, non_blocking=True)
         out_chi2.copy_(res.chi2, non_blocking=True)
@@ -624,27 +629,35 @@ def run_sweep(args):
     e2e_value = ws * w["sets"] * args.steps / (e2e_ms / 1000.0)
     sw.close()
 
-    # the same sweep, one set after another (one worker), same precision and in plain FP64
-    def sequential(precision):
-        one = q.FitSweep(params(precision), workers=1, **kw)
-        one.run(sets[:1], dist[:1], v_obs, sigma)
+    def timed_sweep(precision, nsteps, **form):
+        one = q.FitSweep(params(precision, form.pop("tile", 0)), **form, **kw)
+        one.run(sets, dist, v_obs, sigma)
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record()
-        one.run(sets, dist, v_obs, sigma)
+        for _ in range(nsteps):
+            one.run(sets, dist, v_obs, sigma)
         f1.record()
         rep.barrier()
-        t = rep.max(f0.elapsed_time(f1))
+        t = rep.max(f0.elapsed_time(f1)) / nsteps
         one.close()
-        return {"value": ws * w["sets"] / (t / 1000.0), "unit": "sets/s", "ms_per_step": t, "steps": 1}
+        torch.cuda.empty_cache()
+        return {"value": ws * w["sets"] / (t / 1000.0), "unit": "sets/s", "ms_per_step": t, "steps": nsteps}
 
-    seq_same = plain = None
+    seq_same = plain = unbatched = None
     if not args.no_plain:
-        seq_same = sequential(prec)
-        plain = sequential(q.QUMOND_PREC_FP64)
-        plain["precision"] = PRECISION_NAMES["fp64"] + " (same kernels, same tolerance), one set at a time"
+        nrep = max(1, min(args.steps, 3))
+        # plain FP64 FMG: the same batched kernels and form, FP64 throughout, to the same tolerance
+        plain = timed_sweep(q.QUMOND_PREC_FP64, nrep, batch=choice["batch"], lanes=choice["lanes"],
+                            tile=choice["tile_small"])
+        plain["precision"] = PRECISION_NAMES["fp64"] + " (same batched kernels, same tolerance)"
         plain["speedup_of_value"] = value / plain["value"]
+        # one set per context, 8 contexts side by side (the sweep without batching)
+        unbatched = timed_sweep(prec, nrep, workers=8)
+        unbatched["form"] = "one set per context, 8 contexts on 8 streams"
+        seq_same = timed_sweep(prec, 1, workers=1)
+        seq_same["form"] = "one set after another"
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -660,7 +673,7 @@ def run_sweep(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {q.QUMOND_PREC_MIXED: "f32+f64", q.QUMOND_PREC_MIXED_FIXED: "f32+int64",
                                             q.QUMOND_PREC_FP64: "f64"}[prec],
-            "data": "synthetic", "config": sweep_config(PRECISION_NAMES[args.precision], workers),
+            "data": "synthetic", "config": sweep_config(PRECISION_NAMES[args.precision], choice),
             "solves_per_s": 2 * w["nboxes"] * value,
             "cell_updates_per_s": ws * cells / (ms_total / 1000.0),
             "algorithmic_bytes_per_step": step_bytes,
@@ -669,9 +682,10 @@ def run_sweep(args):
             "e2e": {"value": e2e_value, "unit": "sets/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "gpu_launches_per_step": launches / args.steps,
-            "workers_tuning_ms_per_sweep": tune,
+            "autotune_ms_per_sweep": {"batch %d, lanes %d, tile %d" % k: v for k, v in tune.items()} if tune else None,
             "vcycles_after_fmg_per_set_max": max(max(v) for v in vcyc),
             "best_set": {"index": best, "chi2": float(chi2[best]), "params": [float(v) for v in prm[best]]},
+            "unbatched": unbatched,
             "sequential_same_precision": seq_same,
             "plain_fmg": plain,
             "clocks": clk,
@@ -901,7 +915,7 @@ def run_reference_sweep(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "sets/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": w["sets"] * 1000.0 / value, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": sweep_config("FP64 CPU oracle", 1),
+        "config": sweep_config("FP64 CPU oracle", None),
         "cpu_baseline": {"kind": "oracle", "cores": cpu_cores(), "sample": sample, "value": value, "unit": "sets/s"},
         "e2e": {"value": value, "unit": "sets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -1026,7 +1040,8 @@ def main():
                          "sweep: the 64-set rotation-curve fit sweep at 128^3 x 2 boxes; "
                          "learned: the whole path with the QUMOND solves started from the U-Net guess")
     ap.add_argument("--workers", type=int, default=0,
-                    help="sweep: concurrent workers (0: pick by timing)")
+                    help="sweep: lanes of one 64-set chunk each (0: batch size, lanes and block shape by the "
+                         "autotuner)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one profiled V-cycle on one box instead of the benchmark (for ncu)")
     args = ap.parse_args()

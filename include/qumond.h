@@ -35,6 +35,18 @@
  *   not itself be capturing.
  * - On error the status is returned and qumond_last_error(ctx) describes it.
  *   QUMOND_ERR_NOT_CONVERGED still leaves the best iterate in the output.
+ * - Sets: a context created with params.nsets = S > 1 holds S independent
+ *   problems of the same shape (same n, boxes and parameters; different
+ *   particles, densities, potentials), e.g. the parameter sets of a fit
+ *   sweep.  Every grid argument is then S consecutive grids of (n+1)^3
+ *   elements (set s at s*(n+1)^3), per-particle or per-point arrays hold S
+ *   consecutive runs of np (or nq) entries, rotation-curve outputs S runs of
+ *   nbins, and `stats` points to S structs.  Each step is one launch per
+ *   kernel for all sets.  With a tolerance, V-cycles go on until every set
+ *   has converged; a set that has converged is skipped by the later V-cycles,
+ *   so each set's result is the same as a solve of that set alone.
+ *   NOT_CONVERGED and TIMEOUT are returned when any set fails (the message
+ *   names the set).
  */
 #ifndef QUMOND_H
 #define QUMOND_H
@@ -82,8 +94,11 @@ enum {
 /* Boundary values of box 0 (boxes b >= 1 always interpolate theirs from box
    b-1, Section 2). */
 enum {
-    QUMOND_BC_ZERO = 0,  /* Phi = 0 on the outermost box, as in the paper */
-    QUMOND_BC_GIVEN = 1  /* the caller stores them in the boundary nodes of phi */
+    QUMOND_BC_ZERO = 0,     /* Phi = 0 on the outermost box, as in the paper */
+    QUMOND_BC_GIVEN = 1,    /* the caller stores them in the boundary nodes of phi */
+    QUMOND_BC_MULTIPOLE = 2 /* from the mass inside box 0: qumond_far_field writes them into
+                               the boundary nodes of phiN and phi, and the solves of box 0
+                               keep them (as with QUMOND_BC_GIVEN) */
 };
 
 typedef struct {
@@ -119,6 +134,17 @@ typedef struct {
                            cooperative form is not faster (a grid barrier costs
                            about what a graph launch does) and it serialises
                            concurrent solves, so it is off by default. */
+    int nsets;          /* independent problems of this shape held by the
+                           context (the parameter sets of a rotation-curve fit,
+                           Section 3.5), 1 <= nsets <= 1024 with
+                           nsets * (n + 1) <= 65535; default 1.  See "Sets"
+                           above.  nsets > 1 requires persistent_vcycle = 0. */
+    int tile_small;     /* block shape of the FP32 half-sweeps and prolongations
+                           on the levels with n <= 64: 0 (default) = 8 x 16
+                           threads (32 row entries x 16 rows per block),
+                           1 = 4 x 32, 2 = 2 x 64.  The same bits for every
+                           shape; only the speed differs (picked by timing,
+                           e.g. by the fit sweep's autotuner). */
 } qumond_params;
 
 /* Per-solve report (host struct). */
@@ -134,11 +160,13 @@ typedef struct qumond_ctx qumond_ctx;
 /* Paper defaults: n = 256, one box of 120 kpc, G = 4.30e-3, a0 = 3.6,
    npre = npost = 2, ncycle = 6, rel_tol = 0 (paper mode), max_vcycles = 50,
    QUMOND_PREC_MIXED, QUMOND_BC_ZERO, warm_start = 0, deposit_shift = 24,
-   rc_box_frac = 0.2, box_ratio = 2, use_graphs = 1, persistent_vcycle = 0. */
+   rc_box_frac = 0.2, box_ratio = 2, use_graphs = 1, persistent_vcycle = 0,
+   nsets = 1, tile_small = 0. */
 QUMOND_API void qumond_default_params(qumond_params* p);
 
 /* Validates p and allocates the context's device scratch on the current
-   device (about 10 (n+1)^3 bytes in QUMOND_PREC_MIXED, 20 in FP64).
+   device (about 10 (n+1)^3 bytes per set in QUMOND_PREC_MIXED, 20 in FP64,
+   34 in QUMOND_PREC_MIXED_FIXED).
    Returns INVALID_ARG, OUT_OF_MEMORY or CUDA_ERROR on failure (*out = NULL). */
 QUMOND_API qumond_status qumond_create(const qumond_params* p, qumond_ctx** out);
 
@@ -156,7 +184,10 @@ QUMOND_API const char* qumond_last_error(const qumond_ctx* ctx);
    w = 1-d or d, d the offset inside the cell: exact FP64 products, round half
    to even, so the int64 grid does not depend on order.
    rho_fixed: (n+1)^3 int64, overwritten (required).
-   rho: (n+1)^3 doubles = rho_fixed * 2^-shift / h^3 in Msun/pc^3, or NULL. */
+   rho: (n+1)^3 doubles = rho_fixed * 2^-shift / h^3 in Msun/pc^3, or NULL.
+   With several sets, np is the count per set: set s's particles are
+   entries s*np .. s*np+np-1 (a set with fewer particles pads with
+   particles outside the box, which are skipped). */
 QUMOND_API qumond_status qumond_deposit(qumond_ctx* ctx, int box, const double* x, const double* y, const double* z,
                              const double* mass, int64_t np, int64_t* rho_fixed, double* rho, void* stream);
 
@@ -166,7 +197,7 @@ QUMOND_API qumond_status qumond_deposit(qumond_ctx* ctx, int box, const double* 
    phiN_parent: Phi_N of box-1 (required when box >= 1, ignored for box 0).
    phiN: (n+1)^3 doubles, overwritten: its boundary nodes are set from the
    parent (or by bc_mode for box 0), its interior by the solve.
-   stats: host struct or NULL. */
+   stats: host struct (nsets structs with several sets) or NULL. */
 QUMOND_API qumond_status qumond_solve_newton(qumond_ctx* ctx, int box, const double* rho, const double* phiN_parent,
                                   double* phiN, qumond_stats* stats, void* stream);
 
@@ -203,6 +234,15 @@ QUMOND_API qumond_status qumond_forces(qumond_ctx* ctx, const double* const* phi
 QUMOND_API qumond_status qumond_rotation_curve(qumond_ctx* ctx, const double* const* phi_boxes, int nbins, double rmax,
                                     int nphi, double* r_out, double* vc_out, void* stream);
 
+/* The rotation curve of every set of a context with several sets, each with
+   its own outermost radius: set s uses rmax[s] (a fit sweep scales the radii
+   of its observed points with the set's distance, Section 3.5) and writes
+   its nbins radii and speeds at s * nbins of r_out and vc_out.  rmax: nsets
+   doubles (device, > 0).  Otherwise as qumond_rotation_curve. */
+QUMOND_API qumond_status qumond_rotation_curve_sets(qumond_ctx* ctx, const double* const* phi_boxes, int nbins,
+                                                    const double* rmax, int nphi, double* r_out, double* vc_out,
+                                                    void* stream);
+
 /* Algebraic MOND rotation curve (Eq. 3, compared with the QUMOND curve in
    Section 3.3): the tracers and box rule of qumond_rotation_curve, applied
    to the NEWTONIAN potentials, with the field at each tracer taken as
@@ -234,6 +274,27 @@ QUMOND_API qumond_status qumond_sigma_z(qumond_ctx* ctx, const double* const* ph
    Errors: QUMOND_ERR_INVALID_ARG for nbins < 1, nsets < 0 or a host pointer. */
 QUMOND_API qumond_status qumond_chi2(qumond_ctx* ctx, const double* vc, const double* v_obs, const double* sigma,
                                      int nbins, int nsets, double* chi2, void* stream);
+
+/* Boundary values of box 0 from the mass inside it (QUMOND_BC_MULTIPOLE).
+   Section 2 sets Phi = 0 on a box 2^10 times the galaxy and refines inwards;
+   with fewer boxes the outer boundary lies near the mass, and this computes
+   the values the far field of that mass takes there:
+   - phiN: the exterior multipole expansion, to degree 8, of the node masses
+     m_k = rho_k h_0^3 (every node of box 0) about their centre of mass c,
+       Phi_N(x) = -G sum_k m_k sum_{l<=8} |x_k - c|^l / |x - c|^(l+1) P_l(cos g_k),
+     g_k the angle between x_k - c and x - c (evaluated through the moments
+     of the solid harmonics, FP64, fixed-order sums);
+   - phi: the QUMOND potential of the total mass M as a point at c,
+       F(r) = -A/(2r) + 1/2 [-sqrt(A^2 + C r^2)/r + sqrt(C) asinh(sqrt(C) r/A)],
+     A = G M, C = 4 a0 A, r = |x - c|: F'(r) = nu(G M/(a0 r^2)) G M/r^2, the
+     field of a point mass under Eq. 2.
+   rho: box 0's density ((n+1)^3 doubles, device, e.g. from qumond_deposit);
+   phiN, phi: (n+1)^3 doubles (device): only their boundary nodes are
+   written.  With M = 0 both are set to 0.  Requires bc_mode =
+   QUMOND_BC_MULTIPOLE (else QUMOND_ERR_INVALID_ARG); enqueue it before the
+   solves of box 0.  With several sets, each set's own mass. */
+QUMOND_API qumond_status qumond_far_field(qumond_ctx* ctx, const double* rho, double* phiN, double* phi,
+                                          void* stream);
 
 /* Bound on the polls of one grid barrier of the cooperative small-level
    V-cycle kernel (persistent_vcycle = 1) before the barrier gives up; the

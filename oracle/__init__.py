@@ -28,6 +28,7 @@ from .core import (  # noqa: F401
     chi2,
     rotation_curve_algebraic,
     sigma_z,
+    far_field,
     Box,
     pipeline,
     grid_index,

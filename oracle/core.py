@@ -62,6 +62,7 @@ def _load():
         "ora_chi2": (None, [_P, _P, _P, _I, _I, _P]),
         "ora_rotation_curve_algebraic": (None, [_I, _I, _D, _I, _D, _D, _D, _P, _I, _D, _I, _D, _D, _P, _P]),
         "ora_sigma_z": (None, [_I, _I, _D, _I, _D, _D, _D, _P, _I, _D, _I, _D, _D, _D, _P, _P]),
+        "ora_far_field": (_D, [_I, _D, _D, _D, _D, _P, _D, _D, _I, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -170,6 +171,22 @@ def boundary_fill(n, Lp, cp, up, L, c, u):
     _load().ora_boundary_fill(n, Lp, cp[0], cp[1], cp[2], _ptr(_f64(up)), L, c[0], c[1], c[2], _ptr(u))
 
 
+def far_field(n, L, center, rho, G=4.30e-3, a0=3.6, lmax=8, phiN=None, phi=None):
+    """Boundary values of the outermost box from the mass inside it: the
+    multipole expansion (degree <= lmax) of the node masses for Phi_N and the
+    point-mass QUMOND potential of the total mass for Phi.  Writes the
+    boundary nodes of phiN and phi (new zero arrays when None).
+    Returns (phiN, phi, total mass)."""
+    rho = _f64(rho)
+    _check_grid(rho, n)
+    phiN = np.zeros((n + 1) ** 3) if phiN is None else phiN
+    phi = np.zeros((n + 1) ** 3) if phi is None else phi
+    _check_grid(phiN, n)
+    _check_grid(phi, n)
+    M = _load().ora_far_field(n, L, center[0], center[1], center[2], _ptr(rho), G, a0, lmax, _ptr(phiN), _ptr(phi))
+    return phiN, phi, float(M)
+
+
 # --- forces and rotation curve -------------------------------------------------
 def _ptr_array(arrs):
     arr = (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
@@ -246,12 +263,14 @@ class Box:
 
 
 def pipeline(particles, n, L0, nboxes, *, center=(0.0, 0.0, 0.0), G=4.30e-3, a0=3.6, shift=24,
-             ncycle=6, npre=2, npost=2, tol=0.0, max_vcycles=0, bc_newton=None, bc_mond=None, ratio=2):
+             ncycle=6, npre=2, npost=2, tol=0.0, max_vcycles=0, bc_newton=None, bc_mond=None, ratio=2,
+             far_field_lmax=None):
     """Steps 1-4 of Section 2 for every nested box, outermost first.
 
     Box b has side L0/ratio^b (ratio 2 in the paper).  Box 0 takes its boundary values from bc_newton /
     bc_mond (callables (x, y, z) -> value; None means zero, as in the paper's
-    outermost box); box b >= 1 interpolates them from box b-1 (Section 2)."""
+    outermost box), or, with far_field_lmax set, from far_field() of its own
+    density; box b >= 1 interpolates them from box b-1 (Section 2)."""
     boxes = []
     N = (n + 1) ** 3
     ii = np.arange(n + 1)
@@ -263,9 +282,13 @@ def pipeline(particles, n, L0, nboxes, *, center=(0.0, 0.0, 0.0), G=4.30e-3, a0=
         bx.rho_fixed, bx.kept = cic_deposit(n, L, center, shift, particles.x, particles.y, particles.z, particles.m)
         bx.rho = rho_from_fixed(n, L, shift, bx.rho_fixed)
         f_newton = (4.0 * np.pi * G) * bx.rho
+        if b == 0 and far_field_lmax is not None:
+            ffN, ffM, _ = far_field(n, L, center, bx.rho, G=G, a0=a0, lmax=far_field_lmax)
         for kind in ("newton", "mond"):
             u = np.zeros(N)
-            if b == 0:
+            if b == 0 and far_field_lmax is not None:
+                u[on_bnd] = (ffN if kind == "newton" else ffM)[on_bnd]
+            elif b == 0:
                 bc = bc_newton if kind == "newton" else bc_mond
                 if bc is not None:
                     h = L / n

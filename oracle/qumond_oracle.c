@@ -597,3 +597,132 @@ void ora_sigma_z(int nboxes, int n, double L0, int ratio, double cx, double cy, 
         sig_out[kb] = s2 >= 0.0 ? sqrt(s2) : -sqrt(-s2);
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Far-field boundary values of the outermost box.  Section 2 puts Phi = 0 on
+ * a box 2^10 times larger than the galaxy and refines inwards; with fewer
+ * boxes the outermost boundary lies close to the mass, and the boundary values
+ * come from the mass inside the box instead:
+ *
+ *  - Phi_N: the exterior multipole expansion of the node masses m_k = rho_k h^3
+ *    (all nodes) about their centre of mass c, truncated at degree lmax:
+ *      Phi_N(x) = -G sum_k m_k sum_{l=0}^{lmax} |x_k - c|^l / |x - c|^{l+1} P_l(cos g_k),
+ *    g_k the angle between x_k - c and x - c.  Written with the addition
+ *    theorem of Legendre polynomials, P_l(cos g) = sum_{m=0}^{l} (2 - [m=0])
+ *    (l-m)!/(l+m)! P_l^m(cos t) P_l^m(cos t') cos(m (f - f')), and with the
+ *    solid harmonics T_lm(d) = |d|^l P_l^m(cos t) e^{i m f} of d = (dx, dy, dz)
+ *    (polynomials in dx, dy, dz), the expansion is
+ *      Phi_N(x) = -G sum_l sum_m w_lm [Re T_lm(d) A_lm + Im T_lm(d) B_lm] / |d|^{2l+1},
+ *    w_lm = (2 - [m=0]) (l-m)!/(l+m)!, A_lm + i B_lm = sum_k m_k T_lm(x_k - c), d = x - c.
+ *  - Phi: the QUMOND potential of the whole mass M = sum_k m_k taken as a
+ *    point at c, F(|x - c|) with F'(r) = nu(G M/(a0 r^2)) G M/r^2 and
+ *    nu(y) = 1/2 + 1/2 sqrt(1 + 4/y) (Section 2, Eq. 2 for a spherical mass):
+ *      F(r) = -A/(2r) + (1/2) [ -sqrt(A^2 + C r^2)/r + sqrt(C) asinh(sqrt(C) r / A) ],
+ *    A = G M, C = 4 a0 A.  Far from the galaxy the QUMOND field is that of
+ *    its total mass; only the monopole is kept.
+ *
+ * T_lm follows from P_l^m (taken without the (-1)^m phase, which cancels in
+ * the products): T_mm = (2m-1)!! (dx + i dy)^m, T_{m+1,m} = (2m+1) dz T_mm,
+ * (l-m) T_lm = (2l-1) dz T_{l-1,m} - (l+m-1) |d|^2 T_{l-2,m}.
+ * Writes the boundary nodes of phiN and phi (interior untouched); with M = 0
+ * both are set to 0.  lmax <= 16.  Returns M. */
+#define ORA_LMAX 16
+static void solid_harmonics(int lmax, double dx, double dy, double dz, double re[ORA_LMAX + 1][ORA_LMAX + 1],
+                            double im[ORA_LMAX + 1][ORA_LMAX + 1])
+{
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    double pr = 1.0, pi = 0.0; /* (dx + i dy)^m */
+    double dfact = 1.0;        /* (2m-1)!! */
+    for (int m = 0; m <= lmax; ++m) {
+        if (m > 0) {
+            double nr = pr * dx - pi * dy, ni = pr * dy + pi * dx;
+            pr = nr;
+            pi = ni;
+            dfact *= (double)(2 * m - 1);
+        }
+        re[m][m] = dfact * pr;
+        im[m][m] = dfact * pi;
+        if (m + 1 <= lmax) {
+            re[m + 1][m] = (double)(2 * m + 1) * dz * re[m][m];
+            im[m + 1][m] = (double)(2 * m + 1) * dz * im[m][m];
+        }
+        for (int l = m + 2; l <= lmax; ++l) {
+            re[l][m] = ((double)(2 * l - 1) * dz * re[l - 1][m] - (double)(l + m - 1) * r2 * re[l - 2][m]) / (double)(l - m);
+            im[l][m] = ((double)(2 * l - 1) * dz * im[l - 1][m] - (double)(l + m - 1) * r2 * im[l - 2][m]) / (double)(l - m);
+        }
+    }
+}
+
+double ora_far_field(int n, double L, double cx, double cy, double cz, const double* rho, double G, double a0,
+                     int lmax, double* phiN, double* phi)
+{
+    if (lmax < 0) lmax = 0;
+    if (lmax > ORA_LMAX) lmax = ORA_LMAX;
+    const double h = L / (double)n, h3 = h * h * h;
+    const double x0 = cx - 0.5 * L, y0 = cy - 0.5 * L, z0 = cz - 0.5 * L;
+    /* total mass and centre of mass */
+    double M = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
+    for (int k = 0; k <= n; ++k)
+        for (int j = 0; j <= n; ++j)
+            for (int i = 0; i <= n; ++i) {
+                double m = rho[IDX(n, i, j, k)] * h3;
+                M += m;
+                mx += m * (x0 + i * h);
+                my += m * (y0 + j * h);
+                mz += m * (z0 + k * h);
+            }
+    if (M == 0.0) {
+        for (int k = 0; k <= n; ++k)
+            for (int j = 0; j <= n; ++j)
+                for (int i = 0; i <= n; ++i)
+                    if (i == 0 || i == n || j == 0 || j == n || k == 0 || k == n)
+                        phiN[IDX(n, i, j, k)] = phi[IDX(n, i, j, k)] = 0.0;
+        return 0.0;
+    }
+    const double comx = mx / M, comy = my / M, comz = mz / M;
+    /* moments A_lm + i B_lm */
+    double A[ORA_LMAX + 1][ORA_LMAX + 1], B[ORA_LMAX + 1][ORA_LMAX + 1];
+    double re[ORA_LMAX + 1][ORA_LMAX + 1], im[ORA_LMAX + 1][ORA_LMAX + 1];
+    memset(A, 0, sizeof(A));
+    memset(B, 0, sizeof(B));
+    for (int k = 0; k <= n; ++k)
+        for (int j = 0; j <= n; ++j)
+            for (int i = 0; i <= n; ++i) {
+                double m = rho[IDX(n, i, j, k)] * h3;
+                if (m == 0.0) continue;
+                solid_harmonics(lmax, x0 + i * h - comx, y0 + j * h - comy, z0 + k * h - comz, re, im);
+                for (int l = 0; l <= lmax; ++l)
+                    for (int mm = 0; mm <= l; ++mm) {
+                        A[l][mm] += m * re[l][mm];
+                        B[l][mm] += m * im[l][mm];
+                    }
+            }
+    /* w_lm = (2 - [m=0]) (l-m)!/(l+m)! */
+    double w[ORA_LMAX + 1][ORA_LMAX + 1];
+    for (int l = 0; l <= lmax; ++l)
+        for (int mm = 0; mm <= l; ++mm) {
+            double r = 1.0;
+            for (int t = l - mm + 1; t <= l + mm; ++t) r /= (double)t;
+            w[l][mm] = (mm == 0 ? 1.0 : 2.0) * r;
+        }
+    const double Am = G * M, C = 4.0 * a0 * Am;
+    for (int k = 0; k <= n; ++k)
+        for (int j = 0; j <= n; ++j)
+            for (int i = 0; i <= n; ++i) {
+                if (i != 0 && i != n && j != 0 && j != n && k != 0 && k != n) continue;
+                double dx = x0 + i * h - comx, dy = y0 + j * h - comy, dz = z0 + k * h - comz;
+                double r2 = dx * dx + dy * dy + dz * dz, r = sqrt(r2);
+                solid_harmonics(lmax, dx, dy, dz, re, im);
+                double sum = 0.0, rpow = r; /* |d|^{2l+1} */
+                for (int l = 0; l <= lmax; ++l) {
+                    double sl = 0.0;
+                    for (int mm = 0; mm <= l; ++mm) sl += w[l][mm] * (re[l][mm] * A[l][mm] + im[l][mm] * B[l][mm]);
+                    sum += sl / rpow;
+                    rpow *= r2;
+                }
+                phiN[IDX(n, i, j, k)] = -G * sum;
+                phi[IDX(n, i, j, k)] = -Am / (2.0 * r) +
+                                       0.5 * (-sqrt(Am * Am + C * r2) / r + sqrt(C) * asinh(sqrt(C) * r / Am));
+            }
+    return M;
+}

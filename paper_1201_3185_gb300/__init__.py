@@ -15,7 +15,8 @@ from .qumond import (  # noqa: F401
     QUMOND_PREC_MIXED_FIXED,
     QUMOND_BC_ZERO,
     QUMOND_BC_GIVEN,
+    QUMOND_BC_MULTIPOLE,
     EXPORTED,
 )
 from .pipeline import Pipeline, PipelineResult  # noqa: F401
-from .sweep import FitSweep, SweepResult, tune_workers  # noqa: F401
+from .sweep import FitSweep, SweepResult, autotune, tune_workers  # noqa: F401

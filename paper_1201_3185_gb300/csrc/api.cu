@@ -26,12 +26,13 @@ struct Level {
 enum Kind {
     K_DEPOSIT, K_FIXED_TO_RHO, K_BOUNDARY, K_CONVERT_RHS, K_RESTRICT_FULL, K_COARSE, K_RB_FINEST, K_RB_COARSER,
     K_RESTRICT_RESID, K_PROLONG, K_SET_BOUNDARY, K_ASSIGN_OUTER, K_RESIDUAL_OUTER, K_REDUCE, K_SOURCE, K_FORCES,
-    K_ROTATION_CURVE, K_FIXED_SETUP, K_FIXED_OUTPUT, K_CHI2, K_PROFILE, K_VSUB, K_COUNT
+    K_ROTATION_CURVE, K_FIXED_SETUP, K_FIXED_OUTPUT, K_CHI2, K_PROFILE, K_VSUB, K_FAR_FIELD, K_COUNT
 };
 const char* const kKindNames[K_COUNT] = {
     "cic_deposit", "fixed_to_rho", "boundary_fill", "convert_rhs", "restrict_full", "coarse_solver",
     "rb_half_finest", "rb_half_coarser", "restrict_resid_red", "prolong_black", "set_boundary", "update_outer",
     "residual_outer", "reduce_norms", "qumond_source", "forces", "rotation_curve", "fixed_setup", "fixed_output", "chi2", "profile", "vcycle_small_levels",
+    "far_field",
 };
 constexpr int kMaxTimed = 32768;
 
@@ -63,13 +64,15 @@ struct Tracer {
     int run_count = 0;
     double run_bytes = 0.0;
 
-    void add(const Phase& ph, long long times)
+    // a phase run `times` times; its bytes and cell updates count `work` times
+    // (with several sets, the sets whose correction stopped skip later runs)
+    void add(const Phase& ph, long long times, double work)
     {
         for (int k = 0; k < K_COUNT; ++k) {
             launches[k] += ph.launches[k] * times;
-            bytes[k] += ph.bytes[k] * (double)times;
+            bytes[k] += ph.bytes[k] * work;
         }
-        cell_updates += ph.cell_updates * times;
+        cell_updates += (long long)((double)ph.cell_updates * work);
     }
 };
 
@@ -111,6 +114,9 @@ struct qumond_ctx {
     int64_t* Ufix = nullptr;        // fixed-point master iterate (QUMOND_PREC_MIXED_FIXED), buffer 0
     int64_t* Ufix2 = nullptr;       // its second buffer (the iterate alternates: current = buffer it & 1)
     FixedMaps fmaps{};              // TMA descriptors of the fixed-point arrays (n >= 128)
+    int nsets = 1;                  // independent problems of this shape (every array holds nsets of them)
+    long long pstride = 0;          // doubles between two sets' partial norms
+    bool in_body = false;           // enqueueing a defect-correction V-cycle (sets that stopped are skipped)
     int vtop = -1;                  // top level of the cooperative small-level V-cycle kernel, -1: not used
     int vgrid = 0;                  // its CTAs (one per SM)
     unsigned* vbar = nullptr;       // its grid-barrier counter
@@ -118,6 +124,7 @@ struct qumond_ctx {
     int64_t* Ffix = nullptr;        // fixed-point right-hand side
     unsigned* maxbits = nullptr;
     int* fault = nullptr;           // set by kernels whose bounded waits ran out
+    double* ff = nullptr;           // far-field reductions (QUMOND_BC_MULTIPOLE)
     cudaStream_t cap_stream = nullptr;
     std::vector<SolveGraph> graphs;
     unsigned long long use_clock = 0;
@@ -185,7 +192,8 @@ qumond_status check_params(qumond_ctx* c, const qumond_params* p)
     if (p->max_vcycles < 0 || p->max_vcycles > 10000) return fail(c, QUMOND_ERR_INVALID_ARG, "max_vcycles must be in [0, 10000]");
     if (p->precision != QUMOND_PREC_FP64 && p->precision != QUMOND_PREC_MIXED && p->precision != QUMOND_PREC_MIXED_FIXED)
         return fail(c, QUMOND_ERR_INVALID_ARG, "unknown precision %d", p->precision);
-    if (p->bc_mode != QUMOND_BC_ZERO && p->bc_mode != QUMOND_BC_GIVEN) return fail(c, QUMOND_ERR_INVALID_ARG, "unknown bc_mode %d", p->bc_mode);
+    if (p->bc_mode != QUMOND_BC_ZERO && p->bc_mode != QUMOND_BC_GIVEN && p->bc_mode != QUMOND_BC_MULTIPOLE)
+        return fail(c, QUMOND_ERR_INVALID_ARG, "unknown bc_mode %d", p->bc_mode);
     if (p->warm_start != 0 && p->warm_start != 1) return fail(c, QUMOND_ERR_INVALID_ARG, "warm_start must be 0 or 1");
     if (p->deposit_shift < 0 || p->deposit_shift > 40) return fail(c, QUMOND_ERR_INVALID_ARG, "deposit_shift must be in [0, 40]");
     if (!(p->rc_box_frac > 0.0) || !(p->rc_box_frac <= 0.5)) return fail(c, QUMOND_ERR_INVALID_ARG, "rc_box_frac must be in (0, 0.5]");
@@ -196,6 +204,12 @@ qumond_status check_params(qumond_ctx* c, const qumond_params* p)
         return fail(c, QUMOND_ERR_INVALID_ARG, "persistent_vcycle must be 0 or 1");
     if (p->nboxes > 1 && p->n < 2 * p->box_ratio)
         return fail(c, QUMOND_ERR_INVALID_ARG, "n=%d too small for nested boxes of ratio %d", p->n, p->box_ratio);
+    if (p->nsets < 1 || p->nsets > 1024 || (long long)p->nsets * (p->n + 1) > 65535)
+        return fail(c, QUMOND_ERR_INVALID_ARG, "nsets=%d: need 1 <= nsets <= 1024 and nsets * (n + 1) <= 65535",
+                    p->nsets);
+    if (p->tile_small < 0 || p->tile_small > 2) return fail(c, QUMOND_ERR_INVALID_ARG, "tile_small must be 0, 1 or 2");
+    if (p->nsets > 1 && p->persistent_vcycle)
+        return fail(c, QUMOND_ERR_INVALID_ARG, "persistent_vcycle needs nsets = 1");
     return QUMOND_OK;
 }
 
@@ -234,6 +248,7 @@ template <class Launch>
 void run(qumond_ctx* c, int kind, double bytes, cudaStream_t s, Launch&& launch)
 {
     Tracer& t = c->tr;
+    bytes *= c->nsets;  // every launch covers all sets
     if (t.sink) {
         // timing one class inside a captured graph: one event pair per run of
         // consecutive launches of that class (event-record nodes cost several
@@ -274,8 +289,19 @@ void run(qumond_ctx* c, int kind, double bytes, cudaStream_t s, Launch&& launch)
     t.bytes[kind] += bytes;
 }
 
+inline Sets sets_of(const qumond_ctx* c)
+{
+    Sets st;
+    st.n = c->nsets;
+    st.act = (c->in_body && c->nsets > 1) ? c->d_state : nullptr;
+    st.pstride = c->pstride;
+    st.tile_small = c->p.tile_small;
+    return st;
+}
+
 inline void count_cells(qumond_ctx* c, long long n)
 {
+    n *= c->nsets;
     if (c->tr.sink) c->tr.sink->cell_updates += n;
     else c->tr.cell_updates += n;
 }
@@ -291,7 +317,7 @@ void rb(qumond_ctx* c, int l, int colour, bool zero, double h, cudaStream_t s)
             launch_rb_half_tma(reinterpret_cast<float*>(E<T>(c, l)), reinterpret_cast<const float*>(F<T>(c, l)),
                                c->lev[l].v, colour, c->lev[l].maps, h, c->fault, s);
         else
-            launch_rb_half<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, colour, zero, h, s);
+            launch_rb_half<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, colour, zero, h, s, sets_of(c));
     });
 }
 
@@ -300,7 +326,7 @@ void prolong(qumond_ctx* c, int l, bool add, cudaStream_t s)
 {
     const double nodes = cube(c->lev[l].v.n);
     run(c, K_PROLONG, ((add ? 1.0 : 0.5) + 0.125) * nodes * sizeof(T), s,
-        [&] { launch_prolong_black<T>(E<T>(c, l - 1), c->lev[l - 1].v, E<T>(c, l), c->lev[l].v, add, s); });
+        [&] { launch_prolong_black<T>(E<T>(c, l - 1), c->lev[l - 1].v, E<T>(c, l), c->lev[l].v, add, s, sets_of(c)); });
 }
 
 template <typename T>
@@ -308,7 +334,7 @@ void set_bnd(qumond_ctx* c, int l, const double* u64, cudaStream_t s)
 {
     const double nb = 6.0 * (c->lev[l].v.n + 1) * (double)(c->lev[l].v.n + 1);
     run(c, K_SET_BOUNDARY, nb * (sizeof(T) + (u64 ? 8.0 : 0.0)), s,
-        [&] { launch_set_boundary<T>(E<T>(c, l), c->lev[l].v, u64, c->p.n, s); });
+        [&] { launch_set_boundary<T>(E<T>(c, l), c->lev[l].v, u64, c->p.n, s, sets_of(c)); });
 }
 
 template <typename T>
@@ -322,7 +348,7 @@ cudaError_t coarse(qumond_ctx* c, int box, int fmg_mode, const double* u64, cuda
     cudaError_t err = cudaSuccess;
     run(c, K_COARSE, 2.0 * cube(n) * sizeof(T), s, [&] {
         err = launch_coarse<T>(fmg_mode, E<T>(c, l), F<T>(c, l), c->lev[l].v, level_h(c, box, l), u64, c->p.n,
-                               c->p.ncycle, c->p.npre, c->p.npost, s);
+                               c->p.ncycle, c->p.npre, c->p.npost, s, sets_of(c));
     });
     return err;
 }
@@ -376,7 +402,8 @@ cudaError_t vcycle(qumond_ctx* c, int box, int l, bool zero_guess, cudaStream_t 
     }
     const double nodes = cube(c->lev[l].v.n);
     run(c, K_RESTRICT_RESID, (1.5 + 0.125) * nodes * sizeof(T), s, [&] {
-        launch_restrict_resid_red<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, F<T>(c, l - 1), c->lev[l - 1].v, h, s);
+        launch_restrict_resid_red<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, F<T>(c, l - 1), c->lev[l - 1].v, h, s,
+                                     sets_of(c));
     });
     cudaError_t err = vcycle<T>(c, box, l - 1, true, s);
     if (err != cudaSuccess) return err;
@@ -401,7 +428,7 @@ cudaError_t fmg(qumond_ctx* c, int box, const double* u64, cudaStream_t s)
     for (int l = c->L - 1; l >= c->lc; --l) {
         const double nodes = cube(c->lev[l + 1].v.n);
         run(c, K_RESTRICT_FULL, 1.125 * nodes * sizeof(T), s, [&] {
-            launch_restrict_full<T>(F<T>(c, l + 1), c->lev[l + 1].v, F<T>(c, l), c->lev[l].v, s);
+            launch_restrict_full<T>(F<T>(c, l + 1), c->lev[l + 1].v, F<T>(c, l), c->lev[l].v, s, sets_of(c));
         });
     }
     cudaError_t err = coarse<T>(c, box, 1, u64, s);
@@ -432,16 +459,18 @@ void check(qumond_ctx* c, int box, const double* rhs, double coef, const double*
         nb = fixed_residual_blocks(p.n);
         run(c, K_RESIDUAL_OUTER, cube(p.n) * 20.0, s, [&] {
             launch_fixed_residual(c->Ufix, c->Ffix, p.n, box_h(c, box), c->d_state, first,
-                                  reinterpret_cast<float*>(F<T>(c, c->L)), c->lev[c->L].v, c->partials, s);
+                                  reinterpret_cast<float*>(F<T>(c, c->L)), c->lev[c->L].v, c->partials, s,
+                                  sets_of(c));
         });
     } else {
         run(c, K_RESIDUAL_OUTER, cube(p.n) * (16.0 + sizeof(T)), s, [&] {
-            launch_residual_rows<T>(u, rhs, coef, p.n, box_h(c, box), F<T>(c, c->L), c->lev[c->L].v, c->partials, s);
+            launch_residual_rows<T>(u, rhs, coef, p.n, box_h(c, box), F<T>(c, c->L), c->lev[c->L].v, c->partials, s,
+                                    sets_of(c));
         });
     }
     run(c, K_REDUCE, 16.0 * nb, s, [&] {
         launch_decide(c->partials, nb, c->d_state, p.rel_tol, p.max_vcycles, first, p.rel_tol > 0.0 && p.max_vcycles > 0,
-                      handle, c->fault, s);
+                      handle, c->fault, s, sets_of(c));
     });
 }
 
@@ -457,25 +486,26 @@ cudaError_t enqueue_preamble(qumond_ctx* c, int box, const double* rhs, double c
     const double nodes = cube(n);
     const double nbnd = 6.0 * (n + 1) * (double)(n + 1);
     if (box > 0)
-        run(c, K_BOUNDARY, nbnd * 16.0, s, [&] { launch_boundary_from_parent(parent, u, n, p.box_ratio, s); });
+        run(c, K_BOUNDARY, nbnd * 16.0, s,
+            [&] { launch_boundary_from_parent(parent, u, n, p.box_ratio, s, c->nsets); });
     else if (p.bc_mode == QUMOND_BC_ZERO)
-        run(c, K_BOUNDARY, nbnd * 8.0, s, [&] { launch_boundary_zero(u, n, s); });
+        run(c, K_BOUNDARY, nbnd * 8.0, s, [&] { launch_boundary_zero(u, n, s, c->nsets); });
     const bool fixed = fixed_mode(c) && norms;
     if (!p.warm_start) {
         run(c, K_CONVERT_RHS, nodes * (8.0 + sizeof(T)), s,
-            [&] { launch_convert_rhs<T>(rhs, coef, n, F<T>(c, c->L), c->lev[c->L].v, s); });
+            [&] { launch_convert_rhs<T>(rhs, coef, n, F<T>(c, c->L), c->lev[c->L].v, s, sets_of(c)); });
         cudaError_t err = fmg<T>(c, box, u, s);
         if (err != cudaSuccess) return err;
         if (!fixed)
             run(c, K_ASSIGN_OUTER, nodes * (8.0 + sizeof(T)), s,
-                [&] { launch_assign_outer<T>(u, n, E<T>(c, c->L), c->lev[c->L].v, false, s); });
+                [&] { launch_assign_outer<T>(u, n, E<T>(c, c->L), c->lev[c->L].v, false, s, sets_of(c)); });
     }
     if (fixed) {
         const float* eL = reinterpret_cast<const float*>(E<T>(c, c->L));
         run(c, K_FIXED_SETUP, nodes * 32.0, s, [&] {
-            launch_fixed_scale(eL, c->lev[c->L].v, u, n, p.warm_start != 0, c->maxbits, c->d_state, s);
+            launch_fixed_scale(eL, c->lev[c->L].v, u, n, p.warm_start != 0, c->maxbits, c->d_state, s, sets_of(c));
             launch_fixed_init(eL, c->lev[c->L].v, u, rhs, coef, box_h(c, box), n, p.warm_start != 0, c->d_state,
-                              c->Ufix, c->Ufix2, c->Ffix, s);
+                              c->Ufix, c->Ufix2, c->Ffix, s, sets_of(c));
         });
     }
     if (!p.warm_start) set_bnd<T>(c, c->L, nullptr, s);
@@ -489,7 +519,7 @@ cudaError_t enqueue_post(qumond_ctx* c, double* u, cudaStream_t s)
 {
     if (!fixed_mode(c)) return cudaSuccess;
     run(c, K_FIXED_OUTPUT, cube(c->p.n) * 16.0, s,
-        [&] { launch_fixed_output(c->Ufix, c->Ufix2, u, c->p.n, c->d_state, s); });
+        [&] { launch_fixed_output(c->Ufix, c->Ufix2, u, c->p.n, c->d_state, s, sets_of(c)); });
     return cudaGetLastError();
 }
 
@@ -500,6 +530,11 @@ cudaError_t enqueue_body(qumond_ctx* c, int box, const double* rhs, double coef,
                          const cudaGraphConditionalHandle* handle, cudaStream_t s)
 {
     const int n = c->p.n;
+    struct BodyFlag {  // kernels of this V-cycle skip the sets that have stopped
+        qumond_ctx* c;
+        explicit BodyFlag(qumond_ctx* cc) : c(cc) { c->in_body = true; }
+        ~BodyFlag() { c->in_body = false; }
+    } body_flag(c);
     cudaError_t err = vcycle<T>(c, box, c->L, true, s);
     if (err != cudaSuccess) return err;
     if (fixed_mode(c)) {
@@ -514,17 +549,17 @@ cudaError_t enqueue_body(qumond_ctx* c, int box, const double* rhs, double coef,
                 nb = launch_fixed_update_residual(c->Ufix, c->Ufix2, c->Ffix,
                                                   reinterpret_cast<const float*>(E<T>(c, c->L)), n, box_h(c, box),
                                                   c->d_state, reinterpret_cast<float*>(F<T>(c, c->L)), c->lev[c->L].v,
-                                                  c->partials, s);
+                                                  c->partials, s, sets_of(c));
         });
         const qumond_params& p = c->p;
         run(c, K_REDUCE, 16.0 * nb, s, [&] {
             launch_decide(c->partials, nb, c->d_state, p.rel_tol, p.max_vcycles, false,
-                          p.rel_tol > 0.0 && p.max_vcycles > 0, handle, c->fault, s);
+                          p.rel_tol > 0.0 && p.max_vcycles > 0, handle, c->fault, s, sets_of(c));
         });
         return cudaGetLastError();
     }
     run(c, K_ASSIGN_OUTER, cube(n) * (16.0 + sizeof(T)), s,
-        [&] { launch_assign_outer<T>(u, n, E<T>(c, c->L), c->lev[c->L].v, true, s); });
+        [&] { launch_assign_outer<T>(u, n, E<T>(c, c->L), c->lev[c->L].v, true, s, sets_of(c)); });
     check<T>(c, box, rhs, coef, u, false, handle, s);
     return cudaGetLastError();
 }
@@ -658,6 +693,7 @@ qumond_status solve_t(qumond_ctx* c, int kind, int box, const double* rhs, doubl
     const qumond_params& p = c->p;
     const bool refine = p.rel_tol > 0.0 && p.max_vcycles > 0;
     const bool norms = refine || st != nullptr;
+    const int ns = c->nsets;
     if (p.use_graphs && !(c->tr.on && c->tr.only < 0)) {
         SolveGraph* g = find_graph(c, kind, box, rhs, parent, u, norms);
         if (!g) {
@@ -677,11 +713,18 @@ qumond_status solve_t(qumond_ctx* c, int kind, int box, const double* rhs, doubl
         }
         g->last_use = ++c->use_clock;
         CUDA_TRY(c, cudaGraphLaunch(g->exec, s), "graph launch");
-        c->tr.add(g->pre, 1);
+        c->tr.add(g->pre, 1, 1.0);
         if (!norms) return QUMOND_OK;
-        CUDA_TRY(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, s), "state copy");
+        CUDA_TRY(c, cudaMemcpyAsync(c->h_state, c->d_state, ns * sizeof(SolveState), cudaMemcpyDeviceToHost, s),
+                 "state copy");
         CUDA_TRY(c, cudaStreamSynchronize(s), "solve");
-        c->tr.add(g->body, c->h_state->it);
+        int most = 0;
+        double all = 0.0;
+        for (int q = 0; q < ns; ++q) {
+            most = c->h_state[q].it > most ? c->h_state[q].it : most;
+            all += c->h_state[q].it;
+        }
+        c->tr.add(g->body, most, all / ns);
         for (size_t q = 0; q < g->event_kinds.size(); ++q) {  // one pair per run of g->timed_class launches
             float ms = 0.0f;
             CUDA_TRY(c, cudaEventElapsedTime(&ms, g->events[2 * q], g->events[2 * q + 1]), "trace: elapsed");
@@ -693,26 +736,38 @@ qumond_status solve_t(qumond_ctx* c, int kind, int box, const double* rhs, doubl
         CUDA_TRY(c, enqueue_preamble<T>(c, box, rhs, coef, parent, u, norms, nullptr, s), "solve launch");
         if (!norms) return QUMOND_OK;
         for (;;) {
-            CUDA_TRY(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, s),
+            CUDA_TRY(c, cudaMemcpyAsync(c->h_state, c->d_state, ns * sizeof(SolveState), cudaMemcpyDeviceToHost, s),
                      "state copy");
             CUDA_TRY(c, cudaStreamSynchronize(s), "solve");
-            if (!c->h_state->cont) break;
+            bool any = false;
+            for (int q = 0; q < ns; ++q) any = any || c->h_state[q].cont;
+            if (!any) break;
             CUDA_TRY(c, enqueue_body<T>(c, box, rhs, coef, u, nullptr, s), "vcycle launch");
         }
         CUDA_TRY(c, enqueue_post<T>(c, u, s), "output launch");
     }
-    const SolveState& r = *c->h_state;
-    if (r.fault)
-        return fail(c, QUMOND_ERR_TIMEOUT, "box %d: a kernel gave up waiting for its shared-memory pipeline", box);
-    if (st) {
-        st->vcycles = r.it;
-        st->converged = r.converged;
-        st->rel_residual_fmg = r.rel0;
-        st->rel_residual = r.rel;
+    for (int q = 0; q < ns; ++q)
+        if (c->h_state[q].fault)
+            return fail(c, QUMOND_ERR_TIMEOUT, "box %d: a kernel gave up waiting for its shared-memory pipeline", box);
+    if (st)
+        for (int q = 0; q < ns; ++q) {
+            const SolveState& r = c->h_state[q];
+            st[q].vcycles = r.it;
+            st[q].converged = r.converged;
+            st[q].rel_residual_fmg = r.rel0;
+            st[q].rel_residual = r.rel;
+        }
+    for (int q = 0; q < ns; ++q) {
+        const SolveState& r = c->h_state[q];
+        if (!r.converged) {
+            if (ns == 1)
+                return fail(c, QUMOND_ERR_NOT_CONVERGED, "box %d: relative residual %.3e after %d V-cycles (tol %.3e)",
+                            box, r.rel, r.it, p.rel_tol);
+            return fail(c, QUMOND_ERR_NOT_CONVERGED,
+                        "set %d, box %d: relative residual %.3e after %d V-cycles (tol %.3e)", q, box, r.rel, r.it,
+                        p.rel_tol);
+        }
     }
-    if (!r.converged)
-        return fail(c, QUMOND_ERR_NOT_CONVERGED, "box %d: relative residual %.3e after %d V-cycles (tol %.3e)", box,
-                    r.rel, r.it, p.rel_tol);
     return QUMOND_OK;
 }
 
@@ -783,6 +838,8 @@ void qumond_default_params(qumond_params* p)
     p->box_ratio = 2;
     p->use_graphs = 1;
     p->persistent_vcycle = 0;
+    p->nsets = 1;
+    p->tile_small = 0;
 }
 
 qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
@@ -796,6 +853,8 @@ qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
         return st;
     }
     c->p = *p;
+    c->nsets = p->nsets;
+    const size_t ns = (size_t)p->nsets;
     c->elt = p->precision == QUMOND_PREC_FP64 ? sizeof(double) : sizeof(float);  // FIXED smooths in FP32
     int L = 0;
     while ((2 << L) < p->n) ++L;
@@ -808,7 +867,7 @@ qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
     for (int l = 0; l <= L; ++l) {
         c->lev[l].v = make_view(2 << l);
         if (l < lc) continue;
-        const size_t bytes = (size_t)(2 * c->lev[l].v.cs) * c->elt;
+        const size_t bytes = (size_t)(2 * c->lev[l].v.cs) * c->elt * ns;
         if (cudaMalloc(&c->lev[l].e, bytes) != cudaSuccess || cudaMalloc(&c->lev[l].f, bytes) != cudaSuccess) {
             ok = false;
             break;
@@ -822,21 +881,24 @@ qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
         const int nrows = residual_rows_blocks(p->n > 2 ? p->n : 2);
         const int nouter = residual_outer_blocks(p->n > 2 ? p->n : 2);
         c->max_partials = nrows > nouter ? nrows : nouter;
-        ok = cudaMalloc(&c->partials, sizeof(double) * 2 * (size_t)(c->max_partials + 1)) == cudaSuccess &&
+        c->pstride = 2 * (long long)(c->max_partials + 1);
+        ok = cudaMalloc(&c->partials, sizeof(double) * (size_t)c->pstride * ns) == cudaSuccess &&
              cudaMalloc(&c->d_norms, sizeof(double) * 2) == cudaSuccess &&
              cudaMallocHost(&c->h_norms, sizeof(double) * 2) == cudaSuccess &&
-             cudaMalloc(&c->d_state, sizeof(SolveState)) == cudaSuccess &&
-             cudaMallocHost(&c->h_state, sizeof(SolveState)) == cudaSuccess &&
-             cudaMemset(c->d_state, 0, sizeof(SolveState)) == cudaSuccess &&
+             cudaMalloc(&c->d_state, sizeof(SolveState) * ns) == cudaSuccess &&
+             cudaMallocHost(&c->h_state, sizeof(SolveState) * ns) == cudaSuccess &&
+             cudaMemset(c->d_state, 0, sizeof(SolveState) * ns) == cudaSuccess &&
              cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
              cudaMalloc(&c->fault, sizeof(int)) == cudaSuccess && cudaMemset(c->fault, 0, sizeof(int)) == cudaSuccess &&
+             (p->bc_mode != QUMOND_BC_MULTIPOLE ||
+              cudaMalloc(&c->ff, sizeof(double) * far_field_scratch_doubles(p->nsets)) == cudaSuccess) &&
              prepare_kernels() == cudaSuccess;
-        if (ok && c->elt == sizeof(float))
+        if (ok && c->elt == sizeof(float) && ns == 1)  // the TMA-staged kernels take one set
             for (int l = lc; l <= L; ++l)
                 make_rb_maps(static_cast<float*>(c->lev[l].e), static_cast<float*>(c->lev[l].f), c->lev[l].v,
                              &c->lev[l].maps);
         if (ok && p->precision == QUMOND_PREC_MIXED_FIXED) {
-            const size_t nn = fixed_elems(p->n);
+            const size_t nn = fixed_elems(p->n) * ns;
             const int nfix = fixed_residual_blocks(p->n > 2 ? p->n : 2);
             if (nfix > c->max_partials) ok = false;  // partial buffer sized above covers it
             ok = ok && cudaMalloc(&c->Ufix, nn * sizeof(int64_t)) == cudaSuccess &&
@@ -845,9 +907,9 @@ qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
                  cudaMemset(c->Ufix, 0, nn * sizeof(int64_t)) == cudaSuccess &&
                  cudaMemset(c->Ufix2, 0, nn * sizeof(int64_t)) == cudaSuccess &&
                  cudaMemset(c->Ffix, 0, nn * sizeof(int64_t)) == cudaSuccess &&
-                 cudaMalloc(&c->maxbits, sizeof(unsigned)) == cudaSuccess &&
-                 cudaMemset(c->maxbits, 0, sizeof(unsigned)) == cudaSuccess;
-            if (ok && c->elt == sizeof(float)) {
+                 cudaMalloc(&c->maxbits, sizeof(unsigned) * ns) == cudaSuccess &&
+                 cudaMemset(c->maxbits, 0, sizeof(unsigned) * ns) == cudaSuccess;
+            if (ok && c->elt == sizeof(float) && ns == 1) {
                 const int n = p->n;
                 const long long items = (long long)((n - 1 + 31) / 32) * ((n - 1 + 7) / 8) * ((n - 1 + 15) / 16);
                 if (items <= c->max_partials)
@@ -895,6 +957,7 @@ void qumond_destroy(qumond_ctx* c)
     if (c->h_norms) cudaFreeHost(c->h_norms);
     if (c->d_state) cudaFree(c->d_state);
     if (c->fault) cudaFree(c->fault);
+    if (c->ff) cudaFree(c->ff);
     if (c->Ufix) cudaFree(c->Ufix);
     if (c->Ufix2) cudaFree(c->Ufix2);
     if (c->vbar) cudaFree(c->vbar);
@@ -926,15 +989,16 @@ qumond_status qumond_deposit(qumond_ctx* c, int box, const double* x, const doub
     const double L = box_side(c, box);
     const double inv_h = (double)n / L;
     cudaStream_t s = S(stream);
-    CUDA_TRY(c, cudaMemsetAsync(rho_fixed, 0, sizeof(int64_t) * count, s), "deposit: clear");
+    CUDA_TRY(c, cudaMemsetAsync(rho_fixed, 0, sizeof(int64_t) * count * c->nsets, s), "deposit: clear");
     run(c, K_DEPOSIT, 32.0 * (double)np, s, [&] {
         launch_cic_deposit(x, y, z, mass, np, n, c->p.center[0] - 0.5 * L, c->p.center[1] - 0.5 * L,
-                           c->p.center[2] - 0.5 * L, inv_h, std::ldexp(1.0, c->p.deposit_shift), rho_fixed, s);
+                           c->p.center[2] - 0.5 * L, inv_h, std::ldexp(1.0, c->p.deposit_shift), rho_fixed, s,
+                           c->nsets);
     });
     if (rho) {
         const double scale = std::ldexp(1.0, -c->p.deposit_shift) * (inv_h * inv_h * inv_h);
         run(c, K_FIXED_TO_RHO, 16.0 * (double)count, s,
-            [&] { launch_fixed_to_rho(rho_fixed, rho, count, scale, s); });
+            [&] { launch_fixed_to_rho(rho_fixed, rho, count * c->nsets, scale, s); });
     }
     CUDA_TRY(c, cudaGetLastError(), "deposit launch");
     return QUMOND_OK;
@@ -961,7 +1025,7 @@ qumond_status qumond_source(qumond_ctx* c, int box, const double* phiN, double* 
     if (!device_ptr(phiN) || !device_ptr(src)) return fail(c, QUMOND_ERR_INVALID_ARG, "source: phiN and src must be device pointers");
     if (phiN == src) return fail(c, QUMOND_ERR_INVALID_ARG, "source: src must not alias phiN");
     run(c, K_SOURCE, 16.0 * cube(c->p.n), S(stream),
-        [&] { launch_source(phiN, src, c->p.n, box_h(c, box), c->p.a0, S(stream)); });
+        [&] { launch_source(phiN, src, c->p.n, box_h(c, box), c->p.a0, S(stream), c->nsets); });
     CUDA_TRY(c, cudaGetLastError(), "source launch");
     return QUMOND_OK;
 }
@@ -978,7 +1042,7 @@ qumond_status qumond_forces(qumond_ctx* c, const double* const* phi_boxes, const
     if (!device_ptr(qx) || !device_ptr(qy) || !device_ptr(qz) || !device_ptr(gx) || !device_ptr(gy) || !device_ptr(gz))
         return fail(c, QUMOND_ERR_INVALID_ARG, "forces: point and force arrays must be device pointers");
     run(c, K_FORCES, 48.0 * (double)nq, S(stream),
-        [&] { launch_forces(box_set(c, phi_boxes), qx, qy, qz, nq, gx, gy, gz, S(stream)); });
+        [&] { launch_forces(box_set(c, phi_boxes), qx, qy, qz, nq, gx, gy, gz, S(stream), c->nsets); });
     CUDA_TRY(c, cudaGetLastError(), "forces launch");
     return QUMOND_OK;
 }
@@ -996,9 +1060,28 @@ qumond_status qumond_rotation_curve(qumond_ctx* c, const double* const* phi_boxe
     if (!device_ptr(r_out) || !device_ptr(vc_out)) return fail(c, QUMOND_ERR_INVALID_ARG, "rotation_curve: outputs must be device pointers");
     run(c, K_ROTATION_CURVE, 16.0 * nbins, S(stream), [&] {
         launch_rotation_curve(box_set(c, phi_boxes), c->p.center[0], c->p.center[1], c->p.center[2], nbins, rmax,
-                              nphi, c->p.rc_box_frac, r_out, vc_out, S(stream));
+                              nullptr, nphi, c->p.rc_box_frac, r_out, vc_out, S(stream), c->nsets);
     });
     CUDA_TRY(c, cudaGetLastError(), "rotation_curve launch");
+    return QUMOND_OK;
+}
+
+qumond_status qumond_rotation_curve_sets(qumond_ctx* c, const double* const* phi_boxes, int nbins, const double* rmax,
+                                         int nphi, double* r_out, double* vc_out, void* stream)
+{
+    if (!c) return QUMOND_ERR_INVALID_ARG;
+    c->err.clear();
+    qumond_status st = check_phis(c, phi_boxes, "rotation_curve_sets");
+    if (st != QUMOND_OK) return st;
+    if (nbins < 1 || nbins > 65535) return fail(c, QUMOND_ERR_INVALID_ARG, "rotation_curve_sets: nbins must be in [1, 65535]");
+    if (nphi < 1 || nphi > 1024) return fail(c, QUMOND_ERR_INVALID_ARG, "rotation_curve_sets: nphi must be in [1, 1024]");
+    if (!device_ptr(rmax) || !device_ptr(r_out) || !device_ptr(vc_out))
+        return fail(c, QUMOND_ERR_INVALID_ARG, "rotation_curve_sets: rmax and the outputs must be device pointers");
+    run(c, K_ROTATION_CURVE, 16.0 * nbins, S(stream), [&] {
+        launch_rotation_curve(box_set(c, phi_boxes), c->p.center[0], c->p.center[1], c->p.center[2], nbins, 0.0, rmax,
+                              nphi, c->p.rc_box_frac, r_out, vc_out, S(stream), c->nsets);
+    });
+    CUDA_TRY(c, cudaGetLastError(), "rotation_curve_sets launch");
     return QUMOND_OK;
 }
 
@@ -1019,7 +1102,7 @@ qumond_status profile(qumond_ctx* c, const double* const* phi_boxes, int nbins, 
         return fail(c, QUMOND_ERR_INVALID_ARG, "%s: outputs must be device pointers", what);
     run(c, K_PROFILE, 16.0 * nbins, S(stream), [&] {
         launch_profile(box_set(c, phi_boxes), c->p.center[0], c->p.center[1], c->p.center[2], nbins, rmax, nphi,
-                       c->p.rc_box_frac, mode, c->p.a0, z_eval, h, r_out, out, S(stream));
+                       c->p.rc_box_frac, mode, c->p.a0, z_eval, h, r_out, out, S(stream), c->nsets);
     });
     CUDA_TRY(c, cudaGetLastError(), what);
     return QUMOND_OK;
@@ -1064,6 +1147,26 @@ qumond_status qumond_set_barrier_poll_limit(qumond_ctx* c, int64_t polls)
     for (auto& g : c->graphs) destroy_graph(g);
     c->graphs.clear();
     c->barrier_polls = polls;
+    return QUMOND_OK;
+}
+
+qumond_status qumond_far_field(qumond_ctx* c, const double* rho, double* phiN, double* phi, void* stream)
+{
+    if (!c) return QUMOND_ERR_INVALID_ARG;
+    c->err.clear();
+    if (c->p.bc_mode != QUMOND_BC_MULTIPOLE)
+        return fail(c, QUMOND_ERR_INVALID_ARG, "far_field: the context's bc_mode is not QUMOND_BC_MULTIPOLE");
+    if (!device_ptr(rho) || !device_ptr(phiN) || !device_ptr(phi))
+        return fail(c, QUMOND_ERR_INVALID_ARG, "far_field: rho, phiN and phi must be device pointers");
+    if (phiN == phi || rho == phiN || rho == phi)
+        return fail(c, QUMOND_ERR_INVALID_ARG, "far_field: rho, phiN and phi must be distinct arrays");
+    const double nodes = cube(c->p.n);
+    const double nbnd = 6.0 * (c->p.n + 1) * (double)(c->p.n + 1);
+    run(c, K_FAR_FIELD, 2.0 * 8.0 * nodes + 2.0 * 8.0 * nbnd, S(stream), [&] {
+        launch_far_field(rho, c->p.n, box_side(c, 0), c->p.center[0], c->p.center[1], c->p.center[2], c->p.G,
+                         c->p.a0, phiN, phi, c->ff, c->nsets, S(stream));
+    });
+    CUDA_TRY(c, cudaGetLastError(), "far_field launch");
     return QUMOND_OK;
 }
 

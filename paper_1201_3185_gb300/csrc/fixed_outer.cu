@@ -74,6 +74,10 @@ __global__ void __launch_bounds__(kThreads)
 scan_max_kernel(const float* __restrict__ e, LevelView v, const double* __restrict__ u64, int n, int from_u64,
                 unsigned* __restrict__ out)
 {
+    const int set = blockIdx.y;  // one row of blocks per set
+    e += set * 2 * v.cs;
+    u64 += set * nat_elems(n);
+    out += set;
     unsigned local = 0u;
     const int rows = (n + 1) * (n + 1);
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
@@ -102,6 +106,9 @@ scan_max_kernel(const float* __restrict__ e, LevelView v, const double* __restri
 __global__ void __launch_bounds__(256) scan_max_level_kernel(const float4* __restrict__ e, long long n4,
                                                              unsigned* __restrict__ out)
 {
+    const int set = blockIdx.y;  // one row of blocks per set; n4 float4 per set
+    e += set * n4;
+    out += set;
     unsigned local = 0u;
     for (long long q = blockIdx.x * 256LL + threadIdx.x; q < n4; q += (long long)gridDim.x * 256) {
         const float4 x = e[q];
@@ -122,6 +129,8 @@ __global__ void __launch_bounds__(256) scan_max_level_kernel(const float4* __res
 // normal FP32 numbers; also clears the max for the next solve.
 __global__ void choose_scale_kernel(unsigned* __restrict__ maxbits, SolveState* __restrict__ st)
 {
+    maxbits += blockIdx.x;  // one block per set
+    st += blockIdx.x;
     const float m = __uint_as_float(*maxbits);
     int S = 0;
     if (m > 0.0f && isfinite(m)) {
@@ -150,6 +159,15 @@ fixed_init_pairs_kernel(const float* __restrict__ e, LevelView v, const double* 
                         SolveState* __restrict__ st, long long* __restrict__ U, long long* __restrict__ U2,
                         long long* __restrict__ F)
 {
+    {
+        const int set = blockIdx.y;  // one row of blocks per set
+        e += set * 2 * v.cs;
+        u64 += set * nat_elems(n);
+        rhs += set * nat_elems(n);
+        st += set;
+        const long long fs = set * (long long)(n + 2) * (n + 1) * (n + 1);
+        U += fs, U2 += fs, F += fs;
+    }
     const int pairs = n / 2 + 1;
     const long long idx = blockIdx.x * 256LL + threadIdx.x;
     if (idx >= (long long)pairs * (n + 1) * (n + 1)) return;
@@ -190,8 +208,16 @@ fixed_init_pairs_kernel(const float* __restrict__ e, LevelView v, const double* 
 __global__ void __launch_bounds__(kThreads)
 fixed_residual_kernel(const long long* __restrict__ U, const long long* __restrict__ F, int n, float ih2,
                       const SolveState* __restrict__ st, int want_f, float* __restrict__ r, LevelView v,
-                      double* __restrict__ partials)
+                      double* __restrict__ partials, long long pstride)
 {
+    {
+        const int set = blockIdx.y;  // one row of blocks per set
+        const long long fs = set * (long long)(n + 2) * (n + 1) * (n + 1);
+        U += fs, F += fs;
+        st += set;
+        r += set * 2 * v.cs;
+        partials += set * pstride;
+    }
     const long long P = n + 2, Q = P * (n + 1);
     const float k = pow2f(-st->scale_exp) * ih2;
     const int rows = (n - 1) * (n - 1);
@@ -253,9 +279,20 @@ constexpr int kFW = kFTI + 2, kFH = kFTJ + 2;
 __global__ void __launch_bounds__(kFTI * kFTJ)
 fixed_update_residual_kernel(long long* Ua, long long* Ub, const long long* __restrict__ F,
                              const float* __restrict__ e, int n, float ih2, const SolveState* __restrict__ st,
-                             float* __restrict__ r, LevelView v, double* __restrict__ partials)
+                             float* __restrict__ r, LevelView v, double* __restrict__ partials, long long pstride,
+                             int skip_stopped)
 {
     __shared__ long long pl[3][kFH][kFW];
+    {
+        const int set = blockIdx.y;  // one row of blocks per set
+        st += set;
+        if (skip_stopped && !st->cont) return;
+        const long long fs = set * (long long)(n + 2) * (n + 1) * (n + 1);
+        Ua += fs, Ub += fs, F += fs;
+        e += set * 2 * v.cs;
+        r += set * 2 * v.cs;
+        partials += set * pstride;
+    }
     const bool odd = (st->it & 1) != 0;
     const long long* __restrict__ cur = odd ? Ub : Ua;
     long long* __restrict__ nxt = odd ? Ua : Ub;
@@ -358,6 +395,13 @@ __global__ void __launch_bounds__(kThreads)
 fixed_output_kernel(const long long* Ua, const long long* Ub, double* __restrict__ u, int n,
                     const SolveState* __restrict__ st)
 {
+    {
+        const int set = blockIdx.y;  // one row of blocks per set
+        const long long fs = set * (long long)(n + 2) * (n + 1) * (n + 1);
+        Ua += fs, Ub += fs;
+        u += set * nat_elems(n);
+        st += set;
+    }
     const long long* __restrict__ U = (st->it & 1) ? Ub : Ua;
     const int S = st->scale_exp;
     const int rows = (n - 1) * (n - 1);
@@ -373,34 +417,39 @@ inline int blocks_for_rows(long long rows) { return (int)(rows < kMaxBlocks ? ro
 }  // namespace
 
 void launch_fixed_scale(const float* e, const LevelView& v, const double* u64, int n, bool from_u64, unsigned* maxbits,
-                        SolveState* st, cudaStream_t s)
+                        SolveState* st, cudaStream_t s, const Sets& sets)
 {
+    const unsigned ns = (unsigned)sets.n;
     if (from_u64)
-        scan_max_kernel<<<blocks_for_rows((long long)(n + 1) * (n + 1)), kThreads, 0, s>>>(e, v, u64, n, 1, maxbits);
+        scan_max_kernel<<<dim3(blocks_for_rows((long long)(n + 1) * (n + 1)), ns), kThreads, 0, s>>>(e, v, u64, n, 1,
+                                                                                                  maxbits);
     else
-        scan_max_level_kernel<<<kMaxBlocks, 256, 0, s>>>(reinterpret_cast<const float4*>(e), 2 * v.cs / 4, maxbits);
-    choose_scale_kernel<<<1, 1, 0, s>>>(maxbits, st);
+        scan_max_level_kernel<<<dim3(kMaxBlocks, ns), 256, 0, s>>>(reinterpret_cast<const float4*>(e), 2 * v.cs / 4,
+                                                                   maxbits);
+    choose_scale_kernel<<<ns, 1, 0, s>>>(maxbits, st);
 }
 
 void launch_fixed_init(const float* e, const LevelView& v, const double* u64, const double* rhs, double coef, double h,
-                       int n, bool from_u64, SolveState* st, int64_t* U, int64_t* U2, int64_t* F, cudaStream_t s)
+                       int n, bool from_u64, SolveState* st, int64_t* U, int64_t* U2, int64_t* F, cudaStream_t s,
+                       const Sets& sets)
 {
     const long long threads = (long long)(n / 2 + 1) * (n + 1) * (n + 1);
-    fixed_init_pairs_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+    fixed_init_pairs_kernel<<<dim3((unsigned)((threads + 255) / 256), (unsigned)sets.n), 256, 0, s>>>(
         e, v, u64, rhs, coef * h * h, n, from_u64 ? 1 : 0, st, reinterpret_cast<long long*>(U),
         reinterpret_cast<long long*>(U2), reinterpret_cast<long long*>(F));
 }
 
 int launch_fixed_update_residual(int64_t* U, int64_t* U2, const int64_t* F, const float* e, int n, double h,
-                                 const SolveState* st, float* r, const LevelView& v, double* partials, cudaStream_t s)
+                                 const SolveState* st, float* r, const LevelView& v, double* partials, cudaStream_t s,
+                                 const Sets& sets)
 {
     const long long items = (long long)((n - 1 + kFTI - 1) / kFTI) * ((n - 1 + kFTJ - 1) / kFTJ) *
                             ((n - 1 + kFKC - 1) / kFKC);
     const int cap = fixed_residual_blocks(n);
     const int nb = (int)(items < cap ? items : cap);
-    fixed_update_residual_kernel<<<nb, dim3(kFTI, kFTJ), 0, s>>>(
+    fixed_update_residual_kernel<<<dim3(nb, sets.n), dim3(kFTI, kFTJ), 0, s>>>(
         reinterpret_cast<long long*>(U), reinterpret_cast<long long*>(U2), reinterpret_cast<const long long*>(F), e, n,
-        (float)(1.0 / (h * h)), st, r, v, partials);
+        (float)(1.0 / (h * h)), st, r, v, partials, sets.pstride, sets.act ? 1 : 0);
     return nb;
 }
 
@@ -409,19 +458,21 @@ int fixed_residual_blocks(int n) { return blocks_for_rows((long long)(n - 1) * (
 size_t fixed_elems(int n) { return (size_t)(n + 2) * (n + 1) * (n + 1); }
 
 int launch_fixed_residual(const int64_t* U, const int64_t* F, int n, double h, const SolveState* st, bool want_f,
-                          float* r, const LevelView& v, double* partials, cudaStream_t s)
+                          float* r, const LevelView& v, double* partials, cudaStream_t s, const Sets& sets)
 {
     const int nb = fixed_residual_blocks(n);
-    fixed_residual_kernel<<<nb, kThreads, 0, s>>>(reinterpret_cast<const long long*>(U),
-                                                  reinterpret_cast<const long long*>(F), n, (float)(1.0 / (h * h)), st,
-                                                  want_f ? 1 : 0, r, v, partials);
+    fixed_residual_kernel<<<dim3(nb, sets.n), kThreads, 0, s>>>(reinterpret_cast<const long long*>(U),
+                                                                reinterpret_cast<const long long*>(F), n,
+                                                                (float)(1.0 / (h * h)), st, want_f ? 1 : 0, r, v,
+                                                                partials, sets.pstride);
     return nb;
 }
 
-void launch_fixed_output(const int64_t* U, const int64_t* U2, double* u, int n, const SolveState* st, cudaStream_t s)
+void launch_fixed_output(const int64_t* U, const int64_t* U2, double* u, int n, const SolveState* st, cudaStream_t s,
+                         const Sets& sets)
 {
-    fixed_output_kernel<<<fixed_residual_blocks(n), kThreads, 0, s>>>(reinterpret_cast<const long long*>(U),
-                                                                       reinterpret_cast<const long long*>(U2), u, n, st);
+    fixed_output_kernel<<<dim3(fixed_residual_blocks(n), sets.n), kThreads, 0, s>>>(
+        reinterpret_cast<const long long*>(U), reinterpret_cast<const long long*>(U2), u, n, st);
 }
 
 }  // namespace qumond

@@ -26,6 +26,12 @@ __global__ void cic_deposit_kernel(const double* __restrict__ x, const double* _
                                    double xlo, double ylo, double zlo, double inv_h, double two_shift,
                                    unsigned long long* __restrict__ q)
 {
+    {
+        const int set = blockIdx.y;  // one row of blocks per set: np particles each
+        const long long po = set * np;
+        x += po, y += po, z += po, m += po;
+        q += set * nat_elems(n);
+    }
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= np) return;
     const double tx = __dmul_rn(__dsub_rn(x[p], xlo), inv_h);
@@ -75,13 +81,15 @@ __device__ __forceinline__ void face_node(int face, int a, int b, int n, int& i,
     }
 }
 
+// blockIdx.z = 6 * set + face
 __global__ void boundary_zero_kernel(double* __restrict__ u, int n)
 {
+    const int set = blockIdx.z / 6, face = blockIdx.z - 6 * set;
     const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
     if (a > n) return;
     int i, j, k;
-    face_node(blockIdx.z, a, b, n, i, j, k);
-    u[nat(n, i, j, k)] = 0.0;
+    face_node(face, a, b, n, i, j, k);
+    u[set * nat_elems(n) + nat(n, i, j, k)] = 0.0;
 }
 
 // Trilinear interpolation of a natural-layout grid at index coordinates t.
@@ -116,10 +124,13 @@ __device__ __forceinline__ double trilinear_idx(const double* __restrict__ a, in
 // boundary).
 __global__ void boundary_from_parent_kernel(const double* __restrict__ parent, double* __restrict__ u, int n, int ratio)
 {
+    const int set = blockIdx.z / 6, face = blockIdx.z - 6 * set;  // blockIdx.z = 6 * set + face
+    parent += set * nat_elems(n);
+    u += set * nat_elems(n);
     const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
     if (a > n) return;
     int i, j, k;
-    face_node(blockIdx.z, a, b, n, i, j, k);
+    face_node(face, a, b, n, i, j, k);
     const double inv_r = 1.0 / (double)ratio;
     const double q = 0.5 * (double)n * (1.0 - inv_r);
     u[nat(n, i, j, k)] = trilinear_idx(parent, n, q + inv_r * i, q + inv_r * j, q + inv_r * k);
@@ -231,14 +242,18 @@ __device__ __forceinline__ float flux_z(const SrcPlanes& S, int p, int pp, int y
 
 __global__ void __launch_bounds__(kSrcTX * kSrcTY)
 source_kernel(const double* __restrict__ phi, double* __restrict__ src, int n, float inv_h, float four_a0,
-              float inv_h2)
+              float inv_h2, int zper)
 {
     __shared__ SrcPlanes S;
     __shared__ float Fx[kSrcTY][kSrcTX + 1];  // Fx[y][x + 1]: face (x, x+1), x = -1 .. 31
     __shared__ float Fy[kSrcTY + 1][kSrcTX];  // Fy[y + 1][x]: face (y, y+1), y = -1 .. 7
+    const int set = (int)gridDim.z == zper ? 0 : blockIdx.z / zper;  // blockIdx.z = zper * set + chunk
+    const int kc = blockIdx.z - set * zper;
+    phi += set * nat_elems(n);
+    src += set * nat_elems(n);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kSrcTX + tx;
     const int i0 = blockIdx.x * kSrcTX, j0 = blockIdx.y * kSrcTY;
-    const int k0 = blockIdx.z * kSrcKC;
+    const int k0 = kc * kSrcKC;
     const int k1 = min(k0 + kSrcKC, n + 1);
     const long long P = n + 1;
 
@@ -333,9 +348,11 @@ __device__ __forceinline__ bool find_cell(const BoxGeom& g, int n, double x, dou
     return true;
 }
 
-__device__ __forceinline__ void grad_at(const BoxGeom& g, int n, const int* ijk, const double* d, double* out)
+// set: which of the context's sets (its potentials sit at set (n+1)^3 in every box)
+__device__ __forceinline__ void grad_at(const BoxGeom& g, int n, const int* ijk, const double* d, double* out,
+                                        int set = 0)
 {
-    const double* phi = g.phi;
+    const double* phi = g.phi + set * nat_elems(n);
     const double s = -0.5 / g.h;
     const long long P = n + 1, Q = P * P;
     double gx = 0.0, gy = 0.0, gz = 0.0;
@@ -360,6 +377,11 @@ __global__ void forces_kernel(BoxSet boxes, const double* __restrict__ qx, const
                               const double* __restrict__ qz, long long nq, double* __restrict__ gx,
                               double* __restrict__ gy, double* __restrict__ gz)
 {
+    const int set = blockIdx.y;  // one row of blocks per set: nq points each
+    {
+        const long long po = set * nq;
+        qx += po, qy += po, qz += po, gx += po, gy += po, gz += po;
+    }
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= nq) return;
     const double x = qx[p], y = qy[p], z = qz[p];
@@ -368,7 +390,7 @@ __global__ void forces_kernel(BoxSet boxes, const double* __restrict__ qx, const
         int ijk[3];
         double d[3];
         if (find_cell(boxes.b[b], boxes.n, x, y, z, ijk, d)) {
-            grad_at(boxes.b[b], boxes.n, ijk, d, g);
+            grad_at(boxes.b[b], boxes.n, ijk, d, g, set);
             break;
         }
     }
@@ -381,10 +403,17 @@ __global__ void forces_kernel(BoxSet boxes, const double* __restrict__ qx, const
 // summed in index order by thread 0, so the result is reproducible.
 constexpr int kMaxPhi = 1024;
 
-__global__ void rotation_curve_kernel(BoxSet boxes, double cx, double cy, double cz, int nbins, double rmax, int nphi,
-                                      double frac, double* __restrict__ r_out, double* __restrict__ vc_out)
+// With several sets: blockIdx.y = set, its outermost radius rmax_sets[set]
+// when given, its bins at set * nbins of the outputs.
+__global__ void rotation_curve_kernel(BoxSet boxes, double cx, double cy, double cz, int nbins, double rmax,
+                                      const double* __restrict__ rmax_sets, int nphi, double frac,
+                                      double* __restrict__ r_out, double* __restrict__ vc_out)
 {
     __shared__ double dphidr[kMaxPhi];
+    const int set = blockIdx.y;
+    if (rmax_sets) rmax = rmax_sets[set];
+    r_out += set * (long long)nbins;
+    vc_out += set * (long long)nbins;
     const int kb = blockIdx.x;
     const double R = ((double)kb + 0.5) * rmax / (double)nbins;
     int b0 = 0;
@@ -403,7 +432,7 @@ __global__ void rotation_curve_kernel(BoxSet boxes, double cx, double cy, double
             int ijk[3];
             double d[3];
             if (find_cell(boxes.b[b], boxes.n, x, y, z, ijk, d)) {
-                grad_at(boxes.b[b], boxes.n, ijk, d, g);
+                grad_at(boxes.b[b], boxes.n, ijk, d, g, set);
                 break;
             }
         }
@@ -430,6 +459,9 @@ __global__ void profile_kernel(BoxSet boxes, double cx, double cy, double cz, in
                                double* __restrict__ out)
 {
     __shared__ double val[kMaxPhi];
+    const int set = blockIdx.y;  // one row of blocks per set
+    r_out += set * (long long)nbins;
+    out += set * (long long)nbins;
     const int kb = blockIdx.x;
     const double R = ((double)kb + 0.5) * rmax / (double)nbins;
     int b0 = 0;
@@ -448,7 +480,7 @@ __global__ void profile_kernel(BoxSet boxes, double cx, double cy, double cz, in
             int ijk[3];
             double d[3];
             if (find_cell(boxes.b[b], boxes.n, cx + R * c, cy + R * s, zt, ijk, d)) {
-                grad_at(boxes.b[b], boxes.n, ijk, d, g);
+                grad_at(boxes.b[b], boxes.n, ijk, d, g, set);
                 break;
             }
         }
@@ -476,11 +508,11 @@ __global__ void profile_kernel(BoxSet boxes, double cx, double cy, double cz, in
 // --- launchers ----------------------------------------------------------------
 void launch_cic_deposit(const double* x, const double* y, const double* z, const double* m, long long np, int n,
                         double xlo, double ylo, double zlo, double inv_h, double two_shift, int64_t* q,
-                        cudaStream_t s)
+                        cudaStream_t s, int nsets)
 {
     if (np <= 0) return;
-    cic_deposit_kernel<<<cdiv(np, 256), 256, 0, s>>>(x, y, z, m, np, n, xlo, ylo, zlo, inv_h, two_shift,
-                                                      reinterpret_cast<unsigned long long*>(q));
+    cic_deposit_kernel<<<dim3(cdiv(np, 256), (unsigned)nsets), 256, 0, s>>>(
+        x, y, z, m, np, n, xlo, ylo, zlo, inv_h, two_shift, reinterpret_cast<unsigned long long*>(q));
 }
 
 void launch_fixed_to_rho(const int64_t* q, double* rho, long long count, double scale, cudaStream_t s)
@@ -488,40 +520,46 @@ void launch_fixed_to_rho(const int64_t* q, double* rho, long long count, double 
     fixed_to_rho_kernel<<<cdiv(count, 256), 256, 0, s>>>(reinterpret_cast<const long long*>(q), rho, count, scale);
 }
 
-void launch_boundary_zero(double* u, int n, cudaStream_t s)
+void launch_boundary_zero(double* u, int n, cudaStream_t s, int nsets)
 {
-    boundary_zero_kernel<<<dim3(cdiv(n + 1, 128), (unsigned)(n + 1), 6), 128, 0, s>>>(u, n);
+    boundary_zero_kernel<<<dim3(cdiv(n + 1, 128), (unsigned)(n + 1), 6 * (unsigned)nsets), 128, 0, s>>>(u, n);
 }
 
-void launch_boundary_from_parent(const double* parent, double* u, int n, int ratio, cudaStream_t s)
+void launch_boundary_from_parent(const double* parent, double* u, int n, int ratio, cudaStream_t s, int nsets)
 {
-    boundary_from_parent_kernel<<<dim3(cdiv(n + 1, 128), (unsigned)(n + 1), 6), 128, 0, s>>>(parent, u, n, ratio);
+    boundary_from_parent_kernel<<<dim3(cdiv(n + 1, 128), (unsigned)(n + 1), 6 * (unsigned)nsets), 128, 0, s>>>(
+        parent, u, n, ratio);
 }
 
-void launch_source(const double* phi, double* src, int n, double h, double a0, cudaStream_t s)
+void launch_source(const double* phi, double* src, int n, double h, double a0, cudaStream_t s, int nsets)
 {
-    const dim3 grid(cdiv(n + 1, kSrcTX), cdiv(n + 1, kSrcTY), cdiv(n + 1, kSrcKC));
+    const unsigned zper = cdiv(n + 1, kSrcKC);
+    const dim3 grid(cdiv(n + 1, kSrcTX), cdiv(n + 1, kSrcTY), zper * (unsigned)nsets);
     source_kernel<<<grid, dim3(kSrcTX, kSrcTY), 0, s>>>(phi, src, n, (float)(1.0 / h), (float)(4.0 * a0),
-                                                        (float)(1.0 / (h * h)));
+                                                        (float)(1.0 / (h * h)), (int)zper);
 }
 
 void launch_forces(const BoxSet& boxes, const double* qx, const double* qy, const double* qz, long long nq,
-                   double* gx, double* gy, double* gz, cudaStream_t s)
+                   double* gx, double* gy, double* gz, cudaStream_t s, int nsets)
 {
     if (nq <= 0) return;
-    forces_kernel<<<cdiv(nq, 128), 128, 0, s>>>(boxes, qx, qy, qz, nq, gx, gy, gz);
+    forces_kernel<<<dim3(cdiv(nq, 128), (unsigned)nsets), 128, 0, s>>>(boxes, qx, qy, qz, nq, gx, gy, gz);
 }
 
-void launch_rotation_curve(const BoxSet& boxes, double cx, double cy, double cz, int nbins, double rmax, int nphi,
-                           double frac, double* r_out, double* vc_out, cudaStream_t s)
+void launch_rotation_curve(const BoxSet& boxes, double cx, double cy, double cz, int nbins, double rmax,
+                           const double* rmax_sets, int nphi, double frac, double* r_out, double* vc_out,
+                           cudaStream_t s, int nsets)
 {
-    rotation_curve_kernel<<<nbins, 128, 0, s>>>(boxes, cx, cy, cz, nbins, rmax, nphi, frac, r_out, vc_out);
+    rotation_curve_kernel<<<dim3(nbins, nsets), 128, 0, s>>>(boxes, cx, cy, cz, nbins, rmax, rmax_sets, nphi, frac,
+                                                             r_out, vc_out);
 }
 
 void launch_profile(const BoxSet& boxes, double cx, double cy, double cz, int nbins, double rmax, int nphi, double frac,
-                    int mode, double a0, double z_eval, double h, double* r_out, double* out, cudaStream_t s)
+                    int mode, double a0, double z_eval, double h, double* r_out, double* out, cudaStream_t s,
+                    int nsets)
 {
-    profile_kernel<<<nbins, 128, 0, s>>>(boxes, cx, cy, cz, nbins, rmax, nphi, frac, mode, a0, z_eval, h, r_out, out);
+    profile_kernel<<<dim3(nbins, nsets), 128, 0, s>>>(boxes, cx, cy, cz, nbins, rmax, nphi, frac, mode, a0, z_eval, h,
+                                                      r_out, out);
 }
 
 // Quality of fit (Section 3.5): chi2[s] = (1/nbins) sum_i ((vc[s][i] - v_obs[i]) / sigma[i])^2.

@@ -46,17 +46,34 @@ __device__ __forceinline__ void rb_node(T* __restrict__ own, const T* __restrict
     own[row + m] = (s - h2 * f[row + m]) * sixth;
 }
 
+// The set index of a context with several sets, folded into blockIdx.z
+// (per planes per set): returns it and the plane index within the set.
+__device__ __forceinline__ int set_of(int per, int& within)
+{
+    if ((int)gridDim.z == per) {  // one set: no division
+        within = (int)blockIdx.z;
+        return 0;
+    }
+    const int s = (int)blockIdx.z / per;
+    within = (int)blockIdx.z - s * per;
+    return s;
+}
+
 template <typename T, bool ZERO>
 __global__ void __launch_bounds__(kBX * kBY)
 rb_half_kernel(T* __restrict__ own, const T* __restrict__ other, const T* __restrict__ f, LevelView v, int colour,
-               T h2, T sixth)
+               T h2, T sixth, const SolveState* __restrict__ act)
 {
+    int kz;
+    const int set = set_of(v.n - 1, kz);
+    if (act && !act[set].cont) return;
+    const long long so = (long long)set * 2 * v.cs;
     const int half = v.n >> 1;
     const int m = blockIdx.x * kBX + threadIdx.x;
     const int j = blockIdx.y * kBY + threadIdx.y + 1;
-    const int k = blockIdx.z + 1;
+    const int k = kz + 1;
     if (m >= half || j >= v.n) return;
-    rb_node<T, ZERO>(own, other, f, v, colour, h2, sixth, m, j, k);
+    rb_node<T, ZERO>(own + so, other + so, f + so, v, colour, h2, sixth, m, j, k);
 }
 
 // The same half-sweep on FP32 levels with four consecutive entries of a row
@@ -67,17 +84,31 @@ rb_half_kernel(T* __restrict__ own, const T* __restrict__ other, const T* __rest
 // outside the row's entries; the scalar before entry 0 (read from the padding
 // at the end of the previous row) only feeds the boundary node i = 0, which
 // is not written.
-constexpr int kVX = 8, kVY = 16;  // threads: 32 entries x 16 rows per block
+// Block shapes: VX threads along a row (4 VX entries) x 128/VX rows.  The
+// default 8 x 16 suits large levels; the small levels (n/2 = 8 .. 32 entries
+// per row) leave most of an 8-wide block idle, so a context can pick 4 x 32 or
+// 2 x 64 for levels n <= 64 (params.tile_small).  Every shape gives the same
+// bits: each thread's entries are updated by the same arithmetic.
+constexpr int kVX = 8, kVY = 16;  // default: 32 entries x 16 rows per block
+constexpr int kVThreads = 128;
+constexpr int kTileSmallN = 64;  // the alternative shapes apply to levels with n <= this
 
-template <bool ZERO>
-__global__ void __launch_bounds__(kVX * kVY)
+template <bool ZERO, int VX = kVX>
+__global__ void __launch_bounds__(kVThreads)
 rb_half4_kernel(float* __restrict__ own, const float* __restrict__ other, const float* __restrict__ f, LevelView v,
-                int colour, float h2, float sixth)
+                int colour, float h2, float sixth, const SolveState* __restrict__ act)
 {
+    int kz;
+    const int set = set_of(v.n - 1, kz);
+    if (act && !act[set].cont) return;
+    {
+        const long long so = (long long)set * 2 * v.cs;
+        own += so, other += so, f += so;
+    }
     const int half = v.n >> 1;
-    const int mA = 4 * (blockIdx.x * kVX + threadIdx.x);
-    const int j = blockIdx.y * kVY + threadIdx.y + 1;
-    const int k = blockIdx.z + 1;
+    const int mA = 4 * (blockIdx.x * VX + threadIdx.x);
+    const int j = blockIdx.y * (kVThreads / VX) + threadIdx.y + 1;
+    const int k = kz + 1;
     if (mA >= half || j >= v.n) return;
     const int p = (colour + j + k) & 1;
     const long long row = ((long long)k * (v.n + 1) + j) * v.M;
@@ -145,13 +176,17 @@ __device__ __forceinline__ void restrict_node(const T* __restrict__ ef, const T*
 template <typename T>
 __global__ void __launch_bounds__(kBX * kBY)
 restrict_resid_red_kernel(const T* __restrict__ ef, const T* __restrict__ ff, LevelView vf, T* __restrict__ fc,
-                          LevelView vc, T ih2)
+                          LevelView vc, T ih2, const SolveState* __restrict__ act)
 {
+    int kz;
+    const int set = set_of(vc.n - 1, kz);
+    if (act && !act[set].cont) return;
+    const long long sf = (long long)set * 2 * vf.cs, sc = (long long)set * 2 * vc.cs;
     const int I = blockIdx.x * kBX + threadIdx.x + 1;
     const int J = blockIdx.y * kBY + threadIdx.y + 1;
-    const int K = blockIdx.z + 1;
+    const int K = kz + 1;
     if (I >= vc.n || J >= vc.n) return;
-    restrict_node<T>(ef, ff, vf, fc, vc, ih2, I, J, K);
+    restrict_node<T>(ef + sf, ff + sf, vf, fc + sc, vc, ih2, I, J, K);
 }
 
 // The same restriction on FP32 levels without recomputation: a CTA owns a
@@ -172,11 +207,19 @@ static_assert(kRR * kRG <= kRI * kRJ, "one thread per residual group");
 
 __global__ void __launch_bounds__(kRI * kRJ)
 restrict_resid4_kernel(const float* __restrict__ ef, const float* __restrict__ ff, LevelView vf,
-                       float* __restrict__ fc, LevelView vc, float ih2, int rk)
+                       float* __restrict__ fc, LevelView vc, float ih2, int rk, int zper,
+                       const SolveState* __restrict__ act)
 {
     __shared__ __align__(16) float ring[3][kRR][kRG * 4];
+    int kz;
+    const int set = set_of(zper, kz);
+    if (act && !act[set].cont) return;
+    {
+        const long long sf = (long long)set * 2 * vf.cs;
+        ef += sf, ff += sf, fc += (long long)set * 2 * vc.cs;
+    }
     const int n = vf.n, nc = vc.n;
-    const int I0 = 1 + blockIdx.x * kRI, J0 = 1 + blockIdx.y * kRJ, K0 = 1 + blockIdx.z * rk;
+    const int I0 = 1 + blockIdx.x * kRI, J0 = 1 + blockIdx.y * kRJ, K0 = 1 + kz * rk;
     const int K1 = min(K0 + rk, nc);  // coarse planes K0 .. K1-1
     const int t = threadIdx.x;
     const int mbase = I0 - 1;          // a multiple of 32: the groups start on 16-byte boundaries
@@ -251,14 +294,20 @@ restrict_resid4_kernel(const float* __restrict__ ef, const float* __restrict__ f
 // (entries mA/2 .. mA/2+2 and mA/2 .. mA/2+1), read with 8-byte loads; the
 // sums are prolong_node's, in its order, and the fine row is read and
 // written with 16-byte accesses.
-template <bool ADD>
-__global__ void __launch_bounds__(kVX * kVY)
-prolong_black4_kernel(const float* __restrict__ ec, LevelView vc, float* __restrict__ ef, LevelView vf)
+template <bool ADD, int VX = kVX>
+__global__ void __launch_bounds__(kVThreads)
+prolong_black4_kernel(const float* __restrict__ ec, LevelView vc, float* __restrict__ ef, LevelView vf,
+                      const SolveState* __restrict__ act)
 {
+    int kz;
+    const int set = set_of(vf.n - 1, kz);
+    if (act && !act[set].cont) return;
+    ec += (long long)set * 2 * vc.cs;
+    ef += (long long)set * 2 * vf.cs;
     const int half = vf.n >> 1;
-    const int mA = 4 * (blockIdx.x * kVX + threadIdx.x);
-    const int j = blockIdx.y * kVY + threadIdx.y + 1;
-    const int k = blockIdx.z + 1;
+    const int mA = 4 * (blockIdx.x * VX + threadIdx.x);
+    const int j = blockIdx.y * (kVThreads / VX) + threadIdx.y + 1;
+    const int k = kz + 1;
     if (mA >= half || j >= vf.n) return;
     const int p = (1 + j + k) & 1;  // parity of i of the black nodes in this row
     const int J0 = j >> 1, J1 = (j + 1) >> 1, K0 = k >> 1, K1 = (k + 1) >> 1;
@@ -306,9 +355,13 @@ template <typename T>
 __global__ void __launch_bounds__(kBX * kBY)
 restrict_full_kernel(const T* __restrict__ ff, LevelView vf, T* __restrict__ fc, LevelView vc)
 {
+    int kz;
+    const int set = set_of(vc.n - 1, kz);
+    ff += (long long)set * 2 * vf.cs;
+    fc += (long long)set * 2 * vc.cs;
     const int I = blockIdx.x * kBX + threadIdx.x + 1;
     const int J = blockIdx.y * kBY + threadIdx.y + 1;
-    const int K = blockIdx.z + 1;
+    const int K = kz + 1;
     if (I >= vc.n || J >= vc.n) return;
     const T w[3] = {T(0.25), T(0.5), T(0.25)};
     T acc = T(0);
@@ -340,14 +393,18 @@ __device__ __forceinline__ void prolong_node(const T* __restrict__ ec, const Lev
 
 template <typename T, bool ADD>
 __global__ void __launch_bounds__(kBX * kBY)
-prolong_black_kernel(const T* __restrict__ ec, LevelView vc, T* __restrict__ ef, LevelView vf)
+prolong_black_kernel(const T* __restrict__ ec, LevelView vc, T* __restrict__ ef, LevelView vf,
+                     const SolveState* __restrict__ act)
 {
+    int kz;
+    const int set = set_of(vf.n - 1, kz);
+    if (act && !act[set].cont) return;
     const int half = vf.n >> 1;
     const int m = blockIdx.x * kBX + threadIdx.x;
     const int j = blockIdx.y * kBY + threadIdx.y + 1;
-    const int k = blockIdx.z + 1;
+    const int k = kz + 1;
     if (m >= half || j >= vf.n) return;
-    prolong_node<T, ADD>(ec, vc, ef, vf, m, j, k);
+    prolong_node<T, ADD>(ec + (long long)set * 2 * vc.cs, vc, ef + (long long)set * 2 * vf.cs, vf, m, j, k);
 }
 
 // Boundary nodes of a level <- the finest boundary values at the same
@@ -367,11 +424,15 @@ __device__ __forceinline__ void face_node(int face, int a, int b, int n, int& i,
 template <typename T>
 __global__ void set_boundary_kernel(T* __restrict__ e, LevelView v, const double* __restrict__ u64, int nfine)
 {
+    int face;
+    const int set = set_of(6, face);
+    e += (long long)set * 2 * v.cs;
+    if (u64) u64 += set * nat_elems(nfine);
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = blockIdx.y;
     if (a > v.n) return;
     int i, j, k;
-    face_node(blockIdx.z, a, b, v.n, i, j, k);
+    face_node(face, a, b, v.n, i, j, k);
     T val = T(0);
     if (u64) {
         const int s = nfine / v.n;
@@ -602,10 +663,14 @@ __device__ void coarse_run(unsigned char* smem_raw, int fmg, T* __restrict__ e, 
 template <typename T, int TOP>
 __global__ void __launch_bounds__(kCoarseThreads)
 coarse_kernel(int fmg, T* __restrict__ e, const T* __restrict__ f, LevelView v, T htop, const double* __restrict__ u64,
-              int nfine, int ncycle, int npre, int npost)
+              int nfine, int ncycle, int npre, int npost, const SolveState* __restrict__ act)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    coarse_run<T, TOP>(smem_raw, fmg, e, f, v, htop, u64, nfine, ncycle, npre, npost);
+    const int set = blockIdx.x;  // one CTA per set
+    if (act && !act[set].cont) return;
+    const long long so = (long long)set * 2 * v.cs;
+    coarse_run<T, TOP>(smem_raw, fmg, e + so, f + so, v, htop, u64 ? u64 + set * nat_elems(nfine) : nullptr, nfine,
+                       ncycle, npre, npost);
 }
 
 // ---------------------------------------------------------------------------
@@ -757,20 +822,26 @@ __device__ __forceinline__ long long nat(int n, int i, int j, int k)
 template <typename T>
 __global__ void convert_rhs_kernel(const double* __restrict__ rhs, double coef, int n, T* __restrict__ f, LevelView v)
 {
+    int kz;
+    const int set = set_of(n - 1, kz);
     const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-    const int j = blockIdx.y + 1, k = blockIdx.z + 1;
+    const int j = blockIdx.y + 1, k = kz + 1;
     if (i >= n) return;
-    f[node_off(v, i, j, k)] = (T)(coef * rhs[nat(n, i, j, k)]);
+    f[set * 2 * v.cs + node_off(v, i, j, k)] = (T)(coef * rhs[set * nat_elems(n) + nat(n, i, j, k)]);
 }
 
 template <typename T, bool ADD>
-__global__ void assign_outer_kernel(double* __restrict__ u, int n, const T* __restrict__ e, LevelView v)
+__global__ void assign_outer_kernel(double* __restrict__ u, int n, const T* __restrict__ e, LevelView v,
+                                    const SolveState* __restrict__ act)
 {
+    int kz;
+    const int set = set_of(n - 1, kz);
+    if (act && !act[set].cont) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-    const int j = blockIdx.y + 1, k = blockIdx.z + 1;
+    const int j = blockIdx.y + 1, k = kz + 1;
     if (i >= n) return;
-    const long long o = nat(n, i, j, k);
-    const double d = (double)e[node_off(v, i, j, k)];
+    const long long o = set * nat_elems(n) + nat(n, i, j, k);
+    const double d = (double)e[set * 2 * v.cs + node_off(v, i, j, k)];
     u[o] = ADD ? u[o] + d : d;
 }
 
@@ -829,8 +900,15 @@ constexpr int kRowThreads = 128;
 template <typename T>
 __global__ void __launch_bounds__(kRowThreads)
 residual_rows_kernel(const double* __restrict__ u, const double* __restrict__ rhs, double coef, int n, double ih2,
-                     T* __restrict__ r, LevelView v, double* __restrict__ partials)
+                     T* __restrict__ r, LevelView v, double* __restrict__ partials, long long pstride,
+                     const SolveState* __restrict__ act)
 {
+    const int set = blockIdx.y;  // one row of blocks per set
+    if (act && !act[set].cont) return;
+    u += set * nat_elems(n);
+    rhs += set * nat_elems(n);
+    r += set * 2 * v.cs;
+    partials += set * pstride;
     const long long P = n + 1, Q = P * P;
     const int rows = (n - 1) * (n - 1);
     double rr = 0.0, ff = 0.0;
@@ -900,11 +978,19 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_norms_kernel(const doub
 // finite.  first: this is the residual after FMG (sets the denominator
 // ||coef*rhs||, or 1 when it is 0, and it = 0).  Inside a graph the decision
 // drives the WHILE node through `handle`.
+//
+// Several sets (fault == NULL): block s decides for set s; a set whose
+// correction has already stopped keeps its state; decide_any_kernel then
+// takes over the fault flag and drives the WHILE node.
 template <bool GRAPH>
 __global__ void __launch_bounds__(kReduceThreads)
 decide_kernel(const double* __restrict__ partials, int nblocks, SolveState* __restrict__ st, double tol, int max_it,
-              int first, int refine, cudaGraphConditionalHandle handle, int* __restrict__ fault)
+              int first, int refine, cudaGraphConditionalHandle handle, int* __restrict__ fault, long long pstride)
 {
+    const int set = blockIdx.x;
+    partials += set * pstride;
+    st += set;
+    if (!fault && !first && st->cont == 0) return;
     double a = 0.0, b = 0.0;
     for (int t = threadIdx.x; t < nblocks; t += kReduceThreads) {
         a += partials[2 * t];
@@ -952,8 +1038,29 @@ decide_kernel(const double* __restrict__ partials, int nblocks, SolveState* __re
         st->converged = (finite && !st->fault && (!refine || rel <= tol)) ? 1 : 0;
         const int cont = (refine && finite && !st->fault && rel > tol && st->it < max_it) ? 1 : 0;
         st->cont = cont;
-        if (GRAPH) cudaGraphSetConditional(handle, (unsigned)cont);
+        if (GRAPH && fault) cudaGraphSetConditional(handle, (unsigned)cont);
     }
+}
+
+// After the per-set decisions: a fault recorded since the last check stops
+// every set; the loop goes on while any set goes on.
+template <bool GRAPH>
+__global__ void decide_any_kernel(SolveState* __restrict__ st, int nsets, int first, cudaGraphConditionalHandle handle,
+                                  int* __restrict__ fault)
+{
+    if (threadIdx.x != 0) return;
+    const int faulted = *fault;
+    if (faulted) *fault = 0;
+    unsigned any = 0;
+    for (int q = 0; q < nsets; ++q) {
+        if (faulted) {
+            st[q].fault = 1;
+            st[q].converged = 0;
+            st[q].cont = 0;
+        }
+        any |= (unsigned)st[q].cont;
+    }
+    if (GRAPH) cudaGraphSetConditional(handle, any);
 }
 
 inline dim3 half_grid(int n) { return dim3(cdiv(n / 2, kBX), cdiv(n - 1, kBY), (unsigned)(n - 1)); }
@@ -971,33 +1078,55 @@ size_t coarse_smem_bytes(int n)
 }  // namespace
 
 // --- launchers ------------------------------------------------------------
+// With several sets every grid's z extent (or, for the per-set kernels, its x
+// or y extent) is multiplied by the number of sets; the qumond_create checks
+// keep the products within the launch limits.
+inline dim3 per_sets(dim3 g, const Sets& sets) { return dim3(g.x, g.y, g.z * (unsigned)sets.n); }
+
+// threads along a row of the row-vector kernels on a level of n intervals
+inline int vx_of(int n, const Sets& sets)
+{
+    if (n > kTileSmallN) return kVX;
+    return sets.tile_small == 1 ? 4 : (sets.tile_small == 2 ? 2 : kVX);
+}
+
 template <typename T>
-void launch_rb_half(T* e, const T* f, const LevelView& v, int colour, bool zero_guess, double h, cudaStream_t s)
+void launch_rb_half(T* e, const T* f, const LevelView& v, int colour, bool zero_guess, double h, cudaStream_t s,
+                    const Sets& sets)
 {
     T* own = e + (long long)colour * v.cs;
     const T* other = e + (long long)(colour ^ 1) * v.cs;
     const T* fc = f + (long long)colour * v.cs;
     const dim3 blk(kBX, kBY);
     if (sizeof(T) == sizeof(float) && v.n >= 8) {
-        const dim3 grid(cdiv(v.n / 2, 4 * kVX), cdiv(v.n - 1, kVY), (unsigned)(v.n - 1));
         float* o4 = reinterpret_cast<float*>(own);
         const float* x4 = reinterpret_cast<const float*>(other);
         const float* f4 = reinterpret_cast<const float*>(fc);
-        if (zero_guess)
-            rb_half4_kernel<true><<<grid, dim3(kVX, kVY), 0, s>>>(o4, x4, f4, v, colour, (float)(h * h), 1.0f / 6.0f);
-        else
-            rb_half4_kernel<false><<<grid, dim3(kVX, kVY), 0, s>>>(o4, x4, f4, v, colour, (float)(h * h), 1.0f / 6.0f);
+        const int vx = vx_of(v.n, sets);
+        const dim3 grid(cdiv(v.n / 2, 4 * vx), cdiv(v.n - 1, kVThreads / vx), (unsigned)(v.n - 1) * (unsigned)sets.n);
+        const dim3 blk(vx, kVThreads / vx);
+        const float h2 = (float)(h * h), sixth = 1.0f / 6.0f;
+        switch ((zero_guess ? 8 : 0) + vx) {
+        case 8 + 8: rb_half4_kernel<true, 8><<<grid, blk, 0, s>>>(o4, x4, f4, v, colour, h2, sixth, sets.act); break;
+        case 8 + 4: rb_half4_kernel<true, 4><<<grid, blk, 0, s>>>(o4, x4, f4, v, colour, h2, sixth, sets.act); break;
+        case 8 + 2: rb_half4_kernel<true, 2><<<grid, blk, 0, s>>>(o4, x4, f4, v, colour, h2, sixth, sets.act); break;
+        case 8: rb_half4_kernel<false, 8><<<grid, blk, 0, s>>>(o4, x4, f4, v, colour, h2, sixth, sets.act); break;
+        case 4: rb_half4_kernel<false, 4><<<grid, blk, 0, s>>>(o4, x4, f4, v, colour, h2, sixth, sets.act); break;
+        default: rb_half4_kernel<false, 2><<<grid, blk, 0, s>>>(o4, x4, f4, v, colour, h2, sixth, sets.act); break;
+        }
         return;
     }
     if (zero_guess)
-        rb_half_kernel<T, true><<<half_grid(v.n), blk, 0, s>>>(own, other, fc, v, colour, (T)(h * h), T(1) / T(6));
+        rb_half_kernel<T, true><<<per_sets(half_grid(v.n), sets), blk, 0, s>>>(own, other, fc, v, colour, (T)(h * h),
+                                                                                T(1) / T(6), sets.act);
     else
-        rb_half_kernel<T, false><<<half_grid(v.n), blk, 0, s>>>(own, other, fc, v, colour, (T)(h * h), T(1) / T(6));
+        rb_half_kernel<T, false><<<per_sets(half_grid(v.n), sets), blk, 0, s>>>(own, other, fc, v, colour, (T)(h * h),
+                                                                                 T(1) / T(6), sets.act);
 }
 
 template <typename T>
 void launch_restrict_resid_red(const T* ef, const T* ff, const LevelView& vf, T* fc, const LevelView& vc, double hf,
-                               cudaStream_t s)
+                               cudaStream_t s, const Sets& sets)
 {
     if (sizeof(T) == sizeof(float) && vf.n >= 128) {
         // planes per CTA: as many as keep about two CTAs per multiprocessor busy
@@ -1007,60 +1136,75 @@ void launch_restrict_resid_red(const T* ef, const T* ff, const LevelView& vf, T*
             cudaGetDevice(&dev);
             if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
         }
-        const int tiles = (int)(cdiv(vc.n - 1, kRI) * cdiv(vc.n - 1, kRJ));
+        const int tiles = (int)(cdiv(vc.n - 1, kRI) * cdiv(vc.n - 1, kRJ)) * sets.n;
         int rk = kRK;
         while (rk > 1 && tiles * (int)cdiv(vc.n - 1, rk) < 2 * sms) --rk;
-        const dim3 grid(cdiv(vc.n - 1, kRI), cdiv(vc.n - 1, kRJ), cdiv(vc.n - 1, rk));
+        const int zper = (int)cdiv(vc.n - 1, rk);
+        const dim3 grid(cdiv(vc.n - 1, kRI), cdiv(vc.n - 1, kRJ), (unsigned)(zper * sets.n));
         restrict_resid4_kernel<<<grid, kRI * kRJ, 0, s>>>(reinterpret_cast<const float*>(ef),
                                                            reinterpret_cast<const float*>(ff), vf,
                                                            reinterpret_cast<float*>(fc), vc, (float)(1.0 / (hf * hf)),
-                                                           rk);
+                                                           rk, zper, sets.act);
         return;
     }
-    restrict_resid_red_kernel<T><<<inner_grid(vc.n), dim3(kBX, kBY), 0, s>>>(ef, ff, vf, fc, vc, (T)(1.0 / (hf * hf)));
+    restrict_resid_red_kernel<T><<<per_sets(inner_grid(vc.n), sets), dim3(kBX, kBY), 0, s>>>(
+        ef, ff, vf, fc, vc, (T)(1.0 / (hf * hf)), sets.act);
 }
 
 template <typename T>
-void launch_restrict_full(const T* ff, const LevelView& vf, T* fc, const LevelView& vc, cudaStream_t s)
+void launch_restrict_full(const T* ff, const LevelView& vf, T* fc, const LevelView& vc, cudaStream_t s,
+                          const Sets& sets)
 {
-    restrict_full_kernel<T><<<inner_grid(vc.n), dim3(kBX, kBY), 0, s>>>(ff, vf, fc, vc);
+    restrict_full_kernel<T><<<per_sets(inner_grid(vc.n), sets), dim3(kBX, kBY), 0, s>>>(ff, vf, fc, vc);
 }
 
 template <typename T>
-void launch_prolong_black(const T* ec, const LevelView& vc, T* ef, const LevelView& vf, bool add, cudaStream_t s)
+void launch_prolong_black(const T* ec, const LevelView& vc, T* ef, const LevelView& vf, bool add, cudaStream_t s,
+                          const Sets& sets)
 {
     if (sizeof(T) == sizeof(float) && vf.n >= 8) {
-        const dim3 grid(cdiv(vf.n / 2, 4 * kVX), cdiv(vf.n - 1, kVY), (unsigned)(vf.n - 1));
         const float* c4 = reinterpret_cast<const float*>(ec);
         float* f4 = reinterpret_cast<float*>(ef);
-        if (add)
-            prolong_black4_kernel<true><<<grid, dim3(kVX, kVY), 0, s>>>(c4, vc, f4, vf);
-        else
-            prolong_black4_kernel<false><<<grid, dim3(kVX, kVY), 0, s>>>(c4, vc, f4, vf);
+        const int vx = vx_of(vf.n, sets);
+        const dim3 grid(cdiv(vf.n / 2, 4 * vx), cdiv(vf.n - 1, kVThreads / vx), (unsigned)(vf.n - 1) * (unsigned)sets.n);
+        const dim3 blk(vx, kVThreads / vx);
+        switch ((add ? 8 : 0) + vx) {
+        case 8 + 8: prolong_black4_kernel<true, 8><<<grid, blk, 0, s>>>(c4, vc, f4, vf, sets.act); break;
+        case 8 + 4: prolong_black4_kernel<true, 4><<<grid, blk, 0, s>>>(c4, vc, f4, vf, sets.act); break;
+        case 8 + 2: prolong_black4_kernel<true, 2><<<grid, blk, 0, s>>>(c4, vc, f4, vf, sets.act); break;
+        case 8: prolong_black4_kernel<false, 8><<<grid, blk, 0, s>>>(c4, vc, f4, vf, sets.act); break;
+        case 4: prolong_black4_kernel<false, 4><<<grid, blk, 0, s>>>(c4, vc, f4, vf, sets.act); break;
+        default: prolong_black4_kernel<false, 2><<<grid, blk, 0, s>>>(c4, vc, f4, vf, sets.act); break;
+        }
         return;
     }
     if (add)
-        prolong_black_kernel<T, true><<<half_grid(vf.n), dim3(kBX, kBY), 0, s>>>(ec, vc, ef, vf);
+        prolong_black_kernel<T, true><<<per_sets(half_grid(vf.n), sets), dim3(kBX, kBY), 0, s>>>(ec, vc, ef, vf,
+                                                                                                  sets.act);
     else
-        prolong_black_kernel<T, false><<<half_grid(vf.n), dim3(kBX, kBY), 0, s>>>(ec, vc, ef, vf);
+        prolong_black_kernel<T, false><<<per_sets(half_grid(vf.n), sets), dim3(kBX, kBY), 0, s>>>(ec, vc, ef, vf,
+                                                                                                   sets.act);
 }
 
 template <typename T>
-void launch_set_boundary(T* e, const LevelView& v, const double* u64, int nfine, cudaStream_t s)
+void launch_set_boundary(T* e, const LevelView& v, const double* u64, int nfine, cudaStream_t s, const Sets& sets)
 {
-    set_boundary_kernel<T><<<dim3(cdiv(v.n + 1, 128), (unsigned)(v.n + 1), 6), 128, 0, s>>>(e, v, u64, nfine);
+    set_boundary_kernel<T><<<dim3(cdiv(v.n + 1, 128), (unsigned)(v.n + 1), 6 * (unsigned)sets.n), 128, 0, s>>>(
+        e, v, u64, nfine);
 }
 
 template <typename T>
 cudaError_t launch_coarse(int fmg, T* e, const T* f, const LevelView& v, double h, const double* u64, int nfine,
-                          int ncycle, int npre, int npost, cudaStream_t s)
+                          int ncycle, int npre, int npost, cudaStream_t s, const Sets& sets)
 {
     const size_t bytes = coarse_smem_bytes<T>(v.n);
+    const unsigned g = (unsigned)sets.n;  // one CTA per set
+    const SolveState* act = sets.act;
     switch (v.n) {
-    case 2: coarse_kernel<T, 0><<<1, kCoarseThreads, bytes, s>>>(fmg, e, f, v, (T)h, u64, nfine, ncycle, npre, npost); break;
-    case 4: coarse_kernel<T, 1><<<1, kCoarseThreads, bytes, s>>>(fmg, e, f, v, (T)h, u64, nfine, ncycle, npre, npost); break;
-    case 8: coarse_kernel<T, 2><<<1, kCoarseThreads, bytes, s>>>(fmg, e, f, v, (T)h, u64, nfine, ncycle, npre, npost); break;
-    case 16: coarse_kernel<T, 3><<<1, kCoarseThreads, bytes, s>>>(fmg, e, f, v, (T)h, u64, nfine, ncycle, npre, npost); break;
+    case 2: coarse_kernel<T, 0><<<g, kCoarseThreads, bytes, s>>>(fmg, e, f, v, (T)h, u64, nfine, ncycle, npre, npost, act); break;
+    case 4: coarse_kernel<T, 1><<<g, kCoarseThreads, bytes, s>>>(fmg, e, f, v, (T)h, u64, nfine, ncycle, npre, npost, act); break;
+    case 8: coarse_kernel<T, 2><<<g, kCoarseThreads, bytes, s>>>(fmg, e, f, v, (T)h, u64, nfine, ncycle, npre, npost, act); break;
+    case 16: coarse_kernel<T, 3><<<g, kCoarseThreads, bytes, s>>>(fmg, e, f, v, (T)h, u64, nfine, ncycle, npre, npost, act); break;
     default: return cudaErrorInvalidValue;  // the coarse solver covers the levels n = 2 .. 16
     }
     return cudaSuccess;
@@ -1102,18 +1246,19 @@ int vsub_grid(int sms)
 }
 
 template <typename T>
-void launch_convert_rhs(const double* rhs, double coef, int n, T* f, const LevelView& v, cudaStream_t s)
+void launch_convert_rhs(const double* rhs, double coef, int n, T* f, const LevelView& v, cudaStream_t s,
+                        const Sets& sets)
 {
-    convert_rhs_kernel<T><<<outer_grid(n), kOuterThreads, 0, s>>>(rhs, coef, n, f, v);
+    convert_rhs_kernel<T><<<per_sets(outer_grid(n), sets), kOuterThreads, 0, s>>>(rhs, coef, n, f, v);
 }
 
 template <typename T>
-void launch_assign_outer(double* u, int n, const T* e, const LevelView& v, bool add, cudaStream_t s)
+void launch_assign_outer(double* u, int n, const T* e, const LevelView& v, bool add, cudaStream_t s, const Sets& sets)
 {
     if (add)
-        assign_outer_kernel<T, true><<<outer_grid(n), kOuterThreads, 0, s>>>(u, n, e, v);
+        assign_outer_kernel<T, true><<<per_sets(outer_grid(n), sets), kOuterThreads, 0, s>>>(u, n, e, v, sets.act);
     else
-        assign_outer_kernel<T, false><<<outer_grid(n), kOuterThreads, 0, s>>>(u, n, e, v);
+        assign_outer_kernel<T, false><<<per_sets(outer_grid(n), sets), kOuterThreads, 0, s>>>(u, n, e, v, sets.act);
 }
 
 int residual_outer_blocks(int n)
@@ -1138,21 +1283,32 @@ int residual_rows_blocks(int n)
 
 template <typename T>
 int launch_residual_rows(const double* u, const double* rhs, double coef, int n, double h, T* r, const LevelView& v,
-                         double* partials, cudaStream_t s)
+                         double* partials, cudaStream_t s, const Sets& sets)
 {
     const int nb = residual_rows_blocks(n);
-    residual_rows_kernel<T><<<nb, kRowThreads, 0, s>>>(u, rhs, coef, n, 1.0 / (h * h), r, v, partials);
+    residual_rows_kernel<T><<<dim3(nb, sets.n), kRowThreads, 0, s>>>(u, rhs, coef, n, 1.0 / (h * h), r, v, partials,
+                                                                     sets.pstride, sets.act);
     return nb;
 }
 
 void launch_decide(const double* partials, int nblocks, SolveState* st, double tol, int max_it, bool first,
-                   bool refine, const cudaGraphConditionalHandle* handle, int* fault, cudaStream_t s)
+                   bool refine, const cudaGraphConditionalHandle* handle, int* fault, cudaStream_t s, const Sets& sets)
 {
+    if (sets.n == 1) {
+        if (handle)
+            decide_kernel<true><<<1, kReduceThreads, 0, s>>>(partials, nblocks, st, tol, max_it, first, refine,
+                                                             *handle, fault, 0);
+        else
+            decide_kernel<false><<<1, kReduceThreads, 0, s>>>(partials, nblocks, st, tol, max_it, first, refine, 0,
+                                                              fault, 0);
+        return;
+    }
+    decide_kernel<false><<<sets.n, kReduceThreads, 0, s>>>(partials, nblocks, st, tol, max_it, first, refine, 0,
+                                                           nullptr, sets.pstride);
     if (handle)
-        decide_kernel<true><<<1, kReduceThreads, 0, s>>>(partials, nblocks, st, tol, max_it, first, refine, *handle,
-                                                         fault);
+        decide_any_kernel<true><<<1, 32, 0, s>>>(st, sets.n, first, *handle, fault);
     else
-        decide_kernel<false><<<1, kReduceThreads, 0, s>>>(partials, nblocks, st, tol, max_it, first, refine, 0, fault);
+        decide_any_kernel<false><<<1, 32, 0, s>>>(st, sets.n, first, 0, fault);
 }
 
 cudaError_t prepare_kernels()
@@ -1175,22 +1331,24 @@ void launch_reduce_norms(const double* partials, int nblocks, double* out, cudaS
 }
 
 #define QUMOND_INSTANTIATE(T)                                                                                          \
-    template void launch_rb_half<T>(T*, const T*, const LevelView&, int, bool, double, cudaStream_t);                 \
+    template void launch_rb_half<T>(T*, const T*, const LevelView&, int, bool, double, cudaStream_t, const Sets&);    \
     template void launch_restrict_resid_red<T>(const T*, const T*, const LevelView&, T*, const LevelView&, double,    \
-                                               cudaStream_t);                                                          \
-    template void launch_restrict_full<T>(const T*, const LevelView&, T*, const LevelView&, cudaStream_t);            \
-    template void launch_prolong_black<T>(const T*, const LevelView&, T*, const LevelView&, bool, cudaStream_t);      \
-    template void launch_set_boundary<T>(T*, const LevelView&, const double*, int, cudaStream_t);                     \
+                                               cudaStream_t, const Sets&);                                             \
+    template void launch_restrict_full<T>(const T*, const LevelView&, T*, const LevelView&, cudaStream_t,             \
+                                          const Sets&);                                                                \
+    template void launch_prolong_black<T>(const T*, const LevelView&, T*, const LevelView&, bool, cudaStream_t,       \
+                                          const Sets&);                                                                \
+    template void launch_set_boundary<T>(T*, const LevelView&, const double*, int, cudaStream_t, const Sets&);        \
     template cudaError_t launch_vsub<T>(T* const*, T* const*, const LevelView*, const double*, int, int, int, int,     \
                                         unsigned*, int*, long long, int, cudaStream_t);                               \
     template cudaError_t launch_coarse<T>(int, T*, const T*, const LevelView&, double, const double*, int, int, int,  \
-                                          int, cudaStream_t);                                                          \
-    template void launch_convert_rhs<T>(const double*, double, int, T*, const LevelView&, cudaStream_t);              \
-    template void launch_assign_outer<T>(double*, int, const T*, const LevelView&, bool, cudaStream_t);               \
+                                          int, cudaStream_t, const Sets&);                                             \
+    template void launch_convert_rhs<T>(const double*, double, int, T*, const LevelView&, cudaStream_t, const Sets&); \
+    template void launch_assign_outer<T>(double*, int, const T*, const LevelView&, bool, cudaStream_t, const Sets&);  \
     template int launch_residual_outer<T>(const double*, const double*, double, int, double, T*, const LevelView&,    \
                                           double*, cudaStream_t);                                                      \
     template int launch_residual_rows<T>(const double*, const double*, double, int, double, T*, const LevelView&,     \
-                                         double*, cudaStream_t);
+                                         double*, cudaStream_t, const Sets&);
 
 QUMOND_INSTANTIATE(float)
 QUMOND_INSTANTIATE(double)

@@ -21,6 +21,14 @@ Learned initial guess: with `guess` (a Guess for S = n) and `ctx_warm` (a
 context with warm_start = 1), the QUMOND solve of each box starts from
 Phi_N + the network's output instead of FMG (sequential order only).
 
+Far-field boundary: with bc_mode QUMOND_BC_MULTIPOLE the boundary values of
+box 0 (both potentials) come from qumond_far_field of box 0's density,
+enqueued right after its deposit.
+
+Sets: with a context of several sets (params.nsets > 1) every buffer holds
+one grid per set and the particle arrays hold every set's particles, set
+after set; each call then covers all sets.
+
 Solve timing (measurement only): when `solve_events` is a list, the
 sequential order appends one pair of CUDA timing events per solve, recorded
 on the solve's stream right before and right after the call.
@@ -35,7 +43,7 @@ import math
 
 import torch
 
-from .qumond import Context, Guess
+from .qumond import QUMOND_BC_MULTIPOLE, Context, Guess
 
 
 @dataclass
@@ -61,6 +69,7 @@ class Pipeline:
         self.guess = guess
         self.ctx_warm = ctx_warm
         self.solve_events = None
+        self.far_field = ctx.params.bc_mode == QUMOND_BC_MULTIPOLE
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         nodes = ctx.nodes
         nb = ctx.params.nboxes
@@ -101,6 +110,8 @@ class Pipeline:
 
         for b in range(c.params.nboxes):
             c.qumond_deposit(b, x, y, z, m, self.rho_fixed, self.rho, stream=stream)
+            if b == 0 and self.far_field:
+                c.qumond_far_field(self.rho, self.phiN[0], self.phi[0], stream=stream)
             par_n = self.phiN[b - 1] if b > 0 else None
             par_m = self.phi[b - 1] if b > 0 else None
             ns.append(timed(lambda: c.qumond_solve_newton(b, self.rho, par_n, self.phiN[b], stats=stats,
@@ -152,6 +163,8 @@ class Pipeline:
         try:
             for b in range(nb):
                 self.ctx.qumond_deposit(b, x, y, z, m, self.rho_fixed, self.rho, stream=sa)
+                if b == 0 and self.far_field:  # before src_done[0], which the QUMOND chain waits for
+                    self.ctx.qumond_far_field(self.rho, self.phiN[0], self.phi[0], stream=sa)
                 par = self.phiN[b - 1] if b > 0 else None
                 ns.append(self.ctx.qumond_solve_newton(b, self.rho, par, self.phiN[b], stats=stats, stream=sa))
                 self.ctx.qumond_source(b, self.phiN[b], self.srcs[b], stream=sa)
@@ -177,7 +190,7 @@ class Pipeline:
         ns, ms = self.potentials(x, y, z, m, stats=stats, stream=stream)
         if forces is not None:
             self.ctx.qumond_forces(self.phi, x, y, z, *forces, stream=stream)
-        r = torch.empty(nbins, dtype=torch.float64, device=self.device)
-        vc = torch.empty(nbins, dtype=torch.float64, device=self.device)
+        r = torch.empty(nbins * self.ctx.nsets, dtype=torch.float64, device=self.device)
+        vc = torch.empty(nbins * self.ctx.nsets, dtype=torch.float64, device=self.device)
         self.ctx.qumond_rotation_curve(self.phi, nbins, rmax, nphi, r, vc, stream=stream)
         return PipelineResult(r, vc, ns, ms)

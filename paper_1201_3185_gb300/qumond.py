@@ -33,12 +33,13 @@ QUMOND_PREC_MIXED = 1
 QUMOND_PREC_MIXED_FIXED = 2
 QUMOND_BC_ZERO = 0
 QUMOND_BC_GIVEN = 1
+QUMOND_BC_MULTIPOLE = 2
 
 EXPORTED = (
     "qumond_default_params", "qumond_create", "qumond_destroy", "qumond_last_error", "qumond_deposit",
     "qumond_solve_newton", "qumond_source", "qumond_solve_mond", "qumond_forces", "qumond_rotation_curve",
     "qumond_chi2", "qumond_rotation_curve_algebraic", "qumond_sigma_z", "qumond_trace_classes", "qumond_trace_timing", "qumond_trace_read", "qumond_solve_mond_noalloc",
-    "qumond_set_barrier_poll_limit",
+    "qumond_set_barrier_poll_limit", "qumond_rotation_curve_sets", "qumond_far_field",
     "qumond_guess_num_params", "qumond_guess_create", "qumond_guess_destroy", "qumond_guess_last_error",
     "qumond_guess_set_params", "qumond_guess_get_params", "qumond_guess_make_sample", "qumond_guess_forward",
     "qumond_guess_gradients", "qumond_guess_train_step", "qumond_guess_apply", "qumond_guess_tensor_path",
@@ -68,6 +69,8 @@ class qumond_params(ctypes.Structure):
         ("box_ratio", ctypes.c_int),
         ("use_graphs", ctypes.c_int),
         ("persistent_vcycle", ctypes.c_int),
+        ("nsets", ctypes.c_int),
+        ("tile_small", ctypes.c_int),
     ]
 
 
@@ -116,6 +119,8 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
         "qumond_solve_mond": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(qumond_stats), _P]),
         "qumond_forces": (_I, [_P, _P, _P, _P, _P, _L, _P, _P, _P, _P]),
         "qumond_rotation_curve": (_I, [_P, _P, _I, _D, _I, _P, _P, _P]),
+        "qumond_rotation_curve_sets": (_I, [_P, _P, _I, _P, _I, _P, _P, _P]),
+        "qumond_far_field": (_I, [_P, _P, _P, _P, _P]),
         "qumond_chi2": (_I, [_P, _P, _P, _P, _I, _I, _P, _P]),
         "qumond_rotation_curve_algebraic": (_I, [_P, _P, _I, _D, _I, _P, _P, _P]),
         "qumond_sigma_z": (_I, [_P, _P, _I, _D, _I, _D, _D, _P, _P, _P]),
@@ -268,8 +273,18 @@ class Context:
         return self.params.n
 
     @property
-    def nodes(self) -> int:
+    def nsets(self) -> int:
+        return max(1, self.params.nsets)
+
+    @property
+    def grid_nodes(self) -> int:
+        """Nodes of one grid, (n+1)^3."""
         return (self.params.n + 1) ** 3
+
+    @property
+    def nodes(self) -> int:
+        """Elements of a grid argument: one (n+1)^3 grid per set."""
+        return self.nsets * (self.params.n + 1) ** 3
 
     def box_side(self, box: int) -> float:
         return self.params.L0 / self.params.box_ratio ** box
@@ -284,21 +299,26 @@ class Context:
 
     # -- entry points -------------------------------------------------------------
     def qumond_deposit(self, box, x, y, z, mass, rho_fixed, rho=None, stream=None):
+        """x, y, z, mass: the particles of every set, set s's np at s*np (np = numel / nsets)."""
         npart = x.numel()
+        if npart % self.nsets:
+            raise ValueError("the particle arrays must hold the same count for every set")
         args = [_dev(a, torch.float64, npart, nm) for a, nm in ((x, "x"), (y, "y"), (z, "z"), (mass, "mass"))]
         q = _dev(rho_fixed, torch.int64, self.nodes, "rho_fixed")
         r = _dev(rho, torch.float64, self.nodes, "rho") if rho is not None else None
-        self._check(_lib.qumond_deposit(self._ptr, box, *args, npart, q, r, _stream(stream)))
+        self._check(_lib.qumond_deposit(self._ptr, box, *args, npart // self.nsets, q, r, _stream(stream)))
 
     def _solve(self, fn, box, rhs, parent, out, want_stats, stream):
         a = _dev(rhs, torch.float64, self.nodes, "rhs")
         par = _dev(parent, torch.float64, self.nodes, "parent") if parent is not None else None
         o = _dev(out, torch.float64, self.nodes, "phi")
-        st = qumond_stats()
-        status = fn(self._ptr, box, a, par, o, ctypes.byref(st) if want_stats else None, _stream(stream))
+        st = (qumond_stats * self.nsets)()
+        status = fn(self._ptr, box, a, par, o, ctypes.cast(st, ctypes.POINTER(qumond_stats)) if want_stats else None,
+                    _stream(stream))
         self._check(status)
         if want_stats:
-            return SolveStats(st.vcycles, bool(st.converged), st.rel_residual_fmg, st.rel_residual)
+            out_st = [SolveStats(x.vcycles, bool(x.converged), x.rel_residual_fmg, x.rel_residual) for x in st]
+            return out_st[0] if self.nsets == 1 else out_st
         return None
 
     def qumond_solve_newton(self, box, rho, phiN_parent, phiN, stats=False, stream=None):
@@ -312,6 +332,12 @@ class Context:
     def qumond_solve_mond(self, box, src, phi_parent, phi, stats=False, stream=None):
         return self._solve(_lib.qumond_solve_mond, box, src, phi_parent, phi, stats, stream)
 
+    def qumond_far_field(self, rho, phiN, phi, stream=None):
+        """Boundary values of box 0 from its own mass (bc_mode QUMOND_BC_MULTIPOLE)."""
+        self._check(_lib.qumond_far_field(self._ptr, _dev(rho, torch.float64, self.nodes, "rho"),
+                                          _dev(phiN, torch.float64, self.nodes, "phiN"),
+                                          _dev(phi, torch.float64, self.nodes, "phi"), _stream(stream)))
+
     def _phis(self, phis):
         if len(phis) != self.params.nboxes:
             raise ValueError("need one potential per box (%d)" % self.params.nboxes)
@@ -319,30 +345,43 @@ class Context:
         return (ctypes.c_void_p * len(ptrs))(*ptrs)
 
     def qumond_forces(self, phis, qx, qy, qz, gx, gy, gz, stream=None):
+        """Points and forces of every set, set s's nq at s*nq (nq = numel / nsets)."""
         nq = qx.numel()
+        if nq % self.nsets:
+            raise ValueError("the point arrays must hold the same count for every set")
         arr = self._phis(phis)
         pts = [_dev(a, torch.float64, nq, nm) for a, nm in ((qx, "qx"), (qy, "qy"), (qz, "qz"),
                                                              (gx, "gx"), (gy, "gy"), (gz, "gz"))]
-        self._check(_lib.qumond_forces(self._ptr, ctypes.cast(arr, _P), *pts[:3], nq, *pts[3:], _stream(stream)))
+        self._check(_lib.qumond_forces(self._ptr, ctypes.cast(arr, _P), *pts[:3], nq // self.nsets, *pts[3:],
+                                       _stream(stream)))
 
     def qumond_rotation_curve(self, phis, nbins, rmax, nphi, r_out, vc_out, stream=None):
         arr = self._phis(phis)
-        r = _dev(r_out, torch.float64, nbins, "r_out")
-        v = _dev(vc_out, torch.float64, nbins, "vc_out")
+        r = _dev(r_out, torch.float64, nbins * self.nsets, "r_out")
+        v = _dev(vc_out, torch.float64, nbins * self.nsets, "vc_out")
         self._check(_lib.qumond_rotation_curve(self._ptr, ctypes.cast(arr, _P), nbins, float(rmax), nphi, r, v,
                                                _stream(stream)))
 
+    def qumond_rotation_curve_sets(self, phis, nbins, rmax, nphi, r_out, vc_out, stream=None):
+        """Every set's curve with its own outermost radius rmax[s] (device tensor of nsets)."""
+        arr = self._phis(phis)
+        rm = _dev(rmax, torch.float64, self.nsets, "rmax")
+        r = _dev(r_out, torch.float64, nbins * self.nsets, "r_out")
+        v = _dev(vc_out, torch.float64, nbins * self.nsets, "vc_out")
+        self._check(_lib.qumond_rotation_curve_sets(self._ptr, ctypes.cast(arr, _P), nbins, rm, nphi, r, v,
+                                                    _stream(stream)))
+
     def qumond_rotation_curve_algebraic(self, phiNs, nbins, rmax, nphi, r_out, vc_out, stream=None):
         arr = self._phis(phiNs)
-        r = _dev(r_out, torch.float64, nbins, "r_out")
-        v = _dev(vc_out, torch.float64, nbins, "vc_out")
+        r = _dev(r_out, torch.float64, nbins * self.nsets, "r_out")
+        v = _dev(vc_out, torch.float64, nbins * self.nsets, "vc_out")
         self._check(_lib.qumond_rotation_curve_algebraic(self._ptr, ctypes.cast(arr, _P), nbins, float(rmax), nphi, r,
                                                          v, _stream(stream)))
 
     def qumond_sigma_z(self, phis, nbins, rmax, nphi, z_eval, h, r_out, sigma_out, stream=None):
         arr = self._phis(phis)
-        r = _dev(r_out, torch.float64, nbins, "r_out")
-        v = _dev(sigma_out, torch.float64, nbins, "sigma_out")
+        r = _dev(r_out, torch.float64, nbins * self.nsets, "r_out")
+        v = _dev(sigma_out, torch.float64, nbins * self.nsets, "sigma_out")
         self._check(_lib.qumond_sigma_z(self._ptr, ctypes.cast(arr, _P), nbins, float(rmax), nphi, float(z_eval),
                                         float(h), r, v, _stream(stream)))
 

@@ -1,7 +1,8 @@
-"""Fit sweep (Section 3.5) on the GPU: the chi^2 kernel, whole sweeps against
-the oracle set by set, independence of the worker count, and the full-size
-sweep (64 parameter sets, 129^3 x 2 boxes, 5e5 particles each) against the
-oracle-made target curve.
+"""Fit sweep (Section 3.5) on the GPU: the chi^2 kernel, contexts holding
+several sets against one-set contexts bit for bit, whole batched sweeps
+against the oracle set by set, independence of the batch size, lane count and
+block shape, and the full-size sweep (64 parameter sets, 129^3 x 2 boxes,
+5e5 particles each) against the oracle-made target curve.
 
 Tolerances: v_c 1e-5 relative (the path's stated bound).  chi^2 from curves
 that each carry that bound: with d_i = (v_i - v_obs,i)/sigma_i and
@@ -75,6 +76,78 @@ def device_sets(gal, params):
     return [tuple(to_dev(a) for a in (p.x, p.y, p.z, p.m)) for p in (gal.particles(r) for r in params)]
 
 
+@pytest.mark.parametrize("prec_name,graphs", [("MIXED_FIXED", 1), ("MIXED_FIXED", 0), ("MIXED", 1), ("FP64", 1)])
+def test_context_sets_match_one_set_contexts(q, prec_name, graphs):
+    """A context with nsets = 4: deposit, both solves of two boxes, source,
+    forces and rotation curves of all sets in one launch per kernel; every
+    set's results are the bits of a context holding that set alone, although
+    the sets need different numbers of V-cycles (the converged ones are
+    skipped)."""
+    n, L0, nbins = 64, 80000.0, 20
+    prec = getattr(q, "QUMOND_PREC_" + prec_name)
+    gal = synth.SweepGalaxy(30000, seed=15)
+    params = synth.fit_sweep_parameters(4, seed=16)
+    ps = [gal.particles(r) for r in params]
+    # the last set's particles all lie outside the boxes: its density is zero, so its solves need no V-cycle
+    # after FMG while the others need several, and the later V-cycles must skip it
+    ps[-1] = synth.Particles(ps[-1].x + 1e9, ps[-1].y, ps[-1].z, ps[-1].m)
+    kw = dict(n=n, nboxes=2, L0=L0, precision=prec, rel_tol=1e-10, max_vcycles=40, use_graphs=graphs)
+    many = q.Context(nsets=4, **kw)
+    pm = q.Pipeline(many)
+    x, y, z, m = (to_dev(np.concatenate([getattr(p, a) for p in ps])) for a in "xyzm")
+    g = tuple(torch.empty_like(x) for _ in range(3))
+    res = pm.run(x, y, z, m, nbins=nbins, rmax=20000.0, forces=g, stats=True)
+    rmax = to_dev(np.array([20000.0 * r[0] for r in params]))
+    r3 = torch.empty(4 * nbins, dtype=torch.float64, device="cuda")
+    v3 = torch.empty_like(r3)
+    many.qumond_rotation_curve_sets(pm.phi, nbins, rmax, 64, r3, v3)
+    torch.cuda.synchronize()
+    N = (n + 1) ** 3
+    npart = ps[0].n
+    vcycles = set()
+    for s, p in enumerate(ps):
+        one = q.Context(**kw)
+        p1 = q.Pipeline(one)
+        xs, ys, zs, ms = (to_dev(getattr(p, a)) for a in "xyzm")
+        gs = tuple(torch.empty_like(xs) for _ in range(3))
+        r1 = p1.run(xs, ys, zs, ms, nbins=nbins, rmax=20000.0, forces=gs, stats=True)
+        rs = torch.empty(nbins, dtype=torch.float64, device="cuda")
+        vs = torch.empty_like(rs)
+        one.qumond_rotation_curve(p1.phi, nbins, 20000.0 * params[s][0], 64, rs, vs)
+        torch.cuda.synchronize()
+        for b in range(2):
+            assert torch.equal(pm.phiN[b][s * N:(s + 1) * N], p1.phiN[b]), (s, b)
+            assert torch.equal(pm.phi[b][s * N:(s + 1) * N], p1.phi[b]), (s, b)
+            assert res.newton_stats[b][s].vcycles == r1.newton_stats[b].vcycles
+            assert res.mond_stats[b][s].vcycles == r1.mond_stats[b].vcycles
+            assert res.mond_stats[b][s].converged
+            vcycles.add(res.mond_stats[b][s].vcycles)
+        for a, c in zip(g, gs):
+            assert torch.equal(a[s * npart:(s + 1) * npart], c)
+        assert torch.equal(res.vc[s * nbins:(s + 1) * nbins], r1.vc)
+        assert torch.equal(v3[s * nbins:(s + 1) * nbins], vs)
+        assert torch.equal(r3[s * nbins:(s + 1) * nbins], rs)
+        one.close()
+    assert len(vcycles) > 1 and 0 in vcycles
+    many.close()
+
+
+def test_context_sets_invalid(q):
+    with pytest.raises(q.QumondError):
+        q.Context(n=64, nboxes=1, L0=1.0, nsets=0)
+    with pytest.raises(q.QumondError):
+        q.Context(n=1024, nboxes=1, L0=1.0, nsets=64)  # 64 x 1025 planes exceed the launch limit
+    with pytest.raises(q.QumondError):
+        q.Context(n=64, nboxes=1, L0=1.0, nsets=2, persistent_vcycle=1)
+    with pytest.raises(q.QumondError):
+        q.Context(n=64, nboxes=1, L0=1.0, tile_small=3)
+    ctx = q.Context(n=8, nboxes=1, L0=100.0, nsets=2)
+    a = torch.zeros(3 * 9 ** 3, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):  # particles not a multiple of the set count
+        ctx.qumond_deposit(0, a[:3], a[:3], a[:3], a[:3], torch.zeros(2 * 9 ** 3, dtype=torch.int64, device="cuda"))
+    ctx.close()
+
+
 @pytest.mark.parametrize("prec_name", ["MIXED_FIXED", "MIXED", "FP64"])
 def test_sweep_small_matches_oracle(q, ora, prec_name):
     n, L0, nbins, rmax = 32, 80000.0, 24, 24000.0
@@ -85,7 +158,8 @@ def test_sweep_small_matches_oracle(q, ora, prec_name):
     v_obs = 80.0 + 40.0 * rng.random(nbins)
     sigma = 0.03 * v_obs
     sets = device_sets(gal, params)
-    with q.FitSweep(sweep_params(q, n, L0, prec, 1e-10), nbins=nbins, rmax=rmax, workers=3) as sw:
+    # 7 sets in chunks of 3 on 2 lanes: the last chunk is padded
+    with q.FitSweep(sweep_params(q, n, L0, prec, 1e-10), nbins=nbins, rmax=rmax, batch=3, lanes=2) as sw:
         res = sw.run(sets, params[:, 0], to_dev(v_obs), to_dev(sigma), stats=True)
         torch.cuda.synchronize()
         vc = res.vc.cpu().numpy()
@@ -100,18 +174,21 @@ def test_sweep_small_matches_oracle(q, ora, prec_name):
         assert abs(chi2[s] - want) <= chi2_bound(v_ref, v_obs, sigma), (s, chi2[s], want)
 
 
-def test_sweep_independent_of_workers(q):
-    n, L0, nbins, rmax = 32, 80000.0, 24, 24000.0
+def test_sweep_independent_of_batch_lanes_and_tile(q):
+    n, L0, nbins, rmax = 64, 80000.0, 24, 24000.0
     gal = synth.SweepGalaxy(20000, seed=8)
     params = synth.fit_sweep_parameters(5, seed=9)
     v_obs = to_dev(np.linspace(60.0, 120.0, nbins))
     sigma = 0.03 * v_obs
     sets = device_sets(gal, params)
+    stacked = tuple(torch.cat([s[k] for s in sets]) for k in range(4))
     out = []
-    for workers in (1, 2, 5):
-        with q.FitSweep(sweep_params(q, n, L0, q.QUMOND_PREC_MIXED_FIXED, 1e-8), nbins=nbins, rmax=rmax,
-                        workers=workers) as sw:
-            res = sw.run(sets, params[:, 0], v_obs, sigma)
+    for batch, lanes, tile, parts in ((1, 1, 0, sets), (1, 2, 0, sets), (1, 5, 0, sets), (2, 2, 0, sets),
+                                      (5, 1, 0, stacked), (3, 1, 1, stacked), (4, 2, 2, sets)):
+        prm = sweep_params(q, n, L0, q.QUMOND_PREC_MIXED_FIXED, 1e-8)
+        prm.tile_small = tile
+        with q.FitSweep(prm, nbins=nbins, rmax=rmax, batch=batch, lanes=lanes) as sw:
+            res = sw.run(parts, params[:, 0], v_obs, sigma)
             torch.cuda.synchronize()
             out.append((res.vc.cpu().numpy(), res.chi2.cpu().numpy()))
     for vc, chi2 in out[1:]:
@@ -138,7 +215,8 @@ def test_sweep_full_size(q, ora):
     params = np.vstack([synth.fit_sweep_parameters(64, seed=2012), np.array(s["true_params"])[None, :]])
     sets = device_sets(gal, params)
     prm = sweep_params(q, s["n"], s["L0"], q.QUMOND_PREC_MIXED_FIXED, 1e-8)
-    with q.FitSweep(prm, nbins=s["nbins"], rmax=s["rmax"], workers=16) as sw:
+    # 65 sets in chunks of 32 on 2 lanes (the third chunk is padded)
+    with q.FitSweep(prm, nbins=s["nbins"], rmax=s["rmax"], batch=32, lanes=2) as sw:
         res = sw.run(sets, params[:, 0], to_dev(v_obs), to_dev(sigma), stats=True)
         torch.cuda.synchronize()
         vc, chi2 = res.vc.cpu().numpy(), res.chi2.cpu().numpy()
