@@ -315,7 +315,7 @@ void rb(qumond_ctx* c, int l, int colour, bool zero, double h, cudaStream_t s)
     run(c, l == c->L ? K_RB_FINEST : K_RB_COARSER, (zero ? 1.0 : 1.5) * nodes * sizeof(T), s, [&] {
         if (sizeof(T) == sizeof(float) && !zero && c->lev[l].maps.ok)
             launch_rb_half_tma(reinterpret_cast<float*>(E<T>(c, l)), reinterpret_cast<const float*>(F<T>(c, l)),
-                               c->lev[l].v, colour, c->lev[l].maps, h, c->fault, s);
+                               c->lev[l].v, colour, c->lev[l].maps, h, c->fault, s, sets_of(c));
         else
             launch_rb_half<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, colour, zero, h, s, sets_of(c));
     });
@@ -544,7 +544,7 @@ cudaError_t enqueue_body(qumond_ctx* c, int box, const double* rhs, double coef,
             if (c->fmaps.ok)
                 nb = launch_fixed_update_residual_tma(c->Ufix, c->Ufix2, c->fmaps, n, box_h(c, box), c->d_state,
                                                       reinterpret_cast<float*>(F<T>(c, c->L)), c->lev[c->L].v,
-                                                      c->partials, c->fault, s);
+                                                      c->partials, c->fault, s, sets_of(c));
             else
                 nb = launch_fixed_update_residual(c->Ufix, c->Ufix2, c->Ffix,
                                                   reinterpret_cast<const float*>(E<T>(c, c->L)), n, box_h(c, box),
@@ -893,10 +893,10 @@ qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
              (p->bc_mode != QUMOND_BC_MULTIPOLE ||
               cudaMalloc(&c->ff, sizeof(double) * far_field_scratch_doubles(p->nsets)) == cudaSuccess) &&
              prepare_kernels() == cudaSuccess;
-        if (ok && c->elt == sizeof(float) && ns == 1)  // the TMA-staged kernels take one set
+        if (ok && c->elt == sizeof(float))
             for (int l = lc; l <= L; ++l)
                 make_rb_maps(static_cast<float*>(c->lev[l].e), static_cast<float*>(c->lev[l].f), c->lev[l].v,
-                             &c->lev[l].maps);
+                             &c->lev[l].maps, (int)ns);
         if (ok && p->precision == QUMOND_PREC_MIXED_FIXED) {
             const size_t nn = fixed_elems(p->n) * ns;
             const int nfix = fixed_residual_blocks(p->n > 2 ? p->n : 2);
@@ -909,12 +909,12 @@ qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
                  cudaMemset(c->Ffix, 0, nn * sizeof(int64_t)) == cudaSuccess &&
                  cudaMalloc(&c->maxbits, sizeof(unsigned) * ns) == cudaSuccess &&
                  cudaMemset(c->maxbits, 0, sizeof(unsigned) * ns) == cudaSuccess;
-            if (ok && c->elt == sizeof(float) && ns == 1) {
+            if (ok && c->elt == sizeof(float)) {
                 const int n = p->n;
                 const long long items = (long long)((n - 1 + 31) / 32) * ((n - 1 + 7) / 8) * ((n - 1 + 15) / 16);
                 if (items <= c->max_partials)
                     make_fixed_maps(c->Ufix, c->Ufix2, c->Ffix, static_cast<float*>(c->lev[L].e), c->lev[L].v,
-                                    &c->fmaps);
+                                    &c->fmaps, (int)ns);
             }
         }
     }

@@ -64,13 +64,14 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
     return ok != 0;
 }
 
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+// One box of a 4-D tensor (i, j, k, set); the 4th coordinate selects the set (0 for one set).
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y, int z, int w,
                                             unsigned long long* bar)
 {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
         : "memory");
 }
 
@@ -96,8 +97,18 @@ fixed_update_residual_tma_kernel(const __grid_constant__ CUtensorMap map_u0, con
                                  const __grid_constant__ CUtensorMap map_f, const __grid_constant__ CUtensorMap map_e0,
                                  const __grid_constant__ CUtensorMap map_e1, long long* Ua, long long* Ub, int n,
                                  float ih2, const SolveState* __restrict__ st, float* __restrict__ r, LevelView v,
-                                 double* __restrict__ partials, int* __restrict__ fault)
+                                 double* __restrict__ partials, int* __restrict__ fault, long long pstride,
+                                 int skip_stopped)
 {
+    const int set = blockIdx.y;  // one row of blocks per set
+    st += set;
+    if (skip_stopped && !st->cont) return;  // this set's correction has stopped (whole CTA, before any barrier)
+    {
+        const long long fs = set * (long long)(n + 2) * (n + 1) * (n + 1);
+        Ua += fs, Ub += fs;
+        r += set * 2 * v.cs;
+        partials += set * pstride;
+    }
     __shared__ __align__(128) unsigned char slot[kSlots][kSlotBytes];
     __shared__ __align__(16) long long pl[3][kH][kW];
     __shared__ __align__(8) unsigned long long bar[kSlots];
@@ -137,10 +148,10 @@ fixed_update_residual_tma_kernel(const __grid_constant__ CUtensorMap map_u0, con
         }
         unsigned long long* b = &bar[u % kSlots];
         mbar_expect_tx(b, kUBytes + 2 * kEBytes + kFBytes);
-        tma_load_3d(base, mu, i0 - 2, j0 - 1, q, b);  // x: even int64 index, a 16-byte boundary
-        tma_load_3d(base + kOffE0, &map_e0, i0 / 2 - 4, j0 - 1, q, b);  // x: a multiple of 4 floats
-        tma_load_3d(base + kOffE1, &map_e1, i0 / 2 - 4, j0 - 1, q, b);
-        tma_load_3d(base + kOffF, &map_f, i0, j0, q, b);
+        tma_load_4d(base, mu, i0 - 2, j0 - 1, q, set, b);  // x: even int64 index, a 16-byte boundary
+        tma_load_4d(base + kOffE0, &map_e0, i0 / 2 - 4, j0 - 1, q, set, b);  // x: a multiple of 4 floats
+        tma_load_4d(base + kOffE1, &map_e1, i0 / 2 - 4, j0 - 1, q, set, b);
+        tma_load_4d(base + kOffF, &map_f, i0, j0, q, set, b);
         issued = q + 1;
     };
     if (leader)
@@ -292,46 +303,52 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-bool encode3(EncodeTiledFn enc, CUtensorMap* m, CUtensorMapDataType t, void* base, cuuint64_t d0, cuuint64_t d1,
-             cuuint64_t d2, cuuint64_t s1, cuuint64_t s2, cuuint32_t b0, cuuint32_t b1)
+// rows of d0 elements, planes of d1 rows, d2 planes, d3 sets (strides s1, s2, s3 bytes); boxes b0 x b1 x 1 x 1
+bool encode4(EncodeTiledFn enc, CUtensorMap* m, CUtensorMapDataType t, void* base, cuuint64_t d0, cuuint64_t d1,
+             cuuint64_t d2, cuuint64_t d3, cuuint64_t s1, cuuint64_t s2, cuuint64_t s3, cuuint32_t b0, cuuint32_t b1)
 {
-    const cuuint64_t dims[3] = {d0, d1, d2};
-    const cuuint64_t strides[2] = {s1, s2};
-    const cuuint32_t box[3] = {b0, b1, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    return enc(m, t, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    const cuuint64_t dims[4] = {d0, d1, d2, d3};
+    const cuuint64_t strides[3] = {s1, s2, s3};
+    const cuuint32_t box[4] = {b0, b1, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(m, t, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
 
-bool make_fixed_maps(int64_t* U, int64_t* U2, int64_t* F, float* e, const LevelView& v, FixedMaps* out)
+bool make_fixed_maps(int64_t* U, int64_t* U2, int64_t* F, float* e, const LevelView& v, FixedMaps* out, int nsets)
 {
     out->ok = false;
     const int n = v.n;
     if (n < kMinN) return false;
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
-    const cuuint64_t rowb = (cuuint64_t)(n + 2) * 8, planeb = rowb * (n + 1);
-    const cuuint64_t erow = (cuuint64_t)v.M * 4, eplane = erow * (n + 1);
-    bool ok = encode3(enc, &out->u[0], CU_TENSOR_MAP_DATA_TYPE_INT64, U, n + 2, n + 1, n + 1, rowb, planeb, kW, kH) &&
-              encode3(enc, &out->u[1], CU_TENSOR_MAP_DATA_TYPE_INT64, U2, n + 2, n + 1, n + 1, rowb, planeb, kW, kH) &&
-              encode3(enc, &out->f, CU_TENSOR_MAP_DATA_TYPE_INT64, F, n + 2, n + 1, n + 1, rowb, planeb, kTI, kTJ);
+    const cuuint64_t rowb = (cuuint64_t)(n + 2) * 8, planeb = rowb * (n + 1), setb = planeb * (n + 1);
+    const cuuint64_t erow = (cuuint64_t)v.M * 4, eplane = erow * (n + 1), eset = (cuuint64_t)(2 * v.cs) * 4;
+    const cuuint64_t ns = (cuuint64_t)nsets;
+    bool ok = encode4(enc, &out->u[0], CU_TENSOR_MAP_DATA_TYPE_INT64, U, n + 2, n + 1, n + 1, ns, rowb, planeb, setb,
+                      kW, kH) &&
+              encode4(enc, &out->u[1], CU_TENSOR_MAP_DATA_TYPE_INT64, U2, n + 2, n + 1, n + 1, ns, rowb, planeb, setb,
+                      kW, kH) &&
+              encode4(enc, &out->f, CU_TENSOR_MAP_DATA_TYPE_INT64, F, n + 2, n + 1, n + 1, ns, rowb, planeb, setb, kTI,
+                      kTJ);
     for (int c = 0; ok && c < 2; ++c)
-        ok = encode3(enc, &out->e[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, e + (long long)c * v.cs, v.M, n + 1, n + 1, erow,
-                     eplane, kEW, kH);
+        ok = encode4(enc, &out->e[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, e + (long long)c * v.cs, v.M, n + 1, n + 1, ns,
+                     erow, eplane, eset, kEW, kH);
     out->ok = ok;
     return ok;
 }
 
 int launch_fixed_update_residual_tma(int64_t* U, int64_t* U2, const FixedMaps& maps, int n, double h,
                                      const SolveState* st, float* r, const LevelView& v, double* partials, int* fault,
-                                     cudaStream_t s)
+                                     cudaStream_t s, const Sets& sets)
 {
     const int items = (n / kTI) * ((n - 1 + kTJ - 1) / kTJ) * ((n - 1 + kKC - 1) / kKC);
-    fixed_update_residual_tma_kernel<<<items, dim3(kPX, kTJ), 0, s>>>(
+    fixed_update_residual_tma_kernel<<<dim3(items, sets.n), dim3(kPX, kTJ), 0, s>>>(
         maps.u[0], maps.u[1], maps.f, maps.e[0], maps.e[1], reinterpret_cast<long long*>(U),
-        reinterpret_cast<long long*>(U2), n, (float)(1.0 / (h * h)), st, r, v, partials, fault);
+        reinterpret_cast<long long*>(U2), n, (float)(1.0 / (h * h)), st, r, v, partials, fault, sets.pstride,
+        sets.act ? 1 : 0);
     return items;
 }
 

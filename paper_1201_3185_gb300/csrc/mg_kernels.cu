@@ -91,10 +91,11 @@ rb_half_kernel(T* __restrict__ own, const T* __restrict__ other, const T* __rest
 // bits: each thread's entries are updated by the same arithmetic.
 constexpr int kVX = 8, kVY = 16;  // default: 32 entries x 16 rows per block
 constexpr int kVThreads = 128;
+constexpr int kVBlocksPerSM = 16;  // full occupancy (<= 32 registers): the small levels are latency-bound
 constexpr int kTileSmallN = 64;  // the alternative shapes apply to levels with n <= this
 
 template <bool ZERO, int VX = kVX>
-__global__ void __launch_bounds__(kVThreads)
+__global__ void __launch_bounds__(kVThreads, kVBlocksPerSM)
 rb_half4_kernel(float* __restrict__ own, const float* __restrict__ other, const float* __restrict__ f, LevelView v,
                 int colour, float h2, float sixth, const SolveState* __restrict__ act)
 {
@@ -295,7 +296,7 @@ restrict_resid4_kernel(const float* __restrict__ ef, const float* __restrict__ f
 // sums are prolong_node's, in its order, and the fine row is read and
 // written with 16-byte accesses.
 template <bool ADD, int VX = kVX>
-__global__ void __launch_bounds__(kVThreads)
+__global__ void __launch_bounds__(kVThreads, kVBlocksPerSM)
 prolong_black4_kernel(const float* __restrict__ ec, LevelView vc, float* __restrict__ ef, LevelView vf,
                       const SolveState* __restrict__ act)
 {

@@ -129,9 +129,10 @@ struct RbMaps {
     CUtensorMap fmap[2];  // colour c of the right-hand side, tile boxes
     bool ok = false;
 };
-bool make_rb_maps(float* e, float* f, const LevelView& v, RbMaps* out);
+// 4-D maps (m, j, k, set) over the nsets sets of a level
+bool make_rb_maps(float* e, float* f, const LevelView& v, RbMaps* out, int nsets = 1);
 void launch_rb_half_tma(float* e, const float* f, const LevelView& v, int colour, const RbMaps& maps, double h,
-                        int* fault, cudaStream_t s);
+                        int* fault, cudaStream_t s, const Sets& sets = Sets());
 // Sets kernel attributes (shared memory of the coarse-grid kernel); call
 // before any stream capture.
 cudaError_t prepare_kernels();
@@ -157,11 +158,13 @@ struct FixedMaps {
     CUtensorMap e[2];
     bool ok;
 };
-bool make_fixed_maps(int64_t* U, int64_t* U2, int64_t* F, float* e, const LevelView& v, FixedMaps* out);
+// 4-D maps (i, j, k, set) over the nsets sets
+bool make_fixed_maps(int64_t* U, int64_t* U2, int64_t* F, float* e, const LevelView& v, FixedMaps* out,
+                     int nsets = 1);
 // the fused update + residual with TMA-staged planes (n >= 128); returns the blocks written
 int launch_fixed_update_residual_tma(int64_t* U, int64_t* U2, const FixedMaps& maps, int n, double h,
                                      const SolveState* st, float* r, const LevelView& v, double* partials, int* fault,
-                                     cudaStream_t s);
+                                     cudaStream_t s, const Sets& sets = Sets());
 int launch_fixed_update_residual(int64_t* U, int64_t* U2, const int64_t* F, const float* e, int n, double h,
                                  const SolveState* st, float* r, const LevelView& v, double* partials, cudaStream_t s,
                                  const Sets& sets = Sets());

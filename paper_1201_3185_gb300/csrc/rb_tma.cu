@@ -43,6 +43,7 @@ constexpr int kSlotFloats = kPlaneFloats + kFBytes / sizeof(float);
 constexpr long long kSpinLimit = 1LL << 24;
 // Levels below this size have too few planes per CTA column for the ring to pay off.
 constexpr int kTmaMinN = 256;
+constexpr int kTmaMinNSets = 128;  // with four or more sets in one launch
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -69,13 +70,15 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
     return ok != 0;
 }
 
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+// One box of a 4-D tensor (m, j, k, set) into shared memory; the 4th
+// coordinate selects the set of a context with several sets (0 for one set).
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y, int z, int w,
                                             unsigned long long* bar)
 {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
         : "memory");
 }
 
@@ -98,14 +101,19 @@ __device__ __forceinline__ void drain_after_abort(bool leader, int* abort_flag, 
 
 __global__ void __launch_bounds__(kThreadsX * kTJ)
 rb_tma_kernel(const __grid_constant__ CUtensorMap other_map, const __grid_constant__ CUtensorMap f_map,
-              float* __restrict__ own, LevelView v, int colour, float h2, float sixth, int* __restrict__ fault)
+              float* __restrict__ own, LevelView v, int colour, float h2, float sixth, int* __restrict__ fault,
+              int zper, const SolveState* __restrict__ act)
 {
     __shared__ __align__(128) float plane[kSlots][kSlotFloats];
     __shared__ __align__(8) unsigned long long bar[kSlots];
     __shared__ int abort_flag;
+    // blockIdx.z = zper * set + chunk of planes
+    const int set = (int)gridDim.z == zper ? 0 : (int)blockIdx.z / zper;
+    if (act && !act[set].cont) return;  // this set's correction has stopped (whole CTA, before any barrier)
+    own += (long long)set * 2 * v.cs;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int m0 = blockIdx.x * kTM, j0 = 1 + blockIdx.y * kTJ;
-    const int kb = 1 + blockIdx.z * kKC;
+    const int kb = 1 + ((int)blockIdx.z - set * zper) * kKC;
     const int ke = min(kb + kKC, v.n);  // output planes kb .. ke-1; planes kb-1 .. ke are read
     const bool leader = tx == 0 && ty == 0;
     if (leader) {
@@ -128,8 +136,8 @@ rb_tma_kernel(const __grid_constant__ CUtensorMap other_map, const __grid_consta
             return;
         }
         mbar_expect_tx(&bar[u % kSlots], kPlaneBytes + kFBytes);
-        tma_load_3d(dst, &other_map, m0 - 4, j0 - 1, q, &bar[u % kSlots]);
-        tma_load_3d(fdst, &f_map, m0, j0, q, &bar[u % kSlots]);
+        tma_load_4d(dst, &other_map, m0 - 4, j0 - 1, q, set, &bar[u % kSlots]);
+        tma_load_4d(fdst, &f_map, m0, j0, q, set, &bar[u % kSlots]);
         issued = q + 1;
     };
     if (leader)
@@ -240,23 +248,25 @@ EncodeTiledFn encode_fn()
 
 }  // namespace
 
-bool make_rb_maps(float* e, float* f, const LevelView& v, RbMaps* out)
+bool make_rb_maps(float* e, float* f, const LevelView& v, RbMaps* out, int nsets)
 {
     out->ok = false;
-    if (v.n < kTmaMinN) return false;
+    // one set: only levels with enough planes per CTA column to fill the GPU; several sets fill it together
+    if (v.n < (nsets >= 4 ? kTmaMinNSets : kTmaMinN)) return false;
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)v.M, (cuuint64_t)(v.n + 1), (cuuint64_t)(v.n + 1)};
-    const cuuint64_t strides[2] = {(cuuint64_t)v.M * sizeof(float), (cuuint64_t)v.M * (v.n + 1) * sizeof(float)};
-    const cuuint32_t box[3] = {kBoxX, kBoxY, 1};
-    const cuuint32_t fbox[3] = {kTM, kTJ, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
+    const cuuint64_t dims[4] = {(cuuint64_t)v.M, (cuuint64_t)(v.n + 1), (cuuint64_t)(v.n + 1), (cuuint64_t)nsets};
+    const cuuint64_t strides[3] = {(cuuint64_t)v.M * sizeof(float), (cuuint64_t)v.M * (v.n + 1) * sizeof(float),
+                                   (cuuint64_t)(2 * v.cs) * sizeof(float)};
+    const cuuint32_t box[4] = {kBoxX, kBoxY, 1, 1};
+    const cuuint32_t fbox[4] = {kTM, kTJ, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
     for (int c = 0; c < 2; ++c) {
-        if (enc(&out->map[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, e + (long long)c * v.cs, dims, strides, box, estr,
+        if (enc(&out->map[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, e + (long long)c * v.cs, dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
-        if (enc(&out->fmap[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, f + (long long)c * v.cs, dims, strides, fbox, estr,
+        if (enc(&out->fmap[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, f + (long long)c * v.cs, dims, strides, fbox, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
@@ -266,13 +276,14 @@ bool make_rb_maps(float* e, float* f, const LevelView& v, RbMaps* out)
 }
 
 void launch_rb_half_tma(float* e, const float* f, const LevelView& v, int colour, const RbMaps& maps, double h,
-                        int* fault, cudaStream_t s)
+                        int* fault, cudaStream_t s, const Sets& sets)
 {
+    const int zper = (v.n - 1 + kKC - 1) / kKC;
     const dim3 grid((unsigned)((v.n / 2 + kTM - 1) / kTM), (unsigned)((v.n - 1 + kTJ - 1) / kTJ),
-                    (unsigned)((v.n - 1 + kKC - 1) / kKC));
+                    (unsigned)(zper * sets.n));
     (void)f;
     rb_tma_kernel<<<grid, dim3(kThreadsX, kTJ), 0, s>>>(maps.map[colour ^ 1], maps.fmap[colour], e + (long long)colour * v.cs,
-                                                  v, colour, (float)(h * h), 1.0f / 6.0f, fault);
+                                                  v, colour, (float)(h * h), 1.0f / 6.0f, fault, zper, sets.act);
 }
 
 }  // namespace qumond
