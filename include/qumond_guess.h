@@ -63,11 +63,19 @@ QUMOND_API const char* qumond_guess_last_error(qumond_guess* g);
 /* Convolution path: mode 1 (the default when available) runs the 3x3x3
    convolutions of levels with S >= 16 on the tcgen05 tensor cores with TMEM
    accumulators; mode 0 runs every convolution with mma.sync.  The tcgen05
-   path is available when a one-MMA self-test at the first create reproduced
-   a CPU product; mode 1 is rejected (QUMOND_ERR_INVALID_ARG) otherwise.
-   Both give FP32-accumulated BF16 results (they differ in summation order). */
+   path is available on devices of compute capability 10.3 (the architecture
+   the library is built for); mode 1 is rejected (QUMOND_ERR_INVALID_ARG)
+   otherwise.  Both give FP32-accumulated BF16 results. */
 QUMOND_API qumond_status qumond_guess_tensor_path(qumond_guess* g, int mode);
 QUMOND_API int qumond_guess_tensor_path_available(qumond_guess* g);
+
+/* A unit test of the tcgen05 path's shared-memory descriptors (the PTX ISA's
+   canonical K-major layout without swizzling): one 128 x 16 x 16 BF16 MMA
+   from descriptors built as the convolution builds them, read back from
+   tensor memory and compared with the CPU product of the same small
+   integers.  Returns 1 if every element matches, 0 if not, -1 on a CUDA
+   error.  Uses the current device; not called by any other entry point. */
+QUMOND_API int qumond_guess_tc_selftest(void);
 
 /* Kernels this object has enqueued since it was created: every call above
    and below adds the kernels it launched (0 for a null object). */

@@ -452,7 +452,11 @@ __global__ void set_boundary_kernel(T* __restrict__ e, LevelView v, const double
 //           from u64, or zero), ncycle V-cycles per level;
 //  fmg = 0: one V-cycle from a zero initial guess with zero boundary values.
 // The result (all nodes, boundary included) is written to e.
-constexpr int kCoarseThreads = 512;
+// The shared-memory routines below stride over their nodes by the block's
+// size: the coarse-grid kernel runs them with kCoarseThreads, the cooperative
+// V-cycle kernel (one CTA per SM, more registers) with kVsubThreads.
+constexpr int kCoarseThreads = 1024;
+constexpr int kVsubThreads = 512;
 constexpr int kMaxCoarseLevels = 4;  // n = 2, 4, 8, 16
 
 __host__ __device__ inline int cube(int n) { return (n + 1) * (n + 1) * (n + 1); }
@@ -472,7 +476,7 @@ template <typename T, int N>
 __device__ void sm_relax(T* u, const T* f, T h2, int colour)
 {
     constexpr int M = N - 1, P = N + 1, H = N / 2, TOT = M * M * H;
-    for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) {
+    for (int t = threadIdx.x; t < TOT; t += (int)blockDim.x) {
         const int sl = t % H, row = t / H;
         const int j = row % M + 1, k = row / M + 1;
         const int i = 1 + (((1 + j + k) & 1) != colour ? 1 : 0) + 2 * sl;
@@ -488,7 +492,7 @@ template <typename T, int N>
 __device__ void sm_residual(const T* u, const T* f, T* r, T ih2)
 {
     constexpr int M = N - 1, P = N + 1, TOT = M * M * M;
-    for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) {
+    for (int t = threadIdx.x; t < TOT; t += (int)blockDim.x) {
         const int i = t % M + 1, j = (t / M) % M + 1, k = t / (M * M) + 1;
         const int o = i + P * (j + P * k);
         const T sum = (u[o + 1] + u[o - 1]) + (u[o + P] + u[o - P]) + (u[o + P * P] + u[o - P * P]);
@@ -501,7 +505,7 @@ template <typename T, int NF>
 __device__ void sm_restrict(const T* fine, T* coarse)
 {
     constexpr int NC = NF / 2, MC = NC - 1, PF = NF + 1, PC = NC + 1, TOT = MC * MC * MC;
-    for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) {
+    for (int t = threadIdx.x; t < TOT; t += (int)blockDim.x) {
         const int I = t % MC + 1, J = (t / MC) % MC + 1, K = t / (MC * MC) + 1;
         T acc = T(0);
 #pragma unroll
@@ -522,7 +526,7 @@ template <typename T, int NC>
 __device__ void sm_prolong(const T* coarse, T* fine, bool add)
 {
     constexpr int NF = 2 * NC, M = NF - 1, PF = NF + 1, PC = NC + 1, TOT = M * M * M;
-    for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) {
+    for (int t = threadIdx.x; t < TOT; t += (int)blockDim.x) {
         const int i = t % M + 1, j = (t / M) % M + 1, k = t / (M * M) + 1;
         const int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = j >> 1, J1 = (j + 1) >> 1, K0 = k >> 1, K1 = (k + 1) >> 1;
         T sum = (coarse[I0 + PC * (J0 + PC * K0)] + coarse[I1 + PC * (J0 + PC * K0)])
@@ -540,7 +544,7 @@ template <typename T, int N>
 __device__ void sm_fill(T* a, T val)
 {
     constexpr int TOT = (N + 1) * (N + 1) * (N + 1);
-    for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) a[t] = val;
+    for (int t = threadIdx.x; t < TOT; t += (int)blockDim.x) a[t] = val;
     __syncthreads();
 }
 
@@ -597,7 +601,7 @@ __device__ void sm_inject(CoarseSmem<T>& S, const double* __restrict__ u64, int 
     constexpr int N = 2 << L, P = N + 1, TOT = P * P * P;
     const int st = u64 ? nfine / N : 0;
     const long long PF = nfine + 1;
-    for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) {
+    for (int t = threadIdx.x; t < TOT; t += (int)blockDim.x) {
         const int i = t % P, j = (t / P) % P, k = t / (P * P);
         const bool inner = i > 0 && i < N && j > 0 && j < N && k > 0 && k < N;
         T val = T(0);
@@ -638,7 +642,7 @@ __device__ void coarse_run(unsigned char* smem_raw, int fmg, T* __restrict__ e, 
     constexpr int N = 2 << TOP, P = N + 1, TOT = P * P * P;
     // right-hand side of the top level (interior), zero elsewhere
 #pragma unroll 5
-    for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) {
+    for (int t = threadIdx.x; t < TOT; t += (int)blockDim.x) {
         const int i = t % P, j = (t / P) % P, k = t / (P * P);
         const bool inner = i > 0 && i < N && j > 0 && j < N && k > 0 && k < N;
         S.f[TOP][t] = inner ? f[node_off(v, i, j, k)] : T(0);
@@ -650,12 +654,12 @@ __device__ void coarse_run(unsigned char* smem_raw, int fmg, T* __restrict__ e, 
         __syncthreads();
         sm_fmg_up<T, TOP>(S, htop * T(1 << TOP), ncycle, npre, npost);
     } else {
-        for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) S.u[TOP][t] = T(0);
+        for (int t = threadIdx.x; t < TOT; t += (int)blockDim.x) S.u[TOP][t] = T(0);
         __syncthreads();
         sm_vcycle<T, TOP>(S, htop, npre, npost);
     }
 #pragma unroll 5
-    for (int t = threadIdx.x; t < TOT; t += kCoarseThreads) {
+    for (int t = threadIdx.x; t < TOT; t += (int)blockDim.x) {
         const int i = t % P, j = (t / P) % P, k = t / (P * P);
         e[node_off(v, i, j, k)] = S.u[TOP][t];
     }
@@ -750,7 +754,7 @@ __device__ void vsub_rb(const VsubLevel<T>& L, int colour, bool zero)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kCoarseThreads) vsub_kernel(VsubArgs<T> a)
+__global__ void __launch_bounds__(kVsubThreads) vsub_kernel(VsubArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned gen = 0;
@@ -1229,7 +1233,7 @@ cudaError_t launch_vsub(T* const* e, T* const* f, const LevelView* v, const doub
     if (err != cudaSuccess) return err;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(kCoarseThreads);
+    cfg.blockDim = dim3(kVsubThreads);
     cfg.dynamicSmemBytes = coarse_smem_bytes<T>(v[0].n);
     cfg.stream = s;
     cudaLaunchAttribute at[1];

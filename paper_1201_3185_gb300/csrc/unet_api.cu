@@ -59,7 +59,7 @@ struct qumond_guess {
     float* cpart = nullptr;
     float* hpart = nullptr;
     int cblocks = 0, hblocks = 0;
-    int tc_swap = -1;     // tcgen05 convolutions: descriptor reading found by the self-test, -1 unavailable
+    int tc_ok = 0;        // the device runs tcgen05 (compute capability 10.3, the architecture this library is built for)
     int use_tc = 0;       // 1: tcgen05 convolutions where they apply, 0: mma.sync everywhere
     int* fault = nullptr; // bounded waits of the tcgen05 path
     long long launches = 0;  // kernels enqueued by the API calls (each launch_* helper's count at its call site)
@@ -168,7 +168,7 @@ void conv(qumond_guess* g, int l, cudaStream_t s)
     a.out = w.out, a.ld_out = w.ld_out, a.out_off = w.out_off, a.cout = kLayers[l].cout;
     a.relu = 1;
     a.S = g->S >> kLayers[l].level;
-    a.tc_swap = g->use_tc ? g->tc_swap : -1;
+    a.use_tc = g->use_tc;
     a.fault = g->fault;
     launch_conv3(a, s);
     g->launches += 1;
@@ -220,7 +220,7 @@ void backward(qumond_guess* g, const __nv_bfloat16* target, float k, float loss_
         ConvArgs a{};
         a.in = g->G[l], a.ld_in = cout, a.in_off = 0, a.cin = cout;
         a.w = g->wd[l], a.bias = nullptr, a.relu = 0, a.cout = cin, a.S = S;
-        a.tc_swap = g->use_tc ? g->tc_swap : -1;
+        a.use_tc = g->use_tc;
         a.fault = g->fault;
         const bool from_pool = (l == 2 || l == 4 || l == 6);
         const bool from_cat = (l == 8 || l == 10 || l == 12);
@@ -354,11 +354,12 @@ qumond_status qumond_guess_create(int S, double phi_scale, qumond_guess** out)
     prepare_wgrad();
     prepare_conv3_tc();
     {
-        // once per process: which reading of the tcgen05 shared-memory descriptor reproduces a CPU product
-        static int tc = -2;
-        if (tc == -2) tc = tc_selftest();
-        g->tc_swap = tc;
-        g->use_tc = tc >= 0 ? 1 : 0;
+        int dev = 0, major = 0, minor = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+        g->tc_ok = (major == 10 && minor == 3) ? 1 : 0;
+        g->use_tc = g->tc_ok;
     }
     refresh_bf16(g, nullptr);
     if (cudaDeviceSynchronize() != cudaSuccess) {
@@ -383,13 +384,15 @@ qumond_status qumond_guess_tensor_path(qumond_guess* g, int mode)
     if (!g) return QUMOND_ERR_INVALID_ARG;
     g->err.clear();
     if (mode != 0 && mode != 1) return fail(g, QUMOND_ERR_INVALID_ARG, "tensor_path: mode must be 0 or 1");
-    if (mode == 1 && g->tc_swap < 0)
-        return fail(g, QUMOND_ERR_INVALID_ARG, "tensor_path: the tcgen05 path failed its self-test on this device");
+    if (mode == 1 && !g->tc_ok)
+        return fail(g, QUMOND_ERR_INVALID_ARG, "tensor_path: this device has no tcgen05 tensor cores");
     g->use_tc = mode;
     return QUMOND_OK;
 }
 
-int qumond_guess_tensor_path_available(qumond_guess* g) { return g && g->tc_swap >= 0 ? 1 : 0; }
+int qumond_guess_tensor_path_available(qumond_guess* g) { return g && g->tc_ok ? 1 : 0; }
+
+int qumond_guess_tc_selftest(void) { return tc_selftest(); }
 
 int64_t qumond_guess_launches(qumond_guess* g) { return g ? g->launches : 0; }
 

@@ -27,7 +27,7 @@ struct ConvArgs {
     int relu;
     int S;
     Brick brick;  // set by the launcher
-    int tc_swap;  // tcgen05 path: which descriptor field holds the K stride (0/1, from tc_selftest); -1: mma.sync
+    int use_tc;   // 1: the convolution may run on the tcgen05 path (where conv3_tc_applies); 0: mma.sync
     int* fault;   // set to 3 when a bounded wait of the tcgen05 path gave up
 };
 

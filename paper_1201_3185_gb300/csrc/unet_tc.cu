@@ -15,11 +15,12 @@
 // commits them to an mbarrier; the CTA waits (bounded) before it overwrites
 // the chunk's shared memory.
 //
-// Which of the descriptor's two byte-offset fields holds the K-direction and
-// which the M/N-direction stride is checked once per process by a one-MMA
-// self-test whose every address is in bounds under either reading
-// (tc_selftest); if neither reading reproduces a CPU product the library keeps
-// the mma.sync kernel.
+// The shared-memory descriptors follow the PTX ISA's canonical K-major layout
+// without swizzling: core matrices of 8 rows x 16 bytes, the leading-dimension
+// byte offset (bits 16-29) the distance between core matrices adjacent along
+// K, the stride-dimension byte offset (bits 32-45) the distance between
+// 8-row groups along M (or N).  tc_selftest checks one MMA with that encoding
+// against a CPU product (a unit test; the product path does not call it).
 #include "unet_internal.h"
 
 #include <cstdio>
@@ -38,14 +39,15 @@ constexpr long long kSpinLimit = 1LL << 24;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ unsigned long long sdesc(unsigned addr, unsigned kstride, unsigned mnstride, int swap)
+// Shared-memory matrix descriptor, K-major, no swizzle: start address >> 4 in
+// bits 0-13; leading-dimension byte offset >> 4 (between core matrices along
+// K) in bits 16-29; stride-dimension byte offset >> 4 (between 8-row groups
+// along M or N) in bits 32-45; the descriptor version (1) at bit 46; base
+// offset 0, swizzle mode 0 (bits 61-63).
+__device__ __forceinline__ unsigned long long sdesc(unsigned addr, unsigned kstride, unsigned mnstride)
 {
-    // start address >> 4 in bits 0-13, the two byte offsets >> 4 in bits 16-29 and 32-45,
-    // the descriptor version (1) at bit 46, no swizzle (bits 61-63 = 0)
-    const unsigned lbo = swap ? mnstride : kstride;
-    const unsigned sbo = swap ? kstride : mnstride;
-    return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)((kstride >> 4) & 0x3FFFu) << 16) |
+           ((unsigned long long)((mnstride >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
 // instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, N and M
@@ -150,8 +152,8 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v)
 // Self-test: D (128 x 16) = A (128 x 16) B^T (16 x 16) for small integer
 // operands, A and B in a compact canonical layout (core matrix (g, h) of rows
 // 8g.. and K-columns 8h.. at g*256 + h*128 bytes), read back from TMEM.  Every
-// address either reading of the offset fields can form lies inside A or B.
-__global__ void __launch_bounds__(128) tc_selftest_kernel(float* out, int swap, int* fault)
+// address the descriptors form lies inside A or B.
+__global__ void __launch_bounds__(128) tc_selftest_kernel(float* out, int* fault)
 {
     __shared__ __align__(128) __nv_bfloat16 A[128 * 16];
     __shared__ __align__(128) __nv_bfloat16 B[16 * 16];
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(128) tc_selftest_kernel(float* out, int swap, 
     fence_after();
     const unsigned taddr = slot;
     if (tid == 0) {
-        mma(taddr, sdesc(smem_u32(A), 128, 256, swap), sdesc(smem_u32(B), 128, 256, swap), idesc_bf16(16, 128), 0);
+        mma(taddr, sdesc(smem_u32(A), 128, 256), sdesc(smem_u32(B), 128, 256), idesc_bf16(16, 128), 0);
         commit(&bar);
     }
     const bool ok = mbar_wait(&bar, 0, fault);
@@ -210,7 +212,6 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(ConvArgs a)
     const int x0 = (brick % nbx) * 8, y0 = ((brick / nbx) % nby) * 16, z0 = brick / (nbx * nby);
     const int co0 = blockIdx.y * NT;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int swap = a.tc_swap;
 
     if (warp == 0) tmem_alloc(&slot, kCols);
     if (tid == 0) {
@@ -254,8 +255,8 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(ConvArgs a)
             for (int t = 0; t < 27; ++t) {
                 const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;  // halo offsets 0..2 of the tap
                 const unsigned aoff = (unsigned)(((dz * kHY + dy) * kHX + dx) * 16);
-                const unsigned long long ad = sdesc(hbase + aoff, kPlaneBytes, kHX * 16, swap);
-                const unsigned long long bd = sdesc(wbase + (unsigned)(t * 2 * NT * 16), NT * 16, 128, swap);
+                const unsigned long long ad = sdesc(hbase + aoff, kPlaneBytes, kHX * 16);
+                const unsigned long long bd = sdesc(wbase + (unsigned)(t * 2 * NT * 16), NT * 16, 128);
                 mma(taddr, ad, bd, kIdesc, (c > 0 || t > 0) ? 1 : 0);
             }
             commit(&bar);
@@ -304,7 +305,7 @@ bool conv3_tc_applies(const ConvArgs& a)
 {
     // 16 <= S (the 1 x 16 x 8 brick), channel counts in 16-channel chunks, row strides and offsets in
     // 16-byte units (8 channels) for the vector loads and stores
-    return a.tc_swap >= 0 && a.S >= 16 && a.S % 16 == 0 && a.cin % 16 == 0 && a.cout % 16 == 0 &&
+    return a.use_tc && a.S >= 16 && a.S % 16 == 0 && a.cin % 16 == 0 && a.cout % 16 == 0 &&
            a.ld_in % 8 == 0 && a.in_off % 8 == 0 && a.ld_out % 8 == 0 && a.out_off % 8 == 0 &&
            (!a.mask || (a.ld_mask % 8 == 0 && a.mask_off % 8 == 0));
 }
@@ -330,8 +331,9 @@ void launch_conv3_tc(const ConvArgs& a, cudaStream_t s)
     }
 }
 
-// Runs the self-test with either reading of the descriptor's offset fields and
-// returns the one that reproduces the CPU product (0 or 1), or -1.
+// One MMA with the library's descriptor encoding against the CPU product of
+// the same small integer operands: 1 if every element matches, 0 if not, -1
+// on a CUDA error.  A unit test of the encoding; the product path does not run it.
 int tc_selftest()
 {
     float* d_out = nullptr;
@@ -352,21 +354,18 @@ int tc_selftest()
             for (int k = 0; k < 16; ++k) s += (float)((m + 3 * k) % 7 - 3) * (float)((2 * n + k) % 5 - 2);
             want[m * 16 + n] = s;
         }
-    int found = -1;
-    for (int swap = 0; swap < 2 && found < 0; ++swap) {
-        tc_selftest_kernel<<<1, 128>>>(d_out, swap, d_fault);
-        if (cudaDeviceSynchronize() != cudaSuccess ||
-            cudaMemcpy(got.data(), d_out, got.size() * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) {
-            (void)cudaGetLastError();
-            break;
-        }
-        int fault = 0;
-        cudaMemcpy(&fault, d_fault, sizeof(int), cudaMemcpyDeviceToHost);
-        if (fault == 0 && std::memcmp(got.data(), want.data(), got.size() * sizeof(float)) == 0) found = swap;
-    }
+    int result = -1;
+    tc_selftest_kernel<<<1, 128>>>(d_out, d_fault);
+    int fault = 0;
+    if (cudaDeviceSynchronize() == cudaSuccess &&
+        cudaMemcpy(got.data(), d_out, got.size() * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess &&
+        cudaMemcpy(&fault, d_fault, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess)
+        result = (fault == 0 && std::memcmp(got.data(), want.data(), got.size() * sizeof(float)) == 0) ? 1 : 0;
+    else
+        (void)cudaGetLastError();
     cudaFree(d_out);
     cudaFree(d_fault);
-    return found;
+    return result;
 }
 
 }  // namespace unet

@@ -43,7 +43,7 @@ EXPORTED = (
     "qumond_guess_num_params", "qumond_guess_create", "qumond_guess_destroy", "qumond_guess_last_error",
     "qumond_guess_set_params", "qumond_guess_get_params", "qumond_guess_make_sample", "qumond_guess_forward",
     "qumond_guess_gradients", "qumond_guess_train_step", "qumond_guess_apply", "qumond_guess_tensor_path",
-    "qumond_guess_tensor_path_available", "qumond_guess_status", "qumond_guess_launches",
+    "qumond_guess_tensor_path_available", "qumond_guess_status", "qumond_guess_launches", "qumond_guess_tc_selftest",
 )
 NOALLOC_MAX_N = 64
 
@@ -143,6 +143,7 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
         "qumond_guess_apply": (_I, [_P, _D, ctypes.c_float, _P, _P, _P, _P]),
         "qumond_guess_tensor_path": (_I, [_P, _I]),
         "qumond_guess_tensor_path_available": (_I, [_P]),
+        "qumond_guess_tc_selftest": (_I, []),
         "qumond_guess_launches": (ctypes.c_int64, [_P]),
         "qumond_guess_status": (_I, [_P, _P]),
     }
@@ -474,6 +475,11 @@ class Guess:
 
     def qumond_guess_tensor_path_available(self) -> bool:
         return bool(_lib.qumond_guess_tensor_path_available(self._ptr))
+
+    @staticmethod
+    def qumond_guess_tc_selftest() -> int:
+        """One tcgen05 MMA from the library's descriptors against a CPU product: 1 match, 0 mismatch, -1 error."""
+        return int(_lib.qumond_guess_tc_selftest())
 
     def qumond_guess_status(self, stream=None):
         self._check(_lib.qumond_guess_status(self._ptr, _stream(stream)))

@@ -178,8 +178,14 @@ def test_invalid_arguments(q):
 
 def test_tcgen05_path_available(q):
     g = q.Guess(16, 1e5)
-    assert g.qumond_guess_tensor_path_available(), "the tcgen05 self-test did not reproduce the CPU product"
+    assert g.qumond_guess_tensor_path_available(), "no tcgen05 tensor cores on this device"
     g.close()
+
+
+def test_tcgen05_descriptor_encoding(q):
+    # the documented K-major descriptor layout (leading-dimension offset along K,
+    # stride-dimension offset along M/N) reproduces an exact integer product
+    assert q.Guess.qumond_guess_tc_selftest() == 1
 
 
 @pytest.mark.parametrize("S", [64, 128])

@@ -3,7 +3,8 @@
 1. The two-disk galaxy (stellar exponential disk Sigma0 = 500 Msun/pc^2,
    R_d = 3 kpc; gas disk 1e9 Msun, R_g = 8 kpc), 2e6 particles, seed 1,
    257^3 nodes x 3 nested boxes of 120/60/30 kpc, relative residual 1e-10,
-   FMG with one V-cycle per level, V(2,2): the GPU path runs as bench.py runs
+   FMG with one V-cycle per level, V(2,2), box 0's boundary from the far field
+   of its own mass (QUMOND_BC_MULTIPOLE): the GPU path runs as bench.py runs
    it (two contexts, the QUMOND chain on its own stream concurrent with the
    Newtonian chain, every solve one cached CUDA graph, launched a second time
    so the cached graphs are the ones compared), in the fixed-point and the
@@ -51,7 +52,7 @@ def q():
 def two_disk(ora):
     p = synth.two_component_disk(NP, seed=1, rmax=0.45 * L0, zmax=0.45 * L0)
     # FP64's rounding floor of the relative residual is ~1.6e-12 on the innermost box: the oracle stops there
-    boxes = ora.pipeline(p, N, L0, NB, ncycle=1, tol=1e-12, max_vcycles=30)
+    boxes = ora.pipeline(p, N, L0, NB, ncycle=1, tol=1e-12, max_vcycles=30, far_field_lmax=8)
     for b in boxes:
         assert b.newton_hist[-1] < 1e-11 and b.mond_hist[-1] < 1e-11
     sel = np.random.default_rng(2024).choice(NP, NSAMPLE, replace=False)
@@ -70,7 +71,8 @@ def _bench_pipeline(q, precision, n, nboxes, L0_, **extra):
 def test_two_disk_257cube_3boxes_matches_oracle(q, ora, two_disk, prec_name):
     p, boxes, sel, g_want, vc_want = two_disk
     prec = getattr(q, "QUMOND_PREC_" + prec_name)
-    ca, cb, pipe = _bench_pipeline(q, prec, N, NB, L0, rel_tol=1e-10, max_vcycles=40, ncycle=1, npre=2, npost=2)
+    ca, cb, pipe = _bench_pipeline(q, prec, N, NB, L0, rel_tol=1e-10, max_vcycles=40, ncycle=1, npre=2, npost=2,
+                                   bc_mode=q.QUMOND_BC_MULTIPOLE)
     x, y, z, m = (to_dev(a) for a in (p.x, p.y, p.z, p.m))
     g = tuple(torch.empty_like(x) for _ in range(3))
     for _ in range(2):  # the second run relaunches the cached graphs
