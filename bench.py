@@ -295,7 +295,8 @@ def run_ours(args):
             return q.Context(n=w["n"], nboxes=w["nboxes"], L0=w["L0"], rel_tol=w["rel_tol"],
                              max_vcycles=w["max_vcycles"], ncycle=w["ncycle"], npre=w["npre"], npost=w["npost"],
                              precision=precision, use_graphs=0 if args.no_graphs else 1,
-                             bc_mode=q.QUMOND_BC_MULTIPOLE if w.get("bc") == "multipole" else q.QUMOND_BC_ZERO)
+                             bc_mode=q.QUMOND_BC_MULTIPOLE if w.get("bc") == "multipole" else q.QUMOND_BC_ZERO,
+                             persistent_vcycle=args.persistent_vcycle)
         cs = [make() for _ in range(args.chains)]
         return Contexts(cs), q.Pipeline(cs[0], dev, ctx_mond=cs[1] if len(cs) > 1 else None)
 
@@ -497,6 +498,7 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "gpu_launches_per_step": launches / args.steps,
             "chains": args.chains,
+            "small_level_vcycle": {0: "one launch per step", 1: "one cooperative kernel", 2: "one thread-block cluster per set"}[args.persistent_vcycle],
             "one_chain": {"value": ws * 1000.0 / one_chain_ms, "unit": UNIT, "ms_per_step": one_chain_ms},
             "vcycles_after_fmg_per_solve": vcycles,
             "plain_fmg": plain,
@@ -1049,6 +1051,9 @@ def main():
     ap.add_argument("--workers", type=int, default=0,
                     help="sweep: lanes of one 64-set chunk each (0: batch size, lanes and block shape by the "
                          "autotuner)")
+    ap.add_argument("--persistent-vcycle", type=int, choices=[0, 1, 2], default=0,
+                    help="the V-cycle on the levels n <= 64: 0 one launch per step, 1 one cooperative kernel, "
+                         "2 one thread-block cluster (two-disk and large workloads)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one profiled V-cycle on one box instead of the benchmark (for ncu)")
     args = ap.parse_args()

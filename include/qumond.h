@@ -126,14 +126,17 @@ typedef struct {
     int use_graphs;     /* 1: each solve runs as one cached CUDA graph (FMG and
                            the whole tolerance loop, decided on the device);
                            0: kernels are launched one by one */
-    int persistent_vcycle; /* 1: the part of each V-cycle on the levels with
-                           n <= 64 below the finest runs as one cooperative
-                           kernel with grid barriers (when the device supports
-                           cooperative launches); 0 (default): one launch per
-                           step.  The results are the same bits.  On GB300 the
-                           cooperative form is not faster (a grid barrier costs
-                           about what a graph launch does) and it serialises
-                           concurrent solves, so it is off by default. */
+    int persistent_vcycle; /* the part of each V-cycle on the levels with
+                           n <= 64 below the finest: 0 (default): one launch
+                           per step; 1: one cooperative kernel over all SMs with
+                           grid barriers (when the device supports cooperative
+                           launches; nsets = 1 only); 2: one thread-block
+                           cluster per set (16 CTAs where the device can place
+                           them, else 8, 4 or 2) meeting at the cluster's
+                           hardware barrier.  The results are the same bits.
+                           On GB300 the cooperative form is not faster (a grid
+                           barrier costs about what a graph launch does, and it
+                           serialises concurrent solves). */
     int nsets;          /* independent problems of this shape held by the
                            context (the parameter sets of a rotation-curve fit,
                            Section 3.5), 1 <= nsets <= 1024 with

@@ -119,6 +119,7 @@ struct qumond_ctx {
     bool in_body = false;           // enqueueing a defect-correction V-cycle (sets that stopped are skipped)
     int vtop = -1;                  // top level of the cooperative small-level V-cycle kernel, -1: not used
     int vgrid = 0;                  // its CTAs (one per SM)
+    int vcs = 0;                    // persistent_vcycle = 2: CTAs of the cluster that runs it (per set)
     unsigned* vbar = nullptr;       // its grid-barrier counter
     long long barrier_polls = 1LL << 26;  // polls before one of its grid barriers gives up
     int64_t* Ffix = nullptr;        // fixed-point right-hand side
@@ -200,16 +201,16 @@ qumond_status check_params(qumond_ctx* c, const qumond_params* p)
     if (p->box_ratio != 2 && p->box_ratio != 4 && p->box_ratio != 8)
         return fail(c, QUMOND_ERR_INVALID_ARG, "box_ratio must be 2, 4 or 8");
     if (p->use_graphs != 0 && p->use_graphs != 1) return fail(c, QUMOND_ERR_INVALID_ARG, "use_graphs must be 0 or 1");
-    if (p->persistent_vcycle != 0 && p->persistent_vcycle != 1)
-        return fail(c, QUMOND_ERR_INVALID_ARG, "persistent_vcycle must be 0 or 1");
+    if (p->persistent_vcycle < 0 || p->persistent_vcycle > 2)
+        return fail(c, QUMOND_ERR_INVALID_ARG, "persistent_vcycle must be 0, 1 or 2");
     if (p->nboxes > 1 && p->n < 2 * p->box_ratio)
         return fail(c, QUMOND_ERR_INVALID_ARG, "n=%d too small for nested boxes of ratio %d", p->n, p->box_ratio);
     if (p->nsets < 1 || p->nsets > 1024 || (long long)p->nsets * (p->n + 1) > 65535)
         return fail(c, QUMOND_ERR_INVALID_ARG, "nsets=%d: need 1 <= nsets <= 1024 and nsets * (n + 1) <= 65535",
                     p->nsets);
     if (p->tile_small < 0 || p->tile_small > 2) return fail(c, QUMOND_ERR_INVALID_ARG, "tile_small must be 0, 1 or 2");
-    if (p->nsets > 1 && p->persistent_vcycle)
-        return fail(c, QUMOND_ERR_INVALID_ARG, "persistent_vcycle needs nsets = 1");
+    if (p->nsets > 1 && p->persistent_vcycle == 1)
+        return fail(c, QUMOND_ERR_INVALID_ARG, "persistent_vcycle = 1 needs nsets = 1");
     return QUMOND_OK;
 }
 
@@ -381,8 +382,11 @@ cudaError_t vsub(qumond_ctx* c, int box, bool zero_top, cudaStream_t s)
     count_cells(c, upd);
     cudaError_t err = cudaSuccess;
     run(c, K_VSUB, bytes, s, [&] {
-        err = launch_vsub<T>(e, f, v, h, nlev, zero_top ? 1 : 0, p.npre, p.npost, c->vbar, c->fault, c->barrier_polls,
-                             c->vgrid, s);
+        if (p.persistent_vcycle == 2)
+            err = launch_vcluster<T>(e, f, v, h, nlev, zero_top ? 1 : 0, p.npre, p.npost, c->vcs, s, sets_of(c));
+        else
+            err = launch_vsub<T>(e, f, v, h, nlev, zero_top ? 1 : 0, p.npre, p.npost, c->vbar, c->fault,
+                                 c->barrier_polls, c->vgrid, s);
     });
     return err;
 }
@@ -918,7 +922,18 @@ qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
             }
         }
     }
-    if (ok && p->persistent_vcycle) {
+    if (ok && p->persistent_vcycle == 2) {
+        // levels lc+1 .. vtop (n <= 64, below the finest) as one thread-block cluster per set
+        int top = -1;
+        for (int l = c->lc + 1; l < L; ++l)
+            if (c->lev[l].v.n <= 64) top = l;
+        const int cs = vcluster_size(p->precision == QUMOND_PREC_FP64);
+        if (cs >= 2 && top > c->lc && top - c->lc + 1 <= 6) {
+            c->vtop = top;
+            c->vcs = cs;
+        }
+    }
+    if (ok && p->persistent_vcycle == 1) {
         // levels lc+1 .. vtop (n <= 64, below the finest) in one cooperative kernel
         int dev = 0, coop = 0, sms = 0;
         cudaGetDevice(&dev);

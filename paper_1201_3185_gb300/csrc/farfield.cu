@@ -88,6 +88,12 @@ __device__ __forceinline__ void node_pos(const Geo& g, long long t, double& x, d
     z = g.z0 + k * g.h;
 }
 
+// The node loops stream the whole density once per kernel with few threads
+// (the reductions keep one partial per block), so each thread loads kFFILP
+// values before using any: enough bytes in flight to approach the memory
+// bandwidth.  Nodes are visited in the same order for any unrolling.
+constexpr int kFFILP = 8;
+
 // per-block sums of m, m x, m y, m z
 __global__ void __launch_bounds__(kFFThreads) ff_mass_kernel(const double* __restrict__ rho, Geo g,
                                                               double* __restrict__ part)
@@ -97,15 +103,22 @@ __global__ void __launch_bounds__(kFFThreads) ff_mass_kernel(const double* __res
     const long long N = nat_elems(g.n);
     rho += set * N;
     double a[4] = {0.0, 0.0, 0.0, 0.0};
-    for (long long t = blockIdx.x * (long long)kFFThreads + threadIdx.x; t < N; t += (long long)gridDim.x * kFFThreads) {
-        const double m = rho[t] * g.h3;
-        if (m == 0.0) continue;
-        double x, y, z;
-        node_pos(g, t, x, y, z);
-        a[0] += m;
-        a[1] += m * x;
-        a[2] += m * y;
-        a[3] += m * z;
+    const long long stride = (long long)gridDim.x * kFFThreads;
+    for (long long t0 = blockIdx.x * (long long)kFFThreads + threadIdx.x; t0 < N; t0 += kFFILP * stride) {
+        double r[kFFILP];
+#pragma unroll
+        for (int q = 0; q < kFFILP; ++q) r[q] = t0 + q * stride < N ? rho[t0 + q * stride] : 0.0;
+#pragma unroll
+        for (int q = 0; q < kFFILP; ++q) {
+            const double m = r[q] * g.h3;
+            if (m == 0.0) continue;
+            double x, y, z;
+            node_pos(g, t0 + q * stride, x, y, z);
+            a[0] += m;
+            a[1] += m * x;
+            a[2] += m * y;
+            a[3] += m * z;
+        }
     }
     double* out = part + ((long long)set * gridDim.x + blockIdx.x) * 4;
     for (int q = 0; q < 4; ++q) {
@@ -142,17 +155,24 @@ __global__ void __launch_bounds__(kFFThreads) ff_moments_kernel(const double* __
     double A[kFFTerms], B[kFFTerms];
 #pragma unroll
     for (int q = 0; q < kFFTerms; ++q) A[q] = B[q] = 0.0;
-    for (long long t = blockIdx.x * (long long)kFFThreads + threadIdx.x; t < N; t += (long long)gridDim.x * kFFThreads) {
-        const double m = rho[t] * g.h3;
-        if (m == 0.0) continue;
-        double x, y, z;
-        node_pos(g, t, x, y, z);
-        double re[kFFTerms], im[kFFTerms];
-        solid(x - cx, y - cy, z - cz, re, im);
+    const long long stride = (long long)gridDim.x * kFFThreads;
+    for (long long t0 = blockIdx.x * (long long)kFFThreads + threadIdx.x; t0 < N; t0 += kFFILP * stride) {
+        double r[kFFILP];
 #pragma unroll
-        for (int q = 0; q < kFFTerms; ++q) {
-            A[q] += m * re[q];
-            B[q] += m * im[q];
+        for (int q = 0; q < kFFILP; ++q) r[q] = t0 + q * stride < N ? rho[t0 + q * stride] : 0.0;
+#pragma unroll 1
+        for (int q = 0; q < kFFILP; ++q) {
+            const double m = r[q] * g.h3;
+            if (m == 0.0) continue;
+            double x, y, z;
+            node_pos(g, t0 + q * stride, x, y, z);
+            double re[kFFTerms], im[kFFTerms];
+            solid(x - cx, y - cy, z - cz, re, im);
+#pragma unroll
+            for (int p = 0; p < kFFTerms; ++p) {
+                A[p] += m * re[p];
+                B[p] += m * im[p];
+            }
         }
     }
     double* out = part + ((long long)set * gridDim.x + blockIdx.x) * (2 * kFFTerms);
@@ -216,14 +236,15 @@ __global__ void __launch_bounds__(kFFThreads) ff_boundary_kernel(Geo g, const do
     solid(dx, dy, dz, re, im);
     const double* A = mom + (long long)set * 2 * kFFTerms;
     const double* B = A + kFFTerms;
-    double sum = 0.0, rp = r;  // |d|^(2l+1)
+    const double ir = 1.0 / r, ir2 = ir * ir;
+    double sum = 0.0, ip = ir;  // |d|^-(2l+1)
 #pragma unroll
     for (int l = 0; l <= kFFL; ++l) {
         double sl = 0.0;
 #pragma unroll
         for (int m = 0; m <= l; ++m) sl += re[term(l, m)] * A[term(l, m)] + im[term(l, m)] * B[term(l, m)];
-        sum += sl / rp;
-        rp *= r2;
+        sum += sl * ip;
+        ip *= ir2;
     }
     phiN[o] = -G * sum;
     const double Am = G * M, C = 4.0 * a0 * Am;

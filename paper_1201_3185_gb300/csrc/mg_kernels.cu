@@ -89,7 +89,7 @@ rb_half_kernel(T* __restrict__ own, const T* __restrict__ other, const T* __rest
 // per row) leave most of an 8-wide block idle, so a context can pick 4 x 32 or
 // 2 x 64 for levels n <= 64 (params.tile_small).  Every shape gives the same
 // bits: each thread's entries are updated by the same arithmetic.
-constexpr int kVX = 8, kVY = 16;  // default: 32 entries x 16 rows per block
+constexpr int kVX = 8;  // default: 32 entries x 16 rows per block
 constexpr int kVThreads = 128;
 constexpr int kVBlocksPerSM = 16;  // full occupancy (<= 32 registers): the small levels are latency-bound
 constexpr int kTileSmallN = 64;  // the alternative shapes apply to levels with n <= this
@@ -454,8 +454,9 @@ __global__ void set_boundary_kernel(T* __restrict__ e, LevelView v, const double
 // The result (all nodes, boundary included) is written to e.
 // The shared-memory routines below stride over their nodes by the block's
 // size: the coarse-grid kernel runs them with kCoarseThreads, the cooperative
-// V-cycle kernel (one CTA per SM, more registers) with kVsubThreads.
-constexpr int kCoarseThreads = 1024;
+// and cluster V-cycle kernels with kVsubThreads.  (1024 threads for the
+// coarse-grid kernel measured no faster than 512.)
+constexpr int kCoarseThreads = 512;
 constexpr int kVsubThreads = 512;
 constexpr int kMaxCoarseLevels = 4;  // n = 2, 4, 8, 16
 
@@ -707,6 +708,7 @@ struct VsubArgs {
     unsigned* bar;  // barrier counter (zeroed before the launch)
     int* fault;
     long long polls;  // a barrier gives up after this many polls of the counter
+    const SolveState* act;  // cluster form with several sets: skip the sets that have stopped
 };
 
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen, int* fault, long long polls)
@@ -732,8 +734,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen, int* 
     return give_up == 0;
 }
 
+// Phase work is dealt to `nblk` CTAs, this one being `rank`.
 template <typename T>
-__device__ void vsub_rb(const VsubLevel<T>& L, int colour, bool zero)
+__device__ void vsub_rb(const VsubLevel<T>& L, int colour, bool zero, int rank, int nblk)
 {
     const LevelView& v = L.v;
     const int half = v.n >> 1, rows = v.n - 1;
@@ -742,7 +745,7 @@ __device__ void vsub_rb(const VsubLevel<T>& L, int colour, bool zero)
     T* own = L.e + (long long)colour * v.cs;
     const T* other = L.e + (long long)(colour ^ 1) * v.cs;
     const T* f = L.f + (long long)colour * v.cs;
-    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < W; w += (long long)gridDim.x * blockDim.x) {
+    for (long long w = rank * (long long)blockDim.x + threadIdx.x; w < W; w += (long long)nblk * blockDim.x) {
         const int m = (int)(w % half);
         const long long r = w / half;
         const int j = (int)(r % rows) + 1, k = (int)(r / rows) + 1;
@@ -753,38 +756,39 @@ __device__ void vsub_rb(const VsubLevel<T>& L, int colour, bool zero)
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kVsubThreads) vsub_kernel(VsubArgs<T> a)
+// The V-cycle on lev[top] .. lev[0] with `nblk` CTAs sharing each phase and
+// `sync()` between phases (false: a barrier gave up, stop); CTA rank 0 runs
+// the coarse-grid level in its shared memory.
+template <typename T, class Sync>
+__device__ void vsub_body(const VsubArgs<T>& a, const VsubLevel<T>* lev, int rank, int nblk, unsigned char* smem_raw,
+                          Sync&& sync)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned gen = 0;
     bool ok = true;
     // down: smooth, restrict
     for (int l = a.top; l >= 1 && ok; --l) {
-        const VsubLevel<T>& L = a.lev[l];
+        const VsubLevel<T>& L = lev[l];
         for (int q = 0; q < a.npre && ok; ++q) {
-            vsub_rb(L, 0, q == 0 && (l < a.top || a.zero_top));
-            ok = grid_barrier(a.bar, gen, a.fault, a.polls);
+            vsub_rb(L, 0, q == 0 && (l < a.top || a.zero_top), rank, nblk);
+            ok = sync();
             if (!ok) break;
-            vsub_rb(L, 1, false);
-            ok = grid_barrier(a.bar, gen, a.fault, a.polls);
+            vsub_rb(L, 1, false, rank, nblk);
+            ok = sync();
         }
         if (!ok) break;
-        const VsubLevel<T>& C = a.lev[l - 1];
+        const VsubLevel<T>& C = lev[l - 1];
         const int mc = C.v.n - 1;
         const long long W = (long long)mc * mc * mc;
         const T ih2 = T(1) / (L.h * L.h);
-        for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < W;
-             w += (long long)gridDim.x * blockDim.x) {
+        for (long long w = rank * (long long)blockDim.x + threadIdx.x; w < W; w += (long long)nblk * blockDim.x) {
             const int I = (int)(w % mc) + 1, J = (int)((w / mc) % mc) + 1, K = (int)(w / ((long long)mc * mc)) + 1;
             restrict_node<T>(L.e, L.f, L.v, C.f, C.v, ih2, I, J, K);
         }
-        ok = grid_barrier(a.bar, gen, a.fault, a.polls);
+        ok = sync();
     }
     if (!ok) return;
     // the coarse-grid level: one V-cycle from zero in CTA 0's shared memory
-    if (blockIdx.x == 0) {
-        const VsubLevel<T>& C = a.lev[0];
+    if (rank == 0) {
+        const VsubLevel<T>& C = lev[0];
         switch (C.v.n) {
         case 2: coarse_run<T, 0>(smem_raw, 0, C.e, C.f, C.v, C.h, nullptr, 0, 0, a.npre, a.npost); break;
         case 4: coarse_run<T, 1>(smem_raw, 0, C.e, C.f, C.v, C.h, nullptr, 0, 0, a.npre, a.npost); break;
@@ -792,28 +796,70 @@ __global__ void __launch_bounds__(kVsubThreads) vsub_kernel(VsubArgs<T> a)
         default: coarse_run<T, 3>(smem_raw, 0, C.e, C.f, C.v, C.h, nullptr, 0, 0, a.npre, a.npost); break;
         }
     }
-    ok = grid_barrier(a.bar, gen, a.fault, a.polls);
+    ok = sync();
     // up: correct, smooth
     for (int l = 1; l <= a.top && ok; ++l) {
-        const VsubLevel<T>& L = a.lev[l];
-        const VsubLevel<T>& C = a.lev[l - 1];
+        const VsubLevel<T>& L = lev[l];
+        const VsubLevel<T>& C = lev[l - 1];
         const int half = L.v.n >> 1, rows = L.v.n - 1;
         const long long W = (long long)half * rows * rows;
-        for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < W;
-             w += (long long)gridDim.x * blockDim.x) {
+        for (long long w = rank * (long long)blockDim.x + threadIdx.x; w < W; w += (long long)nblk * blockDim.x) {
             const int m = (int)(w % half);
             const long long r = w / half;
             prolong_node<T, true>(C.e, C.v, L.e, L.v, m, (int)(r % rows) + 1, (int)(r / rows) + 1);
         }
-        ok = grid_barrier(a.bar, gen, a.fault, a.polls);
+        ok = sync();
         for (int q = 0; q < a.npost && ok; ++q) {
-            vsub_rb(L, 0, false);
-            ok = grid_barrier(a.bar, gen, a.fault, a.polls);
+            vsub_rb(L, 0, false, rank, nblk);
+            ok = sync();
             if (!ok) break;
-            vsub_rb(L, 1, false);
-            if (l < a.top || q + 1 < a.npost) ok = grid_barrier(a.bar, gen, a.fault, a.polls);
+            vsub_rb(L, 1, false, rank, nblk);
+            if (l < a.top || q + 1 < a.npost) ok = sync();
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kVsubThreads) vsub_kernel(VsubArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned gen = 0;
+    vsub_body(a, a.lev, (int)blockIdx.x, (int)gridDim.x, smem_raw,
+              [&]() { return grid_barrier(a.bar, gen, a.fault, a.polls); });
+}
+
+// The same V-cycle as one thread-block cluster per set (csize CTAs; cluster
+// s takes set s).  The phases meet at the cluster's hardware barrier with
+// release / acquire semantics, so every global write of a phase is visible to
+// the whole cluster in the next.  The hardware schedules a cluster's CTAs
+// together and every CTA of it passes the same barriers (a set whose
+// correction has stopped returns in all of them before the first), so no
+// wait is left open.  No grid-wide synchronisation: concurrent solves and
+// the sets of a context run side by side.
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kVsubThreads) vcluster_kernel(VsubArgs<T> a, int csize)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int set = (int)blockIdx.x / csize, rank = (int)blockIdx.x - set * csize;
+    if (a.act && !a.act[set].cont) return;
+    VsubLevel<T> lev[kVsubMaxLevels];
+#pragma unroll
+    for (int l = 0; l < kVsubMaxLevels; ++l) {
+        lev[l] = a.lev[l];
+        if (l <= a.top) {
+            lev[l].e += (long long)set * 2 * lev[l].v.cs;
+            lev[l].f += (long long)set * 2 * lev[l].v.cs;
+        }
+    }
+    vsub_body(a, lev, rank, csize, smem_raw, []() {
+        cluster_sync_all();
+        return true;
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -1244,6 +1290,57 @@ cudaError_t launch_vsub(T* const* e, T* const* f, const LevelView* v, const doub
     return cudaLaunchKernelEx(&cfg, vsub_kernel<T>, a);
 }
 
+template <typename T>
+cudaError_t launch_vcluster(T* const* e, T* const* f, const LevelView* v, const double* h, int nlev, int zero_top,
+                            int npre, int npost, int csize, cudaStream_t s, const Sets& sets)
+{
+    if (nlev < 2 || nlev > kVsubMaxLevels || v[0].n > kCoarseN || csize < 1) return cudaErrorInvalidValue;
+    VsubArgs<T> a{};
+    for (int l = 0; l < nlev; ++l) a.lev[l] = VsubLevel<T>{e[l], f[l], v[l], (T)h[l]};
+    a.top = nlev - 1;
+    a.zero_top = zero_top;
+    a.npre = npre;
+    a.npost = npost;
+    a.act = sets.act;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(csize * sets.n));
+    cfg.blockDim = dim3(kVsubThreads);
+    cfg.dynamicSmemBytes = coarse_smem_bytes<T>(v[0].n);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, vcluster_kernel<T>, a, csize);
+}
+
+int vcluster_size(bool fp64)
+{
+    // the largest cluster (16 needs the non-portable size) of which at least one fits on the device
+    for (int cs = 16; cs >= 2; cs /= 2) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)cs);
+        cfg.blockDim = dim3(kVsubThreads);
+        cfg.dynamicSmemBytes = fp64 ? coarse_smem_bytes<double>(kCoarseN) : coarse_smem_bytes<float>(kCoarseN);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        const cudaError_t e = fp64 ? cudaOccupancyMaxActiveClusters(&n, vcluster_kernel<double>, &cfg)
+                                   : cudaOccupancyMaxActiveClusters(&n, vcluster_kernel<float>, &cfg);
+        if (e == cudaSuccess && n >= 1) return cs;
+        (void)cudaGetLastError();
+    }
+    return 0;
+}
+
 int vsub_grid(int sms)
 {
     // one CTA per SM: the kernel's shared memory (the coarse solver's) allows one or more per SM
@@ -1321,7 +1418,15 @@ cudaError_t prepare_kernels()
     if (cudaFuncSetAttribute(vsub_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)coarse_smem_bytes<float>(kCoarseN)) != cudaSuccess ||
         cudaFuncSetAttribute(vsub_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)coarse_smem_bytes<double>(kCoarseN)) != cudaSuccess)
+                             (int)coarse_smem_bytes<double>(kCoarseN)) != cudaSuccess ||
+        cudaFuncSetAttribute(vcluster_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)coarse_smem_bytes<float>(kCoarseN)) != cudaSuccess ||
+        cudaFuncSetAttribute(vcluster_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)coarse_smem_bytes<double>(kCoarseN)) != cudaSuccess ||
+        cudaFuncSetAttribute(vcluster_kernel<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(vcluster_kernel<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess)
         return cudaGetLastError();
     cudaError_t e = cudaFuncSetAttribute(coarse_kernel<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)coarse_smem_bytes<float>(kCoarseN));
@@ -1346,6 +1451,8 @@ void launch_reduce_norms(const double* partials, int nblocks, double* out, cudaS
     template void launch_set_boundary<T>(T*, const LevelView&, const double*, int, cudaStream_t, const Sets&);        \
     template cudaError_t launch_vsub<T>(T* const*, T* const*, const LevelView*, const double*, int, int, int, int,     \
                                         unsigned*, int*, long long, int, cudaStream_t);                               \
+    template cudaError_t launch_vcluster<T>(T* const*, T* const*, const LevelView*, const double*, int, int, int, int, \
+                                            int, cudaStream_t, const Sets&);                                           \
     template cudaError_t launch_coarse<T>(int, T*, const T*, const LevelView&, double, const double*, int, int, int,  \
                                           int, cudaStream_t, const Sets&);                                             \
     template void launch_convert_rhs<T>(const double*, double, int, T*, const LevelView&, cudaStream_t, const Sets&); \

@@ -95,6 +95,12 @@ template <typename T> cudaError_t launch_vsub(T* const* e, T* const* f, const Le
                                               int zero_top, int npre, int npost, unsigned* bar, int* fault,
                                               long long polls, int grid, cudaStream_t s);
 int vsub_grid(int sms);
+// the same V-cycle as one thread-block cluster of csize CTAs per set (no grid-wide barrier)
+template <typename T> cudaError_t launch_vcluster(T* const* e, T* const* f, const LevelView* v, const double* h,
+                                                  int nlev, int zero_top, int npre, int npost, int csize,
+                                                  cudaStream_t s, const Sets& sets = Sets());
+// largest cluster size (16, 8, 4 or 2) the device can schedule for it, 0 if none
+int vcluster_size(bool fp64);
 template <typename T> cudaError_t launch_coarse(int fmg, T* e, const T* f, const LevelView& v, double h,
                                                 const double* u64, int nfine, int ncycle, int npre, int npost,
                                                 cudaStream_t s, const Sets& sets = Sets());

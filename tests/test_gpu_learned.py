@@ -3,11 +3,16 @@ by `python -m paper_1201_3185_gb300.learned train`) gains over the method
 without it, on galaxies it has not seen (129^3 x 2 boxes, two-disk galaxies,
 QUMOND solves to rel. residual 1e-8 in the fixed-point mode).
 
-Starting the QUMOND solve from Phi_N + network output instead of from Phi_N
-alone must save V-cycles in every box, and the solve must end at the same
-discrete solution as the FMG start.  FMG itself is the method's default
-start; the comparison with it is printed (and recorded in the design notes),
-not asserted."""
+* Against a Phi_N start: starting the QUMOND solve from Phi_N + network output
+  saves V-cycles in every box, and the solve ends at the same discrete
+  solution as an accurate (1e-10) solve.
+* Against the method's own start (FMG, Section 2): the network does not pay.
+  Its guess starts from a larger residual than FMG's and needs at least as
+  many V-cycles, and one inference (14 BF16 convolutions over 128^3 voxels,
+  about 2 ms) costs more than the whole FMG start at this size, so the solve
+  from the guess is slower.  The test asserts that measured ordering: FMG
+  stays the default start, and the network is an optional start whose cost
+  the bench reports (bench.py --workload learned)."""
 import os
 
 import numpy as np
@@ -17,7 +22,7 @@ import torch
 pytestmark = pytest.mark.gpu
 
 
-def test_learned_start_saves_vcycles():
+def test_learned_start_against_phiN_and_fmg_starts():
     import paper_1201_3185_gb300 as q
     from paper_1201_3185_gb300 import learned as L
     assert os.path.exists(L.WEIGHTS), "trained weights missing"
@@ -25,6 +30,7 @@ def test_learned_start_saves_vcycles():
     guess = q.Guess(128, L.PHI_SCALE)
     guess.qumond_guess_set_params(torch.from_numpy(L.load_weights()).to(dev))
     work = L.Workload(n=128, particles=200_000, seed=424242, device=dev)
+    L.evaluate(work, guess, 1)  # warm-up: graph capture, first inference
     rows = L.evaluate(work, guess, 2)
     for r in rows:
         print("box %d h*=%.0f pc: " % (r["box"], r["h_star"]) +
@@ -32,7 +38,16 @@ def test_learned_start_saves_vcycles():
                                                                           r[k]["rel_residual_start"], r[k]["ms"])
                         for k in L.STARTS))
         assert r["learned"]["vcycles"] < r["phiN"]["vcycles"]
-        assert r["learned"]["rel_residual"] <= 1e-8
+        assert r["learned"]["rel_residual"] <= 1e-8 and r["fmg"]["rel_residual"] <= 1e-8
         # the solve from the guess and the accurate (1e-10) solve agree to the path's potential bound
         assert r["learned"]["max_rel_diff_vs_accurate"] < 1e-6
+    s = L.summarize(rows)
+    ratio = s["fmg"]["mean_ms"] / s["learned"]["mean_ms"]
+    print("per solve: FMG start %.2f ms, %.1f V-cycles; learned start %.2f ms (inference included), %.1f V-cycles; "
+          "speed of the learned start relative to FMG %.2f" % (s["fmg"]["mean_ms"], s["fmg"]["mean_vcycles"],
+                                                                s["learned"]["mean_ms"], s["learned"]["mean_vcycles"],
+                                                                ratio))
+    assert s["learned"]["median_rel_residual_start"] > s["fmg"]["median_rel_residual_start"]
+    assert s["learned"]["mean_vcycles"] >= s["fmg"]["mean_vcycles"]
+    assert 0.0 < ratio < 1.0
     guess.close()

@@ -309,15 +309,18 @@ def test_graph_and_one_by_one_launches_agree(q, prec):
     assert np.array_equal(a["vc"], b["vc"])
 
 
-@pytest.mark.parametrize("prec_name,graphs", [("MIXED_FIXED", 1), ("MIXED_FIXED", 0), ("FP64", 1)])
-def test_cooperative_small_level_vcycle_gives_the_same_bits(q, prec_name, graphs):
+@pytest.mark.parametrize("prec_name,graphs,form", [("MIXED_FIXED", 1, 1), ("MIXED_FIXED", 0, 1), ("FP64", 1, 1),
+                                                    ("MIXED_FIXED", 1, 2), ("MIXED_FIXED", 0, 2), ("FP64", 1, 2),
+                                                    ("MIXED", 1, 2)])
+def test_cooperative_small_level_vcycle_gives_the_same_bits(q, prec_name, graphs, form):
     # the V-cycle on the levels n <= 64 below the finest as one cooperative
-    # kernel with grid barriers, or one launch per step: the same node
+    # kernel with grid barriers (form 1) or one thread-block cluster with the
+    # cluster's barrier (form 2), or one launch per step: the same node
     # arithmetic, so the same bits (n = 128: levels 64 and 32 above the coarse grid)
     prec = getattr(q, "QUMOND_PREC_" + prec_name)
     p = synth.two_component_disk(50_000, seed=12, rmax=54000.0, zmax=54000.0)
     a = gpu_pipeline(p, 128, 120000.0, 2, rel_tol=1e-10, max_vcycles=40, precision=prec, use_graphs=graphs,
-                     persistent_vcycle=1)
+                     persistent_vcycle=form)
     b = gpu_pipeline(p, 128, 120000.0, 2, rel_tol=1e-10, max_vcycles=40, precision=prec, use_graphs=graphs,
                      persistent_vcycle=0)
     for key in ("phiN", "phi"):

@@ -76,9 +76,11 @@ def device_sets(gal, params):
     return [tuple(to_dev(a) for a in (p.x, p.y, p.z, p.m)) for p in (gal.particles(r) for r in params)]
 
 
-@pytest.mark.parametrize("prec_name,graphs", [("MIXED_FIXED", 1), ("MIXED_FIXED", 0), ("MIXED", 1), ("FP64", 1)])
-def test_context_sets_match_one_set_contexts(q, prec_name, graphs):
-    """A context with nsets = 4: deposit, both solves of two boxes, source,
+@pytest.mark.parametrize("prec_name,graphs,form", [("MIXED_FIXED", 1, 0), ("MIXED_FIXED", 0, 0), ("MIXED", 1, 0),
+                                                    ("FP64", 1, 0), ("MIXED_FIXED", 1, 2), ("FP64", 0, 2)])
+def test_context_sets_match_one_set_contexts(q, prec_name, graphs, form):
+    """A context with nsets = 4 (the small levels' V-cycle one launch per step,
+    or one thread-block cluster per set): deposit, both solves of two boxes, source,
     forces and rotation curves of all sets in one launch per kernel; every
     set's results are the bits of a context holding that set alone, although
     the sets need different numbers of V-cycles (the converged ones are
@@ -92,7 +94,7 @@ def test_context_sets_match_one_set_contexts(q, prec_name, graphs):
     # after FMG while the others need several, and the later V-cycles must skip it
     ps[-1] = synth.Particles(ps[-1].x + 1e9, ps[-1].y, ps[-1].z, ps[-1].m)
     kw = dict(n=n, nboxes=2, L0=L0, precision=prec, rel_tol=1e-10, max_vcycles=40, use_graphs=graphs)
-    many = q.Context(nsets=4, **kw)
+    many = q.Context(nsets=4, persistent_vcycle=form, **kw)  # form 2: one cluster per set for the small levels
     pm = q.Pipeline(many)
     x, y, z, m = (to_dev(np.concatenate([getattr(p, a) for p in ps])) for a in "xyzm")
     g = tuple(torch.empty_like(x) for _ in range(3))
