@@ -1,9 +1,13 @@
 """The far-field boundary of box 0 (QUMOND_BC_MULTIPOLE) against the oracle.
 
 * qumond_far_field on the GPU's own deposit (bit-exact with the oracle's)
-  against ora_far_field: boundary values within 1e-12 of max|Phi| (FP64 on
-  both sides, the moment sums in different orders); interior untouched;
-  every set of a context with several sets against its own oracle run.
+  against ora_far_field: the QUMOND boundary values (FP64 on both sides, the
+  sums in different orders) within 1e-12 of max|Phi|; the Newtonian ones
+  within 1e-12 of max|Phi_N| plus 1e-5 of the largest contribution of the
+  degrees 3..8 (the GPU evaluates those in FP32: a few roundings of 2^-24
+  through the recurrence of depth 8, the sum over m and the FP32 moments,
+  ~1e-6 of the terms, allowed ten times); interior untouched; every set of a
+  context with several sets against its own oracle run.
 * The whole path with the multipole boundary, two chains, graphs, fixed point,
   3 boxes: every potential within 1e-6 of max and the rotation curve within
   1e-5 of the oracle's pipeline with the same boundary.
@@ -48,10 +52,15 @@ def test_far_field_matches_oracle(q, ora, n, nsets):
         r_s = rho[s * N:(s + 1) * N].cpu().numpy()
         assert np.array_equal(qf[s * N:(s + 1) * N].cpu().numpy(), want_q)
         wN, wM, M = ora.far_field(n, L0, (0.0, 0.0, 0.0), r_s, lmax=8)
+        w2, _, _ = ora.far_field(n, L0, (0.0, 0.0, 0.0), r_s, lmax=2)
         gN = phiN[s * N:(s + 1) * N].cpu().numpy()
         gM = phi[s * N:(s + 1) * N].cpu().numpy()
         assert M > 0.0
-        assert np.max(np.abs(gN[b] - wN[b])) < 1e-12 * np.max(np.abs(wN[b])), s
+        high = np.max(np.abs(wN[b] - w2[b]))  # the degrees 3..8
+        err = np.max(np.abs(gN[b] - wN[b]))
+        print("set %d: Phi_N error %.2e of max, high degrees %.2e of max" % (s, err / np.max(np.abs(wN[b])),
+                                                                           high / np.max(np.abs(wN[b]))))
+        assert err < 1e-12 * np.max(np.abs(wN[b])) + 1e-5 * high, s
         assert np.max(np.abs(gM[b] - wM[b])) < 1e-12 * np.max(np.abs(wM[b])), s
         assert np.all(gN[~b] == 7.0) and np.all(gM[~b] == 7.0)
     ctx.close()
