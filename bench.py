@@ -331,7 +331,19 @@ def run_ours(args):
     kstats, _, _ = ctx.qumond_trace_read(reset=True)
     ctx.qumond_trace_timing(False)
 
-    # --- timed region: inputs resident in HBM; each solve is one CUDA graph -------------
+    # --- timed region: inputs resident in HBM; each solve is one CUDA graph.  With two chains
+    # the K steps run pipelined (Pipeline.run_many): the Newtonian chain of step i+1 overlaps
+    # the QUMOND chain, forces and rotation curve of step i; every step is the whole path. ---
+    pipelined = args.chains == 2 and not args.no_pipeline
+
+    def steps_timed(nsteps, pp=None):
+        pp = pp or pipe
+        if pipelined and pp.ctx_mond is not None:
+            return pp.run_many([(xd, yd, zd, md)] * nsteps, nbins=w["nbins"], rmax=w["rmax"], nphi=w["nphi"],
+                               forces=[g] * nsteps)
+        return [step(pp) for _ in range(nsteps)]
+
+    steps_timed(max(2, args.warmup))  # captures the graphs of the pipelined form
     ctx.qumond_trace_read(reset=True)
     clocks = ClockSampler(local)
     barrier()
@@ -339,8 +351,7 @@ def run_ours(args):
     s0 = torch.cuda.Event(enable_timing=True)
     s1 = torch.cuda.Event(enable_timing=True)
     s0.record()
-    for _ in range(args.steps):
-        res = step()
+    res = steps_timed(args.steps)[-1]
     s1.record()
     barrier()
     clk = clocks.stop()
@@ -349,6 +360,21 @@ def run_ours(args):
     step_bytes = sum(k.bytes for k in timed_stats.values()) / args.steps
     ms_step = ms_total / args.steps
     value = ws * args.steps / (ms_total / 1000.0)
+
+    # the same steps one after another (each waits for the previous one to finish)
+    step_by_step = None
+    if pipelined:
+        barrier()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record()
+        for _ in range(args.steps):
+            step()
+        b1.record()
+        barrier()
+        sbs_ms = max_over_ranks(b0.elapsed_time(b1)) / args.steps
+        step_by_step = {"value": ws * 1000.0 / sbs_ms, "unit": UNIT, "ms_per_step": sbs_ms,
+                        "form": "each step's two chains overlap each other only (Pipeline.run per step)"}
 
     # --- kernels timed live: the same steps with one chain (no concurrent solve sharing
     # the GPU), the graphs carrying event-record nodes around each run of consecutive
@@ -414,28 +440,48 @@ def run_ours(args):
                         "GBps": (k.timed_bytes / k.ms / 1e6) if k.ms else None}
                for k in sorted(kstats.values(), key=lambda k: -k.ms) if k.launches}
 
-    # --- end to end through the public API, host buffers ---------------------------------
+    # --- end to end through the public API, host buffers: every step's particles copied in
+    # from pinned host memory, its forces and rotation curve copied out ------------------
     host = [torch.from_numpy(a).pin_memory() for a in (p.x, p.y, p.z, p.m)]
-    out_g = [torch.empty(w["particles"], dtype=torch.float64).pin_memory() for _ in range(3)]
-    out_vc = torch.empty(w["nbins"], dtype=torch.float64).pin_memory()
+    out_g = [[torch.empty(w["particles"], dtype=torch.float64).pin_memory() for _ in range(3)]
+             for _ in range(args.steps if pipelined else 1)]
+    out_vc = torch.empty(args.steps, w["nbins"], dtype=torch.float64).pin_memory()
+    out_r = torch.empty(args.steps, w["nbins"], dtype=torch.float64).pin_memory()
     h2d = sum(t.numel() * t.element_size() for t in host)
-    d2h = sum(t.numel() * t.element_size() for t in out_g) + out_vc.numel() * 8 * 2
+    d2h = sum(t.numel() * t.element_size() for t in out_g[0]) + w["nbins"] * 8 * 2
+    if pipelined:  # device buffers of every step, so that the steps can overlap
+        dev_in = [[torch.empty_like(xd) for _ in range(4)] for _ in range(args.steps)]
+        dev_g = [tuple(torch.empty_like(xd) for _ in range(3)) for _ in range(args.steps)]
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
-        xs, ys, zs, ms_ = (t.to(dev, non_blocking=True) for t in host)
-        gg = tuple(torch.empty_like(xs) for _ in range(3))
-        r = pipe.run(xs, ys, zs, ms_, nbins=w["nbins"], rmax=w["rmax"], nphi=w["nphi"], forces=gg)
-        for a, b in zip(out_g, gg):
-            a.copy_(b, non_blocking=True)
-        out_vc.copy_(r.vc, non_blocking=True)
-        r_host = r.r.to("cpu", non_blocking=True)
+    if pipelined:
+        for i in range(args.steps):
+            for a, b in zip(dev_in[i], host):
+                a.copy_(b, non_blocking=True)
+        rs = pipe.run_many([tuple(d) for d in dev_in], nbins=w["nbins"], rmax=w["rmax"], nphi=w["nphi"],
+                           forces=dev_g)
+        for i in range(args.steps):
+            for a, b in zip(out_g[i], dev_g[i]):
+                a.copy_(b, non_blocking=True)
+            out_vc[i].copy_(rs[i].vc, non_blocking=True)
+            out_r[i].copy_(rs[i].r, non_blocking=True)
+    else:
+        for i in range(args.steps):
+            xs, ys, zs, ms_ = (t.to(dev, non_blocking=True) for t in host)
+            gg = tuple(torch.empty_like(xs) for _ in range(3))
+            r = pipe.run(xs, ys, zs, ms_, nbins=w["nbins"], rmax=w["rmax"], nphi=w["nphi"], forces=gg)
+            for a, b in zip(out_g[0], gg):
+                a.copy_(b, non_blocking=True)
+            out_vc[i].copy_(r.vc, non_blocking=True)
+            out_r[i].copy_(r.r, non_blocking=True)
     e1.record()
     barrier()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1))
     e2e_value = ws * args.steps / (e2e_ms / 1000.0)
+    if pipelined:
+        del dev_in, dev_g
 
     # --- the other arithmetic modes at the same final residual -------------------------
     def time_mode(precision, nsteps):
@@ -498,6 +544,8 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "gpu_launches_per_step": launches / args.steps,
             "chains": args.chains,
+            "pipelined_steps": pipelined,
+            "step_by_step": step_by_step,
             "small_level_vcycle": {0: "one launch per step", 1: "one cooperative kernel", 2: "one thread-block cluster per set"}[args.persistent_vcycle],
             "one_chain": {"value": ws * 1000.0 / one_chain_ms, "unit": UNIT, "ms_per_step": one_chain_ms},
             "vcycles_after_fmg_per_solve": vcycles,
@@ -1051,6 +1099,8 @@ def main():
     ap.add_argument("--workers", type=int, default=0,
                     help="sweep: lanes of one 64-set chunk each (0: batch size, lanes and block shape by the "
                          "autotuner)")
+    ap.add_argument("--no-pipeline", action="store_true",
+                    help="time the steps one after another instead of pipelining successive steps' chains")
     ap.add_argument("--persistent-vcycle", type=int, choices=[0, 1, 2], default=0,
                     help="the V-cycle on the levels n <= 64: 0 one launch per step, 1 one cooperative kernel, "
                          "2 one thread-block cluster (two-disk and large workloads)")

@@ -184,6 +184,133 @@ class Pipeline:
         caller.wait_event(end_b)
         return ns, ms
 
+    def run_many(self, inputs, *, nbins=50, rmax=30000.0, nphi=64, forces=None, stream=None):
+        """The whole path (as run()) for a sequence of evaluations, one (x, y,
+        z, m) tuple of device tensors each, with the two chains pipelined
+        across evaluations: the Newtonian chain of evaluation i+1 (deposits,
+        far field, Newtonian solves, sources) runs while the QUMOND chain
+        finishes evaluation i (its QUMOND solves, then the forces and the
+        rotation curve, which this form runs on the QUMOND chain's context and
+        stream).  Every evaluation runs the kernels of run() in the same order
+        on the same data, so its results are the same bits.
+
+        Ordering between the chains, with CUDA events: the source of box b of
+        evaluation i+1 waits for the QUMOND solve of box b of evaluation i
+        (they share the source buffer); with the far-field boundary, box 0's
+        potential alternates between two buffers, and the far field of
+        evaluation i+2 waits until evaluation i's forces and curve are done.
+        forces: None, or one (gx, gy, gz) tuple per evaluation.  Needs two
+        contexts (ctx_mond).  Returns one PipelineResult per evaluation (r,
+        vc; no solve statistics)."""
+        if self.ctx_mond is None:
+            raise ValueError("run_many pipelines the two chains: it needs ctx_mond")
+        if self.guess is not None:
+            raise ValueError("the learned guess runs in the sequential order only")
+        nev = len(inputs)
+        if forces is not None and len(forces) != nev:
+            raise ValueError("need one forces tuple per evaluation")
+        nb = self.ctx.params.nboxes
+        dev = self.device
+        caller = stream if stream is not None else torch.cuda.current_stream(dev)
+        sa, sb = self._streams
+        if self.far_field and not hasattr(self, "_phi0_alt"):
+            self._phi0_alt = torch.zeros_like(self.phi[0])
+        phi0 = [self.phi[0], getattr(self, "_phi0_alt", self.phi[0])]
+        results = [PipelineResult(torch.empty(nbins * self.ctx.nsets, dtype=torch.float64, device=dev),
+                                  torch.empty(nbins * self.ctx.nsets, dtype=torch.float64, device=dev))
+                   for _ in range(nev)]
+        start = torch.cuda.Event()
+        start.record(caller)
+        sa.wait_event(start)
+        sb.wait_event(start)
+        src_done = [[torch.cuda.Event() for _ in range(nb)] for _ in range(nev)]
+        mond_done = [[torch.cuda.Event() for _ in range(nb)] for _ in range(nev)]
+        eval_done = [torch.cuda.Event() for _ in range(nev)]
+        ready = [[threading.Event() for _ in range(nb)] for _ in range(nev)]
+        mond_rec = [[threading.Event() for _ in range(nb)] for _ in range(nev)]
+        eval_rec = [threading.Event() for _ in range(nev)]
+        failed = []
+
+        def phis_of(i):
+            return [phi0[i % 2] if self.far_field else self.phi[0]] + self.phi[1:]
+
+        def mond_chain():
+            with torch.cuda.device(dev):
+                try:
+                    for i in range(nev):
+                        phis = phis_of(i)
+                        for b in range(nb):
+                            ready[i][b].wait()
+                            if failed:
+                                return
+                            sb.wait_event(src_done[i][b])
+                            self.ctx_mond.qumond_solve_mond(b, self.srcs[b], phis[b - 1] if b > 0 else None, phis[b],
+                                                            stream=sb)
+                            mond_done[i][b].record(sb)
+                            mond_rec[i][b].set()
+                        x, y, z, _ = inputs[i]
+                        if forces is not None:
+                            self.ctx_mond.qumond_forces(phis, x, y, z, *forces[i], stream=sb)
+                        self.ctx_mond.qumond_rotation_curve(phis, nbins, rmax, nphi, results[i].r, results[i].vc,
+                                                            stream=sb)
+                        eval_done[i].record(sb)
+                        eval_rec[i].set()
+                except Exception:
+                    failed.append(True)
+                    for ev in [e for row in mond_rec for e in row] + eval_rec:
+                        ev.set()
+                    raise
+
+        fut = self._pool.submit(mond_chain)
+        try:
+            for i in range(nev):
+                x, y, z, m = inputs[i]
+                phis = phis_of(i)
+                for b in range(nb):
+                    self.ctx.qumond_deposit(b, x, y, z, m, self.rho_fixed, self.rho, stream=sa)
+                    if b == 0 and self.far_field:
+                        if i >= 2:  # box 0's potential buffer of evaluation i-2 is free once its forces and curve are
+                            eval_rec[i - 2].wait()
+                            if failed:
+                                break
+                            sa.wait_event(eval_done[i - 2])
+                        self.ctx.qumond_far_field(self.rho, self.phiN[0], phis[0], stream=sa)
+                    par = self.phiN[b - 1] if b > 0 else None
+                    self.ctx.qumond_solve_newton(b, self.rho, par, self.phiN[b], stream=sa)
+                    if i >= 1:  # the source buffer of box b is free once evaluation i-1's QUMOND solve has read it
+                        mond_rec[i - 1][b].wait()
+                        if failed:
+                            break
+                        sa.wait_event(mond_done[i - 1][b])
+                    self.ctx.qumond_source(b, self.phiN[b], self.srcs[b], stream=sa)
+                    src_done[i][b].record(sa)
+                    ready[i][b].set()
+                if failed:
+                    break
+        except Exception:
+            failed.append(True)
+            for row in ready:
+                for e in row:
+                    e.set()
+            try:
+                fut.result()
+            except Exception:
+                pass
+            raise
+        if failed:
+            for row in ready:
+                for e in row:
+                    e.set()
+        fut.result()  # re-raises the QUMOND chain's error
+        end_a, end_b = torch.cuda.Event(), torch.cuda.Event()
+        end_a.record(sa)
+        end_b.record(sb)
+        caller.wait_event(end_a)
+        caller.wait_event(end_b)
+        if self.far_field and nev % 2 == 0:  # self.phi holds the last evaluation's potentials
+            self.phi[0], self._phi0_alt = self._phi0_alt, self.phi[0]
+        return results
+
     def run(self, x, y, z, m, *, nbins=50, rmax=30000.0, nphi=64, forces=None, stats=False, stream=None):
         """The whole path: potentials, then forces at (x, y, z) into `forces`
         (a tuple gx, gy, gz of tensors, or None to skip) and the rotation curve."""

@@ -384,3 +384,42 @@ def test_invalid_arguments_rejected(q):
     with pytest.raises(q.QumondError):  # box out of range
         ctx.qumond_source(2, dev, torch.zeros_like(dev))
     ctx.close()
+
+
+@pytest.mark.parametrize("bc", ["zero", "multipole"])
+def test_pipelined_evaluations_give_the_same_bits(q, bc):
+    # run_many overlaps the Newtonian chain of evaluation i+1 with the QUMOND
+    # chain, forces and curve of evaluation i; every evaluation must give the
+    # bits of a lone run()
+    gals = [synth.two_component_disk(40_000, seed=40 + s, rmax=54000.0, zmax=54000.0) for s in range(2)]
+    kw = dict(n=64, nboxes=3, L0=120000.0, rel_tol=1e-10, max_vcycles=40, precision=q.QUMOND_PREC_MIXED_FIXED,
+              bc_mode=q.QUMOND_BC_MULTIPOLE if bc == "multipole" else q.QUMOND_BC_ZERO)
+    dev = [tuple(to_dev(getattr(g, a)) for a in "xyzm") for g in gals]
+    want = []
+    for d in dev:
+        ca, cb = q.Context(**kw), q.Context(**kw)
+        pipe = q.Pipeline(ca, ctx_mond=cb)
+        g = tuple(torch.empty_like(d[0]) for _ in range(3))
+        r = pipe.run(*d, nbins=30, rmax=20000.0, forces=g)
+        torch.cuda.synchronize()
+        want.append((r.vc.clone(), [t.clone() for t in g], [t.clone() for t in pipe.phi]))
+        pipe.close()
+        ca.close()
+        cb.close()
+    ca, cb = q.Context(**kw), q.Context(**kw)
+    pipe = q.Pipeline(ca, ctx_mond=cb)
+    order = [0, 1, 1, 0, 1]
+    inputs = [dev[k] for k in order]
+    forces = [tuple(torch.empty_like(dev[k][0]) for _ in range(3)) for k in order]
+    for _ in range(2):  # the second pass relaunches the cached graphs
+        res = pipe.run_many(inputs, nbins=30, rmax=20000.0, forces=forces)
+    torch.cuda.synchronize()
+    for i, k in enumerate(order):
+        assert torch.equal(res[i].vc, want[k][0]), i
+        for a, b in zip(forces[i], want[k][1]):
+            assert torch.equal(a, b), i
+    for a, b in zip(pipe.phi, want[order[-1]][2]):  # the potentials of the last evaluation
+        assert torch.equal(a, b)
+    pipe.close()
+    ca.close()
+    cb.close()
