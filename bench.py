@@ -3,10 +3,13 @@
 
 One step = one evaluation of the whole path for one galaxy: for each of the
 3 nested boxes (120, 60, 30 kpc; 257^3 nodes each) the CIC deposit of 2e6
-particles, the Newtonian FMG solve, the QUMOND source and the QUMOND FMG
-solve (FP32 smoothing with FP64 defect correction to a relative residual of
-1e-10), then the forces at every particle and a 50-bin rotation curve.
-The metric is QUMOND solves per second (one solve = one step).
+particles (box 0's outer boundary from the far field of its mass), the
+Newtonian FMG solve, the QUMOND source and the QUMOND FMG solve (FP32
+smoothing with defect correction to a relative residual of 1e-10, on a 64-bit
+fixed-point iterate by default, in FP64 with --precision mixed), then the
+forces at every particle and a 50-bin rotation curve.  The metric is QUMOND
+solves per second (one solve = one such step); successive steps run with the
+two solve chains pipelined across them (Pipeline.run_many).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -296,7 +299,7 @@ def run_ours(args):
                              max_vcycles=w["max_vcycles"], ncycle=w["ncycle"], npre=w["npre"], npost=w["npost"],
                              precision=precision, use_graphs=0 if args.no_graphs else 1,
                              bc_mode=q.QUMOND_BC_MULTIPOLE if w.get("bc") == "multipole" else q.QUMOND_BC_ZERO,
-                             persistent_vcycle=args.persistent_vcycle)
+                             persistent_vcycle=args.persistent_vcycle, small_cluster=args.small_cluster)
         cs = [make() for _ in range(args.chains)]
         return Contexts(cs), q.Pipeline(cs[0], dev, ctx_mond=cs[1] if len(cs) > 1 else None)
 
@@ -546,7 +549,7 @@ def run_ours(args):
             "chains": args.chains,
             "pipelined_steps": pipelined,
             "step_by_step": step_by_step,
-            "small_level_vcycle": {0: "one launch per step", 1: "one cooperative kernel", 2: "one thread-block cluster per set"}[args.persistent_vcycle],
+            "small_level_vcycle": {0: "one graph kernel node per smoothing, restriction and prolongation", 1: "one cooperative kernel", 2: "one thread-block cluster per set", 3: "the level n = 32 and those under it in the distributed shared memory of one thread-block cluster per set"}[args.persistent_vcycle],
             "one_chain": {"value": ws * 1000.0 / one_chain_ms, "unit": UNIT, "ms_per_step": one_chain_ms},
             "vcycles_after_fmg_per_solve": vcycles,
             "plain_fmg": plain,
@@ -1101,9 +1104,12 @@ def main():
                          "autotuner)")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="time the steps one after another instead of pipelining successive steps' chains")
-    ap.add_argument("--persistent-vcycle", type=int, choices=[0, 1, 2], default=0,
-                    help="the V-cycle on the levels n <= 64: 0 one launch per step, 1 one cooperative kernel, "
-                         "2 one thread-block cluster (two-disk and large workloads)")
+    ap.add_argument("--persistent-vcycle", type=int, choices=[0, 1, 2, 3], default=0,
+                    help="the V-cycle on the small levels: 0 one launch per step, 1 one cooperative kernel, "
+                         "2 one thread-block cluster (levels n <= 64, global memory), 3 one thread-block cluster "
+                         "holding the level n = 32 in distributed shared memory (two-disk and large workloads)")
+    ap.add_argument("--small-cluster", type=int, choices=[0, 4, 8, 16], default=0,
+                    help="CTAs per cluster of --persistent-vcycle 3 (0: 8)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one profiled V-cycle on one box instead of the benchmark (for ncu)")
     args = ap.parse_args()

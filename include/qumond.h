@@ -126,28 +126,37 @@ typedef struct {
     int use_graphs;     /* 1: each solve runs as one cached CUDA graph (FMG and
                            the whole tolerance loop, decided on the device);
                            0: kernels are launched one by one */
-    int persistent_vcycle; /* the part of each V-cycle on the levels with
-                           n <= 64 below the finest: 0 (default): one launch
-                           per step; 1: one cooperative kernel over all SMs with
-                           grid barriers (when the device supports cooperative
-                           launches; nsets = 1 only); 2: one thread-block
-                           cluster per set (16 CTAs where the device can place
-                           them, else 8, 4 or 2) meeting at the cluster's
-                           hardware barrier.  The results are the same bits.
-                           On GB300 the cooperative form is not faster (a grid
-                           barrier costs about what a graph launch does, and it
+    int persistent_vcycle; /* the part of each V-cycle on the small levels
+                           below the finest: 0 (default): one launch per
+                           step; 1: the levels n <= 64 as one cooperative
+                           kernel over all SMs with grid barriers (when the
+                           device supports cooperative launches; nsets = 1
+                           only); 2: the levels n <= 64 as one thread-block
+                           cluster per set (16 CTAs where the device can
+                           place them, else 8, 4 or 2) meeting at the
+                           cluster's hardware barrier, data in global memory;
+                           3: the level n = 32 and those under it as one
+                           cluster of small_cluster CTAs per set holding the
+                           level in distributed shared memory (FP32 smoothing
+                           and finest n >= 64 only; otherwise, or where the
+                           cluster cannot be placed, mode 0).  The results
+                           are the same bits in every mode.  On GB300 the
+                           cooperative form is not faster (a grid barrier
+                           costs about what a graph launch does, and it
                            serialises concurrent solves). */
     int nsets;          /* independent problems of this shape held by the
                            context (the parameter sets of a rotation-curve fit,
                            Section 3.5), 1 <= nsets <= 1024 with
                            nsets * (n + 1) <= 65535; default 1.  See "Sets"
-                           above.  nsets > 1 requires persistent_vcycle = 0. */
+                           above.  nsets > 1 excludes persistent_vcycle = 1. */
     int tile_small;     /* block shape of the FP32 half-sweeps and prolongations
                            on the levels with n <= 64: 0 (default) = 8 x 16
                            threads (32 row entries x 16 rows per block),
                            1 = 4 x 32, 2 = 2 x 64.  The same bits for every
                            shape; only the speed differs (picked by timing,
                            e.g. by the fit sweep's autotuner). */
+    int small_cluster;  /* CTAs per cluster of persistent_vcycle = 3: 4, 8 or
+                           16 (16 is a non-portable cluster size), 0 = 8. */
 } qumond_params;
 
 /* Per-solve report (host struct). */
@@ -164,7 +173,7 @@ typedef struct qumond_ctx qumond_ctx;
    npre = npost = 2, ncycle = 6, rel_tol = 0 (paper mode), max_vcycles = 50,
    QUMOND_PREC_MIXED, QUMOND_BC_ZERO, warm_start = 0, deposit_shift = 24,
    rc_box_frac = 0.2, box_ratio = 2, use_graphs = 1, persistent_vcycle = 0,
-   nsets = 1, tile_small = 0. */
+   nsets = 1, tile_small = 0, small_cluster = 0. */
 QUMOND_API void qumond_default_params(qumond_params* p);
 
 /* Validates p and allocates the context's device scratch on the current

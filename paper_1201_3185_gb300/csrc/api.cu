@@ -119,7 +119,7 @@ struct qumond_ctx {
     bool in_body = false;           // enqueueing a defect-correction V-cycle (sets that stopped are skipped)
     int vtop = -1;                  // top level of the cooperative small-level V-cycle kernel, -1: not used
     int vgrid = 0;                  // its CTAs (one per SM)
-    int vcs = 0;                    // persistent_vcycle = 2: CTAs of the cluster that runs it (per set)
+    int vcs = 0;                    // persistent_vcycle = 2 or 3: CTAs of the cluster that runs it (per set)
     unsigned* vbar = nullptr;       // its grid-barrier counter
     long long barrier_polls = 1LL << 26;  // polls before one of its grid barriers gives up
     int64_t* Ffix = nullptr;        // fixed-point right-hand side
@@ -201,8 +201,10 @@ qumond_status check_params(qumond_ctx* c, const qumond_params* p)
     if (p->box_ratio != 2 && p->box_ratio != 4 && p->box_ratio != 8)
         return fail(c, QUMOND_ERR_INVALID_ARG, "box_ratio must be 2, 4 or 8");
     if (p->use_graphs != 0 && p->use_graphs != 1) return fail(c, QUMOND_ERR_INVALID_ARG, "use_graphs must be 0 or 1");
-    if (p->persistent_vcycle < 0 || p->persistent_vcycle > 2)
-        return fail(c, QUMOND_ERR_INVALID_ARG, "persistent_vcycle must be 0, 1 or 2");
+    if (p->persistent_vcycle < 0 || p->persistent_vcycle > 3)
+        return fail(c, QUMOND_ERR_INVALID_ARG, "persistent_vcycle must be 0, 1, 2 or 3");
+    if (p->small_cluster != 0 && p->small_cluster != 4 && p->small_cluster != 8 && p->small_cluster != 16)
+        return fail(c, QUMOND_ERR_INVALID_ARG, "small_cluster must be 0, 4, 8 or 16");
     if (p->nboxes > 1 && p->n < 2 * p->box_ratio)
         return fail(c, QUMOND_ERR_INVALID_ARG, "n=%d too small for nested boxes of ratio %d", p->n, p->box_ratio);
     if (p->nsets < 1 || p->nsets > 1024 || (long long)p->nsets * (p->n + 1) > 65535)
@@ -382,6 +384,13 @@ cudaError_t vsub(qumond_ctx* c, int box, bool zero_top, cudaStream_t s)
     count_cells(c, upd);
     cudaError_t err = cudaSuccess;
     run(c, K_VSUB, bytes, s, [&] {
+        if constexpr (sizeof(T) == sizeof(float)) {
+            if (p.persistent_vcycle == 3) {
+                err = launch_vslab(reinterpret_cast<float*>(e[1]), reinterpret_cast<const float*>(f[1]), v[1], h[1],
+                                   h[0], zero_top ? 1 : 0, p.npre, p.npost, c->vcs, s, sets_of(c));
+                return;
+            }
+        }
         if (p.persistent_vcycle == 2)
             err = launch_vcluster<T>(e, f, v, h, nlev, zero_top ? 1 : 0, p.npre, p.npost, c->vcs, s, sets_of(c));
         else
@@ -844,6 +853,7 @@ void qumond_default_params(qumond_params* p)
     p->persistent_vcycle = 0;
     p->nsets = 1;
     p->tile_small = 0;
+    p->small_cluster = 0;
 }
 
 qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
@@ -930,6 +940,14 @@ qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
         const int cs = vcluster_size(p->precision == QUMOND_PREC_FP64);
         if (cs >= 2 && top > c->lc && top - c->lc + 1 <= 6) {
             c->vtop = top;
+            c->vcs = cs;
+        }
+    }
+    if (ok && p->persistent_vcycle == 3 && c->elt == sizeof(float) && lc + 1 < L && c->lev[lc + 1].v.n == 32) {
+        // the 32-interval level (below the finest) and the levels under it in one cluster's shared memory
+        const int cs = vslab_size(p->small_cluster ? p->small_cluster : 8);
+        if (cs > 0) {
+            c->vtop = lc + 1;
             c->vcs = cs;
         }
     }

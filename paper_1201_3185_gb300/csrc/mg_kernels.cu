@@ -470,43 +470,75 @@ struct CoarseSmem {
 };
 
 // Every level size is a compile-time constant (N = 2 << L), so the index
-// arithmetic below is shifts and multiplications.
-// One colour of the interior of an N-level: row (j, k) holds that colour's
-// nodes at i = first, first + 2, ... (first = 1 or 2), N/2 slots per row.
-template <typename T, int N>
-__device__ void sm_relax(T* u, const T* f, T h2, int colour)
+// arithmetic below is shifts and multiplications.  Each routine is run either
+// by the whole block (W = false: stride blockDim.x, a multiple of 8, and a
+// block barrier at the end) or by warp 0 alone (W = true: the levels n <= 4,
+// at most 27 nodes a phase, stride 32 and a warp barrier), which spares the
+// smallest levels a block-wide barrier per phase; the arithmetic of every
+// node is the same either way.
+template <bool W>
+__device__ __forceinline__ int sm_stride()
 {
-    constexpr int M = N - 1, P = N + 1, H = N / 2, TOT = M * M * H;
-    for (int t = threadIdx.x; t < TOT; t += (int)blockDim.x) {
-        const int sl = t % H, row = t / H;
-        const int j = row % M + 1, k = row / M + 1;
-        const int i = 1 + (((1 + j + k) & 1) != colour ? 1 : 0) + 2 * sl;
-        if (i > M) continue;
-        const int o = i + P * (j + P * k);
-        const T sum = (u[o + 1] + u[o - 1]) + (u[o + P] + u[o - P]) + (u[o + P * P] + u[o - P * P]);
-        u[o] = (sum - h2 * f[o]) * (T(1) / T(6));
-    }
-    __syncthreads();
+    return W ? 32 : (int)blockDim.x;
 }
 
-template <typename T, int N>
+template <bool W>
+__device__ __forceinline__ void sm_sync()
+{
+    if (W)
+        __syncwarp();
+    else
+        __syncthreads();
+}
+
+// One colour of the interior of an N-level: row (j, k) holds that colour's
+// nodes at i = first, first + 2, ... (first = 1 or 2), N/2 slots per row.
+// The stride is a multiple of N/2, so a thread keeps its slot and steps its
+// row (j, k) without divisions.
+template <typename T, int N, bool W = false>
+__device__ void sm_relax(T* u, const T* f, T h2, int colour)
+{
+    constexpr int M = N - 1, P = N + 1, H = N / 2, ROWS = M * M;
+    const int dr = sm_stride<W>() / H;  // rows advanced per pass
+    const int dj = dr % M, dk = dr / M;
+    const int sl = (int)threadIdx.x % H;
+    int row = (int)threadIdx.x / H;
+    int j = row % M + 1, k = row / M + 1;
+    for (; row < ROWS; row += dr) {
+        const int i = 1 + (((1 + j + k) & 1) != colour ? 1 : 0) + 2 * sl;
+        if (i <= M) {
+            const int o = i + P * (j + P * k);
+            const T sum = (u[o + 1] + u[o - 1]) + (u[o + P] + u[o - P]) + (u[o + P * P] + u[o - P * P]);
+            u[o] = (sum - h2 * f[o]) * (T(1) / T(6));
+        }
+        j += dj;
+        k += dk;
+        if (j > M) {
+            j -= M;
+            ++k;
+        }
+    }
+    sm_sync<W>();
+}
+
+template <typename T, int N, bool W = false>
 __device__ void sm_residual(const T* u, const T* f, T* r, T ih2)
 {
     constexpr int M = N - 1, P = N + 1, TOT = M * M * M;
-    for (int t = threadIdx.x; t < TOT; t += (int)blockDim.x) {
+    for (int t = threadIdx.x; t < TOT; t += sm_stride<W>()) {
         const int i = t % M + 1, j = (t / M) % M + 1, k = t / (M * M) + 1;
         const int o = i + P * (j + P * k);
         const T sum = (u[o + 1] + u[o - 1]) + (u[o + P] + u[o - P]) + (u[o + P * P] + u[o - P * P]);
         r[o] = f[o] - (sum - T(6) * u[o]) * ih2;
     }
-    __syncthreads();
+    sm_sync<W>();
 }
 
-template <typename T, int NF>
+template <typename T, int NF, bool W = false>
 __device__ void sm_restrict(const T* fine, T* coarse)
 {
     constexpr int NC = NF / 2, MC = NC - 1, PF = NF + 1, PC = NC + 1, TOT = MC * MC * MC;
-    for (int t = threadIdx.x; t < TOT; t += (int)blockDim.x) {
+    for (int t = threadIdx.x; t < TOT; t += sm_stride<W>()) {
         const int I = t % MC + 1, J = (t / MC) % MC + 1, K = t / (MC * MC) + 1;
         T acc = T(0);
 #pragma unroll
@@ -520,14 +552,14 @@ __device__ void sm_restrict(const T* fine, T* coarse)
                 }
         coarse[I + PC * (J + PC * K)] = acc;
     }
-    __syncthreads();
+    sm_sync<W>();
 }
 
-template <typename T, int NC>
+template <typename T, int NC, bool W = false>
 __device__ void sm_prolong(const T* coarse, T* fine, bool add)
 {
     constexpr int NF = 2 * NC, M = NF - 1, PF = NF + 1, PC = NC + 1, TOT = M * M * M;
-    for (int t = threadIdx.x; t < TOT; t += (int)blockDim.x) {
+    for (int t = threadIdx.x; t < TOT; t += sm_stride<W>()) {
         const int i = t % M + 1, j = (t / M) % M + 1, k = t / (M * M) + 1;
         const int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = j >> 1, J1 = (j + 1) >> 1, K0 = k >> 1, K1 = (k + 1) >> 1;
         T sum = (coarse[I0 + PC * (J0 + PC * K0)] + coarse[I1 + PC * (J0 + PC * K0)])
@@ -538,49 +570,53 @@ __device__ void sm_prolong(const T* coarse, T* fine, bool add)
         const int o = i + PF * (j + PF * k);
         fine[o] = add ? fine[o] + sum : sum;
     }
-    __syncthreads();
+    sm_sync<W>();
 }
 
-template <typename T, int N>
+template <typename T, int N, bool W = false>
 __device__ void sm_fill(T* a, T val)
 {
     constexpr int TOT = (N + 1) * (N + 1) * (N + 1);
-    for (int t = threadIdx.x; t < TOT; t += (int)blockDim.x) a[t] = val;
-    __syncthreads();
+    for (int t = threadIdx.x; t < TOT; t += sm_stride<W>()) a[t] = val;
+    sm_sync<W>();
 }
 
 // The single unknown of the 3^3 grid (Section 2): u = (sum of 6 nbrs - h^2 f)/6.
-template <typename T>
+template <typename T, bool W = false>
 __device__ void sm_coarsest(T* u, const T* f, T h)
 {
     if (threadIdx.x == 0) {
         const T sum = (u[14] + u[12]) + (u[16] + u[10]) + (u[22] + u[4]);
         u[13] = (sum - h * h * f[13]) * (T(1) / T(6));
     }
-    __syncthreads();
+    sm_sync<W>();
 }
 
 // V(npre, npost) cycle from level L down to the 3^3 grid; the coarser levels
-// start from zero (zero boundary values), level L from what u[L] holds.
-template <typename T, int L>
+// start from zero (zero boundary values), level L from what u[L] holds.  The
+// levels n <= 4 are run by warp 0 while the rest of the block waits.
+template <typename T, int L, bool W = false>
 __device__ void sm_vcycle(CoarseSmem<T>& S, T h, int npre, int npost)
 {
     constexpr int N = 2 << L;
-    if constexpr (L == 0) {
-        sm_coarsest(S.u[0], S.f[0], h);
+    if constexpr (!W && L <= 1) {
+        if (threadIdx.x < 32) sm_vcycle<T, L, true>(S, h, npre, npost);
+        __syncthreads();
+    } else if constexpr (L == 0) {
+        sm_coarsest<T, W>(S.u[0], S.f[0], h);
     } else {
         for (int q = 0; q < npre; ++q) {
-            sm_relax<T, N>(S.u[L], S.f[L], h * h, 0);
-            sm_relax<T, N>(S.u[L], S.f[L], h * h, 1);
+            sm_relax<T, N, W>(S.u[L], S.f[L], h * h, 0);
+            sm_relax<T, N, W>(S.u[L], S.f[L], h * h, 1);
         }
-        sm_residual<T, N>(S.u[L], S.f[L], S.r[L], T(1) / (h * h));
-        sm_restrict<T, N>(S.r[L], S.f[L - 1]);
-        sm_fill<T, N / 2>(S.u[L - 1], T(0));
-        sm_vcycle<T, L - 1>(S, h * T(2), npre, npost);
-        sm_prolong<T, N / 2>(S.u[L - 1], S.u[L], true);
+        sm_residual<T, N, W>(S.u[L], S.f[L], S.r[L], T(1) / (h * h));
+        sm_restrict<T, N, W>(S.r[L], S.f[L - 1]);
+        sm_fill<T, N / 2, W>(S.u[L - 1], T(0));
+        sm_vcycle<T, L - 1, W>(S, h * T(2), npre, npost);
+        sm_prolong<T, N / 2, W>(S.u[L - 1], S.u[L], true);
         for (int q = 0; q < npost; ++q) {
-            sm_relax<T, N>(S.u[L], S.f[L], h * h, 0);
-            sm_relax<T, N>(S.u[L], S.f[L], h * h, 1);
+            sm_relax<T, N, W>(S.u[L], S.f[L], h * h, 0);
+            sm_relax<T, N, W>(S.u[L], S.f[L], h * h, 1);
         }
     }
 }
@@ -863,6 +899,268 @@ __global__ void __launch_bounds__(kVsubThreads) vcluster_kernel(VsubArgs<T> a, i
 }
 
 // ---------------------------------------------------------------------------
+// The V-cycle from the 32-interval level down, in shared memory: one
+// thread-block cluster of C CTAs per set.  CTA r keeps the planes
+// k0 .. k1-1 of that level's e and f (both colours, each plane's rows laid
+// out as in global memory); CTA 0 also keeps the boundary plane 0 and CTA
+// C-1 the boundary plane 32.  A node on the first or last plane of a slab
+// reads the plane beyond it from the adjacent CTA's shared memory
+// (distributed shared memory, through a table of per-plane addresses).
+// Phases, separated by the cluster's hardware barrier (release / acquire):
+//   npre (red, black) half-sweeps;
+//   full weighting of the red residuals, written straight into CTA 0's
+//   arrays of the 16-interval level;
+//   one V-cycle of the levels 16 .. 2 in CTA 0 (sm_vcycle, as coarse_run);
+//   the trilinear correction of the black nodes, read from CTA 0;
+//   npost (red, black) half-sweeps;
+// then each CTA writes its interior nodes back.  The arithmetic of every
+// node is that of the per-step kernels (rb_half4_kernel, restrict_node,
+// coarse_run, prolong_node) in the same order, with the same constants, so
+// the result is the same bits; the 32-interval level costs one launch and
+// no global traffic between its phases.
+constexpr int kSlabN = 32;
+constexpr int kSlabP = kSlabN + 1;
+constexpr int kSlabM = ((kSlabN / 2 + 1) + 3) & ~3;  // row length of the colour-split layout (make_view)
+constexpr int kSlabColour = kSlabP * kSlabM;         // floats of one colour of one plane
+constexpr int kSlabPlane = 2 * kSlabColour;          // floats of one plane, both colours
+constexpr int kSlabThreads = 512;
+constexpr int kSlabCoarseP = kSlabN / 2 + 1;  // 17: natural layout of CTA 0's 16-interval arrays
+
+__host__ __device__ inline int slab_depth(int csize) { return (kSlabN - 1 + csize - 1) / csize; }
+
+struct SlabArgs {
+    float* e;  // the 32-interval level (set 0; set s at + 2 s cs)
+    const float* f;
+    long long cs;
+    float h2, sixth, ih2;  // that level's h^2, 1/6 and 1/h^2 as the per-step kernels take them
+    float hc;              // h of the 16-interval level
+    int zero_top, npre, npost, csize;
+    const SolveState* act;
+};
+
+__device__ __forceinline__ float* cluster_map(float* p, int rank)
+{
+    unsigned long long out;
+    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(reinterpret_cast<unsigned long long>(p)), "r"(rank));
+    return reinterpret_cast<float*>(out);
+}
+
+__device__ __forceinline__ unsigned cluster_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// One half-sweep of `colour` over the slab's planes (per-node arithmetic of
+// rb_half4_kernel: (x pair) + (y pair) + (z pair), then (sum - h2 f) / 6).
+template <bool ZERO>
+__device__ __forceinline__ void slab_rb(float* const* pe, const float* const* pf, int k0, int k1, int colour,
+                                        float h2, float sixth)
+{
+    const int tot = (k1 - k0) * (kSlabN - 1) * (kSlabN / 2);
+    for (int t = threadIdx.x; t < tot; t += kSlabThreads) {
+        const int m = t & (kSlabN / 2 - 1);
+        const int r = t >> 4;
+        const int j = r % (kSlabN - 1) + 1, k = k0 + r / (kSlabN - 1);
+        const int p = (colour + j + k) & 1;
+        if (p == 0 && m == 0) continue;  // i = 0 is a boundary node
+        const int row = j * kSlabM;
+        float sum = 0.0f;
+        if (!ZERO) {
+            const int oc = (colour ^ 1) * kSlabColour + row;
+            const float* o = pe[k] + oc;
+            const float lo = o[m - 1 + p], hi = o[m + p];
+            const float y0 = o[m - kSlabM], y1 = o[m + kSlabM];
+            const float z0 = pe[k - 1][oc + m], z1 = pe[k + 1][oc + m];
+            sum = (lo + hi) + (y0 + y1) + (z0 + z1);
+        }
+        const float fv = pf[k][colour * kSlabColour + row + m];
+        pe[k][colour * kSlabColour + row + m] = (sum - h2 * fv) * sixth;
+    }
+}
+
+// red_residual on the slab tables
+__device__ __forceinline__ float slab_red_residual(float* const* pe, const float* const* pf, int i, int j, int k,
+                                                   float ih2)
+{
+    const int p = (j + k) & 1;
+    const int m = i >> 1;
+    const int row = j * kSlabM;
+    const float* eb = pe[k] + kSlabColour + row;
+    const float s = (eb[m - 1 + p] + eb[m + p]) + (eb[m - kSlabM] + eb[m + kSlabM]) +
+                    (pe[k - 1][kSlabColour + row + m] + pe[k + 1][kSlabColour + row + m]);
+    return pf[k][row + m] - (s - 6.0f * pe[k][row + m]) * ih2;
+}
+
+__global__ void __launch_bounds__(kSlabThreads) vslab_kernel(SlabArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int C = a.csize;
+    const int set = (int)blockIdx.x / C;
+    const int rank = (int)cluster_rank();
+    if (a.act && !a.act[set].cont) return;  // the whole cluster reads the same flag
+    const int q = slab_depth(C);
+    const int k0 = 1 + rank * q;
+    const int k1 = min(kSlabN, k0 + q);
+    float* se = reinterpret_cast<float*>(smem_raw);  // slot s holds plane k0 - 1 + s
+    float* sf = se + (size_t)(q + 2) * kSlabPlane;   // slot s holds plane k0 + s
+    float** pe = reinterpret_cast<float**>(sf + (size_t)q * kSlabPlane);
+    float** pf = pe + 40;
+    unsigned char* coarse_raw = reinterpret_cast<unsigned char*>(pf + 40);
+    CoarseSmem<float> S;
+    {
+        float* base = reinterpret_cast<float*>(coarse_raw);
+        for (int l = 0; l <= 3; ++l) {
+            const int c = cube(2 << l);
+            S.u[l] = base;
+            S.f[l] = base + c;
+            S.r[l] = base + 2 * c;
+            base += 3 * c;
+        }
+    }
+    float* const e = a.e + (long long)set * 2 * a.cs;
+    const float* const f = a.f + (long long)set * 2 * a.cs;
+    constexpr int kC3 = kSlabCoarseP * kSlabCoarseP * kSlabCoarseP;
+
+    // plane tables: plane k of e lives in the CTA that owns it (plane 0 in CTA 0, plane 32 in CTA C-1)
+    if (threadIdx.x <= kSlabN) {
+        const int k = threadIdx.x;
+        const int owner = k == 0 ? 0 : (k == kSlabN ? C - 1 : (k - 1) / q);
+        const int slot = k - (1 + owner * q) + 1;
+        float* local = se + (size_t)slot * kSlabPlane;
+        pe[k] = owner == rank ? local : cluster_map(local, owner);
+        if (k >= 1 && k < kSlabN) {
+            float* lf = sf + (size_t)(k - (1 + owner * q)) * kSlabPlane;
+            pf[k] = owner == rank ? lf : cluster_map(lf, owner);
+        }
+    }
+    // own planes of f (and of e unless the correction starts from zero), and the boundary planes held here
+    {
+        const int kb = (rank == 0) ? 0 : k0;
+        const int ke = (rank == C - 1) ? kSlabN + 1 : k1;
+        const int n4 = kSlabColour / 4;  // float4 per colour-plane
+        for (int t = threadIdx.x; t < (k1 - k0) * 2 * n4; t += kSlabThreads) {
+            const int kk = t / (2 * n4), c = (t / n4) & 1, x = t % n4;
+            const float4* src = reinterpret_cast<const float4*>(f + (long long)c * a.cs +
+                                                                (long long)(k0 + kk) * kSlabColour);
+            reinterpret_cast<float4*>(sf + (size_t)kk * kSlabPlane + c * kSlabColour)[x] = src[x];
+        }
+        for (int t = threadIdx.x; t < (ke - kb) * 2 * n4; t += kSlabThreads) {
+            const int kk = t / (2 * n4), c = (t / n4) & 1, x = t % n4;
+            const int k = kb + kk;
+            float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (!a.zero_top)
+                v = reinterpret_cast<const float4*>(e + (long long)c * a.cs + (long long)k * kSlabColour)[x];
+            reinterpret_cast<float4*>(se + (size_t)(k - k0 + 1) * kSlabPlane + c * kSlabColour)[x] = v;
+        }
+        if (rank == 0)  // coarse_run with a zero start: u = 0, f = 0 off the interior
+            for (int t = threadIdx.x; t < kC3; t += kSlabThreads) {
+                S.u[3][t] = 0.0f;
+                S.f[3][t] = 0.0f;
+            }
+    }
+    __syncthreads();
+    cluster_sync_all();
+
+    // pre-smoothing
+    for (int qq = 0; qq < a.npre; ++qq) {
+        if (qq == 0 && a.zero_top)
+            slab_rb<true>(pe, pf, k0, k1, 0, a.h2, a.sixth);
+        else
+            slab_rb<false>(pe, pf, k0, k1, 0, a.h2, a.sixth);
+        cluster_sync_all();
+        slab_rb<false>(pe, pf, k0, k1, 1, a.h2, a.sixth);
+        cluster_sync_all();
+    }
+    // restriction of the red residuals onto the coarse planes K with 2K in this slab
+    {
+        float* fc = rank == 0 ? S.f[3] : cluster_map(S.f[3], 0);
+        const int K0 = (k0 + 1) >> 1, K1 = (k1 + 1) >> 1;  // 2K in [k0, k1)
+        constexpr int MC = kSlabN / 2 - 1;
+        const int tot = (K1 - K0) * MC * MC;
+        for (int t = threadIdx.x; t < tot; t += kSlabThreads) {
+            const int I = t % MC + 1, J = (t / MC) % MC + 1, K = K0 + t / (MC * MC);
+            const int i = 2 * I, j = 2 * J, k = 2 * K;
+            const float ih2 = a.ih2;
+            float edge = (slab_red_residual(pe, pf, i + 1, j + 1, k, ih2) + slab_red_residual(pe, pf, i - 1, j + 1, k, ih2))
+                       + (slab_red_residual(pe, pf, i + 1, j - 1, k, ih2) + slab_red_residual(pe, pf, i - 1, j - 1, k, ih2));
+            edge += (slab_red_residual(pe, pf, i + 1, j, k + 1, ih2) + slab_red_residual(pe, pf, i - 1, j, k + 1, ih2))
+                  + (slab_red_residual(pe, pf, i + 1, j, k - 1, ih2) + slab_red_residual(pe, pf, i - 1, j, k - 1, ih2));
+            edge += (slab_red_residual(pe, pf, i, j + 1, k + 1, ih2) + slab_red_residual(pe, pf, i, j - 1, k + 1, ih2))
+                  + (slab_red_residual(pe, pf, i, j + 1, k - 1, ih2) + slab_red_residual(pe, pf, i, j - 1, k - 1, ih2));
+            const float centre = slab_red_residual(pe, pf, i, j, k, ih2);
+            fc[I + kSlabCoarseP * (J + kSlabCoarseP * K)] = 0.125f * centre + 0.03125f * edge;
+        }
+    }
+    cluster_sync_all();
+    if (rank == 0) sm_vcycle<float, 3>(S, a.hc, a.npre, a.npost);
+    cluster_sync_all();
+    // coarse-grid correction of the black nodes (prolong_node's sums in its order); the coarse planes
+    // k0/2 .. k1/2 that this slab interpolates from are first copied from CTA 0 into the same place of
+    // this CTA's (otherwise unused) coarse arrays, so that CTA 0's shared memory is read once per value
+    {
+        if (rank != 0) {
+            const float* src = cluster_map(S.u[3], 0);
+            const int lo = (k0 >> 1) * kSlabCoarseP * kSlabCoarseP;
+            const int hi = ((k1 >> 1) + 1) * kSlabCoarseP * kSlabCoarseP;
+            for (int t = lo + threadIdx.x; t < hi; t += 4 * kSlabThreads) {
+                float v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (t + u * kSlabThreads < hi) v[u] = src[t + u * kSlabThreads];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (t + u * kSlabThreads < hi) S.u[3][t + u * kSlabThreads] = v[u];
+            }
+            __syncthreads();
+        }
+        const float* ec = S.u[3];
+        const int tot = (k1 - k0) * (kSlabN - 1) * (kSlabN / 2);
+        for (int t = threadIdx.x; t < tot; t += kSlabThreads) {
+            const int m = t & (kSlabN / 2 - 1);
+            const int r = t >> 4;
+            const int j = r % (kSlabN - 1) + 1, k = k0 + r / (kSlabN - 1);
+            const int p = (1 + j + k) & 1;
+            const int i = 2 * m + p;
+            if (i < 1) continue;
+            const int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = j >> 1, J1 = (j + 1) >> 1, K0 = k >> 1, K1 = (k + 1) >> 1;
+            constexpr int PC = kSlabCoarseP;
+            float s = (ec[I0 + PC * (J0 + PC * K0)] + ec[I1 + PC * (J0 + PC * K0)])
+                    + (ec[I0 + PC * (J1 + PC * K0)] + ec[I1 + PC * (J1 + PC * K0)]);
+            s += (ec[I0 + PC * (J0 + PC * K1)] + ec[I1 + PC * (J0 + PC * K1)])
+               + (ec[I0 + PC * (J1 + PC * K1)] + ec[I1 + PC * (J1 + PC * K1)]);
+            s *= 0.125f;
+            float* o = pe[k] + kSlabColour + j * kSlabM + m;
+            *o = *o + s;
+        }
+    }
+    cluster_sync_all();
+    // post-smoothing
+    for (int qq = 0; qq < a.npost; ++qq) {
+        slab_rb<false>(pe, pf, k0, k1, 0, a.h2, a.sixth);
+        cluster_sync_all();
+        slab_rb<false>(pe, pf, k0, k1, 1, a.h2, a.sixth);
+        cluster_sync_all();  // also: no CTA leaves while a neighbour still reads its planes
+    }
+    // the interior nodes of this slab back to global memory
+    {
+        const int tot = (k1 - k0) * 2 * (kSlabN - 1) * (kSlabN / 2);
+        for (int t = threadIdx.x; t < tot; t += kSlabThreads) {
+            const int m = t & (kSlabN / 2 - 1);
+            const int r = t >> 4;
+            const int j = r % (kSlabN - 1) + 1;
+            const int r2 = r / (kSlabN - 1);
+            const int c = r2 & 1, k = k0 + (r2 >> 1);
+            const int p = (c + j + k) & 1;
+            if (p == 0 && m == 0) continue;
+            const int o = c * kSlabColour + j * kSlabM + m;
+            e[(long long)c * a.cs + (long long)k * kSlabColour + j * kSlabM + m] = se[(size_t)(k - k0 + 1) * kSlabPlane + o];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // FP64 outer steps on the caller's natural-layout arrays (n intervals).
 __device__ __forceinline__ long long nat(int n, int i, int j, int k)
 {
@@ -1126,6 +1424,15 @@ size_t coarse_smem_bytes(int n)
     return tot * sizeof(T);
 }
 
+// shared memory of the slab V-cycle kernel: e planes (slab + 2), f planes
+// (slab), the two plane tables, and CTA 0's arrays of the levels 16 .. 2
+inline size_t slab_smem_bytes(int csize)
+{
+    const int q = slab_depth(csize);
+    return sizeof(float) * (size_t)kSlabPlane * (size_t)(2 * q + 2) + 2 * 40 * sizeof(float*) +
+           coarse_smem_bytes<float>(kSlabN / 2);
+}
+
 }  // namespace
 
 // --- launchers ------------------------------------------------------------
@@ -1341,6 +1648,61 @@ int vcluster_size(bool fp64)
     return 0;
 }
 
+cudaError_t launch_vslab(float* e, const float* f, const LevelView& v, double h, double hc, int zero_top, int npre,
+                         int npost, int csize, cudaStream_t s, const Sets& sets)
+{
+    if (v.n != kSlabN || v.M != kSlabM || (v.cs & 3) != 0 || (reinterpret_cast<uintptr_t>(e) & 15) != 0 ||
+        (reinterpret_cast<uintptr_t>(f) & 15) != 0 || !(csize == 4 || csize == 8 || csize == 16))
+        return cudaErrorInvalidValue;
+    SlabArgs a{};
+    a.e = e;
+    a.f = f;
+    a.cs = v.cs;
+    a.h2 = (float)(h * h);
+    a.sixth = 1.0f / 6.0f;
+    a.ih2 = (float)(1.0 / (h * h));
+    a.hc = (float)hc;
+    a.zero_top = zero_top;
+    a.npre = npre;
+    a.npost = npost;
+    a.csize = csize;
+    a.act = sets.act;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(csize * sets.n));
+    cfg.blockDim = dim3(kSlabThreads);
+    cfg.dynamicSmemBytes = slab_smem_bytes(csize);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, vslab_kernel, a);
+}
+
+int vslab_size(int want)
+{
+    // `want` CTAs per cluster (4, 8 or 16) if at least one such cluster fits on the device, else 0
+    if (!(want == 4 || want == 8 || want == 16)) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)want);
+    cfg.blockDim = dim3(kSlabThreads);
+    cfg.dynamicSmemBytes = slab_smem_bytes(want);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)want;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, vslab_kernel, &cfg) == cudaSuccess && n >= 1) return want;
+    (void)cudaGetLastError();
+    return 0;
+}
+
 int vsub_grid(int sms)
 {
     // one CTA per SM: the kernel's shared memory (the coarse solver's) allows one or more per SM
@@ -1427,6 +1789,10 @@ cudaError_t prepare_kernels()
             cudaSuccess ||
         cudaFuncSetAttribute(vcluster_kernel<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
             cudaSuccess)
+        return cudaGetLastError();
+    if (cudaFuncSetAttribute(vslab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab_smem_bytes(4)) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(vslab_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
         return cudaGetLastError();
     cudaError_t e = cudaFuncSetAttribute(coarse_kernel<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)coarse_smem_bytes<float>(kCoarseN));

@@ -101,6 +101,12 @@ template <typename T> cudaError_t launch_vcluster(T* const* e, T* const* f, cons
                                                   cudaStream_t s, const Sets& sets = Sets());
 // largest cluster size (16, 8, 4 or 2) the device can schedule for it, 0 if none
 int vcluster_size(bool fp64);
+// The V-cycle from the 32-interval level down in the shared memory of one
+// thread-block cluster of csize (4, 8 or 16) CTAs per set (FP32 levels; v is
+// the 32-interval level, h its spacing, hc that of the 16-interval level).
+cudaError_t launch_vslab(float* e, const float* f, const LevelView& v, double h, double hc, int zero_top, int npre,
+                         int npost, int csize, cudaStream_t s, const Sets& sets);
+int vslab_size(int want);
 template <typename T> cudaError_t launch_coarse(int fmg, T* e, const T* f, const LevelView& v, double h,
                                                 const double* u64, int nfine, int ncycle, int npre, int npost,
                                                 cudaStream_t s, const Sets& sets = Sets());

@@ -71,6 +71,7 @@ class qumond_params(ctypes.Structure):
         ("persistent_vcycle", ctypes.c_int),
         ("nsets", ctypes.c_int),
         ("tile_small", ctypes.c_int),
+        ("small_cluster", ctypes.c_int),
     ]
 
 

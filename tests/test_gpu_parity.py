@@ -329,6 +329,53 @@ def test_cooperative_small_level_vcycle_gives_the_same_bits(q, prec_name, graphs
     assert [s.vcycles for s in a["mond_stats"]] == [s.vcycles for s in b["mond_stats"]]
 
 
+@pytest.mark.parametrize("prec_name,graphs,cluster", [("MIXED_FIXED", 1, 0), ("MIXED_FIXED", 0, 8), ("MIXED", 1, 4),
+                                                       ("MIXED_FIXED", 1, 16), ("MIXED", 0, 16)])
+def test_shared_memory_small_vcycle_gives_the_same_bits(q, prec_name, graphs, cluster):
+    # the level n = 32 and the levels under it in the distributed shared
+    # memory of one thread-block cluster (form 3, 4 / 8 / 16 CTAs) or one
+    # launch per step: the same node arithmetic, so the same bits; n = 64
+    # (level 32 right under the finest) and n = 128 (level 64 between them)
+    prec = getattr(q, "QUMOND_PREC_" + prec_name)
+    p = synth.two_component_disk(50_000, seed=13, rmax=54000.0, zmax=54000.0)
+    for n in (64, 128):
+        kw = dict(rel_tol=1e-10, max_vcycles=40, precision=prec, use_graphs=graphs)
+        a = gpu_pipeline(p, n, 120000.0, 2, persistent_vcycle=3, small_cluster=cluster, **kw)
+        b = gpu_pipeline(p, n, 120000.0, 2, persistent_vcycle=0, **kw)
+        for key in ("phiN", "phi"):
+            for x, y in zip(a[key], b[key]):
+                assert np.array_equal(x, y), (n, key)
+        assert [s.vcycles for s in a["mond_stats"]] == [s.vcycles for s in b["mond_stats"]]
+
+
+def test_shared_memory_small_vcycle_is_the_form_that_runs(q):
+    # with form 3 every V-cycle below the finest level reaches the cluster
+    # kernel (class vcycle_small_levels) and the coarse-grid kernel runs only
+    # for FMG; form 3 on an FP64 context, or with the finest level at n = 32,
+    # is the per-step form
+    p = synth.two_component_disk(20_000, seed=14, rmax=54000.0, zmax=54000.0)
+    x, y, z, m = (to_dev(a) for a in (p.x, p.y, p.z, p.m))
+    for n, prec, expect in ((128, q.QUMOND_PREC_MIXED_FIXED, True), (64, q.QUMOND_PREC_MIXED, True),
+                            (32, q.QUMOND_PREC_MIXED_FIXED, False), (128, q.QUMOND_PREC_FP64, False)):
+        ctx = q.Context(n=n, nboxes=1, L0=120000.0, rel_tol=1e-10, max_vcycles=40, precision=prec,
+                        use_graphs=0, persistent_vcycle=3)
+        pipe = q.Pipeline(ctx)
+        ctx.qumond_trace_read(reset=True)
+        res = pipe.run(x, y, z, m, nbins=10, rmax=20000.0, stats=True)
+        torch.cuda.synchronize()
+        st, _, _ = ctx.qumond_trace_read()
+        vc = res.newton_stats[0].vcycles + res.mond_stats[0].vcycles
+        if expect:
+            # FMG: ncycle V-cycles on each level above the coarse grid reach level 32 once each
+            levels_above = n.bit_length() - 1 - 4
+            assert st["vcycle_small_levels"].launches == vc + 2 * levels_above * ctx.params.ncycle, n
+            assert st["coarse_solver"].launches == 2
+        else:
+            assert st["vcycle_small_levels"].launches == 0
+        pipe.close()
+        ctx.close()
+
+
 def test_concurrent_chains_give_the_same_bits(q):
     # the QUMOND chain on its own context and stream, concurrent with the
     # Newtonian chain: the same kernels in the same order within each chain

@@ -77,7 +77,8 @@ def device_sets(gal, params):
 
 
 @pytest.mark.parametrize("prec_name,graphs,form", [("MIXED_FIXED", 1, 0), ("MIXED_FIXED", 0, 0), ("MIXED", 1, 0),
-                                                    ("FP64", 1, 0), ("MIXED_FIXED", 1, 2), ("FP64", 0, 2)])
+                                                    ("FP64", 1, 0), ("MIXED_FIXED", 1, 2), ("FP64", 0, 2),
+                                                    ("MIXED_FIXED", 1, 3), ("MIXED", 0, 3)])
 def test_context_sets_match_one_set_contexts(q, prec_name, graphs, form):
     """A context with nsets = 4 (the small levels' V-cycle one launch per step,
     or one thread-block cluster per set): deposit, both solves of two boxes, source,
@@ -94,7 +95,7 @@ def test_context_sets_match_one_set_contexts(q, prec_name, graphs, form):
     # after FMG while the others need several, and the later V-cycles must skip it
     ps[-1] = synth.Particles(ps[-1].x + 1e9, ps[-1].y, ps[-1].z, ps[-1].m)
     kw = dict(n=n, nboxes=2, L0=L0, precision=prec, rel_tol=1e-10, max_vcycles=40, use_graphs=graphs)
-    many = q.Context(nsets=4, persistent_vcycle=form, **kw)  # form 2: one cluster per set for the small levels
+    many = q.Context(nsets=4, persistent_vcycle=form, **kw)  # forms 2, 3: one cluster per set for the small levels
     pm = q.Pipeline(many)
     x, y, z, m = (to_dev(np.concatenate([getattr(p, a) for p in ps])) for a in "xyzm")
     g = tuple(torch.empty_like(x) for _ in range(3))
@@ -143,6 +144,10 @@ def test_context_sets_invalid(q):
         q.Context(n=64, nboxes=1, L0=1.0, nsets=2, persistent_vcycle=1)
     with pytest.raises(q.QumondError):
         q.Context(n=64, nboxes=1, L0=1.0, tile_small=3)
+    with pytest.raises(q.QumondError):
+        q.Context(n=64, nboxes=1, L0=1.0, persistent_vcycle=3, small_cluster=2)
+    with pytest.raises(q.QumondError):
+        q.Context(n=64, nboxes=1, L0=1.0, persistent_vcycle=4)
     ctx = q.Context(n=8, nboxes=1, L0=100.0, nsets=2)
     a = torch.zeros(3 * 9 ** 3, dtype=torch.float64, device="cuda")
     with pytest.raises(ValueError):  # particles not a multiple of the set count
