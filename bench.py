@@ -586,10 +586,11 @@ def run_sweep(args):
     w = WORKLOAD
     prec = {"fp64": q.QUMOND_PREC_FP64, "mixed": q.QUMOND_PREC_MIXED, "fixed": q.QUMOND_PREC_MIXED_FIXED}[args.precision]
 
-    def params(precision, tile=0):
+    def params(precision, tile=0, form=3):
         return q.default_params(n=w["n"], nboxes=w["nboxes"], L0=w["L0"], rel_tol=w["rel_tol"],
                                 max_vcycles=w["max_vcycles"], ncycle=w["ncycle"], npre=w["npre"], npost=w["npost"],
-                                precision=precision, use_graphs=0 if args.no_graphs else 1, tile_small=tile)
+                                precision=precision, use_graphs=0 if args.no_graphs else 1, tile_small=tile,
+                                persistent_vcycle=form)
 
     gal, prm, v_obs_h, sigma_h = sweep_inputs()
     host_sets = [gal.particles(r) for r in prm]
@@ -601,10 +602,12 @@ def run_sweep(args):
     kw = dict(nbins=w["nbins"], rmax=w["rmax"], nphi=w["nphi"], device=dev)
 
     if args.workers:
-        choice, tune = {"batch": w["sets"], "lanes": args.workers, "tile_small": 0}, None
+        choice, tune = {"batch": w["sets"], "lanes": args.workers, "tile_small": 0,
+                        "persistent_vcycle": args.persistent_vcycle}, None
     else:
         choice, tune = q.autotune(params(prec), sets, dist, v_obs, sigma, **kw)
-    sw = q.FitSweep(params(prec, choice["tile_small"]), batch=choice["batch"], lanes=choice["lanes"], **kw)
+    sw = q.FitSweep(params(prec, choice["tile_small"], choice["persistent_vcycle"]), batch=choice["batch"],
+                    lanes=choice["lanes"], **kw)
     ctx = Contexts(sw.ctxs)
     for _ in range(args.warmup):
         sw.run(sets, dist, v_obs, sigma)
@@ -634,7 +637,8 @@ def run_sweep(args):
 
     # kernel classes timed live inside the batched graphs (the tuned batch, one lane): event-record nodes
     # around each run of consecutive launches of the class in the FMG part of every solve
-    one = q.FitSweep(params(prec, choice["tile_small"]), batch=choice["batch"], lanes=1, **kw)
+    one = q.FitSweep(params(prec, choice["tile_small"], choice["persistent_vcycle"]), batch=choice["batch"], lanes=1,
+                     **kw)
     c1 = Contexts(one.ctxs)
     nsub = choice["batch"]
     sub = tuple(a[:nsub * (a.numel() // w["sets"])] for a in sets)
@@ -741,7 +745,8 @@ def run_sweep(args):
             "e2e": {"value": e2e_value, "unit": "sets/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "gpu_launches_per_step": launches / args.steps,
-            "autotune_ms_per_sweep": {"batch %d, lanes %d, tile %d" % k: v for k, v in tune.items()} if tune else None,
+            "autotune_ms_per_sweep": {"batch %d, lanes %d, tile %d, small-level form %d" % k: v
+                                      for k, v in tune.items()} if tune else None,
             "vcycles_after_fmg_per_set_max": max(max(v) for v in vcyc),
             "best_set": {"index": best, "chi2": float(chi2[best]), "params": [float(v) for v in prm[best]]},
             "unbatched": unbatched,
@@ -1104,7 +1109,7 @@ def main():
                          "autotuner)")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="time the steps one after another instead of pipelining successive steps' chains")
-    ap.add_argument("--persistent-vcycle", type=int, choices=[0, 1, 2, 3], default=0,
+    ap.add_argument("--persistent-vcycle", type=int, choices=[0, 1, 2, 3], default=3,
                     help="the V-cycle on the small levels: 0 one launch per step, 1 one cooperative kernel, "
                          "2 one thread-block cluster (levels n <= 64, global memory), 3 one thread-block cluster "
                          "holding the level n = 32 in distributed shared memory (two-disk and large workloads)")

@@ -127,19 +127,20 @@ typedef struct {
                            the whole tolerance loop, decided on the device);
                            0: kernels are launched one by one */
     int persistent_vcycle; /* the part of each V-cycle on the small levels
-                           below the finest: 0 (default): one launch per
-                           step; 1: the levels n <= 64 as one cooperative
+                           below the finest: 0: one launch per step; 1: the
+                           levels n <= 64 as one cooperative
                            kernel over all SMs with grid barriers (when the
                            device supports cooperative launches; nsets = 1
                            only); 2: the levels n <= 64 as one thread-block
                            cluster per set (16 CTAs where the device can
                            place them, else 8, 4 or 2) meeting at the
                            cluster's hardware barrier, data in global memory;
-                           3: the level n = 32 and those under it as one
-                           cluster of small_cluster CTAs per set holding the
-                           level in distributed shared memory (FP32 smoothing
-                           and finest n >= 64 only; otherwise, or where the
-                           cluster cannot be placed, mode 0).  The results
+                           3 (default): the level n = 32 and those under it
+                           as one cluster of small_cluster CTAs per set
+                           holding the level in distributed shared memory
+                           (FP32 smoothing and finest n >= 64 only;
+                           otherwise, or where the cluster cannot be placed,
+                           mode 0).  The results
                            are the same bits in every mode.  On GB300 the
                            cooperative form is not faster (a grid barrier
                            costs about what a graph launch does, and it
@@ -172,7 +173,7 @@ typedef struct qumond_ctx qumond_ctx;
 /* Paper defaults: n = 256, one box of 120 kpc, G = 4.30e-3, a0 = 3.6,
    npre = npost = 2, ncycle = 6, rel_tol = 0 (paper mode), max_vcycles = 50,
    QUMOND_PREC_MIXED, QUMOND_BC_ZERO, warm_start = 0, deposit_shift = 24,
-   rc_box_frac = 0.2, box_ratio = 2, use_graphs = 1, persistent_vcycle = 0,
+   rc_box_frac = 0.2, box_ratio = 2, use_graphs = 1, persistent_vcycle = 3,
    nsets = 1, tile_small = 0, small_cluster = 0. */
 QUMOND_API void qumond_default_params(qumond_params* p);
 

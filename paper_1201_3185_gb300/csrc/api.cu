@@ -850,7 +850,7 @@ void qumond_default_params(qumond_params* p)
     p->rc_box_frac = 0.2;
     p->box_ratio = 2;
     p->use_graphs = 1;
-    p->persistent_vcycle = 0;
+    p->persistent_vcycle = 3;
     p->nsets = 1;
     p->tile_small = 0;
     p->small_cluster = 0;

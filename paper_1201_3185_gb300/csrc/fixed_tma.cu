@@ -9,9 +9,10 @@
 // (i, j) columns, i from a multiple of 32, and 16 k-planes; for every plane it
 // needs, one thread issues four 3-D boxes (U over i0-2 .. i0+33 and a one-row
 // halo, the two colour rows of e covering the same nodes, F of the tile) into
-// a four-slot shared-memory ring completed by mbarriers, so each input byte
-// crosses HBM once and the loads of three planes are in flight while a plane
-// is processed.  A thread works on a pair of consecutive nodes (i even, i+1):
+// a three-slot shared-memory ring completed by mbarriers, so each input byte
+// crosses HBM once and the loads of the next plane are in flight while a
+// plane is processed (three slots rather than four leave room for seven CTAs
+// per multiprocessor instead of six, which measured faster).  A thread works on a pair of consecutive nodes (i even, i+1):
 // the pairs start on 16-byte boundaries in every staged array, so the update
 // and the stencil use 16-byte shared-memory loads and stores.  Waits are bounded:
 // after kSpinLimit polls a CTA records a fault (reported by the solve as a
@@ -35,7 +36,7 @@ static_assert(kOffE0 >= kUBytes && kOffE1 >= kOffE0 + kEBytes && kOffF >= kOffE1
                   kSlotBytes >= kOffF + kFBytes && kOffE0 % 128 == 0 && kOffE1 % 128 == 0 && kOffF % 128 == 0 &&
                   kSlotBytes % 128 == 0,
               "slot parts are disjoint and 128-byte aligned");
-constexpr int kSlots = 4;
+constexpr int kSlots = 3;
 constexpr long long kSpinLimit = 1LL << 24;
 constexpr int kMinN = 128;
 

@@ -18,7 +18,8 @@ radii scaled by that set's distance factor (the observed radii are fixed
 angles) and one kernel computes every set's chi^2 at the end.
 
 `autotune` picks the batch size, the number of lanes and the block shape of
-the small-level kernels (params.tile_small) by timing the sweep itself.
+the small-level kernels (params.tile_small) and the form of the small-level
+V-cycle (params.persistent_vcycle) by timing the sweep itself.
 """
 from __future__ import annotations
 
@@ -162,19 +163,25 @@ def _copy(p: qumond_params) -> qumond_params:
 
 
 def autotune(params: qumond_params, particles, distance, v_obs, sigma, *, nbins: int, rmax: float, nphi: int = 64,
-             batches=(8, 16, 32, 64), lanes=(1, 2, 4), tiles=(0, 1, 2), repeats: int = 2, device=None):
-    """Picks the batch size, the number of lanes and the small-level block
-    shape (params.tile_small) by timing: each candidate runs the given sweep
-    once untimed (graph capture) and `repeats` times timed with CUDA events.
-    The block shape is searched at the best (batch, lanes).  Results do not
-    depend on the choice (each set's arithmetic is the same), only the time
-    does.  Returns ({"batch", "lanes", "tile_small"}, {candidate: ms})."""
+             batches=(8, 16, 32, 64), lanes=(1, 2, 4), tiles=(0, 1, 2), forms=(3, 0), repeats: int = 2, device=None):
+    """Picks the batch size, the number of lanes, the small-level block shape
+    (params.tile_small) and the form of the small-level V-cycle
+    (params.persistent_vcycle: 3, one cluster per set holding the level n = 32
+    in shared memory, or 0, one launch per step) by timing: each candidate
+    runs the given sweep once untimed (graph capture) and `repeats` times
+    timed with CUDA events.  Batch and lanes are searched with params' own
+    form and tile 0, the block shape at the best (batch, lanes), the form at
+    the best of those.  Results do not depend on the choice (each set's
+    arithmetic is the same), only the time does.  Returns ({"batch", "lanes",
+    "tile_small", "persistent_vcycle"}, {(batch, lanes, tile, form): ms})."""
     nsets = len(distance)
     times = {}
+    form0 = params.persistent_vcycle
 
-    def time_one(b, k, tile):
+    def time_one(b, k, tile, form):
         p = _copy(params)
         p.tile_small = tile
+        p.persistent_vcycle = form
         with FitSweep(p, nbins=nbins, rmax=rmax, nphi=nphi, batch=b, lanes=k, device=device) as sw:
             sw.run(particles, distance, v_obs, sigma)
             t0 = torch.cuda.Event(enable_timing=True)
@@ -191,13 +198,17 @@ def autotune(params: qumond_params, particles, distance, v_obs, sigma, *, nbins:
     for b, k in itertools.product(batches, lanes):
         if b > max(1, nsets) or (k > 1 and b * k > max(1, nsets) + b - 1):
             continue  # more lanes than chunks
-        times[(b, k, 0)] = time_one(b, k, 0)
-    b0, k0, _ = min(times, key=times.get)
+        times[(b, k, 0, form0)] = time_one(b, k, 0, form0)
+    b0, k0, _, _ = min(times, key=times.get)
     for tile in tiles:
-        if (b0, k0, tile) not in times:
-            times[(b0, k0, tile)] = time_one(b0, k0, tile)
+        if (b0, k0, tile, form0) not in times:
+            times[(b0, k0, tile, form0)] = time_one(b0, k0, tile, form0)
+    _, _, t0, _ = min(times, key=times.get)
+    for form in forms:
+        if (b0, k0, t0, form) not in times:
+            times[(b0, k0, t0, form)] = time_one(b0, k0, t0, form)
     best = min(times, key=times.get)
-    return {"batch": best[0], "lanes": best[1], "tile_small": best[2]}, times
+    return {"batch": best[0], "lanes": best[1], "tile_small": best[2], "persistent_vcycle": best[3]}, times
 
 
 def tune_workers(params: qumond_params, particles, distance, v_obs, sigma, *, nbins: int, rmax: float, nphi: int = 64,
