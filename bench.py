@@ -338,28 +338,55 @@ def run_ours(args):
     # the K steps run pipelined (Pipeline.run_many): the Newtonian chain of step i+1 overlaps
     # the QUMOND chain, forces and rotation curve of step i; every step is the whole path. ---
     pipelined = args.chains == 2 and not args.no_pipeline
+    # lanes: independent steps spread over several pipelines (two contexts each) that run concurrently
+    # (paper_1201_3185_gb300.run_lanes); every step is still the whole path on one pipeline's buffers
+    lane_sets = [(ctx, pipe)]
+    lane_g = [g]
 
-    def steps_timed(nsteps, pp=None):
+    def lane_pipes(nl):
+        while len(lane_sets) < nl:
+            lane_sets.append(new_pipeline(prec))
+            lane_g.append(tuple(torch.empty_like(xd) for _ in range(3)))
+        return [pp for _, pp in lane_sets[:nl]]
+
+    def steps_timed(nsteps, pp=None, nl=1):
         pp = pp or pipe
         if pipelined and pp.ctx_mond is not None:
-            return pp.run_many([(xd, yd, zd, md)] * nsteps, nbins=w["nbins"], rmax=w["rmax"], nphi=w["nphi"],
-                               forces=[g] * nsteps)
+            pipes = lane_pipes(nl)
+            return q.run_lanes(pipes, [(xd, yd, zd, md)] * nsteps, nbins=w["nbins"], rmax=w["rmax"],
+                               nphi=w["nphi"], forces=[lane_g[i % nl] for i in range(nsteps)])
         return [step(pp) for _ in range(nsteps)]
 
-    steps_timed(max(2, args.warmup))  # captures the graphs of the pipelined form
-    ctx.qumond_trace_read(reset=True)
+    lanes = max(1, args.lanes) if pipelined else 1
+    lanes_tried = None
+    if pipelined and args.lanes == 0:  # pick the number of lanes (1 or 2) by timing a few steps of each
+        lanes_tried = {}
+        for nl in (1, 2):
+            steps_timed(max(2, args.warmup), nl=nl)  # captures the graphs of the lanes' contexts
+            barrier()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record()
+            steps_timed(8, nl=nl)
+            a1.record()
+            barrier()
+            lanes_tried[nl] = ws * 8 * 1000.0 / max_over_ranks(a0.elapsed_time(a1))
+        lanes = max(lanes_tried, key=lanes_tried.get)
+    steps_timed(max(2, args.warmup), nl=lanes)  # captures the graphs of the pipelined form
+    ctx_all = Contexts([c for cx, _ in lane_sets[:lanes] for c in cx.ctxs])
+    ctx_all.qumond_trace_read(reset=True)
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
     s0 = torch.cuda.Event(enable_timing=True)
     s1 = torch.cuda.Event(enable_timing=True)
     s0.record()
-    res = steps_timed(args.steps)[-1]
+    res = steps_timed(args.steps, nl=lanes)[-1]
     s1.record()
     barrier()
     clk = clocks.stop()
     ms_total = max_over_ranks(s0.elapsed_time(s1))
-    timed_stats, launches, cell_updates = ctx.qumond_trace_read(reset=True)
+    timed_stats, launches, cell_updates = ctx_all.qumond_trace_read(reset=True)
     step_bytes = sum(k.bytes for k in timed_stats.values()) / args.steps
     ms_step = ms_total / args.steps
     value = ws * args.steps / (ms_total / 1000.0)
@@ -455,21 +482,36 @@ def run_ours(args):
     if pipelined:  # device buffers of every step, so that the steps can overlap
         dev_in = [[torch.empty_like(xd) for _ in range(4)] for _ in range(args.steps)]
         dev_g = [tuple(torch.empty_like(xd) for _ in range(3)) for _ in range(args.steps)]
+        h2d_stream, d2h_stream = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     if pipelined:
-        for i in range(args.steps):
-            for a, b in zip(dev_in[i], host):
-                a.copy_(b, non_blocking=True)
-        rs = pipe.run_many([tuple(d) for d in dev_in], nbins=w["nbins"], rmax=w["rmax"], nphi=w["nphi"],
-                           forces=dev_g)
-        for i in range(args.steps):
-            for a, b in zip(out_g[i], dev_g[i]):
-                a.copy_(b, non_blocking=True)
-            out_vc[i].copy_(rs[i].vc, non_blocking=True)
-            out_r[i].copy_(rs[i].r, non_blocking=True)
+        # copies in on one stream (each step's first kernel waits for its own copy), results out on
+        # another as each step completes, so that the transfers overlap the other steps' kernels
+        cur = torch.cuda.current_stream(dev)
+        h2d_stream.wait_stream(cur)
+        d2h_stream.wait_stream(cur)
+        ready = []
+        with torch.cuda.stream(h2d_stream):
+            for i in range(args.steps):
+                for a, b in zip(dev_in[i], host):
+                    a.copy_(b, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(h2d_stream)
+                ready.append(ev)
+        rs = q.run_lanes(lane_pipes(lanes), [tuple(d) for d in dev_in], nbins=w["nbins"], rmax=w["rmax"],
+                         nphi=w["nphi"], forces=dev_g, ready=ready)
+        with torch.cuda.stream(d2h_stream):
+            for i in range(args.steps):
+                d2h_stream.wait_event(rs[i].done)
+                for a, b in zip(out_g[i], dev_g[i]):
+                    a.copy_(b, non_blocking=True)
+                out_vc[i].copy_(rs[i].vc, non_blocking=True)
+                out_r[i].copy_(rs[i].r, non_blocking=True)
+        cur.wait_stream(h2d_stream)
+        cur.wait_stream(d2h_stream)
     else:
         for i in range(args.steps):
             xs, ys, zs, ms_ = (t.to(dev, non_blocking=True) for t in host)
@@ -505,6 +547,10 @@ def run_ours(args):
 
     plain = None
     fp64_dc = None
+    for cx, pp in lane_sets[1:]:  # the extra lanes
+        pp.close()
+        cx.close()
+    del lane_sets[1:]
     if not args.no_plain and prec != q.QUMOND_PREC_FP64:
         pipe.close()
         ctx.close()
@@ -548,6 +594,8 @@ def run_ours(args):
             "gpu_launches_per_step": launches / args.steps,
             "chains": args.chains,
             "pipelined_steps": pipelined,
+            "lanes": lanes,
+            "lanes_tried": lanes_tried,
             "step_by_step": step_by_step,
             "small_level_vcycle": {0: "one graph kernel node per smoothing, restriction and prolongation", 1: "one cooperative kernel", 2: "one thread-block cluster per set", 3: "the level n = 32 and those under it in the distributed shared memory of one thread-block cluster per set"}[args.persistent_vcycle],
             "one_chain": {"value": ws * 1000.0 / one_chain_ms, "unit": UNIT, "ms_per_step": one_chain_ms},
@@ -1113,6 +1161,9 @@ def main():
                     help="the V-cycle on the small levels: 0 one launch per step, 1 one cooperative kernel, "
                          "2 one thread-block cluster (levels n <= 64, global memory), 3 one thread-block cluster "
                          "holding the level n = 32 in distributed shared memory (two-disk and large workloads)")
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="two-disk and large: pipelines (two contexts each) running independent steps "
+                         "concurrently; 0: 1 or 2, whichever times faster")
     ap.add_argument("--small-cluster", type=int, choices=[0, 4, 8, 16], default=0,
                     help="CTAs per cluster of --persistent-vcycle 3 (0: 8)")
     ap.add_argument("--profile-case", action="store_true",

@@ -18,5 +18,5 @@ from .qumond import (  # noqa: F401
     QUMOND_BC_MULTIPOLE,
     EXPORTED,
 )
-from .pipeline import Pipeline, PipelineResult  # noqa: F401
+from .pipeline import Pipeline, PipelineResult, run_lanes  # noqa: F401
 from .sweep import FitSweep, SweepResult, autotune, tune_workers  # noqa: F401

@@ -52,6 +52,7 @@ class PipelineResult:
     vc: torch.Tensor
     newton_stats: list = field(default_factory=list)
     mond_stats: list = field(default_factory=list)
+    done: object = None  # run_many: CUDA event recorded once this evaluation's forces and curve are written
 
 
 class Pipeline:
@@ -184,7 +185,7 @@ class Pipeline:
         caller.wait_event(end_b)
         return ns, ms
 
-    def run_many(self, inputs, *, nbins=50, rmax=30000.0, nphi=64, forces=None, stream=None):
+    def run_many(self, inputs, *, nbins=50, rmax=30000.0, nphi=64, forces=None, stream=None, ready=None):
         """The whole path (as run()) for a sequence of evaluations, one (x, y,
         z, m) tuple of device tensors each, with the two chains pipelined
         across evaluations: the Newtonian chain of evaluation i+1 (deposits,
@@ -199,9 +200,13 @@ class Pipeline:
         (they share the source buffer); with the far-field boundary, box 0's
         potential alternates between two buffers, and the far field of
         evaluation i+2 waits until evaluation i's forces and curve are done.
-        forces: None, or one (gx, gy, gz) tuple per evaluation.  Needs two
-        contexts (ctx_mond).  Returns one PipelineResult per evaluation (r,
-        vc; no solve statistics)."""
+        forces: None, or one (gx, gy, gz) tuple per evaluation.  ready: None,
+        or one CUDA event (or None) per evaluation that its first kernel waits
+        for, e.g. the end of the copy of its particles on another stream, so
+        that copies overlap the evaluations before it.  Needs two contexts
+        (ctx_mond).  Returns one PipelineResult per evaluation (r, vc, and
+        `done`, an event recorded once its forces and curve are written; no
+        solve statistics)."""
         if self.ctx_mond is None:
             raise ValueError("run_many pipelines the two chains: it needs ctx_mond")
         if self.guess is not None:
@@ -209,6 +214,8 @@ class Pipeline:
         nev = len(inputs)
         if forces is not None and len(forces) != nev:
             raise ValueError("need one forces tuple per evaluation")
+        if ready is not None and len(ready) != nev:
+            raise ValueError("need one ready event (or None) per evaluation")
         nb = self.ctx.params.nboxes
         dev = self.device
         caller = stream if stream is not None else torch.cuda.current_stream(dev)
@@ -226,7 +233,7 @@ class Pipeline:
         src_done = [[torch.cuda.Event() for _ in range(nb)] for _ in range(nev)]
         mond_done = [[torch.cuda.Event() for _ in range(nb)] for _ in range(nev)]
         eval_done = [torch.cuda.Event() for _ in range(nev)]
-        ready = [[threading.Event() for _ in range(nb)] for _ in range(nev)]
+        handoff = [[threading.Event() for _ in range(nb)] for _ in range(nev)]
         mond_rec = [[threading.Event() for _ in range(nb)] for _ in range(nev)]
         eval_rec = [threading.Event() for _ in range(nev)]
         failed = []
@@ -240,7 +247,7 @@ class Pipeline:
                     for i in range(nev):
                         phis = phis_of(i)
                         for b in range(nb):
-                            ready[i][b].wait()
+                            handoff[i][b].wait()
                             if failed:
                                 return
                             sb.wait_event(src_done[i][b])
@@ -266,6 +273,8 @@ class Pipeline:
             for i in range(nev):
                 x, y, z, m = inputs[i]
                 phis = phis_of(i)
+                if ready is not None and ready[i] is not None:
+                    sa.wait_event(ready[i])
                 for b in range(nb):
                     self.ctx.qumond_deposit(b, x, y, z, m, self.rho_fixed, self.rho, stream=sa)
                     if b == 0 and self.far_field:
@@ -284,12 +293,12 @@ class Pipeline:
                         sa.wait_event(mond_done[i - 1][b])
                     self.ctx.qumond_source(b, self.phiN[b], self.srcs[b], stream=sa)
                     src_done[i][b].record(sa)
-                    ready[i][b].set()
+                    handoff[i][b].set()
                 if failed:
                     break
         except Exception:
             failed.append(True)
-            for row in ready:
+            for row in handoff:
                 for e in row:
                     e.set()
             try:
@@ -298,7 +307,7 @@ class Pipeline:
                 pass
             raise
         if failed:
-            for row in ready:
+            for row in handoff:
                 for e in row:
                     e.set()
         fut.result()  # re-raises the QUMOND chain's error
@@ -309,6 +318,8 @@ class Pipeline:
         caller.wait_event(end_b)
         if self.far_field and nev % 2 == 0:  # self.phi holds the last evaluation's potentials
             self.phi[0], self._phi0_alt = self._phi0_alt, self.phi[0]
+        for res, ev in zip(results, eval_done):
+            res.done = ev
         return results
 
     def run(self, x, y, z, m, *, nbins=50, rmax=30000.0, nphi=64, forces=None, stats=False, stream=None):
@@ -321,3 +332,58 @@ class Pipeline:
         vc = torch.empty(nbins * self.ctx.nsets, dtype=torch.float64, device=self.device)
         self.ctx.qumond_rotation_curve(self.phi, nbins, rmax, nphi, r, vc, stream=stream)
         return PipelineResult(r, vc, ns, ms)
+
+
+def run_lanes(pipes, inputs, *, nbins=50, rmax=30000.0, nphi=64, forces=None, ready=None, stream=None):
+    """Independent evaluations spread over several pipelines ("lanes", each
+    with its own two contexts, buffers and streams) that run concurrently on
+    the device: evaluation i goes to pipes[i % len(pipes)], and each lane
+    pipelines its share as run_many does, from its own host thread (a solve
+    call returns once its statistics are read, so every lane needs one).
+    Each evaluation runs the kernels of run() on its own lane's buffers, so
+    its results are the same bits.  forces / ready: as in run_many, one per
+    evaluation (forces tuples of evaluations that run concurrently must be
+    distinct).  Results in input order; every lane's work is ordered before
+    later work on `stream` (the caller's current stream by default)."""
+    nl = len(pipes)
+    nev = len(inputs)
+    caller = stream if stream is not None else torch.cuda.current_stream(pipes[0].device)
+    results = [None] * nev
+    errors = []
+    # each lane starts after the caller's earlier work and ends on a stream of its own, which the caller waits
+    # for once every lane is enqueued (a lane's end must not hold up another lane's start)
+    start = torch.cuda.Event()
+    start.record(caller)
+    lane_streams = []
+    for pp in pipes:
+        if not hasattr(pp, "_lane_stream"):
+            pp._lane_stream = torch.cuda.Stream(pp.device)
+        pp._lane_stream.wait_event(start)
+        lane_streams.append(pp._lane_stream)
+
+    def lane(k):
+        idx = list(range(k, nev, nl))
+        if not idx:
+            return
+        try:
+            with torch.cuda.device(pipes[k].device):
+                rs = pipes[k].run_many([inputs[i] for i in idx], nbins=nbins, rmax=rmax, nphi=nphi,
+                                       forces=None if forces is None else [forces[i] for i in idx],
+                                       ready=None if ready is None else [ready[i] for i in idx],
+                                       stream=lane_streams[k])
+            for i, r in zip(idx, rs):
+                results[i] = r
+        except Exception as exc:  # re-raised in the calling thread
+            errors.append(exc)
+
+    threads = [threading.Thread(target=lane, args=(k,), name="qumond-lane-%d" % k) for k in range(1, nl)]
+    for t in threads:
+        t.start()
+    lane(0)
+    for t in threads:
+        t.join()
+    for ls in lane_streams:
+        caller.wait_stream(ls)
+    if errors:
+        raise errors[0]
+    return results

@@ -436,7 +436,8 @@ def test_invalid_arguments_rejected(q):
 @pytest.mark.parametrize("bc", ["zero", "multipole"])
 def test_pipelined_evaluations_give_the_same_bits(q, bc):
     # run_many overlaps the Newtonian chain of evaluation i+1 with the QUMOND
-    # chain, forces and curve of evaluation i; every evaluation must give the
+    # chain, forces and curve of evaluation i, and run_lanes spreads the
+    # evaluations over concurrent pipelines; every evaluation must give the
     # bits of a lone run()
     gals = [synth.two_component_disk(40_000, seed=40 + s, rmax=54000.0, zmax=54000.0) for s in range(2)]
     kw = dict(n=64, nboxes=3, L0=120000.0, rel_tol=1e-10, max_vcycles=40, precision=q.QUMOND_PREC_MIXED_FIXED,
@@ -467,6 +468,33 @@ def test_pipelined_evaluations_give_the_same_bits(q, bc):
             assert torch.equal(a, b), i
     for a, b in zip(pipe.phi, want[order[-1]][2]):  # the potentials of the last evaluation
         assert torch.equal(a, b)
+    # the same evaluations over two lanes (two pipelines running concurrently), each evaluation's particles
+    # copied in on another stream that its first kernel waits for
+    cc, cd = q.Context(**kw), q.Context(**kw)
+    pipe2 = q.Pipeline(cc, ctx_mond=cd)
+    copies = [tuple(torch.empty_like(t) for t in dev[k]) for k in order]
+    forces2 = [tuple(torch.empty_like(dev[k][0]) for _ in range(3)) for k in order]
+    side = torch.cuda.Stream()
+    for _ in range(2):
+        ready = []
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for c, k in zip(copies, order):
+                for a, b in zip(c, dev[k]):
+                    a.copy_(b, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(side)
+                ready.append(ev)
+        res2 = q.run_lanes([pipe, pipe2], copies, nbins=30, rmax=20000.0, forces=forces2, ready=ready)
+    torch.cuda.synchronize()
+    for i, k in enumerate(order):
+        assert res2[i].done is not None
+        assert torch.equal(res2[i].vc, want[k][0]), i
+        for a, b in zip(forces2[i], want[k][1]):
+            assert torch.equal(a, b), i
+    pipe2.close()
+    cc.close()
+    cd.close()
     pipe.close()
     ca.close()
     cb.close()
