@@ -573,8 +573,8 @@ def run_ours(args):
             cm.close()
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(p)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and w["kind"] != "large":  # (513^3: minutes per step)
+        cpu = cpu_baseline(args)
 
     if rank == 0:
         line = {
@@ -1059,15 +1059,25 @@ def cpu_cores():
     return int(n) if n else (os.cpu_count() or 1)
 
 
-def cpu_baseline(p, steps=2):
-    import oracle
-    oracle.build()
+def cpu_baseline(args, steps=2):
+    """The oracle timed as the reference arm times it -- `bench.py --impl reference` in a process of its own
+    (nothing of this process's GPU work, threads or pinned memory around it), 3 untimed and `steps` timed
+    whole steps -- so that the two CPU figures are the same measurement."""
     w = WORKLOAD
-    times = [oracle_step(p) for _ in range(steps)]
-    value = 1.0 / statistics.mean(times)
-    return {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-            "sample": "%d steps, each %s (%.1f s per step)" % (steps, STEP_SAMPLE % (w["nboxes"], w["rel_tol"]),
-                                                             statistics.mean(times))}
+    cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--workload", args.workload,
+           "--steps", str(steps), "--warmup", "3", "--precision", args.precision]
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1200)
+    line = None
+    for ln in r.stdout.splitlines():
+        if ln.startswith("{"):
+            line = json.loads(ln)
+    if r.returncode != 0 or not line or "value" not in line:
+        raise RuntimeError("oracle timing failed: %s" % (r.stderr[-2000:] or r.stdout[-2000:]))
+    return {"value": line["value"], "unit": UNIT, "cores": line["cpu_baseline"]["cores"], "kind": "oracle",
+            "sample": "3 untimed and %d timed steps in a process of its own (bench.py --impl reference), each %s "
+                      "(%.1f s per step)" % (steps, STEP_SAMPLE % (w["nboxes"], w["rel_tol"]),
+                                             line["ms_per_step"] / 1000.0)}
 
 
 def run_reference(args):

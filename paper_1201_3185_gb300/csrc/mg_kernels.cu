@@ -494,7 +494,8 @@ __device__ __forceinline__ void sm_sync()
 // One colour of the interior of an N-level: row (j, k) holds that colour's
 // nodes at i = first, first + 2, ... (first = 1 or 2), N/2 slots per row.
 // The stride is a multiple of N/2, so a thread keeps its slot and steps its
-// row (j, k) without divisions.
+// row (j, k) without divisions (the residual and the prolongation below do
+// the same with N lanes per row, the last one idle).
 template <typename T, int N, bool W = false>
 __device__ void sm_relax(T* u, const T* f, T h2, int colour)
 {
@@ -524,12 +525,24 @@ __device__ void sm_relax(T* u, const T* f, T h2, int colour)
 template <typename T, int N, bool W = false>
 __device__ void sm_residual(const T* u, const T* f, T* r, T ih2)
 {
-    constexpr int M = N - 1, P = N + 1, TOT = M * M * M;
-    for (int t = threadIdx.x; t < TOT; t += sm_stride<W>()) {
-        const int i = t % M + 1, j = (t / M) % M + 1, k = t / (M * M) + 1;
-        const int o = i + P * (j + P * k);
-        const T sum = (u[o + 1] + u[o - 1]) + (u[o + P] + u[o - P]) + (u[o + P * P] + u[o - P * P]);
-        r[o] = f[o] - (sum - T(6) * u[o]) * ih2;
+    constexpr int M = N - 1, P = N + 1, ROWS = M * M;
+    const int dr = sm_stride<W>() / N;  // rows advanced per pass: a row is N lanes, the last one idle
+    const int dj = dr % M, dk = dr / M;
+    const int i = (int)threadIdx.x % N + 1;
+    int row = (int)threadIdx.x / N;
+    int j = row % M + 1, k = row / M + 1;
+    for (; row < ROWS; row += dr) {
+        if (i <= M) {
+            const int o = i + P * (j + P * k);
+            const T sum = (u[o + 1] + u[o - 1]) + (u[o + P] + u[o - P]) + (u[o + P * P] + u[o - P * P]);
+            r[o] = f[o] - (sum - T(6) * u[o]) * ih2;
+        }
+        j += dj;
+        k += dk;
+        if (j > M) {
+            j -= M;
+            ++k;
+        }
     }
     sm_sync<W>();
 }
@@ -558,17 +571,29 @@ __device__ void sm_restrict(const T* fine, T* coarse)
 template <typename T, int NC, bool W = false>
 __device__ void sm_prolong(const T* coarse, T* fine, bool add)
 {
-    constexpr int NF = 2 * NC, M = NF - 1, PF = NF + 1, PC = NC + 1, TOT = M * M * M;
-    for (int t = threadIdx.x; t < TOT; t += sm_stride<W>()) {
-        const int i = t % M + 1, j = (t / M) % M + 1, k = t / (M * M) + 1;
-        const int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = j >> 1, J1 = (j + 1) >> 1, K0 = k >> 1, K1 = (k + 1) >> 1;
-        T sum = (coarse[I0 + PC * (J0 + PC * K0)] + coarse[I1 + PC * (J0 + PC * K0)])
-              + (coarse[I0 + PC * (J1 + PC * K0)] + coarse[I1 + PC * (J1 + PC * K0)]);
-        sum += (coarse[I0 + PC * (J0 + PC * K1)] + coarse[I1 + PC * (J0 + PC * K1)])
-             + (coarse[I0 + PC * (J1 + PC * K1)] + coarse[I1 + PC * (J1 + PC * K1)]);
-        sum *= T(0.125);
-        const int o = i + PF * (j + PF * k);
-        fine[o] = add ? fine[o] + sum : sum;
+    constexpr int NF = 2 * NC, M = NF - 1, PF = NF + 1, PC = NC + 1, ROWS = M * M;
+    const int dr = sm_stride<W>() / NF;  // rows advanced per pass: a row is NF lanes, the last one idle
+    const int dj = dr % M, dk = dr / M;
+    const int i = (int)threadIdx.x % NF + 1;
+    int row = (int)threadIdx.x / NF;
+    int j = row % M + 1, k = row / M + 1;
+    for (; row < ROWS; row += dr) {
+        if (i <= M) {
+            const int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = j >> 1, J1 = (j + 1) >> 1, K0 = k >> 1, K1 = (k + 1) >> 1;
+            T sum = (coarse[I0 + PC * (J0 + PC * K0)] + coarse[I1 + PC * (J0 + PC * K0)])
+                  + (coarse[I0 + PC * (J1 + PC * K0)] + coarse[I1 + PC * (J1 + PC * K0)]);
+            sum += (coarse[I0 + PC * (J0 + PC * K1)] + coarse[I1 + PC * (J0 + PC * K1)])
+                 + (coarse[I0 + PC * (J1 + PC * K1)] + coarse[I1 + PC * (J1 + PC * K1)]);
+            sum *= T(0.125);
+            const int o = i + PF * (j + PF * k);
+            fine[o] = add ? fine[o] + sum : sum;
+        }
+        j += dj;
+        k += dk;
+        if (j > M) {
+            j -= M;
+            ++k;
+        }
     }
     sm_sync<W>();
 }

@@ -76,17 +76,19 @@ def device_sets(gal, params):
     return [tuple(to_dev(a) for a in (p.x, p.y, p.z, p.m)) for p in (gal.particles(r) for r in params)]
 
 
-@pytest.mark.parametrize("prec_name,graphs,form", [("MIXED_FIXED", 1, 0), ("MIXED_FIXED", 0, 0), ("MIXED", 1, 0),
-                                                    ("FP64", 1, 0), ("MIXED_FIXED", 1, 2), ("FP64", 0, 2),
-                                                    ("MIXED_FIXED", 1, 3), ("MIXED", 0, 3)])
-def test_context_sets_match_one_set_contexts(q, prec_name, graphs, form):
+@pytest.mark.parametrize("prec_name,graphs,form,n", [("MIXED_FIXED", 1, 0, 64), ("MIXED_FIXED", 0, 0, 64),
+                                                      ("MIXED", 1, 0, 64), ("FP64", 1, 0, 64),
+                                                      ("MIXED_FIXED", 1, 2, 64), ("FP64", 0, 2, 64),
+                                                      ("MIXED_FIXED", 1, 3, 64), ("MIXED", 0, 3, 64),
+                                                      ("MIXED_FIXED", 1, 3, 128)])
+def test_context_sets_match_one_set_contexts(q, prec_name, graphs, form, n):
     """A context with nsets = 4 (the small levels' V-cycle one launch per step,
     or one thread-block cluster per set): deposit, both solves of two boxes, source,
     forces and rotation curves of all sets in one launch per kernel; every
     set's results are the bits of a context holding that set alone, although
     the sets need different numbers of V-cycles (the converged ones are
     skipped)."""
-    n, L0, nbins = 64, 80000.0, 20
+    L0, nbins = 80000.0, 20
     prec = getattr(q, "QUMOND_PREC_" + prec_name)
     gal = synth.SweepGalaxy(30000, seed=15)
     params = synth.fit_sweep_parameters(4, seed=16)
