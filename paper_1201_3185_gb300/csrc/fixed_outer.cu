@@ -204,7 +204,12 @@ fixed_init_pairs_kernel(const float* __restrict__ e, LevelView v, const double* 
 // the finest level; per-block partial sums of r^2 (and, on the first check,
 // of f^2 with f = F 2^-S / h^2).  The squares are summed as (R 2^-30)^2 in
 // FP32 (|R| <= 2^60, so they lie in [2^-60, 2^60]: no overflow or
-// underflow) and scaled back per block in FP64.
+// underflow) and scaled back per block in FP64.  A thread takes a pair of
+// consecutive nodes (i even, i+1; rows of n+2 entries, so the pair starts on
+// a 16-byte boundary): 16-byte loads of the pair and of its four neighbour
+// pairs, two scalars for the x-neighbours past the ends; the two nodes are
+// one red and one black entry with the same index, so the stores of a warp
+// are contiguous in each colour array.
 __global__ void __launch_bounds__(kThreads)
 fixed_residual_kernel(const long long* __restrict__ U, const long long* __restrict__ F, int n, float ih2,
                       const SolveState* __restrict__ st, int want_f, float* __restrict__ r, LevelView v,
@@ -220,21 +225,46 @@ fixed_residual_kernel(const long long* __restrict__ U, const long long* __restri
     }
     const long long P = n + 2, Q = P * (n + 1);
     const float k = pow2f(-st->scale_exp) * ih2;
-    const int rows = (n - 1) * (n - 1);
+    const int half = n / 2;
+    const long long items = (long long)(n - 1) * (n - 1) * half;  // (row, pair)
     float rr = 0.0f, ff = 0.0f;
     constexpr float kDown = 9.313225746154785e-10f;  // 2^-30
-    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int j = row % (n - 1) + 1, kk = row / (n - 1) + 1;
-        for (int i = threadIdx.x + 1; i < n; i += kThreads) {
-            const long long o = fix(n, i, j, kk);
-            const long long s = (U[o + 1] + U[o - 1]) + (U[o + P] + U[o - P]) + (U[o + Q] + U[o - Q]) - 6 * U[o];
-            const long long fv = F[o];
-            const float R = i64_to_f32(fv - s);
-            r[node_off(v, i, j, kk)] = R * k;
-            const float Rs = R * kDown;
+    for (long long it = blockIdx.x * (long long)kThreads + threadIdx.x; it < items;
+         it += (long long)gridDim.x * kThreads) {
+        const int m = (int)(it % half);
+        const long long row = it / half;
+        const int j = (int)(row % (n - 1)) + 1, kk = (int)(row / (n - 1)) + 1;
+        const int i = 2 * m;  // nodes i (i = 0 is a boundary node) and i + 1 (<= n - 1)
+        const long long o = fix(n, i, j, kk);
+        const longlong2 c = *reinterpret_cast<const longlong2*>(U + o);
+        const long long left = U[o - 1], right = U[o + 2];
+        const longlong2 yp = *reinterpret_cast<const longlong2*>(U + o + P);
+        const longlong2 ym = *reinterpret_cast<const longlong2*>(U + o - P);
+        const longlong2 zp = *reinterpret_cast<const longlong2*>(U + o + Q);
+        const longlong2 zm = *reinterpret_cast<const longlong2*>(U + o - Q);
+        const longlong2 fv = *reinterpret_cast<const longlong2*>(F + o);
+        // the same integer sums as one node per thread (exact, so their order does not matter)
+        const long long s0 = (c.y + left) + (yp.x + ym.x) + (zp.x + zm.x) - 6 * c.x;
+        const long long s1 = (right + c.x) + (yp.y + ym.y) + (zp.y + zm.y) - 6 * c.y;
+        const long long rowb = ((long long)kk * (v.n + 1) + j) * v.M + m;
+        const int c0 = (i + j + kk) & 1;  // colour of node i; node i + 1 has the other one
+        if (i >= 1) {
+            const float R0 = i64_to_f32(fv.x - s0);
+            r[(long long)c0 * v.cs + rowb] = R0 * k;
+            const float Rs = R0 * kDown;
             rr = fmaf(Rs, Rs, rr);
             if (want_f) {
-                const float Fs = i64_to_f32(fv) * kDown;
+                const float Fs = i64_to_f32(fv.x) * kDown;
+                ff = fmaf(Fs, Fs, ff);
+            }
+        }
+        {
+            const float R1 = i64_to_f32(fv.y - s1);
+            r[(long long)(c0 ^ 1) * v.cs + rowb] = R1 * k;
+            const float Rs = R1 * kDown;
+            rr = fmaf(Rs, Rs, rr);
+            if (want_f) {
+                const float Fs = i64_to_f32(fv.y) * kDown;
                 ff = fmaf(Fs, Fs, ff);
             }
         }

@@ -1193,15 +1193,22 @@ __device__ __forceinline__ long long nat(int n, int i, int j, int k)
     return (long long)i + P * ((long long)j + P * (long long)k);
 }
 
+// f = coef rhs on interior nodes, a pair of consecutive nodes (2m, 2m+1) per
+// thread: one red and one black entry with the same index m, so the stores of
+// a warp are contiguous in each colour array.
 template <typename T>
 __global__ void convert_rhs_kernel(const double* __restrict__ rhs, double coef, int n, T* __restrict__ f, LevelView v)
 {
     int kz;
     const int set = set_of(n - 1, kz);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y + 1, k = kz + 1;
-    if (i >= n) return;
-    f[set * 2 * v.cs + node_off(v, i, j, k)] = (T)(coef * rhs[set * nat_elems(n) + nat(n, i, j, k)]);
+    if (m >= n / 2) return;
+    const double* src = rhs + set * nat_elems(n) + nat(n, 2 * m, j, k);
+    T* row = f + set * 2 * v.cs + ((long long)k * (v.n + 1) + j) * v.M + m;
+    const int c = (2 * m + j + k) & 1;  // colour of node 2m; node 2m+1 has the other one
+    if (m > 0) row[(long long)c * v.cs] = (T)(coef * src[0]);  // node 0 is a boundary node
+    row[(long long)(c ^ 1) * v.cs] = (T)(coef * src[1]);
 }
 
 template <typename T, bool ADD>
@@ -1738,7 +1745,8 @@ template <typename T>
 void launch_convert_rhs(const double* rhs, double coef, int n, T* f, const LevelView& v, cudaStream_t s,
                         const Sets& sets)
 {
-    convert_rhs_kernel<T><<<per_sets(outer_grid(n), sets), kOuterThreads, 0, s>>>(rhs, coef, n, f, v);
+    const dim3 g(cdiv(n / 2, kOuterThreads), (unsigned)(n - 1), (unsigned)(n - 1));
+    convert_rhs_kernel<T><<<per_sets(g, sets), kOuterThreads, 0, s>>>(rhs, coef, n, f, v);
 }
 
 template <typename T>
