@@ -299,13 +299,42 @@ def run_ours(args):
                              max_vcycles=w["max_vcycles"], ncycle=w["ncycle"], npre=w["npre"], npost=w["npost"],
                              precision=precision, use_graphs=0 if args.no_graphs else 1,
                              bc_mode=q.QUMOND_BC_MULTIPOLE if w.get("bc") == "multipole" else q.QUMOND_BC_ZERO,
-                             persistent_vcycle=args.persistent_vcycle, small_cluster=args.small_cluster)
+                             persistent_vcycle=args.persistent_vcycle, small_cluster=args.small_cluster,
+                             dc_vcycles=args.dc_vcycles)
         cs = [make() for _ in range(args.chains)]
         return Contexts(cs), q.Pipeline(cs[0], dev, ctx_mond=cs[1] if len(cs) > 1 else None)
 
-    ctx, pipe = new_pipeline(prec)
     xd, yd, zd, md = (torch.from_numpy(a).to(dev) for a in (p.x, p.y, p.z, p.m))
     g = tuple(torch.empty_like(xd) for _ in range(3))
+
+    # V-cycles per defect-correction step: 2 or 4, whichever times faster on a few pipelined steps of this
+    # workload (every choice meets the same tolerance; only the number of residual checks differs)
+    dc_tried = None
+    if args.dc_vcycles == 0:
+        dc_tried = {}
+        for dc in (2, 4):
+            args.dc_vcycles = dc
+            cx, pp = new_pipeline(prec)
+            runs = lambda k: (pp.run_many([(xd, yd, zd, md)] * k, nbins=w["nbins"], rmax=w["rmax"], nphi=w["nphi"],
+                                          forces=[g] * k) if pp.ctx_mond is not None else
+                              [pp.run(xd, yd, zd, md, nbins=w["nbins"], rmax=w["rmax"], nphi=w["nphi"], forces=g)
+                               for _ in range(k)])
+            runs(max(2, args.warmup))
+            barrier()
+            d0 = torch.cuda.Event(enable_timing=True)
+            d1 = torch.cuda.Event(enable_timing=True)
+            d0.record()
+            runs(6)
+            d1.record()
+            barrier()
+            dc_tried[dc] = ws * 6 * 1000.0 / max_over_ranks(d0.elapsed_time(d1))
+            pp.close()
+            cx.close()
+            del pp, cx
+            torch.cuda.empty_cache()
+        args.dc_vcycles = max(dc_tried, key=dc_tried.get)
+
+    ctx, pipe = new_pipeline(prec)
 
     def step(pp=None):
         pp = pp or pipe
@@ -596,6 +625,8 @@ def run_ours(args):
             "pipelined_steps": pipelined,
             "lanes": lanes,
             "lanes_tried": lanes_tried,
+            "dc_vcycles": args.dc_vcycles,
+            "dc_vcycles_tried": dc_tried,
             "step_by_step": step_by_step,
             "small_level_vcycle": {0: "one graph kernel node per smoothing, restriction and prolongation", 1: "one cooperative kernel", 2: "one thread-block cluster per set", 3: "the level n = 32 and those under it in the distributed shared memory of one thread-block cluster per set"}[args.persistent_vcycle],
             "one_chain": {"value": ws * 1000.0 / one_chain_ms, "unit": UNIT, "ms_per_step": one_chain_ms},
@@ -1174,6 +1205,9 @@ def main():
     ap.add_argument("--lanes", type=int, default=0,
                     help="two-disk and large: pipelines (two contexts each) running independent steps "
                          "concurrently; 0: 1 or 2, whichever times faster")
+    ap.add_argument("--dc-vcycles", type=int, default=0,
+                    help="two-disk and large: V-cycles per defect-correction step (params.dc_vcycles); 0: 2 or 4, "
+                         "whichever times faster")
     ap.add_argument("--small-cluster", type=int, choices=[0, 4, 8, 16], default=0,
                     help="CTAs per cluster of --persistent-vcycle 3 (0: 8)")
     ap.add_argument("--profile-case", action="store_true",

@@ -158,6 +158,16 @@ typedef struct {
                            e.g. by the fit sweep's autotuner). */
     int small_cluster;  /* CTAs per cluster of persistent_vcycle = 3: 4, 8 or
                            16 (16 is a non-portable cluster size), 0 = 8. */
+    int dc_vcycles;     /* tolerance mode: V-cycles on the correction
+                           equation per defect-correction step, 1 <= dc_vcycles
+                           <= 8 (default 2).  Each step then solves L e = r
+                           more closely before u += e and the next residual,
+                           so fewer residual checks (each a full pass over u
+                           and the right-hand side) are needed.  max_vcycles
+                           and the reported vcycles count V-cycles; the
+                           residual is checked after every dc_vcycles of
+                           them (so the cap is max_vcycles rounded up to a
+                           multiple of dc_vcycles). */
 } qumond_params;
 
 /* Per-solve report (host struct). */
@@ -174,7 +184,7 @@ typedef struct qumond_ctx qumond_ctx;
    npre = npost = 2, ncycle = 6, rel_tol = 0 (paper mode), max_vcycles = 50,
    QUMOND_PREC_MIXED, QUMOND_BC_ZERO, warm_start = 0, deposit_shift = 24,
    rc_box_frac = 0.2, box_ratio = 2, use_graphs = 1, persistent_vcycle = 3,
-   nsets = 1, tile_small = 0, small_cluster = 0. */
+   nsets = 1, tile_small = 0, small_cluster = 0, dc_vcycles = 2. */
 QUMOND_API void qumond_default_params(qumond_params* p);
 
 /* Validates p and allocates the context's device scratch on the current

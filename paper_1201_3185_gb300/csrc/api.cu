@@ -205,6 +205,7 @@ qumond_status check_params(qumond_ctx* c, const qumond_params* p)
         return fail(c, QUMOND_ERR_INVALID_ARG, "persistent_vcycle must be 0, 1, 2 or 3");
     if (p->small_cluster != 0 && p->small_cluster != 4 && p->small_cluster != 8 && p->small_cluster != 16)
         return fail(c, QUMOND_ERR_INVALID_ARG, "small_cluster must be 0, 4, 8 or 16");
+    if (p->dc_vcycles < 1 || p->dc_vcycles > 8) return fail(c, QUMOND_ERR_INVALID_ARG, "dc_vcycles must be in [1, 8]");
     if (p->nboxes > 1 && p->n < 2 * p->box_ratio)
         return fail(c, QUMOND_ERR_INVALID_ARG, "n=%d too small for nested boxes of ratio %d", p->n, p->box_ratio);
     if (p->nsets < 1 || p->nsets > 1024 || (long long)p->nsets * (p->n + 1) > 65535)
@@ -462,6 +463,9 @@ cudaError_t fmg(qumond_ctx* c, int box, const double* u64, cudaStream_t s)
 // to continue (device-side; drives the graph's WHILE node when capturing).
 inline bool fixed_mode(const qumond_ctx* c) { return c->p.precision == QUMOND_PREC_MIXED_FIXED; }
 
+// defect-correction steps allowed by max_vcycles (dc_vcycles V-cycles each, the last one may go past it)
+inline int dc_steps(const qumond_params& p) { return (p.max_vcycles + p.dc_vcycles - 1) / p.dc_vcycles; }
+
 template <typename T>
 void check(qumond_ctx* c, int box, const double* rhs, double coef, const double* u, bool first,
            const cudaGraphConditionalHandle* handle, cudaStream_t s)
@@ -482,7 +486,7 @@ void check(qumond_ctx* c, int box, const double* rhs, double coef, const double*
         });
     }
     run(c, K_REDUCE, 16.0 * nb, s, [&] {
-        launch_decide(c->partials, nb, c->d_state, p.rel_tol, p.max_vcycles, first, p.rel_tol > 0.0 && p.max_vcycles > 0,
+        launch_decide(c->partials, nb, c->d_state, p.rel_tol, dc_steps(p), first, p.rel_tol > 0.0 && p.max_vcycles > 0,
                       handle, c->fault, s, sets_of(c));
     });
 }
@@ -548,8 +552,10 @@ cudaError_t enqueue_body(qumond_ctx* c, int box, const double* rhs, double coef,
         explicit BodyFlag(qumond_ctx* cc) : c(cc) { c->in_body = true; }
         ~BodyFlag() { c->in_body = false; }
     } body_flag(c);
-    cudaError_t err = vcycle<T>(c, box, c->L, true, s);
-    if (err != cudaSuccess) return err;
+    for (int q = 0; q < c->p.dc_vcycles; ++q) {  // the first from e = 0, the others continue it
+        cudaError_t err = vcycle<T>(c, box, c->L, q == 0, s);
+        if (err != cudaSuccess) return err;
+    }
     if (fixed_mode(c)) {
         // update and residual in one pass (U' into the other buffer), then the decision
         int nb = 0;
@@ -566,7 +572,7 @@ cudaError_t enqueue_body(qumond_ctx* c, int box, const double* rhs, double coef,
         });
         const qumond_params& p = c->p;
         run(c, K_REDUCE, 16.0 * nb, s, [&] {
-            launch_decide(c->partials, nb, c->d_state, p.rel_tol, p.max_vcycles, false,
+            launch_decide(c->partials, nb, c->d_state, p.rel_tol, dc_steps(p), false,
                           p.rel_tol > 0.0 && p.max_vcycles > 0, handle, c->fault, s, sets_of(c));
         });
         return cudaGetLastError();
@@ -765,7 +771,7 @@ qumond_status solve_t(qumond_ctx* c, int kind, int box, const double* rhs, doubl
     if (st)
         for (int q = 0; q < ns; ++q) {
             const SolveState& r = c->h_state[q];
-            st[q].vcycles = r.it;
+            st[q].vcycles = r.it * p.dc_vcycles;
             st[q].converged = r.converged;
             st[q].rel_residual_fmg = r.rel0;
             st[q].rel_residual = r.rel;
@@ -775,10 +781,10 @@ qumond_status solve_t(qumond_ctx* c, int kind, int box, const double* rhs, doubl
         if (!r.converged) {
             if (ns == 1)
                 return fail(c, QUMOND_ERR_NOT_CONVERGED, "box %d: relative residual %.3e after %d V-cycles (tol %.3e)",
-                            box, r.rel, r.it, p.rel_tol);
+                            box, r.rel, r.it * p.dc_vcycles, p.rel_tol);
             return fail(c, QUMOND_ERR_NOT_CONVERGED,
-                        "set %d, box %d: relative residual %.3e after %d V-cycles (tol %.3e)", q, box, r.rel, r.it,
-                        p.rel_tol);
+                        "set %d, box %d: relative residual %.3e after %d V-cycles (tol %.3e)", q, box, r.rel,
+                        r.it * p.dc_vcycles, p.rel_tol);
         }
     }
     return QUMOND_OK;
@@ -854,6 +860,7 @@ void qumond_default_params(qumond_params* p)
     p->nsets = 1;
     p->tile_small = 0;
     p->small_cluster = 0;
+    p->dc_vcycles = 2;
 }
 
 qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)

@@ -193,6 +193,8 @@ extern "C" qumond_status qumond_solve_mond_noalloc(const qumond_params* p, int b
         return set_err(err, err_len, QUMOND_ERR_INVALID_ARG, "npre, npost in [1,16] and ncycle in [1,128] required");
     if (!(p->rel_tol >= 0.0) || p->max_vcycles < 0 || p->max_vcycles > 10000)
         return set_err(err, err_len, QUMOND_ERR_INVALID_ARG, "rel_tol >= 0 and max_vcycles in [0,10000] required");
+    if (p->dc_vcycles < 1 || p->dc_vcycles > 8)
+        return set_err(err, err_len, QUMOND_ERR_INVALID_ARG, "dc_vcycles must be in [1, 8]");
     if (p->bc_mode != QUMOND_BC_ZERO && p->bc_mode != QUMOND_BC_GIVEN)
         return set_err(err, err_len, QUMOND_ERR_INVALID_ARG, "unknown bc_mode");
     if (p->warm_start != 0 && p->warm_start != 1)
@@ -268,10 +270,10 @@ extern "C" qumond_status qumond_solve_mond_noalloc(const qumond_params* p, int b
     const double rel0 = rel;
     int made = 0;
     while (ce == cudaSuccess && refine && rel > p->rel_tol && made < p->max_vcycles && std::isfinite(rel)) {
-        ce = S.vcycle(S.L, true);
+        for (int q = 0; q < p->dc_vcycles && ce == cudaSuccess; ++q) ce = S.vcycle(S.L, q == 0);
         if (ce != cudaSuccess) break;
         launch_assign_outer<float>(phi, n, S.lev[S.L].e, S.lev[S.L].v, true, S.s);
-        ++made;
+        made += p->dc_vcycles;
         ce = S.norms_of(phi, src, &rr, &ff);
         rel = std::sqrt(rr) / denom;
     }

@@ -72,6 +72,7 @@ class qumond_params(ctypes.Structure):
         ("nsets", ctypes.c_int),
         ("tile_small", ctypes.c_int),
         ("small_cluster", ctypes.c_int),
+        ("dc_vcycles", ctypes.c_int),
     ]
 
 

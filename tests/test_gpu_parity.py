@@ -111,7 +111,7 @@ def test_fp64_extra_vcycles_match_oracle(q, ora, n):
     f = rng.standard_normal((n + 1) ** 3)
     bc = rng.standard_normal((n + 1) ** 3)
     got, _, err = solve_given(q, n, 10.0, f, bc, precision=q.QUMOND_PREC_FP64, ncycle=1, rel_tol=1e-300,
-                              max_vcycles=3)
+                              max_vcycles=3, dc_vcycles=1)
     assert err is not None and err.status == 3  # NOT_CONVERGED, best iterate kept
     want = np.where(an.boundary_mask(n), bc, 0.0)
     made, _ = ora.solve(n, 10.0 / n, want, f, ncycle=1, tol=1e-300, max_vcycles=3)
@@ -145,6 +145,38 @@ def test_tolerance_mode_matches_oracle(q, ora, n, prec):
     inner = ~an.boundary_mask(n)
     floor = 96.0 * 2.0 ** -53 * np.sqrt(np.sum((got[inner] / h2) ** 2) / ora.interior_sumsq(n, f))
     assert abs(rel - st.rel_residual) <= 1e-2 * st.rel_residual + floor + 1e-14
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_vcycles_per_correction_step(q, ora, prec):
+    # several V-cycles on the correction equation per defect-correction step
+    # (dc_vcycles): the same tolerance is met with the same accuracy against
+    # the oracle, the reported V-cycles are whole steps, and in FP64 (where a
+    # V-cycle on the correction from zero is a V-cycle on u) the iterates are
+    # those of as many plain V-cycles
+    n = 64
+    x, y, z = an.node_coords(n, 4000.0)
+    f = np.exp(-(x * x + y * y + 4 * z * z) / 2e5) * 0.05
+    bc = -1000.0 / np.sqrt(x * x + y * y + z * z + 1e6)
+    want = np.where(an.boundary_mask(n), bc, 0.0)
+    ora.solve(n, 4000.0 / n, want, f, tol=1e-12, max_vcycles=60)
+    counts = {}
+    for dc in (1, 2, 3, 4):
+        got, st, _ = solve_given(q, n, 4000.0, f, bc, precision=prec, rel_tol=1e-10, max_vcycles=40, dc_vcycles=dc)
+        assert st.converged and st.rel_residual <= 1e-10
+        assert st.vcycles % dc == 0
+        assert rel_max(got, want) < (1e-9 if prec == 0 else 1e-6)
+        counts[dc] = st.vcycles
+    # a step of dc V-cycles reduces the residual at least as much as dc steps of one
+    assert all(counts[dc] <= counts[1] + dc - 1 for dc in counts)
+    if prec == 0:
+        rng = np.random.default_rng(8)
+        fr = rng.standard_normal((n + 1) ** 3)
+        br = rng.standard_normal((n + 1) ** 3)
+        a, _, ea = solve_given(q, n, 10.0, fr, br, precision=0, ncycle=1, rel_tol=1e-300, max_vcycles=4, dc_vcycles=2)
+        b, _, eb = solve_given(q, n, 10.0, fr, br, precision=0, ncycle=1, rel_tol=1e-300, max_vcycles=4, dc_vcycles=1)
+        assert ea is not None and eb is not None  # the cap is reached: NOT_CONVERGED, best iterate kept
+        assert rel_max(a, b) < 1e-11
 
 
 def test_coarsest_grid_special_case(q):

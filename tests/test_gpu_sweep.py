@@ -150,6 +150,8 @@ def test_context_sets_invalid(q):
         q.Context(n=64, nboxes=1, L0=1.0, persistent_vcycle=3, small_cluster=2)
     with pytest.raises(q.QumondError):
         q.Context(n=64, nboxes=1, L0=1.0, persistent_vcycle=4)
+    with pytest.raises(q.QumondError):
+        q.Context(n=64, nboxes=1, L0=1.0, dc_vcycles=0)
     ctx = q.Context(n=8, nboxes=1, L0=100.0, nsets=2)
     a = torch.zeros(3 * 9 ** 3, dtype=torch.float64, device="cuda")
     with pytest.raises(ValueError):  # particles not a multiple of the set count
