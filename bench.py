@@ -665,11 +665,11 @@ def run_sweep(args):
     w = WORKLOAD
     prec = {"fp64": q.QUMOND_PREC_FP64, "mixed": q.QUMOND_PREC_MIXED, "fixed": q.QUMOND_PREC_MIXED_FIXED}[args.precision]
 
-    def params(precision, tile=0, form=3):
+    def params(precision, tile=0, form=3, dc=2):
         return q.default_params(n=w["n"], nboxes=w["nboxes"], L0=w["L0"], rel_tol=w["rel_tol"],
                                 max_vcycles=w["max_vcycles"], ncycle=w["ncycle"], npre=w["npre"], npost=w["npost"],
                                 precision=precision, use_graphs=0 if args.no_graphs else 1, tile_small=tile,
-                                persistent_vcycle=form)
+                                persistent_vcycle=form, dc_vcycles=dc)
 
     gal, prm, v_obs_h, sigma_h = sweep_inputs()
     host_sets = [gal.particles(r) for r in prm]
@@ -682,11 +682,11 @@ def run_sweep(args):
 
     if args.workers:
         choice, tune = {"batch": w["sets"], "lanes": args.workers, "tile_small": 0,
-                        "persistent_vcycle": args.persistent_vcycle}, None
+                        "persistent_vcycle": args.persistent_vcycle, "dc_vcycles": max(1, args.dc_vcycles)}, None
     else:
         choice, tune = q.autotune(params(prec), sets, dist, v_obs, sigma, **kw)
-    sw = q.FitSweep(params(prec, choice["tile_small"], choice["persistent_vcycle"]), batch=choice["batch"],
-                    lanes=choice["lanes"], **kw)
+    sw = q.FitSweep(params(prec, choice["tile_small"], choice["persistent_vcycle"], choice["dc_vcycles"]),
+                    batch=choice["batch"], lanes=choice["lanes"], **kw)
     ctx = Contexts(sw.ctxs)
     for _ in range(args.warmup):
         sw.run(sets, dist, v_obs, sigma)
@@ -716,8 +716,8 @@ def run_sweep(args):
 
     # kernel classes timed live inside the batched graphs (the tuned batch, one lane): event-record nodes
     # around each run of consecutive launches of the class in the FMG part of every solve
-    one = q.FitSweep(params(prec, choice["tile_small"], choice["persistent_vcycle"]), batch=choice["batch"], lanes=1,
-                     **kw)
+    one = q.FitSweep(params(prec, choice["tile_small"], choice["persistent_vcycle"], choice["dc_vcycles"]),
+                     batch=choice["batch"], lanes=1, **kw)
     c1 = Contexts(one.ctxs)
     nsub = choice["batch"]
     sub = tuple(a[:nsub * (a.numel() // w["sets"])] for a in sets)
@@ -772,7 +772,7 @@ def run_sweep(args):
     sw.close()
 
     def timed_sweep(precision, nsteps, **form):
-        one = q.FitSweep(params(precision, form.pop("tile", 0)), **form, **kw)
+        one = q.FitSweep(params(precision, form.pop("tile", 0), 3, form.pop("dc", 2)), **form, **kw)
         one.run(sets, dist, v_obs, sigma)
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
@@ -792,13 +792,13 @@ def run_sweep(args):
         nrep = max(1, min(args.steps, 3))
         # plain FP64 FMG: the same batched kernels and form, FP64 throughout, to the same tolerance
         plain = timed_sweep(q.QUMOND_PREC_FP64, nrep, batch=choice["batch"], lanes=choice["lanes"],
-                            tile=choice["tile_small"])
+                            tile=choice["tile_small"], dc=choice["dc_vcycles"])
         plain["precision"] = PRECISION_NAMES["fp64"] + " (same batched kernels, same tolerance)"
         plain["speedup_of_value"] = value / plain["value"]
         # one set per context, 8 contexts side by side (the sweep without batching)
-        unbatched = timed_sweep(prec, nrep, workers=8)
+        unbatched = timed_sweep(prec, nrep, workers=8, dc=choice["dc_vcycles"])
         unbatched["form"] = "one set per context, 8 contexts on 8 streams"
-        seq_same = timed_sweep(prec, 1, workers=1)
+        seq_same = timed_sweep(prec, 1, workers=1, dc=choice["dc_vcycles"])
         seq_same["form"] = "one set after another"
 
     cpu = None
@@ -824,7 +824,7 @@ def run_sweep(args):
             "e2e": {"value": e2e_value, "unit": "sets/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "gpu_launches_per_step": launches / args.steps,
-            "autotune_ms_per_sweep": {"batch %d, lanes %d, tile %d, small-level form %d" % k: v
+            "autotune_ms_per_sweep": {"batch %d, lanes %d, tile %d, small-level form %d, dc %d" % k: v
                                       for k, v in tune.items()} if tune else None,
             "vcycles_after_fmg_per_set_max": max(max(v) for v in vcyc),
             "best_set": {"index": best, "chi2": float(chi2[best]), "params": [float(v) for v in prm[best]]},

@@ -18,8 +18,9 @@ radii scaled by that set's distance factor (the observed radii are fixed
 angles) and one kernel computes every set's chi^2 at the end.
 
 `autotune` picks the batch size, the number of lanes and the block shape of
-the small-level kernels (params.tile_small) and the form of the small-level
-V-cycle (params.persistent_vcycle) by timing the sweep itself.
+the small-level kernels (params.tile_small), the form of the small-level
+V-cycle (params.persistent_vcycle) and the V-cycles per defect-correction
+step (params.dc_vcycles) by timing the sweep itself.
 """
 from __future__ import annotations
 
@@ -163,25 +164,31 @@ def _copy(p: qumond_params) -> qumond_params:
 
 
 def autotune(params: qumond_params, particles, distance, v_obs, sigma, *, nbins: int, rmax: float, nphi: int = 64,
-             batches=(8, 16, 32, 64), lanes=(1, 2, 4), tiles=(0, 1, 2), forms=(3, 0), repeats: int = 2, device=None):
+             batches=(8, 16, 32, 64), lanes=(1, 2, 4), tiles=(0, 1, 2), forms=(3, 0), dcs=(2, 3, 4), repeats: int = 2,
+             device=None):
     """Picks the batch size, the number of lanes, the small-level block shape
-    (params.tile_small) and the form of the small-level V-cycle
+    (params.tile_small), the form of the small-level V-cycle
     (params.persistent_vcycle: 3, one cluster per set holding the level n = 32
-    in shared memory, or 0, one launch per step) by timing: each candidate
-    runs the given sweep once untimed (graph capture) and `repeats` times
-    timed with CUDA events.  Batch and lanes are searched with params' own
-    form and tile 0, the block shape at the best (batch, lanes), the form at
-    the best of those.  Results do not depend on the choice (each set's
-    arithmetic is the same), only the time does.  Returns ({"batch", "lanes",
-    "tile_small", "persistent_vcycle"}, {(batch, lanes, tile, form): ms})."""
+    in shared memory, or 0, one launch per step) and the V-cycles per
+    defect-correction step (params.dc_vcycles) by timing: each candidate runs
+    the given sweep once untimed (graph capture) and `repeats` times timed
+    with CUDA events.  Batch and lanes are searched with params' own form and
+    dc_vcycles and tile 0, the block shape at the best (batch, lanes), the
+    form at the best of those, dc_vcycles last.  Batch, lanes, block shape and
+    form do not change any set's results (each set's arithmetic is the same);
+    dc_vcycles changes how many V-cycles a set makes before its residual meets
+    the same tolerance.  Returns ({"batch", "lanes", "tile_small",
+    "persistent_vcycle", "dc_vcycles"}, {(batch, lanes, tile, form, dc): ms})."""
     nsets = len(distance)
     times = {}
     form0 = params.persistent_vcycle
+    dc0 = params.dc_vcycles
 
-    def time_one(b, k, tile, form):
+    def time_one(b, k, tile, form, dc):
         p = _copy(params)
         p.tile_small = tile
         p.persistent_vcycle = form
+        p.dc_vcycles = dc
         with FitSweep(p, nbins=nbins, rmax=rmax, nphi=nphi, batch=b, lanes=k, device=device) as sw:
             sw.run(particles, distance, v_obs, sigma)
             t0 = torch.cuda.Event(enable_timing=True)
@@ -198,17 +205,22 @@ def autotune(params: qumond_params, particles, distance, v_obs, sigma, *, nbins:
     for b, k in itertools.product(batches, lanes):
         if b > max(1, nsets) or (k > 1 and b * k > max(1, nsets) + b - 1):
             continue  # more lanes than chunks
-        times[(b, k, 0, form0)] = time_one(b, k, 0, form0)
-    b0, k0, _, _ = min(times, key=times.get)
+        times[(b, k, 0, form0, dc0)] = time_one(b, k, 0, form0, dc0)
+    b0, k0, _, _, _ = min(times, key=times.get)
     for tile in tiles:
-        if (b0, k0, tile, form0) not in times:
-            times[(b0, k0, tile, form0)] = time_one(b0, k0, tile, form0)
-    _, _, t0, _ = min(times, key=times.get)
+        if (b0, k0, tile, form0, dc0) not in times:
+            times[(b0, k0, tile, form0, dc0)] = time_one(b0, k0, tile, form0, dc0)
+    _, _, t0, _, _ = min(times, key=times.get)
     for form in forms:
-        if (b0, k0, t0, form) not in times:
-            times[(b0, k0, t0, form)] = time_one(b0, k0, t0, form)
+        if (b0, k0, t0, form, dc0) not in times:
+            times[(b0, k0, t0, form, dc0)] = time_one(b0, k0, t0, form, dc0)
+    _, _, _, f0, _ = min(times, key=times.get)
+    for dc in dcs:
+        if (b0, k0, t0, f0, dc) not in times:
+            times[(b0, k0, t0, f0, dc)] = time_one(b0, k0, t0, f0, dc)
     best = min(times, key=times.get)
-    return {"batch": best[0], "lanes": best[1], "tile_small": best[2], "persistent_vcycle": best[3]}, times
+    return {"batch": best[0], "lanes": best[1], "tile_small": best[2], "persistent_vcycle": best[3],
+            "dc_vcycles": best[4]}, times
 
 
 def tune_workers(params: qumond_params, particles, distance, v_obs, sigma, *, nbins: int, rmax: float, nphi: int = 64,
