@@ -95,7 +95,7 @@ struct SolveGraph {
     std::vector<int> event_kinds;     // launches in each run
     std::vector<double> event_bytes;  // algorithmic bytes of each run
 };
-constexpr size_t kMaxGraphs = 32;
+constexpr size_t kMaxGraphs = 64;
 
 }  // namespace
 
