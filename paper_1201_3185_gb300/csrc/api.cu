@@ -416,8 +416,12 @@ cudaError_t vcycle(qumond_ctx* c, int box, int l, bool zero_guess, cudaStream_t 
     }
     const double nodes = cube(c->lev[l].v.n);
     run(c, K_RESTRICT_RESID, (1.5 + 0.125) * nodes * sizeof(T), s, [&] {
-        launch_restrict_resid_red<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, F<T>(c, l - 1), c->lev[l - 1].v, h, s,
-                                     sets_of(c));
+        if (sizeof(T) == sizeof(float) && c->lev[l].maps.ok)
+            launch_restrict_tma(reinterpret_cast<float*>(F<T>(c, l - 1)), c->lev[l].v, c->lev[l - 1].v, c->lev[l].maps,
+                                h, c->fault, s, sets_of(c));
+        else
+            launch_restrict_resid_red<T>(E<T>(c, l), F<T>(c, l), c->lev[l].v, F<T>(c, l - 1), c->lev[l - 1].v, h, s,
+                                         sets_of(c));
     });
     cudaError_t err = vcycle<T>(c, box, l - 1, true, s);
     if (err != cudaSuccess) return err;

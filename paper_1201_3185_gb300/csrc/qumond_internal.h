@@ -139,12 +139,17 @@ void launch_decide(const double* partials, int nblocks, SolveState* st, double t
 struct RbMaps {
     CUtensorMap map[2];   // colour c of the iterate as a 3-D tensor (m, j, k), tile + halo boxes
     CUtensorMap fmap[2];  // colour c of the right-hand side, tile boxes
+    CUtensorMap rmap_black, rmap_red, rmap_f;  // the restriction's boxes (black with halo, red, red f)
     bool ok = false;
 };
 // 4-D maps (m, j, k, set) over the nsets sets of a level
 bool make_rb_maps(float* e, float* f, const LevelView& v, RbMaps* out, int nsets = 1);
 void launch_rb_half_tma(float* e, const float* f, const LevelView& v, int colour, const RbMaps& maps, double h,
                         int* fault, cudaStream_t s, const Sets& sets = Sets());
+// Full weighting of the red residuals of the fine level whose maps are given (right after a black half-sweep)
+// into the coarse right-hand side fc, the fine planes staged by the TMA unit.
+void launch_restrict_tma(float* fc, const LevelView& vf, const LevelView& vc, const RbMaps& maps, double hf,
+                         int* fault, cudaStream_t s, const Sets& sets = Sets());
 // Sets kernel attributes (shared memory of the coarse-grid kernel); call
 // before any stream capture.
 cudaError_t prepare_kernels();

@@ -226,6 +226,178 @@ rb_tma_kernel(const __grid_constant__ CUtensorMap other_map, const __grid_consta
     drain_after_abort(leader, &abort_flag, bar, kb - 1, landed, issued);
 }
 
+// ---------------------------------------------------------------------------
+// Restriction of the red residuals (after a black half-sweep the black
+// residuals vanish) onto the coarse level, with the fine planes staged by the
+// TMA unit.  A CTA owns a tile of 32 x 8 coarse (I, J) columns and up to 8
+// coarse planes K0 .. K1-1, and walks the fine planes 2K0-2 .. 2K1: for each,
+// three boxes land in a five-slot ring completed by one mbarrier -- the black
+// entries mbase-4 .. mbase+39 of the fine rows 2J0-2 .. 2J0+16 (mbase = I0-1,
+// a multiple of 32), and the red entries and f of the red rows 2J0-1 ..
+// 2J0+15, entries mbase .. mbase+35.  The red residuals of fine plane k are
+// computed from the black planes k-1, k, k+1 of the ring (four consecutive
+// entries per thread, red_residual's arithmetic in its order) into a
+// three-plane residual ring; after each odd plane 2K+1 the coarse plane K is
+// full-weighted from it with restrict_node's sums in their order.  Each fine
+// value crosses HBM once and the loads of three planes are in flight while
+// one is processed.  Boxes outside the level read zeros; they only feed
+// residuals that no coarse interior node uses.  Waits are bounded as in the
+// half-sweep.
+constexpr int kRTI = 32, kRTJ = 8, kRTK = 8;  // coarse tile, the most coarse planes per CTA
+constexpr int kRBX = 44, kRBY = 2 * kRTJ + 3;  // black box: 44 entries x 19 rows
+constexpr int kRRX = 36, kRRY = 2 * kRTJ + 1;  // red and f boxes: 36 entries x 17 rows
+constexpr int kRG = kRRX / 4;                  // groups of four red entries per fine row
+constexpr int kRBlackFloats = ((kRBX * kRBY * 4 + 127) / 128) * 128 / 4;
+constexpr int kRRedFloats = ((kRRX * kRRY * 4 + 127) / 128) * 128 / 4;
+constexpr int kRSlotFloats = kRBlackFloats + 2 * kRRedFloats;
+constexpr int kRSlots = 5;
+constexpr unsigned kRPlaneBytes = (kRBX * kRBY + 2 * kRRX * kRRY) * 4;
+constexpr size_t kRSmemBytes = sizeof(float) * ((size_t)kRSlots * kRSlotFloats + 3 * kRRY * kRRX);
+static_assert(kRRY * kRG <= kRTI * kRTJ, "one thread per residual group");
+static_assert((kRBX * 4) % 16 == 0 && (kRRX * 4) % 16 == 0, "box rows are whole 16-byte units");
+
+__device__ __forceinline__ void restrict_drain(bool leader, int* abort_flag, unsigned long long* bar, int first,
+                                               int landed, int issued)
+{
+    __syncthreads();
+    if (!leader || !*(volatile int*)abort_flag) return;
+    for (int q = landed; q < issued; ++q) {
+        const int u = q - first;
+        long long spins = 0;
+        while (!mbar_try_wait(&bar[u % kRSlots], (unsigned)((u / kRSlots) & 1)) && ++spins <= kSpinLimit) {
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kRTI * kRTJ)
+restrict_tma_kernel(const __grid_constant__ CUtensorMap black_map, const __grid_constant__ CUtensorMap red_map,
+                    const __grid_constant__ CUtensorMap f_map, float* __restrict__ fc, LevelView vf, LevelView vc,
+                    float ih2, int* __restrict__ fault, int zper, const SolveState* __restrict__ act)
+{
+    extern __shared__ __align__(128) float rsm[];
+    float(*ring)[kRRY][kRRX] = reinterpret_cast<float(*)[kRRY][kRRX]>(rsm + kRSlots * kRSlotFloats);
+    __shared__ __align__(8) unsigned long long bar[kRSlots];
+    __shared__ int abort_flag;
+    const int set = (int)gridDim.z == zper ? 0 : (int)blockIdx.z / zper;
+    if (act && !act[set].cont) return;  // this set's correction has stopped (whole CTA, before any barrier)
+    fc += (long long)set * 2 * vc.cs;
+    const int n = vf.n, nc = vc.n;
+    const int I0 = 1 + blockIdx.x * kRTI, J0 = 1 + blockIdx.y * kRTJ;
+    const int K0 = 1 + ((int)blockIdx.z - set * zper) * kRTK;
+    const int K1 = min(K0 + kRTK, nc);  // coarse planes K0 .. K1-1
+    const int mbase = I0 - 1;           // a multiple of 32
+    const int jb = 2 * J0 - 2;          // first black row of the box; the red rows start at jb + 1
+    const int first = 2 * K0 - 2, last = 2 * K1;  // fine planes staged
+    const int t = threadIdx.x;
+    const bool leader = t == 0;
+    if (leader) {
+        abort_flag = 0;
+        for (int q = 0; q < kRSlots; ++q) mbar_init(&bar[q], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int issued = first, landed = first;
+    auto slot_of = [&](int q) { return rsm + ((q - first) % kRSlots) * kRSlotFloats; };
+    auto issue = [&](int q) {  // plane q into its slot (leader only); nothing more once a wait gave up
+        if (*(volatile int*)&abort_flag) return;
+        const int u = q - first;
+        float* base = rsm + (u % kRSlots) * kRSlotFloats;
+        if (((smem_u32(base) | smem_u32(base + kRBlackFloats) | smem_u32(base + kRBlackFloats + kRRedFloats)) &
+             127u) != 0u) {  // never issue a copy the TMA unit would reject
+            atomicExch(fault, 2);
+            atomicExch(&abort_flag, 1);
+            return;
+        }
+        unsigned long long* b = &bar[u % kRSlots];
+        mbar_expect_tx(b, kRPlaneBytes);
+        tma_load_4d(base, &black_map, mbase - 4, jb, q, set, b);  // x: a multiple of 4 floats
+        tma_load_4d(base + kRBlackFloats, &red_map, mbase, jb + 1, q, set, b);
+        tma_load_4d(base + kRBlackFloats + kRRedFloats, &f_map, mbase, jb + 1, q, set, b);
+        issued = q + 1;
+    };
+    if (leader)
+        for (int q = first; q < first + kRSlots && q <= last; ++q) issue(q);
+    bool ok = true;
+    const bool lane0 = (t & 31) == 0;
+    auto wait = [&](int q) {
+        if (lane0) {
+            const int u = q - first;
+            long long spins = 0;
+            while (ok && !mbar_try_wait(&bar[u % kRSlots], (unsigned)((u / kRSlots) & 1))) {
+                if (++spins > kSpinLimit || *(volatile int*)&abort_flag) {
+                    ok = false;
+                    atomicExch(fault, 1);
+                    *(volatile int*)&abort_flag = 1;  // the leader stops issuing copies
+                }
+            }
+            if (ok) landed = q + 1;
+        }
+        __syncwarp();
+    };
+    // residual phase: red row rr (fine row jb + 1 + rr), group rg (entries mbase + 4 rg .. + 3)
+    const int rr = t / kRG, rg = t % kRG;
+    const int jf = jb + 1 + rr;
+    const bool ract = t < kRRY * kRG && jf >= 1 && jf <= n - 1 && mbase + 4 * rg < vf.M;
+    const int cb = (rr + 1) * kRBX + 4 + 4 * rg;  // black box index of entry mbase + 4 rg in the same row
+    const int cr = rr * kRRX + 4 * rg;            // red / f box index
+    // coarse phase: node (I, J)
+    const int cI = t % kRTI, cJ = t / kRTI;
+    const int I = I0 + cI, J = J0 + cJ;
+    const bool cact = I <= nc - 1 && J <= nc - 1;
+    for (int k = first + 1; k <= last - 1; ++k) {
+        if (k == first + 1) {
+            wait(first);
+            wait(first + 1);
+        }
+        wait(k + 1);
+        if (ract) {
+            const float* bm = slot_of(k - 1);
+            const float* b0 = slot_of(k);
+            const float* bp = slot_of(k + 1);
+            const float* red = b0 + kRBlackFloats;
+            const float* fr = red + kRRedFloats;
+            const int p = (jf + k) & 1;
+            const float4 V = *reinterpret_cast<const float4*>(b0 + cb);
+            const float x[6] = {b0[cb - 1], V.x, V.y, V.z, V.w, b0[cb + 4]};
+            const float4 Y0 = *reinterpret_cast<const float4*>(b0 + cb - kRBX);
+            const float4 Y1 = *reinterpret_cast<const float4*>(b0 + cb + kRBX);
+            const float4 Z0 = *reinterpret_cast<const float4*>(bm + cb);
+            const float4 Z1 = *reinterpret_cast<const float4*>(bp + cb);
+            const float4 E = *reinterpret_cast<const float4*>(red + cr);
+            const float4 F = *reinterpret_cast<const float4*>(fr + cr);
+            const float y0[4] = {Y0.x, Y0.y, Y0.z, Y0.w}, y1[4] = {Y1.x, Y1.y, Y1.z, Y1.w};
+            const float z0[4] = {Z0.x, Z0.y, Z0.z, Z0.w}, z1[4] = {Z1.x, Z1.y, Z1.z, Z1.w};
+            const float ev[4] = {E.x, E.y, E.z, E.w}, fv[4] = {F.x, F.y, F.z, F.w};
+            float r[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float lo = p ? x[e + 1] : x[e];
+                const float hi = p ? x[e + 2] : x[e + 1];
+                const float sum = (lo + hi) + (y0[e] + y1[e]) + (z0[e] + z1[e]);
+                r[e] = fv[e] - (sum - 6.0f * ev[e]) * ih2;
+            }
+            *reinterpret_cast<float4*>(&ring[k % 3][rr][4 * rg]) = make_float4(r[0], r[1], r[2], r[3]);
+        }
+        __syncthreads();
+        if ((k & 1) && k >= 2 * K0 + 1 && cact && ok) {
+            const int K = (k - 1) >> 1;
+            const float(*pm)[kRRX] = ring[(k + 1) % 3];  // fine plane 2K-1
+            const float(*p0)[kRRX] = ring[(k + 2) % 3];  // 2K
+            const float(*pp)[kRRX] = ring[k % 3];        // 2K+1
+            // fine node (i, j) = (2I, 2J): row 2cJ+1 of the tile; entries I-1 (i-1) and I (i, i+1)
+            const int a = 2 * cJ + 1, lo = cI, hi = cI + 1;
+            float edge = (p0[a + 1][hi] + p0[a + 1][lo]) + (p0[a - 1][hi] + p0[a - 1][lo]);
+            edge += (pp[a][hi] + pp[a][lo]) + (pm[a][hi] + pm[a][lo]);
+            edge += (pp[a + 1][hi] + pp[a - 1][hi]) + (pm[a + 1][hi] + pm[a - 1][hi]);
+            const float centre = p0[a][hi];
+            fc[node_off(vc, I, J, K)] = 0.125f * centre + 0.03125f * edge;
+        }
+        __syncthreads();  // the slot of plane k-1 is free
+        if (leader && k + kRSlots - 1 <= last) issue(k + kRSlots - 1);
+    }
+    restrict_drain(leader, &abort_flag, bar, first, landed, issued);
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -261,6 +433,21 @@ bool make_rb_maps(float* e, float* f, const LevelView& v, RbMaps* out, int nsets
     const cuuint32_t box[4] = {kBoxX, kBoxY, 1, 1};
     const cuuint32_t fbox[4] = {kTM, kTJ, 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const cuuint32_t bbox[4] = {kRBX, kRBY, 1, 1};
+    const cuuint32_t rbox[4] = {kRRX, kRRY, 1, 1};
+    auto enc1 = [&](CUtensorMap* m, float* base, const cuuint32_t* bx) {
+        return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, bx, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    // the restriction's boxes: black iterate with halo, red iterate, red right-hand side
+    if (!enc1(&out->rmap_black, e + v.cs, bbox) || !enc1(&out->rmap_red, e, rbox) || !enc1(&out->rmap_f, f, rbox))
+        return false;
+    if (cudaFuncSetAttribute(restrict_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRSmemBytes) !=
+        cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
     for (int c = 0; c < 2; ++c) {
         if (enc(&out->map[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, e + (long long)c * v.cs, dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -273,6 +460,16 @@ bool make_rb_maps(float* e, float* f, const LevelView& v, RbMaps* out, int nsets
     }
     out->ok = true;
     return true;
+}
+
+void launch_restrict_tma(float* fc, const LevelView& vf, const LevelView& vc, const RbMaps& maps, double hf,
+                         int* fault, cudaStream_t s, const Sets& sets)
+{
+    const int zper = (vc.n - 1 + kRTK - 1) / kRTK;
+    const dim3 grid((unsigned)((vc.n - 1 + kRTI - 1) / kRTI), (unsigned)((vc.n - 1 + kRTJ - 1) / kRTJ),
+                    (unsigned)(zper * sets.n));
+    restrict_tma_kernel<<<grid, kRTI * kRTJ, kRSmemBytes, s>>>(maps.rmap_black, maps.rmap_red, maps.rmap_f, fc, vf, vc,
+                                                              (float)(1.0 / (hf * hf)), fault, zper, sets.act);
 }
 
 void launch_rb_half_tma(float* e, const float* f, const LevelView& v, int colour, const RbMaps& maps, double h,
