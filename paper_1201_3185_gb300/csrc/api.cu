@@ -330,7 +330,13 @@ void prolong(qumond_ctx* c, int l, bool add, cudaStream_t s)
 {
     const double nodes = cube(c->lev[l].v.n);
     run(c, K_PROLONG, ((add ? 1.0 : 0.5) + 0.125) * nodes * sizeof(T), s,
-        [&] { launch_prolong_black<T>(E<T>(c, l - 1), c->lev[l - 1].v, E<T>(c, l), c->lev[l].v, add, s, sets_of(c)); });
+        [&] {
+            if (sizeof(T) == sizeof(float) && add && c->lev[l].maps.pok)
+                launch_prolong_tma(reinterpret_cast<float*>(E<T>(c, l)), c->lev[l].v, c->lev[l].maps, c->fault, s,
+                                   sets_of(c));
+            else
+                launch_prolong_black<T>(E<T>(c, l - 1), c->lev[l - 1].v, E<T>(c, l), c->lev[l].v, add, s, sets_of(c));
+        });
 }
 
 template <typename T>
@@ -919,9 +925,13 @@ qumond_status qumond_create(const qumond_params* p, qumond_ctx** out)
               cudaMalloc(&c->ff, sizeof(double) * far_field_scratch_doubles(p->nsets)) == cudaSuccess) &&
              prepare_kernels() == cudaSuccess;
         if (ok && c->elt == sizeof(float))
-            for (int l = lc; l <= L; ++l)
+            for (int l = lc; l <= L; ++l) {
                 make_rb_maps(static_cast<float*>(c->lev[l].e), static_cast<float*>(c->lev[l].f), c->lev[l].v,
                              &c->lev[l].maps, (int)ns);
+                if (l > 0)
+                    make_prolong_maps(static_cast<float*>(c->lev[l - 1].e), c->lev[l - 1].v,
+                                      static_cast<float*>(c->lev[l].e), c->lev[l].v, &c->lev[l].maps, (int)ns);
+            }
         if (ok && p->precision == QUMOND_PREC_MIXED_FIXED) {
             const size_t nn = fixed_elems(p->n) * ns;
             const int nfix = fixed_residual_blocks(p->n > 2 ? p->n : 2);

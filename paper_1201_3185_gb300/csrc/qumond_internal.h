@@ -140,7 +140,9 @@ struct RbMaps {
     CUtensorMap map[2];   // colour c of the iterate as a 3-D tensor (m, j, k), tile + halo boxes
     CUtensorMap fmap[2];  // colour c of the right-hand side, tile boxes
     CUtensorMap rmap_black, rmap_red, rmap_f;  // the restriction's boxes (black with halo, red, red f)
+    CUtensorMap pmap_fine, pmap_c[2];  // the prolongation's boxes: this level's black tile, the coarser level's colours
     bool ok = false;
+    bool pok = false;  // the prolongation maps are set
 };
 // 4-D maps (m, j, k, set) over the nsets sets of a level
 bool make_rb_maps(float* e, float* f, const LevelView& v, RbMaps* out, int nsets = 1);
@@ -150,6 +152,11 @@ void launch_rb_half_tma(float* e, const float* f, const LevelView& v, int colour
 // into the coarse right-hand side fc, the fine planes staged by the TMA unit.
 void launch_restrict_tma(float* fc, const LevelView& vf, const LevelView& vc, const RbMaps& maps, double hf,
                          int* fault, cudaStream_t s, const Sets& sets = Sets());
+// The coarse-grid correction of this level's black nodes from the next coarser level (ec, vc), planes staged by
+// the TMA unit; make_prolong_maps adds the boxes to this level's maps (after make_rb_maps).
+bool make_prolong_maps(float* ec, const LevelView& vc, float* ef, const LevelView& vf, RbMaps* out, int nsets = 1);
+void launch_prolong_tma(float* ef, const LevelView& vf, const RbMaps& maps, int* fault, cudaStream_t s,
+                        const Sets& sets = Sets());
 // Sets kernel attributes (shared memory of the coarse-grid kernel); call
 // before any stream capture.
 cudaError_t prepare_kernels();

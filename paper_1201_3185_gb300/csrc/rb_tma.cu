@@ -398,6 +398,151 @@ restrict_tma_kernel(const __grid_constant__ CUtensorMap black_map, const __grid_
     restrict_drain(leader, &abort_flag, bar, first, landed, issued);
 }
 
+// ---------------------------------------------------------------------------
+// The coarse-grid correction of the black nodes of a fine level with TMA maps
+// (prolong_black4_kernel's arithmetic, add), the planes staged by the TMA
+// unit.  A CTA owns 64 black entries x 8 rows of the fine level (four entries
+// per thread, 16 x 8 threads) and walks a chunk of 16 fine planes.  The slot
+// of fine plane q holds the CTA's black tile of plane q and both colours of the
+// coarse plane (q+1)/2 (entries m0/2 .. m0/2+35 of the coarse rows j0/2 ..
+// j0/2+4); fine plane k interpolates from coarse planes k/2 and (k+1)/2, held
+// by the slots of planes k-1 and k, so the ring starts one plane early.  The
+// black values are read once through the TMA unit and written back with
+// 16-byte stores; waits are bounded as in the half-sweep.
+constexpr int kPTM = 64, kPTJ = 8, kPKC = 16;  // fine tile (black entries x rows), planes per CTA
+constexpr int kPCX = 36, kPCY = kPTJ / 2 + 1;  // coarse box per colour: 36 entries x 5 rows
+constexpr int kPFineFloats = kPTM * kPTJ;      // 512 floats = 2048 bytes
+constexpr int kPCoarseFloats = ((kPCX * kPCY * 4 + 127) / 128) * 128 / 4;
+constexpr int kPSlotFloats = kPFineFloats + 2 * kPCoarseFloats;
+constexpr int kPSlots = 4;
+constexpr unsigned kPPlaneBytes = (kPTM * kPTJ + 2 * kPCX * kPCY) * 4;
+static_assert((kPFineFloats * 4) % 128 == 0 && (kPCoarseFloats * 4) % 128 == 0, "slot parts 128-byte aligned");
+
+__global__ void __launch_bounds__((kPTM / 4) * kPTJ)
+prolong_tma_kernel(const __grid_constant__ CUtensorMap fine_map, const __grid_constant__ CUtensorMap c0_map,
+                   const __grid_constant__ CUtensorMap c1_map, float* __restrict__ ef, LevelView vf, int* __restrict__ fault,
+                   int zper, const SolveState* __restrict__ act)
+{
+    __shared__ __align__(128) float slotm[kPSlots][kPSlotFloats];
+    __shared__ __align__(8) unsigned long long bar[kPSlots];
+    __shared__ int abort_flag;
+    const int set = (int)gridDim.z == zper ? 0 : (int)blockIdx.z / zper;
+    if (act && !act[set].cont) return;  // this set's correction has stopped (whole CTA, before any barrier)
+    ef += (long long)set * 2 * vf.cs;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int m0 = blockIdx.x * kPTM, j0 = 1 + blockIdx.y * kPTJ;
+    const int kb = 1 + ((int)blockIdx.z - set * zper) * kPKC;
+    const int ke = min(kb + kPKC, vf.n);  // fine planes kb .. ke-1; planes kb-1 .. ke-1 are staged
+    const int first = kb - 1;
+    const int Jb = j0 >> 1, cx0 = m0 >> 1;
+    const bool leader = tx == 0 && ty == 0;
+    if (leader) {
+        abort_flag = 0;
+        for (int q = 0; q < kPSlots; ++q) mbar_init(&bar[q], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int issued = first, landed = first;
+    auto issue = [&](int q) {  // plane q into its slot (leader only); nothing more once a wait gave up
+        if (*(volatile int*)&abort_flag) return;
+        const int u = q - first;
+        float* base = &slotm[u % kPSlots][0];
+        if (((smem_u32(base) | smem_u32(base + kPFineFloats) | smem_u32(base + kPFineFloats + kPCoarseFloats)) &
+             127u) != 0u) {  // never issue a copy the TMA unit would reject
+            atomicExch(fault, 2);
+            atomicExch(&abort_flag, 1);
+            return;
+        }
+        unsigned long long* b = &bar[u % kPSlots];
+        mbar_expect_tx(b, kPPlaneBytes);
+        tma_load_4d(base, &fine_map, m0, j0, q, set, b);  // x: a multiple of 64 floats
+        tma_load_4d(base + kPFineFloats, &c0_map, cx0, Jb, (q + 1) >> 1, set, b);  // x: a multiple of 32 floats
+        tma_load_4d(base + kPFineFloats + kPCoarseFloats, &c1_map, cx0, Jb, (q + 1) >> 1, set, b);
+        issued = q + 1;
+    };
+    if (leader)
+        for (int q = first; q < first + kPSlots && q <= ke - 1; ++q) issue(q);
+    bool ok = true;
+    const bool lane0 = ((tx + ty * (kPTM / 4)) & 31) == 0;
+    auto wait = [&](int q) {
+        if (lane0) {
+            const int u = q - first;
+            long long spins = 0;
+            while (ok && !mbar_try_wait(&bar[u % kPSlots], (unsigned)((u / kPSlots) & 1))) {
+                if (++spins > kSpinLimit || *(volatile int*)&abort_flag) {
+                    ok = false;
+                    atomicExch(fault, 1);
+                    *(volatile int*)&abort_flag = 1;  // the leader stops issuing copies
+                }
+            }
+            if (ok) landed = q + 1;
+        }
+        __syncwarp();
+    };
+    const int half = vf.n >> 1;
+    const int j = j0 + ty;
+    const int mA = m0 + 4 * tx;
+    const bool act4 = j < vf.n && mA < half;
+    const int J0 = j >> 1, J1 = (j + 1) >> 1;
+    for (int k = kb; k < ke; ++k) {
+        if (k == kb) wait(k - 1);
+        wait(k);
+        if (act4) {
+            const int p = (1 + j + k) & 1;  // parity of i of the black nodes in this row
+            const int K0 = k >> 1, K1 = (k + 1) >> 1;
+            // coarse plane K is carried by the slot of fine plane 2K-1 or 2K: K1 by plane k, K0 by plane k-1
+            const float* s1 = &slotm[(k - first) % kPSlots][0];
+            const float* s0 = K0 == K1 ? s1 : &slotm[(k - 1 - first) % kPSlots][0];
+            auto row5 = [&](int Jr, const float* sl, int Kr, float* cc) {
+                const int ca = (mA + Jr + Kr) & 1;  // colour of the even d
+                const int base = (Jr - Jb) * kPCX + ((mA >> 1) - cx0);
+                const float* A = sl + kPFineFloats + ca * kPCoarseFloats + base;
+                const float* B = sl + kPFineFloats + (ca ^ 1) * kPCoarseFloats + base;
+                const float2 a2 = *reinterpret_cast<const float2*>(A);
+                const float2 b2 = *reinterpret_cast<const float2*>(B);
+                cc[0] = a2.x, cc[1] = b2.x, cc[2] = a2.y, cc[3] = b2.y, cc[4] = A[2];
+            };
+            float c00[5], c10[5], c01[5], c11[5];  // (J0, K0), (J1, K0), (J0, K1), (J1, K1)
+            row5(J0, s0, K0, c00);
+            row5(J1, s0, K0, c10);
+            row5(J0, s1, K1, c01);
+            row5(J1, s1, K1, c11);
+            const float4 cur = *reinterpret_cast<const float4*>(s1 + ty * kPTM + 4 * tx);
+            const float cv[4] = {cur.x, cur.y, cur.z, cur.w};
+            float r[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                // I0 = mA + e, I1 = mA + e + p
+                const float a0 = c00[e], a1 = p ? c00[e + 1] : c00[e];
+                const float b0 = c10[e], b1 = p ? c10[e + 1] : c10[e];
+                const float d0 = c01[e], d1 = p ? c01[e + 1] : c01[e];
+                const float g0 = c11[e], g1 = p ? c11[e + 1] : c11[e];
+                float sv = (a0 + a1) + (b0 + b1);
+                sv += (d0 + d1) + (g0 + g1);
+                sv *= 0.125f;
+                r[e] = cv[e] + sv;
+            }
+            float* o = ef + vf.cs + ((long long)k * (vf.n + 1) + j) * vf.M + mA;
+            if (p == 0 && mA == 0) {  // i = 0 is a boundary node
+                o[1] = r[1], o[2] = r[2], o[3] = r[3];
+            } else {
+                *reinterpret_cast<float4*>(o) = make_float4(r[0], r[1], r[2], r[3]);
+            }
+        }
+        __syncthreads();  // the slot of plane k-1 is free
+        if (leader && k - 1 + kPSlots <= ke - 1) issue(k - 1 + kPSlots);
+    }
+    // drain after a fault, as in the half-sweep
+    __syncthreads();
+    if (leader && *(volatile int*)&abort_flag)
+        for (int q = landed; q < issued; ++q) {
+            const int u = q - first;
+            long long spins = 0;
+            while (!mbar_try_wait(&bar[u % kPSlots], (unsigned)((u / kPSlots) & 1)) && ++spins <= kSpinLimit) {
+            }
+        }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -460,6 +605,39 @@ bool make_rb_maps(float* e, float* f, const LevelView& v, RbMaps* out, int nsets
     }
     out->ok = true;
     return true;
+}
+
+bool make_prolong_maps(float* ec, const LevelView& vc, float* ef, const LevelView& vf, RbMaps* out, int nsets)
+{
+    out->pok = false;
+    if (!out->ok || vf.n != 2 * vc.n || (vc.M & 3) != 0) return false;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    auto enc1 = [&](CUtensorMap* m, float* base, const LevelView& v, cuuint32_t bx, cuuint32_t by) {
+        const cuuint64_t dims[4] = {(cuuint64_t)v.M, (cuuint64_t)(v.n + 1), (cuuint64_t)(v.n + 1), (cuuint64_t)nsets};
+        const cuuint64_t strides[3] = {(cuuint64_t)v.M * sizeof(float), (cuuint64_t)v.M * (v.n + 1) * sizeof(float),
+                                       (cuuint64_t)(2 * v.cs) * sizeof(float)};
+        const cuuint32_t box[4] = {bx, by, 1, 1};
+        return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    if (!enc1(&out->pmap_fine, ef + vf.cs, vf, kPTM, kPTJ) || !enc1(&out->pmap_c[0], ec, vc, kPCX, kPCY) ||
+        !enc1(&out->pmap_c[1], ec + vc.cs, vc, kPCX, kPCY))
+        return false;
+    out->pok = true;
+    return true;
+}
+
+void launch_prolong_tma(float* ef, const LevelView& vf, const RbMaps& maps, int* fault, cudaStream_t s,
+                        const Sets& sets)
+{
+    const int zper = (vf.n - 1 + kPKC - 1) / kPKC;
+    const dim3 grid((unsigned)((vf.n / 2 + kPTM - 1) / kPTM), (unsigned)((vf.n - 1 + kPTJ - 1) / kPTJ),
+                    (unsigned)(zper * sets.n));
+    prolong_tma_kernel<<<grid, dim3(kPTM / 4, kPTJ), 0, s>>>(maps.pmap_fine, maps.pmap_c[0], maps.pmap_c[1], ef, vf,
+                                                             fault, zper, sets.act);
 }
 
 void launch_restrict_tma(float* fc, const LevelView& vf, const LevelView& vc, const RbMaps& maps, double hf,
