@@ -388,9 +388,9 @@ def run_ours(args):
 
     lanes = max(1, args.lanes) if pipelined else 1
     lanes_tried = None
-    if pipelined and args.lanes == 0:  # pick the number of lanes (1 or 2) by timing a few steps of each
+    if pipelined and args.lanes == 0:  # pick the number of lanes (1, 2 or 3) by timing a few steps of each
         lanes_tried = {}
-        for nl in (1, 2):
+        for nl in (1, 2, 3):
             steps_timed(max(2, args.warmup), nl=nl)  # captures the graphs of the lanes' contexts
             barrier()
             a0 = torch.cuda.Event(enable_timing=True)
@@ -1208,7 +1208,7 @@ def main():
                          "holding the level n = 32 in distributed shared memory (two-disk and large workloads)")
     ap.add_argument("--lanes", type=int, default=0,
                     help="two-disk and large: pipelines (two contexts each) running independent steps "
-                         "concurrently; 0: 1 or 2, whichever times faster")
+                         "concurrently; 0: 1, 2 or 3, whichever times faster")
     ap.add_argument("--dc-vcycles", type=int, default=0,
                     help="two-disk and large: V-cycles per defect-correction step (params.dc_vcycles); 0: 2 or 4, "
                          "whichever times faster")
