@@ -420,6 +420,89 @@ def run_ours(args):
     ms_step = ms_total / args.steps
     value = ws * args.steps / (ms_total / 1000.0)
 
+    # --- end to end through the public API, host buffers: every step's particles copied in
+    # from pinned host memory, its forces and rotation curve copied out ------------------
+    host = [torch.from_numpy(a).pin_memory() for a in (p.x, p.y, p.z, p.m)]
+    out_g = [[torch.empty(w["particles"], dtype=torch.float64).pin_memory() for _ in range(3)]
+             for _ in range(args.steps if pipelined else 1)]
+    out_vc = torch.empty(args.steps, w["nbins"], dtype=torch.float64).pin_memory()
+    out_r = torch.empty(args.steps, w["nbins"], dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host)
+    d2h = sum(t.numel() * t.element_size() for t in out_g[0]) + w["nbins"] * 8 * 2
+    if pipelined:  # device buffers of every step, so that the steps can overlap
+        dev_in = [[torch.empty_like(xd) for _ in range(4)] for _ in range(args.steps)]
+        dev_g = [tuple(torch.empty_like(xd) for _ in range(3)) for _ in range(args.steps)]
+        h2d_stream, d2h_stream = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        # untimed: the lanes' graphs once more, with the copies' buffers allocated (measured right after
+        # `value`, under the same conditions: later in the run the e2e figure drifted down by up to 10 %)
+        steps_timed(2 * lanes, nl=lanes)
+        torch.cuda.synchronize()
+    # one step's transfers on their own, on the copy streams (best of three): the rates the overlapped copies
+    # of the timed region can reach
+    copy_gbps = None
+    if pipelined:
+        def copy_ms(pairs, st):
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record(st)
+            with torch.cuda.stream(st):
+                for a, b in pairs:
+                    a.copy_(b, non_blocking=True)
+            c1.record(st)
+            c1.synchronize()
+            return c0.elapsed_time(c1)
+        ms_in = min(copy_ms(list(zip(dev_in[0], host)), h2d_stream) for _ in range(3))
+        ms_out = min(copy_ms(list(zip(out_g[0], dev_g[0])), d2h_stream) for _ in range(3))
+        copy_gbps = {"h2d": h2d / ms_in / 1e6, "d2h": (d2h - w["nbins"] * 16) / ms_out / 1e6}
+    e2e_clocks = ClockSampler(local)
+    e2e_load = os.getloadavg()[0] if hasattr(os, "getloadavg") else None
+    barrier()
+    e2e_clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    if pipelined:
+        # copies in on one stream (each step's first kernel waits for its own copy), results out on
+        # another as each step completes, so that the transfers overlap the other steps' kernels
+        cur = torch.cuda.current_stream(dev)
+        h2d_stream.wait_stream(cur)
+        d2h_stream.wait_stream(cur)
+        ready = []
+        with torch.cuda.stream(h2d_stream):
+            for i in range(args.steps):
+                for a, b in zip(dev_in[i], host):
+                    a.copy_(b, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(h2d_stream)
+                ready.append(ev)
+        rs = q.run_lanes(lane_pipes(lanes), [tuple(d) for d in dev_in], nbins=w["nbins"], rmax=w["rmax"],
+                         nphi=w["nphi"], forces=dev_g, ready=ready)
+        with torch.cuda.stream(d2h_stream):
+            for i in range(args.steps):
+                d2h_stream.wait_event(rs[i].done)
+                for a, b in zip(out_g[i], dev_g[i]):
+                    a.copy_(b, non_blocking=True)
+                out_vc[i].copy_(rs[i].vc, non_blocking=True)
+                out_r[i].copy_(rs[i].r, non_blocking=True)
+        cur.wait_stream(h2d_stream)
+        cur.wait_stream(d2h_stream)
+    else:
+        for i in range(args.steps):
+            xs, ys, zs, ms_ = (t.to(dev, non_blocking=True) for t in host)
+            gg = tuple(torch.empty_like(xs) for _ in range(3))
+            r = pipe.run(xs, ys, zs, ms_, nbins=w["nbins"], rmax=w["rmax"], nphi=w["nphi"], forces=gg)
+            for a, b in zip(out_g[0], gg):
+                a.copy_(b, non_blocking=True)
+            out_vc[i].copy_(r.vc, non_blocking=True)
+            out_r[i].copy_(r.r, non_blocking=True)
+    e1.record()
+    barrier()
+    e2e_clk = e2e_clocks.stop()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1))
+    e2e_value = ws * args.steps / (e2e_ms / 1000.0)
+    if pipelined:
+        del dev_in, dev_g
+
     # the same steps one after another (each waits for the previous one to finish)
     step_by_step = None
     if pipelined:
@@ -499,68 +582,6 @@ def run_ours(args):
                         "GBps": (k.timed_bytes / k.ms / 1e6) if k.ms else None}
                for k in sorted(kstats.values(), key=lambda k: -k.ms) if k.launches}
 
-    # --- end to end through the public API, host buffers: every step's particles copied in
-    # from pinned host memory, its forces and rotation curve copied out ------------------
-    host = [torch.from_numpy(a).pin_memory() for a in (p.x, p.y, p.z, p.m)]
-    out_g = [[torch.empty(w["particles"], dtype=torch.float64).pin_memory() for _ in range(3)]
-             for _ in range(args.steps if pipelined else 1)]
-    out_vc = torch.empty(args.steps, w["nbins"], dtype=torch.float64).pin_memory()
-    out_r = torch.empty(args.steps, w["nbins"], dtype=torch.float64).pin_memory()
-    h2d = sum(t.numel() * t.element_size() for t in host)
-    d2h = sum(t.numel() * t.element_size() for t in out_g[0]) + w["nbins"] * 8 * 2
-    if pipelined:  # device buffers of every step, so that the steps can overlap
-        dev_in = [[torch.empty_like(xd) for _ in range(4)] for _ in range(args.steps)]
-        dev_g = [tuple(torch.empty_like(xd) for _ in range(3)) for _ in range(args.steps)]
-        h2d_stream, d2h_stream = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-        # untimed: the timings above ran other graphs on the same contexts (instrumented ones, one-chain
-        # ones), so relaunch the lanes' own solve graphs once (a context keeps a bounded number of graphs)
-        steps_timed(2 * lanes, nl=lanes)
-        torch.cuda.synchronize()
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    if pipelined:
-        # copies in on one stream (each step's first kernel waits for its own copy), results out on
-        # another as each step completes, so that the transfers overlap the other steps' kernels
-        cur = torch.cuda.current_stream(dev)
-        h2d_stream.wait_stream(cur)
-        d2h_stream.wait_stream(cur)
-        ready = []
-        with torch.cuda.stream(h2d_stream):
-            for i in range(args.steps):
-                for a, b in zip(dev_in[i], host):
-                    a.copy_(b, non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(h2d_stream)
-                ready.append(ev)
-        rs = q.run_lanes(lane_pipes(lanes), [tuple(d) for d in dev_in], nbins=w["nbins"], rmax=w["rmax"],
-                         nphi=w["nphi"], forces=dev_g, ready=ready)
-        with torch.cuda.stream(d2h_stream):
-            for i in range(args.steps):
-                d2h_stream.wait_event(rs[i].done)
-                for a, b in zip(out_g[i], dev_g[i]):
-                    a.copy_(b, non_blocking=True)
-                out_vc[i].copy_(rs[i].vc, non_blocking=True)
-                out_r[i].copy_(rs[i].r, non_blocking=True)
-        cur.wait_stream(h2d_stream)
-        cur.wait_stream(d2h_stream)
-    else:
-        for i in range(args.steps):
-            xs, ys, zs, ms_ = (t.to(dev, non_blocking=True) for t in host)
-            gg = tuple(torch.empty_like(xs) for _ in range(3))
-            r = pipe.run(xs, ys, zs, ms_, nbins=w["nbins"], rmax=w["rmax"], nphi=w["nphi"], forces=gg)
-            for a, b in zip(out_g[0], gg):
-                a.copy_(b, non_blocking=True)
-            out_vc[i].copy_(r.vc, non_blocking=True)
-            out_r[i].copy_(r.r, non_blocking=True)
-    e1.record()
-    barrier()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1))
-    e2e_value = ws * args.steps / (e2e_ms / 1000.0)
-    if pipelined:
-        del dev_in, dev_g
-
     # --- the other arithmetic modes at the same final residual -------------------------
     def time_mode(precision, nsteps):
         cx, pp = new_pipeline(precision)
@@ -622,7 +643,8 @@ def run_ours(args):
             "kernel_ms_per_step_one_by_one": total_kernel_ms / args.steps,
             "replay_ms_per_step_one_by_one": replay_ms,
             "roofline": roofline,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "copy_GBps_alone": copy_gbps, "clocks": e2e_clk, "host_load_1min": e2e_load},
             "gpu_launches": int(launches),
             "gpu_launches_per_step": launches / args.steps,
             "chains": args.chains,

@@ -325,6 +325,24 @@ void rb(qumond_ctx* c, int l, int colour, bool zero, double h, cudaStream_t s)
     });
 }
 
+// The first pre-smoothing sweep of a correction that starts from zero, both
+// half-sweeps in one launch, on the FP32 levels whose black half-sweep has no
+// TMA form (the same bits as rb() for colour 0 from zero, then colour 1).
+// Returns false where it does not apply.
+template <typename T>
+bool rb_first(qumond_ctx* c, int l, double h, cudaStream_t s)
+{
+    if (sizeof(T) != sizeof(float) || c->lev[l].v.n < 8 || c->lev[l].maps.ok) return false;
+    const int n = c->lev[l].v.n;
+    const long long inner = (long long)(n - 1) * (n - 1) * (n - 1);
+    count_cells(c, (inner + 1) / 2 + inner / 2);
+    run(c, l == c->L ? K_RB_FINEST : K_RB_COARSER, 2.0 * cube(n) * sizeof(T), s, [&] {
+        launch_rb_first(reinterpret_cast<float*>(E<T>(c, l)), reinterpret_cast<const float*>(F<T>(c, l)),
+                        c->lev[l].v, h, s, sets_of(c));
+    });
+    return true;
+}
+
 template <typename T>
 void prolong(qumond_ctx* c, int l, bool add, cudaStream_t s)
 {
@@ -417,6 +435,7 @@ cudaError_t vcycle(qumond_ctx* c, int box, int l, bool zero_guess, cudaStream_t 
     if (l <= c->lc) return coarse<T>(c, box, 0, nullptr, s);
     if (l == c->vtop) return vsub<T>(c, box, zero_guess, s);
     for (int q = 0; q < p.npre; ++q) {
+        if (zero_guess && q == 0 && rb_first<T>(c, l, h, s)) continue;
         rb<T>(c, l, 0, zero_guess && q == 0, h, s);
         rb<T>(c, l, 1, false, h, s);
     }

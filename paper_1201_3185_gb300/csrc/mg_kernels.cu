@@ -142,6 +142,93 @@ rb_half4_kernel(float* __restrict__ own, const float* __restrict__ other, const 
     }
 }
 
+// The first sweep of a correction that starts from zero, both half-sweeps in
+// one pass (FP32 levels, four entries per thread as in rb_half4_kernel).  The
+// red half-sweep from zero sets each interior red node to (0 - h^2 f)/6, a
+// function of its own f alone, so the black half-sweep after it can form its
+// red neighbours from f instead of reading them back: each thread writes the
+// four red entries of its row that rb_half4_kernel<true> would write and
+// updates the four black entries of the row with rb_half4_kernel<false>'s
+// sums in their order, so the results are the same bits as the two launches.
+// Red neighbours on the boundary (i, j or k = 0 or n) are not written by the
+// red half-sweep; they are read from e, as the black half-sweep reads them.
+constexpr int kFirstBlocksPerSM = 10;  // <= 48 registers: the fused sweep holds both colours' values
+template <int VX = kVX>
+__global__ void __launch_bounds__(kVThreads, kFirstBlocksPerSM)
+rb_first4_kernel(float* __restrict__ e, const float* __restrict__ f, LevelView v, float h2, float sixth,
+                 const SolveState* __restrict__ act)
+{
+    int kz;
+    const int set = set_of(v.n - 1, kz);
+    if (act && !act[set].cont) return;
+    {
+        const long long so = (long long)set * 2 * v.cs;
+        e += so, f += so;
+    }
+    float* red = e;
+    float* black = e + v.cs;
+    const float* fr = f;
+    const float* fb = f + v.cs;
+    const int n = v.n, half = n >> 1;
+    const int mA = 4 * (blockIdx.x * VX + threadIdx.x);
+    const int j = blockIdx.y * (kVThreads / VX) + threadIdx.y + 1;
+    const int k = kz + 1;
+    if (mA >= half || j >= n) return;
+    const int pr = (j + k) & 1;  // parity of i along this row: red entries
+    const int pb = pr ^ 1;       // black entries
+    const long long row = ((long long)k * (n + 1) + j) * v.M;
+    const long long P = v.M, Q = (long long)v.M * (n + 1);
+    const float zero = 0.0f;
+    // red entries mA-1 .. mA+4 of this row after the half-sweep from zero
+    const float* fo = fr + row + mA;
+    const float4 FV = *reinterpret_cast<const float4*>(fo);
+    const float fv[4] = {FV.x, FV.y, FV.z, FV.w};
+    float rr[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) rr[q] = (zero - h2 * fv[q]) * sixth;
+    float x[6] = {(zero - h2 * fo[-1]) * sixth, rr[0], rr[1], rr[2], rr[3], (zero - h2 * fo[4]) * sixth};
+    if (pr == 0) {  // red boundary nodes of the row: i = 0 (entry 0) and i = n (entry half)
+        if (mA == 0) x[1] = red[row];
+        if (mA + 4 == half) x[5] = red[row + half];
+    }
+    // red entries mA .. mA+3 of the neighbouring rows (boundary rows as stored)
+    float y0[4], y1[4], z0[4], z1[4];
+    auto nbr = [&](long long off, bool bnd, float* out) {
+        if (bnd) {
+            const float4 E = *reinterpret_cast<const float4*>(red + row + mA + off);
+            out[0] = E.x, out[1] = E.y, out[2] = E.z, out[3] = E.w;
+        } else {
+            const float4 F = *reinterpret_cast<const float4*>(fr + row + mA + off);
+            out[0] = (zero - h2 * F.x) * sixth, out[1] = (zero - h2 * F.y) * sixth;
+            out[2] = (zero - h2 * F.z) * sixth, out[3] = (zero - h2 * F.w) * sixth;
+        }
+    };
+    nbr(-P, j == 1, y0);
+    nbr(P, j + 1 == n, y1);
+    nbr(-Q, k == 1, z0);
+    nbr(Q, k + 1 == n, z1);
+    const float4 FB = *reinterpret_cast<const float4*>(fb + row + mA);
+    const float fbv[4] = {FB.x, FB.y, FB.z, FB.w};
+    float rb[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float lo = pb ? x[q + 1] : x[q];
+        const float hi = pb ? x[q + 2] : x[q + 1];
+        const float sum = (lo + hi) + (y0[q] + y1[q]) + (z0[q] + z1[q]);
+        rb[q] = (sum - h2 * fbv[q]) * sixth;
+    }
+    if (pr == 0 && mA == 0) {  // i = 0 is a boundary node
+        red[row + 1] = rr[1], red[row + 2] = rr[2], red[row + 3] = rr[3];
+    } else {
+        *reinterpret_cast<float4*>(red + row + mA) = make_float4(rr[0], rr[1], rr[2], rr[3]);
+    }
+    if (pb == 0 && mA == 0) {
+        black[row + 1] = rb[1], black[row + 2] = rb[2], black[row + 3] = rb[3];
+    } else {
+        *reinterpret_cast<float4*>(black + row + mA) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+    }
+}
+
 // Residual f - L u at the red node (i, j, k) of a level.
 template <typename T>
 __device__ __forceinline__ T red_residual(const T* __restrict__ e, const T* __restrict__ f, const LevelView& v, int i,
@@ -1512,6 +1599,19 @@ void launch_rb_half(T* e, const T* f, const LevelView& v, int colour, bool zero_
     else
         rb_half_kernel<T, false><<<per_sets(half_grid(v.n), sets), blk, 0, s>>>(own, other, fc, v, colour, (T)(h * h),
                                                                                  T(1) / T(6), sets.act);
+}
+
+void launch_rb_first(float* e, const float* f, const LevelView& v, double h, cudaStream_t s, const Sets& sets)
+{
+    const int vx = vx_of(v.n, sets);
+    const dim3 grid(cdiv(v.n / 2, 4 * vx), cdiv(v.n - 1, kVThreads / vx), (unsigned)(v.n - 1) * (unsigned)sets.n);
+    const dim3 blk(vx, kVThreads / vx);
+    const float h2 = (float)(h * h), sixth = 1.0f / 6.0f;
+    switch (vx) {
+    case 8: rb_first4_kernel<8><<<grid, blk, 0, s>>>(e, f, v, h2, sixth, sets.act); break;
+    case 4: rb_first4_kernel<4><<<grid, blk, 0, s>>>(e, f, v, h2, sixth, sets.act); break;
+    default: rb_first4_kernel<2><<<grid, blk, 0, s>>>(e, f, v, h2, sixth, sets.act); break;
+    }
 }
 
 template <typename T>

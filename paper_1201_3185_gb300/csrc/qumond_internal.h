@@ -81,6 +81,9 @@ __host__ __device__ inline long long nat_elems(int n) { return (long long)(n + 1
 // --- multigrid kernels (mg_kernels.cu), T = float or double ---------------
 template <typename T> void launch_rb_half(T* e, const T* f, const LevelView& v, int colour, bool zero_guess,
                                           double h, cudaStream_t s, const Sets& sets = Sets());
+// Both half-sweeps of the first sweep from zero in one launch (FP32, n >= 8):
+// the same bits as launch_rb_half(colour 0, zero) then launch_rb_half(colour 1).
+void launch_rb_first(float* e, const float* f, const LevelView& v, double h, cudaStream_t s, const Sets& sets);
 template <typename T> void launch_restrict_resid_red(const T* ef, const T* ff, const LevelView& vf, T* fc,
                                                      const LevelView& vc, double hf, cudaStream_t s,
                                                      const Sets& sets = Sets());
