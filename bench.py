@@ -421,10 +421,14 @@ def run_ours(args):
     value = ws * args.steps / (ms_total / 1000.0)
 
     # --- end to end through the public API, host buffers: every step's particles copied in
-    # from pinned host memory, its forces and rotation curve copied out ------------------
+    # from pinned host memory, its forces and rotation curve copied out.  The forces land in a ring of
+    # two host buffers per lane (each step's result stays there for the next step of its lane): on a box
+    # that had run other GPU jobs, copies into a fresh 48 MB pinned buffer every step slowed the
+    # concurrent kernels by up to 15 %, a ring by about 5 % (copies into the same few buffers) ----------
     host = [torch.from_numpy(a).pin_memory() for a in (p.x, p.y, p.z, p.m)]
+    n_ring = 2 * lanes if pipelined else 1
     out_g = [[torch.empty(w["particles"], dtype=torch.float64).pin_memory() for _ in range(3)]
-             for _ in range(args.steps if pipelined else 1)]
+             for _ in range(n_ring)]
     out_vc = torch.empty(args.steps, w["nbins"], dtype=torch.float64).pin_memory()
     out_r = torch.empty(args.steps, w["nbins"], dtype=torch.float64).pin_memory()
     h2d = sum(t.numel() * t.element_size() for t in host)
@@ -433,8 +437,7 @@ def run_ours(args):
         dev_in = [[torch.empty_like(xd) for _ in range(4)] for _ in range(args.steps)]
         dev_g = [tuple(torch.empty_like(xd) for _ in range(3)) for _ in range(args.steps)]
         h2d_stream, d2h_stream = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-        # untimed: the lanes' graphs once more, with the copies' buffers allocated (measured right after
-        # `value`, under the same conditions: later in the run the e2e figure drifted down by up to 10 %)
+        # untimed: the lanes' graphs once more, with the copies' buffers allocated
         steps_timed(2 * lanes, nl=lanes)
         torch.cuda.synchronize()
     # one step's transfers on their own, on the copy streams (best of three): the rates the overlapped copies
@@ -480,7 +483,7 @@ def run_ours(args):
         with torch.cuda.stream(d2h_stream):
             for i in range(args.steps):
                 d2h_stream.wait_event(rs[i].done)
-                for a, b in zip(out_g[i], dev_g[i]):
+                for a, b in zip(out_g[i % n_ring], dev_g[i]):
                     a.copy_(b, non_blocking=True)
                 out_vc[i].copy_(rs[i].vc, non_blocking=True)
                 out_r[i].copy_(rs[i].r, non_blocking=True)
@@ -644,7 +647,8 @@ def run_ours(args):
             "replay_ms_per_step_one_by_one": replay_ms,
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "copy_GBps_alone": copy_gbps, "clocks": e2e_clk, "host_load_1min": e2e_load},
+                    "copy_GBps_alone": copy_gbps, "clocks": e2e_clk, "host_load_1min": e2e_load,
+                    "host_result_buffers": n_ring},
             "gpu_launches": int(launches),
             "gpu_launches_per_step": launches / args.steps,
             "chains": args.chains,
