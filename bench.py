@@ -196,15 +196,17 @@ def measured_peaks():
         return None
 
 
-def ncu_traffic(kernel: str):
+def ncu_traffic(kernel: str, n: int, nsets: int = 1):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None when there is none or the kernel's source file changed since."""
+    None when there is none, it was taken on another grid size or number of
+    sets (the write-back share depends on how much of a launch stays in L2),
+    or the kernel's source file changed since."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
     except (OSError, ValueError):
         return None
     k = t.get("kernels", {}).get(kernel)
-    if not k:
+    if not k or k.get("n") != n or k.get("nsets", 1) != nsets:
         return None
     src = os.path.join(ROOT, k["source"])
     if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != k.get("source_hash"):
@@ -563,7 +565,7 @@ def run_ours(args):
     achieved = dom.timed_bytes / dom.ms / 1e6 if dom.ms else None  # GB/s
     roofline = {"bound": "hbm", "kernel": dom.name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None,
-                "traffic": ncu_traffic(dom.name),
+                "traffic": ncu_traffic(dom.name, w["n"]),
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_ms": avg_ms, "timed_launches": dom.timed,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s",
