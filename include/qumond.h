@@ -390,12 +390,12 @@ QUMOND_API qumond_status qumond_trace_read(qumond_ctx* ctx, qumond_kernel_stat* 
    The call makes no cudaMalloc, cudaFree or other allocating call.  The first
    call on each device does a one-time set-up with that device current: it
    looks up the array's device address and caches it, and sets the kernel
-   attributes the solve needs (neither allocates).  Make that first call
-   before any stream capture.  The cached address assumes the device is not
-   reset: calling cudaDeviceReset in the same process and then this entry
-   point again is not supported.  When a tolerance is set (rel_tol > 0 and
-   max_vcycles > 0) or stats is non-NULL, the call copies residual norms to
-   a host buffer and synchronises `stream` after each residual check.
+   attributes the solve needs (neither allocates).  The cached address
+   assumes the device is not reset: calling cudaDeviceReset in the same
+   process and then this entry point again is not supported.  When a
+   tolerance is set (rel_tol > 0 and max_vcycles > 0) or stats is non-NULL,
+   the call copies residual norms to a host buffer and synchronises `stream`
+   after each residual check.
    All calls on a device share the array, which keeps the previous call's
    contents (each call clears it before use): calls whose GPU work overlaps,
    on different streams or host threads, race and give wrong results. */
