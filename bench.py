@@ -782,19 +782,44 @@ def run_sweep(args):
                 "live_ms_per_set": {nm: v[1] for nm, v in live.items()},
                 "live_GBps": {nm: v[0].timed_bytes / v[0].ms / 1e6 for nm, v in live.items() if v[0].ms}}
 
-    # end to end: every set's particles copied from pinned host memory, chi^2 and curves read back
+    # end to end: every set's particles copied from pinned host memory, chi^2 and curves read back.  The
+    # particles of step i+1 are copied on a stream of their own into the second of two device buffers while
+    # step i computes (a buffer is refilled once the step that read it is done)
     host = [torch.from_numpy(np.concatenate([getattr(p, a) for p in host_sets])).pin_memory() for a in "xyzm"]
     out_vc = torch.empty(w["sets"], w["nbins"], dtype=torch.float64).pin_memory()
     out_chi2 = torch.empty(w["sets"], dtype=torch.float64).pin_memory()
     h2d = sum(t.numel() * t.element_size() for t in host)
     d2h = out_vc.numel() * 8 + out_chi2.numel() * 8
+    dbuf = [tuple(torch.empty(t.shape, dtype=t.dtype, device=dev) for t in host) for _ in range(2)]
+    copy_stream = torch.cuda.Stream(dev)
+    cur = torch.cuda.current_stream(dev)
+    done = []
+
+    def copy_in(i):
+        if i == 0:
+            copy_stream.wait_stream(cur)
+        if i >= 2:
+            copy_stream.wait_event(done[i - 2])  # the step that read this buffer
+        with torch.cuda.stream(copy_stream):
+            for a, b in zip(dbuf[i % 2], host):
+                a.copy_(b, non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(copy_stream)
+        return ev
+
     rep.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
-        dsets = tuple(t.to(dev, non_blocking=True) for t in host)
-        res = sw.run(dsets, dist, v_obs, sigma)
+    ready = copy_in(0)
+    for i in range(args.steps):
+        cur.wait_event(ready)
+        if i + 1 < args.steps:
+            ready = copy_in(i + 1)
+        res = sw.run(dbuf[i % 2], dist, v_obs, sigma)
+        ev = torch.cuda.Event()
+        ev.record(cur)
+        done.append(ev)
         out_vc.copy_(res.vc, non_blocking=True)
         out_chi2.copy_(res.chi2, non_blocking=True)
     e1.record()
