@@ -9,7 +9,8 @@ smoothing with defect correction to a relative residual of 1e-10, on a 64-bit
 fixed-point iterate by default, in FP64 with --precision mixed), then the
 forces at every particle and a 50-bin rotation curve.  The metric is QUMOND
 solves per second (one solve = one such step); successive steps run with the
-two solve chains pipelined across them (Pipeline.run_many).
+two solve chains pipelined across them (Pipeline.run_many), dealt to 1, 2 or
+3 lanes of such pipelines (run_lanes), whichever a short timing picks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
